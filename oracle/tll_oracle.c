@@ -1,0 +1,415 @@
+/*
+ * tll_oracle.c -- plain FP64 CPU oracle for the batched lens log-likelihood.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or call this file.  It is used by tests/, by __graft_entry__.smoke()
+ * and by bench.py's cpu_baseline / reference leg, and nowhere else.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * It computes, slowly and literally, what the paper "CSST Strong Lensing
+ * Preparation: Fast Modelling of Galaxy-Galaxy Strong Lenses in the Big Data
+ * Era" (arXiv:2503.08586, TinyLensGpu) defines for one parameter vector:
+ *
+ *   lens equation                 Sec. 2.1, Eq. (1)
+ *   image formation               Sec. 2.1, Eq. (2)
+ *   4x4 supersampling + binning   Sec. 2.1 (text after Eq. 2)
+ *   PSF convolution               Sec. 2.1, Eq. (3)
+ *   Gaussian likelihood           Sec. 2.2, Eq. (5)
+ *   linear amplitudes (delta fn)  Sec. 2.2, Eq. (6)
+ *   d = B L s + n, NNLS           Sec. 2.3, Eq. (7) and the penalty after it
+ *   Sersic profile, b_n           Sec. 2.4, Eqs. (8), (9)
+ *   elliptical coordinates        Sec. 2.4, Eq. (10)
+ *   ellipticity components        Sec. 2.4, Eq. (11)
+ *   power-law / SIE convergence   Sec. 2.4, Eq. (12), gamma = 2
+ *   external shear                Sec. 2.4, Eqs. (13), (14)
+ *
+ * Readings taken where the paper is silent or ambiguous (each one is also
+ * listed in the design notes):
+ *   R1 grid: pixel (i row, j col) centre at (x0 + j*dpix, y0 + i*dpix);
+ *      subpixel (a, c) of an s x s pixel at offset ((c+1/2)/s - 1/2)*dpix in x
+ *      and ((a+1/2)/s - 1/2)*dpix in y.  Units: arcsec.
+ *   R2 binning: a pixel takes the MEAN of its s*s subpixel values.
+ *   R3 convolution: true convolution with the PSF normalised to unit sum,
+ *      output the same size as the image, zero outside the image.
+ *   R4 SIE: Eq. (12) with gamma = 2 and R replaced by the elliptical radius of
+ *      Eq. (10), kappa = theta_E / (2 sqrt(q x'^2 + y'^2/q)); its deflection is
+ *      the Kormann et al. (1994) closed form, written out in sie_alpha().
+ *      The singular centre is regularised by psi >= 1e-12 arcsec.
+ *   R5 shear: (gamma_1, gamma_2) are the Cartesian shear components
+ *      gamma_1 = (psi_11 - psi_22)/2, gamma_2 = psi_12, so
+ *      psi_ext = gamma_1 (x^2 - y^2)/2 + gamma_2 x y about the origin; this is
+ *      Eq. (13) with gamma_1 = -gamma cos 2phi, gamma_2 = -gamma sin 2phi,
+ *      which satisfies Eq. (14).
+ *   R6 b_n: the exact root of Eq. (9), P(2n, b_n) = 1/2, no approximation.
+ *   R7 amplitudes: non-negative least squares over the two unit-amplitude
+ *      columns (lens light, lensed source); in "fixed" mode the amplitudes are
+ *      the I_e slots of the parameter vector instead.
+ *   R8 likelihood: log L = -chi^2/2 - sum_{w>0} log(2 pi sigma^2)/2; a pixel
+ *      whose sigma is not finite and > 0, or whose datum is not finite, is
+ *      masked (weight 0, no normalisation term).
+ *   R9 invalid parameter vectors (|eps| >= 1, r_e <= 0, n outside [0.2, 10],
+ *      theta_E < 0, non-finite entries) give log L = -infinity.
+ *
+ * Parameter vector layout (21 doubles / floats):
+ *   [0] theta_E  [1] eps1_m [2] eps2_m [3] x_m [4] y_m [5] gamma_1 [6] gamma_2
+ *   [7] I_e^L [8] r_e^L [9] n^L [10] eps1_L [11] eps2_L [12] x_L [13] y_L
+ *   [14] I_e^S [15] r_e^S [16] n^S [17] eps1_S [18] eps2_S [19] x_S [20] y_S
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORA_NPAR 21
+
+/* ---------------------------------------------------------------- Eq. (11) */
+/* Ellipticity components -> (q, position angle).  Eq. (11):
+ * (eps1, eps2) = (1-q)/(1+q) (cos 2 theta_p, sin 2 theta_p), inverted.
+ * Returns -1 when |eps| >= 1 (no ellipse). */
+int ora_ellipse(double e1, double e2, double *q, double *phi)
+{
+    double e = sqrt(e1 * e1 + e2 * e2);
+    if (!(e < 1.0)) return -1;
+    *q = (1.0 - e) / (1.0 + e);
+    *phi = 0.5 * atan2(e2, e1);
+    return 0;
+}
+
+/* ----------------------------------------------------------------- Eq. (9) */
+/* Regularised lower incomplete gamma P(a, x) = gamma(a, x) / Gamma(a), from
+ * its power series gamma(a,x) = x^a e^{-x} sum_k x^k / (a (a+1) ... (a+k)).
+ * All terms are positive, so the sum has no cancellation. */
+double ora_gammainc_P(double a, double x)
+{
+    if (x <= 0.0) return 0.0;
+    double term = 1.0 / a, sum = term;
+    for (int k = 1; k < 100000; ++k) {
+        term *= x / (a + k);
+        sum += term;
+        if (term < sum * 1e-17) break;
+    }
+    return exp(a * log(x) - x - lgamma(a)) * sum;
+}
+
+/* b_n of Eq. (9): Gamma(2n) = 2 gamma(2n, b_n), i.e. P(2n, b_n) = 1/2.
+ * P(2n, .) increases monotonically from 0 to 1, and its median is below 2n,
+ * so [0, 2n + 1] brackets the root; plain bisection to the last bit. */
+double ora_sersic_bn(double n)
+{
+    double a = 2.0 * n, lo = 0.0, hi = a + 1.0;
+    while (ora_gammainc_P(a, hi) < 0.5) hi *= 2.0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (ora_gammainc_P(a, mid) < 0.5) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* --------------------------------------------------- Eqs. (8), (10), (11) */
+/* Unit-amplitude elliptical Sersic at (x, y): Eq. (8) with I_e = 1 and R
+ * replaced by R_p of Eq. (10), rotated by theta_p about (cx, cy). */
+double ora_sersic(double x, double y, double cx, double cy, double q,
+                  double phi, double re, double n, double bn)
+{
+    double c = cos(phi), s = sin(phi);
+    double x1 = (x - cx) * c + (y - cy) * s;          /* Eq. (10), first row */
+    double x2 = -(x - cx) * s + (y - cy) * c;         /* Eq. (10), second row */
+    double Rp = sqrt(x1 * x1 * q + x2 * x2 / q);      /* Eq. (10), third row */
+    return exp(-bn * (pow(Rp / re, 1.0 / n) - 1.0)); /* Eq. (8) */
+}
+
+/* ------------------------------------------------------------ Eq. (12) */
+/* SIE deflection (reading R4).  In the frame rotated by phi about (xc, yc)
+ * (the rotation of Eq. 10), with f = sqrt(1 - q^2), psi = sqrt(q^2 x'^2 + y'^2):
+ *   alpha_x' = theta_E sqrt(q)/f * atan (f x'/psi)
+ *   alpha_y' = theta_E sqrt(q)/f * atanh(f y'/psi)
+ * and rotated back by +phi.  For q = 1 (f = 0) it is the singular isothermal
+ * sphere, alpha = theta_E (x', y')/r. */
+void ora_sie_alpha(double x, double y, double thE, double q, double phi,
+                   double xc, double yc, double *ax, double *ay)
+{
+    double c = cos(phi), s = sin(phi);
+    double xp = (x - xc) * c + (y - yc) * s;
+    double yp = -(x - xc) * s + (y - yc) * c;
+    double psi = sqrt(q * q * xp * xp + yp * yp);
+    if (psi < 1e-12) psi = 1e-12;
+    double f = sqrt(1.0 - q * q);
+    double axp, ayp;
+    if (f > 0.0) {
+        double pre = thE * sqrt(q) / f;
+        axp = pre * atan(f * xp / psi);
+        ayp = pre * atanh(f * yp / psi);
+    } else {
+        axp = thE * xp / psi;
+        ayp = thE * yp / psi;
+    }
+    *ax = axp * c - ayp * s;
+    *ay = axp * s + ayp * c;
+}
+
+/* ------------------------------------------------------ Eqs. (13), (14) */
+/* External shear potential (reading R5): psi = g1 (x^2 - y^2)/2 + g2 x y. */
+double ora_shear_potential(double x, double y, double g1, double g2)
+{
+    return 0.5 * g1 * (x * x - y * y) + g2 * x * y;
+}
+
+/* Its gradient, the shear deflection. */
+void ora_shear_alpha(double x, double y, double g1, double g2,
+                     double *ax, double *ay)
+{
+    *ax = g1 * x + g2 * y;
+    *ay = g2 * x - g1 * y;
+}
+
+/* ------------------------------------------------------------ parameters */
+typedef struct {
+    double thE, qm, phim, xm, ym, g1, g2;
+    double IeL, reL, nL, qL, phiL, xL, yL, bL;
+    double IeS, reS, nS, qS, phiS, xS, yS, bS;
+} ora_model;
+
+/* Decode one parameter vector; returns -1 for an invalid vector (R9). */
+int ora_decode(const double *p, ora_model *m)
+{
+    for (int k = 0; k < ORA_NPAR; ++k)
+        if (!isfinite(p[k])) return -1;
+    if (p[0] < 0.0) return -1;
+    if (ora_ellipse(p[1], p[2], &m->qm, &m->phim)) return -1;
+    if (ora_ellipse(p[10], p[11], &m->qL, &m->phiL)) return -1;
+    if (ora_ellipse(p[17], p[18], &m->qS, &m->phiS)) return -1;
+    if (!(p[8] > 0.0) || !(p[15] > 0.0)) return -1;
+    if (!(p[9] >= 0.2 && p[9] <= 10.0)) return -1;
+    if (!(p[16] >= 0.2 && p[16] <= 10.0)) return -1;
+    m->thE = p[0]; m->xm = p[3]; m->ym = p[4]; m->g1 = p[5]; m->g2 = p[6];
+    m->IeL = p[7]; m->reL = p[8]; m->nL = p[9]; m->xL = p[12]; m->yL = p[13];
+    m->IeS = p[14]; m->reS = p[15]; m->nS = p[16]; m->xS = p[19]; m->yS = p[20];
+    m->bL = ora_sersic_bn(m->nL);
+    m->bS = ora_sersic_bn(m->nS);
+    return 0;
+}
+
+/* Lens equation, Eq. (1): beta = theta - alpha_SIE(theta) - alpha_shear(theta). */
+void ora_trace(const ora_model *m, double x, double y, double *bx, double *by)
+{
+    double ax, ay, sx, sy;
+    ora_sie_alpha(x, y, m->thE, m->qm, m->phim, m->xm, m->ym, &ax, &ay);
+    ora_shear_alpha(x, y, m->g1, m->g2, &sx, &sy);
+    *bx = x - ax - sx;
+    *by = y - ay - sy;
+}
+
+/* Public wrapper of the lens equation for one point (used by the pins). */
+int ora_trace_point(const double *p, double x, double y, double *bx, double *by)
+{
+    ora_model m;
+    if (ora_decode(p, &m)) return -1;
+    ora_trace(&m, x, y, bx, by);
+    return 0;
+}
+
+/* ------------------------------------------------------------ the image */
+/* Unit-amplitude lens-light and lensed-source columns (the two columns of L in
+ * Eq. 7), before the PSF: each subpixel of an s x s grid per pixel (R1) is
+ * evaluated with Eq. (2) split into its two terms, then binned by the mean
+ * (R2).  Lens light at theta, source at beta(theta) of Eq. (1). */
+void ora_columns(const ora_model *m, int ny, int nx, double dpix, int sub,
+                 double x0, double y0, double *lens, double *src)
+{
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < nx; ++j) {
+            double sl = 0.0, ss = 0.0;
+            for (int a = 0; a < sub; ++a)
+                for (int c = 0; c < sub; ++c) {
+                    double x = x0 + j * dpix + ((c + 0.5) / sub - 0.5) * dpix;
+                    double y = y0 + i * dpix + ((a + 0.5) / sub - 0.5) * dpix;
+                    double bx, by;
+                    sl += ora_sersic(x, y, m->xL, m->yL, m->qL, m->phiL,
+                                     m->reL, m->nL, m->bL);
+                    ora_trace(m, x, y, &bx, &by);
+                    ss += ora_sersic(bx, by, m->xS, m->yS, m->qS, m->phiS,
+                                     m->reS, m->nS, m->bS);
+                }
+            lens[i * nx + j] = sl / (double)(sub * sub);
+            src[i * nx + j] = ss / (double)(sub * sub);
+        }
+}
+
+/* Eq. (3) on the pixel grid (R3): out(i,j) = sum_{r,c} K[r][c] img(i-(r-h), j-(c-h)),
+ * h = (k-1)/2, zero outside the image.  The caller passes the PSF already
+ * normalised to unit sum. */
+void ora_convolve(const double *img, int ny, int nx, const double *psf, int k,
+                  double *out)
+{
+    int h = (k - 1) / 2;
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < nx; ++j) {
+            double acc = 0.0;
+            for (int r = 0; r < k; ++r)
+                for (int c = 0; c < k; ++c) {
+                    int ii = i - (r - h), jj = j - (c - h);
+                    if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                    acc += psf[r * k + c] * img[ii * nx + jj];
+                }
+            out[i * nx + j] = acc;
+        }
+}
+
+/* Normalise a PSF to unit sum (R3).  Returns -1 if its sum is not > 0. */
+int ora_psf_normalise(const double *psf_in, int k, double *psf_out)
+{
+    double s = 0.0;
+    for (int t = 0; t < k * k; ++t) s += psf_in[t];
+    if (!(s > 0.0) || !isfinite(s)) return -1;
+    for (int t = 0; t < k * k; ++t) psf_out[t] = psf_in[t] / s;
+    return 0;
+}
+
+/* Pixel weights w = 1/sigma^2 with the masking rule of R8. */
+void ora_weights(const double *data, const double *sigma, int npix, double *w)
+{
+    for (int t = 0; t < npix; ++t) {
+        double s = sigma[t];
+        w[t] = (isfinite(s) && s > 0.0 && isfinite(data[t])) ? 1.0 / (s * s) : 0.0;
+    }
+}
+
+/* chi^2 of Eq. (5) for amplitudes (sl, ss): sum_i w_i (d_i - sl ml_i - ss ms_i)^2,
+ * by a direct pass over the pixels. */
+double ora_chi2(const double *ml, const double *ms, const double *d,
+                const double *w, int npix, double sl, double ss)
+{
+    double chi2 = 0.0;
+    for (int t = 0; t < npix; ++t) {
+        if (w[t] == 0.0) continue;
+        double r = d[t] - sl * ml[t] - ss * ms[t];
+        chi2 += w[t] * r * r;
+    }
+    return chi2;
+}
+
+/* Non-negative least squares over two columns (Sec. 2.3: minimise
+ * ||(M s - d)/n|| subject to s >= 0).  The minimiser of a convex quadratic
+ * over the quadrant is the unconstrained minimiser of one of its faces
+ * {both free, lens only, source only, none} that is feasible; all four are
+ * formed from A = M^T W M, b = M^T W d and the best feasible one (by a direct
+ * chi^2 pass) is returned.  Ties go to fewer free columns, then the lens
+ * column. */
+void ora_nnls2(const double *ml, const double *ms, const double *d,
+               const double *w, int npix, double *s_out)
+{
+    double All = 0, Als = 0, Ass = 0, bl = 0, bs = 0;
+    for (int t = 0; t < npix; ++t) {
+        if (w[t] == 0.0) continue;      /* masked pixel (R8) */
+        All += w[t] * ml[t] * ml[t];
+        Als += w[t] * ml[t] * ms[t];
+        Ass += w[t] * ms[t] * ms[t];
+        bl += w[t] * ml[t] * d[t];
+        bs += w[t] * ms[t] * d[t];
+    }
+    double cand[4][2];
+    int ok[4] = {1, 0, 0, 0};
+    cand[0][0] = 0.0; cand[0][1] = 0.0;
+    if (All > 0.0 && bl > 0.0) { ok[1] = 1; cand[1][0] = bl / All; cand[1][1] = 0.0; }
+    if (Ass > 0.0 && bs > 0.0) { ok[2] = 1; cand[2][0] = 0.0; cand[2][1] = bs / Ass; }
+    double det = All * Ass - Als * Als;
+    if (det > 0.0) {
+        double sl = (Ass * bl - Als * bs) / det;
+        double ss = (All * bs - Als * bl) / det;
+        if (sl > 0.0 && ss > 0.0) { ok[3] = 1; cand[3][0] = sl; cand[3][1] = ss; }
+    }
+    int best = 0;
+    double bestc = ora_chi2(ml, ms, d, w, npix, 0.0, 0.0);
+    for (int k = 1; k < 4; ++k) {
+        if (!ok[k]) continue;
+        double c = ora_chi2(ml, ms, d, w, npix, cand[k][0], cand[k][1]);
+        if (c < bestc) { bestc = c; best = k; }
+    }
+    s_out[0] = cand[best][0];
+    s_out[1] = cand[best][1];
+}
+
+/* A lens: observed image, noise map, PSF and grid, as the oracle holds it. */
+typedef struct {
+    int ny, nx, sub, k;
+    double dpix, x0, y0;
+    const double *data, *sigma, *psf; /* psf: raw, normalised here */
+} ora_lens;
+
+/* Everything for one parameter vector.  mode 0: NNLS amplitudes (R7);
+ * mode 1: fixed amplitudes from the I_e slots.  Optional outputs (may be
+ * NULL): the two blurred unit columns, the blurred model, the amplitudes.
+ * Returns log L (R8), -INFINITY for an invalid vector (R9). */
+double ora_loglike_full(const ora_lens *L, const double *p, int mode,
+                        double *ml_out, double *ms_out, double *model_out,
+                        double *amps_out)
+{
+    ora_model m;
+    int npix = L->ny * L->nx;
+    if (ora_decode(p, &m)) return -INFINITY;
+    double *il = malloc(sizeof(double) * npix), *is = malloc(sizeof(double) * npix);
+    double *ml = malloc(sizeof(double) * npix), *ms = malloc(sizeof(double) * npix);
+    double *w = malloc(sizeof(double) * npix);
+    double *psf = malloc(sizeof(double) * L->k * L->k);
+    double res = -INFINITY;
+    if (!il || !is || !ml || !ms || !w || !psf) goto done;
+    if (ora_psf_normalise(L->psf, L->k, psf)) goto done;
+    ora_columns(&m, L->ny, L->nx, L->dpix, L->sub, L->x0, L->y0, il, is);
+    ora_convolve(il, L->ny, L->nx, psf, L->k, ml);   /* B L_l, Eq. (7) */
+    ora_convolve(is, L->ny, L->nx, psf, L->k, ms);   /* B L_s, Eq. (7) */
+    ora_weights(L->data, L->sigma, npix, w);
+    double s[2];
+    if (mode == 0) ora_nnls2(ml, ms, L->data, w, npix, s);
+    else { s[0] = m.IeL; s[1] = m.IeS; }
+    double chi2 = ora_chi2(ml, ms, L->data, w, npix, s[0], s[1]);
+    double norm = 0.0;
+    for (int t = 0; t < npix; ++t)
+        if (w[t] > 0.0) norm += log(2.0 * M_PI / w[t]);
+    res = -0.5 * chi2 - 0.5 * norm;                  /* log of Eq. (5) */
+    if (ml_out) memcpy(ml_out, ml, sizeof(double) * npix);
+    if (ms_out) memcpy(ms_out, ms, sizeof(double) * npix);
+    if (model_out)
+        for (int t = 0; t < npix; ++t) model_out[t] = s[0] * ml[t] + s[1] * ms[t];
+    if (amps_out) { amps_out[0] = s[0]; amps_out[1] = s[1]; }
+done:
+    free(il); free(is); free(ml); free(ms); free(w); free(psf);
+    return res;
+}
+
+/* Unblurred unit columns for one vector (for per-stage parity checks).
+ * Returns -1 for an invalid vector. */
+int ora_unblurred_columns(const ora_lens *L, const double *p, double *il, double *is)
+{
+    ora_model m;
+    if (ora_decode(p, &m)) return -1;
+    ora_columns(&m, L->ny, L->nx, L->dpix, L->sub, L->x0, L->y0, il, is);
+    return 0;
+}
+
+/* Batch of B vectors (params row-major [B][21]); parallel over vectors only
+ * (each vector's arithmetic is unchanged).  nthreads <= 0: library default. */
+void ora_loglike_batch(const ora_lens *L, const double *params, int B, int mode,
+                       double *out, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; ++b)
+        out[b] = ora_loglike_full(L, params + (size_t)b * ORA_NPAR, mode,
+                                  NULL, NULL, NULL, NULL);
+    (void)nthreads;
+}
+
+/* Number of threads an OpenMP region of this library would use. */
+int ora_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

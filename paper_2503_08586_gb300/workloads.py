@@ -1,0 +1,278 @@
+"""Seeded synthetic lens workloads (inputs only).
+
+This module draws parameter vectors from priors, samples PSFs at pixel
+centres, and adds noise.  It holds none of the likelihood's arithmetic: the
+noiseless image it needs is produced by a ``render(params) -> (m_lens,
+m_source)`` callable that the caller supplies (the FP64 oracle in the tests,
+the library's own ``model_columns`` in the benchmark), so the same generator
+serves both sides without either importing the other.
+
+Workloads (the paper's datasets -- the 1,000 CSST-like mocks and the SLACS HST
+images -- are not available; these seeded stand-ins echo their image sizes,
+pixel scales, PSFs and the Sec. 3 / Table 1 model: SIE + external shear,
+Sersic lens light tied to the mass centre, Sersic source):
+
+  plain64     64x64 at 0.05"/px, 4x4 subpixels, 11x11 Gaussian PSF FWHM 0.1"
+  csst100     100x100 at 0.074"/px, 4x4 subpixels, 21x21 Gaussian PSF FWHM
+              0.15", noise = sky + Poisson term
+  hst200      200x200 at 0.05"/px, 5x5 subpixels, 31x31 Moffat PSF
+              (beta = 3, FWHM 0.1")
+  ragged      many lenses, sides in {64,100,128,160,200}, PSF 11..31 px
+  stream      Poisson job arrivals for the serving loop
+
+Seeds: workload k uses numpy PCG64 seeded with 2503085860 + k.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2503085860
+NPARAM = 21
+
+PARAM_NAMES = [
+    "theta_E", "eps1_m", "eps2_m", "x_m", "y_m", "gamma_1", "gamma_2",
+    "Ie_L", "re_L", "n_L", "eps1_L", "eps2_L", "x_L", "y_L",
+    "Ie_S", "re_S", "n_S", "eps1_S", "eps2_S", "x_S", "y_S",
+]
+
+# Spread used by the shrinking-Gaussian "sampler" draws around a truth.
+PRIOR_WIDTH = np.array([
+    0.29, 0.10, 0.10, 0.05, 0.05, 0.05, 0.05,
+    0.0, 0.26, 0.87, 0.10, 0.10, 0.05, 0.05,
+    0.0, 0.26, 0.87, 0.10, 0.10, 0.15, 0.15,
+])
+
+
+@dataclass
+class WorkloadSpec:
+    name: str
+    ny: int
+    nx: int
+    pixel_scale: float
+    sub: int
+    psf_size: int
+    psf_kind: str          # "gaussian" | "moffat"
+    psf_fwhm_arcsec: float
+    batch: int
+    noise_kind: str        # "sky" | "sky+poisson"
+    moffat_beta: float = 3.0
+    seed_offset: int = 0
+
+
+WORKLOADS = {
+    "plain64": WorkloadSpec("plain64", 64, 64, 0.05, 4, 11, "gaussian", 0.10,
+                            256, "sky", seed_offset=1),
+    "csst100": WorkloadSpec("csst100", 100, 100, 0.074, 4, 21, "gaussian", 0.15,
+                            4096, "sky+poisson", seed_offset=2),
+    "hst200": WorkloadSpec("hst200", 200, 200, 0.05, 5, 31, "moffat", 0.10,
+                           2048, "sky+poisson", seed_offset=3),
+}
+
+
+# ------------------------------------------------------------------ PSFs
+def gaussian_psf(size: int, fwhm_px: float) -> np.ndarray:
+    """Circular Gaussian sampled at pixel centres, unit sum, float32."""
+    if size % 2 != 1:
+        raise ValueError("PSF size must be odd")
+    sig = fwhm_px / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    r = np.arange(size) - (size - 1) / 2
+    g = np.exp(-0.5 * (r / sig) ** 2)
+    k = np.outer(g, g)
+    return (k / k.sum()).astype(np.float32)
+
+
+def moffat_psf(size: int, fwhm_px: float, beta: float) -> np.ndarray:
+    """Circular Moffat sampled at pixel centres, unit sum, float32."""
+    if size % 2 != 1:
+        raise ValueError("PSF size must be odd")
+    alpha = fwhm_px / (2.0 * math.sqrt(2.0 ** (1.0 / beta) - 1.0))
+    r = np.arange(size) - (size - 1) / 2
+    rr = r[:, None] ** 2 + r[None, :] ** 2
+    k = (1.0 + rr / alpha ** 2) ** (-beta)
+    return (k / k.sum()).astype(np.float32)
+
+
+def make_psf(spec: WorkloadSpec) -> np.ndarray:
+    fwhm_px = spec.psf_fwhm_arcsec / spec.pixel_scale
+    if spec.psf_kind == "gaussian":
+        return gaussian_psf(spec.psf_size, fwhm_px)
+    return moffat_psf(spec.psf_size, fwhm_px, spec.moffat_beta)
+
+
+# ---------------------------------------------------------------- priors
+def _eps(rng, n, qlo=0.5, qhi=1.0):
+    """Ellipticity components for q ~ U[qlo, qhi], position angle ~ U[0, pi)
+    (change of variables to the paper's ellipticity parametrisation)."""
+    q = rng.uniform(qlo, qhi, n)
+    pa = rng.uniform(0.0, math.pi, n)
+    e = (1.0 - q) / (1.0 + q)
+    return e * np.cos(2 * pa), e * np.sin(2 * pa)
+
+
+def draw_prior(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n parameter vectors from the workload priors, float32 [n, 21]:
+    theta_E ~ U[0.5,1.5]"; mass q ~ U[0.5,1], PA ~ U[0,pi); centre ~ N(0,0.05");
+    gamma_1,2 ~ N(0,0.05); lens and source Sersic n ~ U[1,4], r_e ~ U[0.1,1]",
+    q ~ U[0.5,1], PA ~ U[0,pi); lens-light centre = mass centre (Table 1);
+    source centre uniform in a disc of radius 0.3"; I_e slots = 1."""
+    p = np.zeros((n, NPARAM), dtype=np.float64)
+    p[:, 0] = rng.uniform(0.5, 1.5, n)
+    p[:, 1], p[:, 2] = _eps(rng, n)
+    p[:, 3] = rng.normal(0.0, 0.05, n)
+    p[:, 4] = rng.normal(0.0, 0.05, n)
+    p[:, 5] = rng.normal(0.0, 0.05, n)
+    p[:, 6] = rng.normal(0.0, 0.05, n)
+    p[:, 7] = 1.0
+    p[:, 8] = rng.uniform(0.1, 1.0, n)
+    p[:, 9] = rng.uniform(1.0, 4.0, n)
+    p[:, 10], p[:, 11] = _eps(rng, n)
+    p[:, 12] = p[:, 3]
+    p[:, 13] = p[:, 4]
+    p[:, 14] = 1.0
+    p[:, 15] = rng.uniform(0.1, 1.0, n)
+    p[:, 16] = rng.uniform(1.0, 4.0, n)
+    p[:, 17], p[:, 18] = _eps(rng, n)
+    rad = 0.3 * np.sqrt(rng.uniform(0.0, 1.0, n))
+    ang = rng.uniform(0.0, 2 * math.pi, n)
+    p[:, 19] = rad * np.cos(ang)
+    p[:, 20] = rad * np.sin(ang)
+    return p.astype(np.float32)
+
+
+def shrinking_draws(rng, truth: np.ndarray, n: int, lo_frac: float = 0.01):
+    """n vectors ~ N(truth, sigma_j), sigma_j shrinking geometrically from the
+    prior width to lo_frac of it (a stand-in for a sampler converging);
+    entries clipped into the valid region.  float32 [n, 21]."""
+    frac = np.geomspace(1.0, lo_frac, n)
+    p = truth[None, :].astype(np.float64) + rng.normal(size=(n, NPARAM)) * (
+        frac[:, None] * PRIOR_WIDTH[None, :])
+    p[:, 0] = np.clip(p[:, 0], 0.05, 3.5)
+    for a, b in ((1, 2), (10, 11), (17, 18)):
+        e = np.hypot(p[:, a], p[:, b])
+        s = np.where(e > 0.6, 0.6 / np.maximum(e, 1e-30), 1.0)
+        p[:, a] *= s
+        p[:, b] *= s
+    p[:, 8] = np.clip(p[:, 8], 0.05, 4.0)
+    p[:, 15] = np.clip(p[:, 15], 0.05, 2.0)
+    p[:, 9] = np.clip(p[:, 9], 0.3, 8.0)
+    p[:, 16] = np.clip(p[:, 16], 0.3, 8.0)
+    p[:, 12] = p[:, 3]
+    p[:, 13] = p[:, 4]
+    return p.astype(np.float32)
+
+
+# ----------------------------------------------------------------- lenses
+@dataclass
+class SynthLens:
+    ny: int
+    nx: int
+    pixel_scale: float
+    sub: int
+    psf: np.ndarray          # float32 [k, k], unit sum
+    data: np.ndarray         # float32 [ny, nx]
+    noise: np.ndarray        # float32 [ny, nx], sigma per pixel
+    truth: np.ndarray        # float32 [21]; I_e slots = true amplitudes
+    x0: float = 0.0
+    y0: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+
+def centred_origin(n: int, pixel_scale: float) -> float:
+    """Coordinate of pixel 0's centre for an image centred on the origin."""
+    return -(n - 1) * pixel_scale / 2.0
+
+
+def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
+               peak_snr=50.0, sky_sigma=1.0, truth=None) -> SynthLens:
+    """One lens: truth from the priors, noiseless image from render(truth)
+    (blurred unit-amplitude lens and source columns), amplitudes set so that
+    each component's brightest blurred pixel is peak_snr * sky_sigma, then
+    Gaussian noise.  noise_kind "sky": sigma = sky_sigma; "sky+poisson":
+    sigma^2 = sky^2 + max(model,0)/g with g chosen so the Poisson term equals
+    sky^2 at the source peak."""
+    if truth is None:
+        truth = draw_prior(rng, 1)[0]
+    truth = truth.astype(np.float32).copy()
+    ml, ms = render(truth)
+    ml = np.asarray(ml, dtype=np.float64)
+    ms = np.asarray(ms, dtype=np.float64)
+    al = peak_snr * sky_sigma / max(ml.max(), 1e-30)
+    as_ = peak_snr * sky_sigma / max(ms.max(), 1e-30)
+    truth[7] = al
+    truth[14] = as_
+    model = al * ml + as_ * ms
+    if noise_kind == "sky":
+        var = np.full_like(model, sky_sigma ** 2)
+    else:
+        g = peak_snr * sky_sigma / sky_sigma ** 2
+        var = sky_sigma ** 2 + np.maximum(model, 0.0) / g
+    sigma = np.sqrt(var)
+    data = model + rng.normal(size=model.shape) * sigma
+    return SynthLens(ny, nx, pixel_scale, sub, psf.astype(np.float32),
+                     data.astype(np.float32), sigma.astype(np.float32), truth,
+                     centred_origin(nx, pixel_scale),
+                     centred_origin(ny, pixel_scale))
+
+
+def workload(name: str, render_factory, batch: int | None = None):
+    """(lens, params[B, 21]) for a named single-lens workload.
+    render_factory(pixel_scale, sub, psf, ny, nx) -> render(params)."""
+    spec = WORKLOADS[name]
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + spec.seed_offset))
+    psf = make_psf(spec)
+    render = render_factory(spec.pixel_scale, spec.sub, psf, spec.ny, spec.nx)
+    lens = synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf,
+                      render, spec.noise_kind)
+    B = spec.batch if batch is None else batch
+    params = draw_prior(rng, B)
+    return lens, params
+
+
+# ----------------------------------------------------------- ragged / stream
+RAGGED_SIDES = (64, 100, 128, 160, 200)
+
+
+def ragged_specs(n_lenses: int, seed_offset: int = 4):
+    """Image sides and PSF sizes of a ragged multi-lens batch (no rendering):
+    side ~ U{64,100,128,160,200}, PSF size ~ U{11,13,...,31}, Gaussian PSF of
+    FWHM = size/7 px, 0.074"/px, 4x4 subpixels."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_offset))
+    sides = rng.choice(RAGGED_SIDES, size=n_lenses)
+    ks = 11 + 2 * rng.integers(0, 11, size=n_lenses)
+    return rng, [(int(s), int(k)) for s, k in zip(sides, ks)]
+
+
+def ragged_workload(n_lenses: int, per_lens: int, render_factory,
+                    pixel_scale=0.074, sub=4, seed_offset: int = 4):
+    """List of (lens, params[per_lens, 21]) for a ragged batch."""
+    rng, specs = ragged_specs(n_lenses, seed_offset)
+    out = []
+    for side, k in specs:
+        psf = gaussian_psf(k, k / 7.0)
+        render = render_factory(pixel_scale, sub, psf, side, side)
+        lens = synth_lens(rng, side, side, pixel_scale, sub, psf, render,
+                          "sky+poisson")
+        params = shrinking_draws(rng, lens.truth, per_lens)
+        out.append((lens, params))
+    return out
+
+
+def request_stream(n_jobs: int, rate_hz: float = 20.0, iters: int = 300,
+                   batch_lo: int = 500, batch_hi: int = 5000,
+                   side_lo: int = 64, side_hi: int = 200, seed_offset: int = 5):
+    """Job descriptors of a Poisson request stream: arrival time (s), image
+    side, PSF size, and the batch size of each of its sampler iterations."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_offset))
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
+    jobs = []
+    for j in range(n_jobs):
+        side = int(rng.integers(side_lo, side_hi + 1))
+        k = int(11 + 2 * rng.integers(0, 11))
+        batches = rng.integers(batch_lo, batch_hi + 1, size=iters)
+        jobs.append({"arrival": float(t[j]), "side": side, "psf": k,
+                     "batches": [int(b) for b in batches],
+                     "seed": int(rng.integers(0, 2 ** 31))})
+    return jobs
