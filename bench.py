@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the batched lens log-likelihood on GB300.
+
+Workload (default csst100): a CSST-like lens, 100x100 pixels at 0.074"/px,
+4x4 subpixels, 21x21 Gaussian PSF, SIE + external shear mass, Sersic lens
+light + Sersic source, non-negative linear amplitudes; B = 4096 parameter
+vectors per step drawn from the priors.  One step = one batched call
+(prologue + fused ray-trace / light / bin / PSF / likelihood kernel) over the
+whole batch with inputs resident in HBM; the L2 is flushed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (the reference arm).  Multi-GPU runs are
+independent replicas (weak scaling): each rank evaluates its own batch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("log-likelihood evals/s (100×100, 4×4 subpix) served vs plain; "
+          "p50/p99 latency")
+UNIT = "evals/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+# ------------------------------------------------------------ work model
+def flops_per_eval(ny, nx, sub, k, separable) -> float:
+    """Algorithmic FP32 work of one likelihood evaluation (add, sub, mul,
+    div = 1 flop; FMA = 2; each transcendental evaluation = 1):
+    per subpixel 72 flops + 9 transcendentals (grid 4, SIE 24 + sqrt, atan,
+    atanh; shear 8; lens equation 2; two Sersics 2 x (16 + sqrt, pow, exp);
+    binning 2); per pixel: mean 2, PSF 2 channels x (2K separable | K^2
+    direct) taps x 2, five weighted sums 15."""
+    npix = ny * nx
+    per_sub = 72 + 9
+    taps = 2 * k if separable else k * k
+    per_pix = sub * sub * per_sub + 2 + 2 * taps * 2 + 15
+    return float(npix * per_pix)
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
+    return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096):
+    """The FP64 oracle, as it stands, on all host cores over a bounded
+    sample of the same batch (about budget_cpu_s of CPU work)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                    lens.x0, lens.y0)
+    P = params.astype(np.float64)
+    n0 = min(2 * cores, len(P))
+    t = time.perf_counter()
+    o.loglike_batch(P[:n0], nthreads=cores)
+    dt = time.perf_counter() - t
+    per_cpu = dt * cores / n0
+    n = int(min(max_n, len(P), max(n0, budget_cpu_s / max(per_cpu, 1e-9))))
+    t = time.perf_counter()
+    o.loglike_batch(P[:n], nthreads=cores)
+    wall = time.perf_counter() - t
+    return {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the {len(P)} vectors of one step, FP64 C oracle, "
+                      f"OpenMP over vectors on {cores} threads",
+            "wall_s": wall}
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_2503_08586_gb300 import build, tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    tll.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = W.WORKLOADS[args.workload]
+    B = args.batch or spec.batch
+    lens, params = W.workload(args.workload, tll.columns_renderer, batch=B)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                 lens.x0, lens.y0)
+    info = L.info()
+    p_dev = torch.from_numpy(params).to(dev)
+    out = torch.empty(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    L.profile(True)
+    for _ in range(args.warmup):
+        L.loglike_batch(p_dev, out)
+    barrier()
+    clocks = ClockSampler(local)
+    step_ms, main_ms, pro_ms = [], [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.loglike_batch(p_dev, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        a, b = L.profile_last()
+        pro_ms.append(a)
+        main_ms.append(b)
+    barrier()
+    clk = clocks.stop()
+    L.profile(False)
+    launches = 2 * args.steps
+    total = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / args.steps
+    value = B * ws / (ms_per_step / 1e3)
+    ll = out.cpu().numpy()
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    p_host = torch.from_numpy(params).pin_memory()
+    o_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        L.loglike_batch_host(p_host, o_host)
+    barrier()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.loglike_batch_host(p_host, o_host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = B * ws / (e2e_total / args.steps / 1e3)
+    assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return None
+
+    fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0], info["separable"])
+    main_avg = statistics.mean(main_ms)
+    achieved = fpe * B / (main_avg / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": (f"{args.workload}: {lens.ny}x{lens.nx} px at {lens.pixel_scale}\"/px, "
+                         f"{lens.sub}x{lens.sub} subpixels, {lens.psf.shape[0]}x"
+                         f"{lens.psf.shape[0]} {spec.psf_kind} PSF "
+                         f"({'separable' if info['separable'] else 'direct'} conv), "
+                         f"SIE+shear, Sersic lens+source, NNLS amplitudes"),
+            "batch_per_gpu": B, "global_batch": B * ws, "path": "plain",
+            "parallelism": f"replicas x{ws}",
+            "l2": "flushed between timed steps (256 MB write, outside the events)"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "subpixel_evals_per_s": value * lens.ny * lens.nx * lens.sub ** 2,
+        "kernel_ms": {"k_prologue": statistics.mean(pro_ms), "k_loglike": main_avg},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_loglike",
+                     "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                                   f"x {SM_MAX_MHZ:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "impl": "ours",
+    }
+    if not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(lens, params)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, same workload /
+    metric; each step a bounded sample of the batch."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2503_08586_gb300 import workloads as W
+    oracle.build()
+    spec = W.WORKLOADS[args.workload]
+    B = args.batch or spec.batch
+    lens, params = W.workload(args.workload, oracle.columns_renderer, batch=B)
+    cores = os.cpu_count() or 1
+    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                    lens.x0, lens.y0)
+    P = params.astype(np.float64)
+    S = min(B, args.ref_sample or 4 * cores)
+    for w in range(args.warmup):
+        o.loglike_batch(P[:S], nthreads=cores)
+    times = []
+    for k in range(args.steps):
+        off = (k * S) % max(1, B - S + 1)
+        t = time.perf_counter()
+        o.loglike_batch(P[off:off + S], nthreads=cores)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = S / (ms / 1e3)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"{args.workload} ({lens.ny}x{lens.nx}, s={lens.sub}, "
+                               f"K={lens.psf.shape[0]}), {S} of {B} vectors per step",
+                   "batch_per_gpu": S, "global_batch": S, "path": "plain"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{S} vectors per step of the {B}-vector batch"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="csst100")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=0)
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

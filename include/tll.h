@@ -1,0 +1,172 @@
+/*
+ * tll.h -- C ABI of the GB300 (sm_103a) lens log-likelihood library, libtll.so.
+ *
+ * The library evaluates, for a batch of parameter vectors against one
+ * observed strong-lens image, the forward model and Gaussian log-likelihood
+ * of arXiv:2503.08586 (TinyLensGpu):
+ *   - lens equation beta = theta - alpha(theta) (Sec. 2.1, Eq. 1) with an
+ *     SIE (Sec. 2.4, Eq. 12 at gamma = 2) plus external shear (Eqs. 13, 14);
+ *   - image formation I = I_L(theta) + I_S(beta) (Eq. 2) with elliptical
+ *     Sersic light (Eqs. 8-11), on an s x s supersampled grid binned back to
+ *     pixels (Sec. 2.1, text after Eq. 2);
+ *   - PSF convolution (Eq. 3);
+ *   - non-negative linear amplitudes of the lens and source columns
+ *     (Sec. 2.3, Eq. 7 and the penalty after it; Sec. 2.2, Eq. 6);
+ *   - the Gaussian log-likelihood (Sec. 2.2, Eq. 5).
+ * All arithmetic runs in this library's CUDA kernels.  There is no CPU
+ * fallback: every entry point returns TLL_ECUDA when no usable GPU exists.
+ *
+ * Conventions shared by all entry points
+ *   Grid: pixel (i row, j column) has its centre at (x0 + j*pixel_scale,
+ *     y0 + i*pixel_scale) arcsec; subpixel (a, c) of its s x s grid sits at
+ *     offset ((c + 1/2)/s - 1/2, (a + 1/2)/s - 1/2) * pixel_scale.  Images are
+ *     float32, row-major [ny][nx].
+ *   Parameter vector (TLL_NPARAM = 21 float32, row-major [B][21]):
+ *     [0] theta_E  [1] eps1_m [2] eps2_m [3] x_m [4] y_m [5] gamma_1
+ *     [6] gamma_2  [7] I_e^L [8] r_e^L [9] n^L [10] eps1_L [11] eps2_L
+ *     [12] x_L [13] y_L [14] I_e^S [15] r_e^S [16] n^S [17] eps1_S
+ *     [18] eps2_S [19] x_S [20] y_S
+ *     (ellipticities as Eq. 11; shear components with
+ *     psi_ext = gamma_1 (x^2 - y^2)/2 + gamma_2 x y about the origin, which is
+ *     Eq. 13 on the branch gamma_1 = -gamma cos 2phi of Eq. 14; I_e slots
+ *     are used only with TLL_AMP_FIXED.)
+ *   Invalid vectors (|eps| >= 1, r_e <= 0, n outside [0.2, 10],
+ *     theta_E < 0, a non-finite entry) give log L = -INFINITY; the rest of
+ *     the batch is unaffected.
+ *   Masking: a pixel whose noise sigma is not finite and > 0, or whose datum
+ *     is not finite, has weight 0 and no normalisation term.
+ *   log L = -chi^2/2 - sum_{unmasked} log(2 pi sigma_i^2)/2, in FP64.
+ *   Errors: every int-returning call returns TLL_OK (0) or a TLL_E* code and
+ *     never aborts; tll_last_error() gives a message for the calling thread.
+ */
+#ifndef TLL_H
+#define TLL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TLL_NPARAM 21
+#define TLL_MAX_SUB 8      /* largest supersampling factor s */
+#define TLL_MAX_PSF 63     /* largest PSF side */
+#define TLL_MAX_SIDE 4096  /* largest image side */
+
+enum {
+    TLL_OK = 0,
+    TLL_EINVAL = 1,   /* invalid argument (null pointer, bad size, ...) */
+    TLL_ENOMEM = 2,   /* device or host allocation failed */
+    TLL_ECUDA = 3,    /* CUDA runtime error or no usable GPU */
+    TLL_ETIMEOUT = 4, /* a bounded wait ran out */
+    TLL_EBUSY = 5     /* no capacity right now (server admission) */
+};
+
+/* Amplitude modes (the `flags` of tll_create_lens, low bits). */
+enum {
+    TLL_AMP_LINEAR = 0, /* amplitudes by non-negative least squares (Sec. 2.3) */
+    TLL_AMP_FIXED = 1   /* amplitudes are the I_e slots [7], [14] */
+};
+/* Extra flag bit: never take the separable-PSF fast path (testing). */
+#define TLL_FLAG_DIRECT_CONV 0x100
+
+typedef struct tll_lens tll_lens; /* opaque; owns device copies of its data */
+
+typedef struct {
+    int nx, ny;          /* image size in pixels */
+    float pixel_scale;   /* arcsec per pixel, > 0 */
+    int sub;             /* supersampling factor s, 1..TLL_MAX_SUB */
+    float x0, y0;        /* arcsec coordinates of pixel (0, 0)'s centre */
+} tll_grid_t;
+
+/*
+ * tll_create_lens -- copy one observed lens to the current CUDA device.
+ *   image  host float32 [ny][nx], the data d (Sec. 2.3)
+ *   noise  host float32 [ny][nx], sigma per pixel (Eq. 5); see Masking
+ *   psf    host float32 [psf_size][psf_size], odd side <= TLL_MAX_PSF, finite,
+ *          positive sum; the library normalises it to unit sum (Eq. 3)
+ *   grid   image geometry (see Grid)
+ *   flags  TLL_AMP_LINEAR or TLL_AMP_FIXED, optionally | TLL_FLAG_DIRECT_CONV
+ *   out    receives the new lens
+ * The caller keeps ownership of all input buffers.  The lens owns its device
+ * memory and per-launch scratch; destroy it with tll_destroy_lens.
+ * Errors: TLL_EINVAL (null pointer, bad size, non-finite PSF, zero PSF sum),
+ * TLL_ENOMEM, TLL_ECUDA.
+ */
+int tll_create_lens(const float *image, const float *noise, const float *psf,
+                    int psf_size, const tll_grid_t *grid, int flags,
+                    tll_lens **out);
+
+/*
+ * tll_loglike_batch -- log L of B parameter vectors (Eqs. 1-3, 5-12).
+ *   params  DEVICE float32 [B][TLL_NPARAM] (see Parameter vector)
+ *   B       number of vectors, >= 0 (0: no work, TLL_OK)
+ *   out     DEVICE float64 [B]
+ *   stream  cudaStream_t to launch on (NULL: the legacy default stream)
+ * Asynchronous: returns after enqueueing; the caller synchronises the
+ * stream before reading out.  params and out stay owned by the caller and
+ * must not be touched until the stream reaches this work.  Calls on one lens
+ * must not overlap on different streams (they share the lens's scratch).
+ * Errors: TLL_EINVAL, TLL_ENOMEM (scratch growth), TLL_ECUDA (launch).
+ */
+int tll_loglike_batch(tll_lens *L, const float *params, int B, double *out,
+                      void *stream);
+
+/*
+ * tll_loglike_batch_host -- tll_loglike_batch from HOST buffers: copies
+ * params (host float32 [B][21]) to the device, runs the batch and copies the
+ * log-likelihoods back to out (host float64 [B]), all on `stream`, and
+ * waits for the stream.  Pinned host buffers make the copies asynchronous
+ * DMA.  Errors: as tll_loglike_batch.
+ */
+int tll_loglike_batch_host(tll_lens *L, const float *params, int B,
+                           double *out, void *stream);
+
+/*
+ * tll_model_image -- the blurred model image I^m (Eq. 3) of one vector with
+ * its amplitudes: linear (NNLS) or fixed, per the lens's mode.
+ *   params     host float32 [TLL_NPARAM]
+ *   image_out  host float32 [ny][nx]
+ *   amps_out   host float32 [2] (lens, source amplitude) or NULL
+ *   loglike_out host float64 [1] or NULL
+ * Synchronous.  An invalid vector gives TLL_EINVAL.
+ */
+int tll_model_image(tll_lens *L, const float *params, float *image_out,
+                    float *amps_out, double *loglike_out);
+
+/*
+ * tll_model_columns -- the two unit-amplitude columns of L (Eq. 7) for one
+ * vector: lens light and lensed source, binned, before (blurred = 0) or after
+ * (blurred = 1) the PSF.  params host [21]; lens_out, src_out host float32
+ * [ny][nx].  Synchronous.  An invalid vector gives TLL_EINVAL.
+ */
+int tll_model_columns(tll_lens *L, const float *params, float *lens_out,
+                      float *src_out, int blurred);
+
+/*
+ * tll_profile_enable / tll_profile_last -- per-launch timing for profiling.
+ * While enabled (on != 0), each tll_loglike_batch / _host call records CUDA
+ * events on its stream before the prologue launch, between the two launches
+ * and after the main launch.  tll_profile_last waits for the last call's
+ * events and returns the prologue and main-kernel durations in ms.  The
+ * events belong to the lens.  Errors: TLL_EINVAL (not enabled, no call yet),
+ * TLL_ECUDA.
+ */
+int tll_profile_enable(tll_lens *L, int on);
+int tll_profile_last(tll_lens *L, float *prologue_ms, float *main_ms);
+
+/* Image size and mode of a lens (any pointer may be NULL). */
+int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
+                  int *flags, int *separable);
+
+/* Release a lens and its device memory (NULL is a no-op). */
+void tll_destroy_lens(tll_lens *L);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *tll_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int tll_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLL_H */

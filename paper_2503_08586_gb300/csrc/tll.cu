@@ -1,0 +1,825 @@
+// tll.cu -- kernels and C ABI of libtll.so (GB300, sm_103a).
+//
+// Hot path per batch (one stream, two launches):
+//   k_prologue  one thread per parameter vector: ellipse, b_n (FP64),
+//               SIE prefactors -> a 32-float constant block per vector.
+//   k_loglike   persistent CTAs, one parameter vector at a time per CTA:
+//               (1) ray-trace + Sersic light on the s x s subpixels of every
+//                   pixel, binned to two float images (lens, source) held in
+//                   shared memory (or, for images too large for it, in a
+//                   per-CTA global scratch slot that stays in L2);
+//               (2) PSF convolution of both images -- separable (row pass in
+//                   place, then column pass) when the PSF is an outer
+//                   product to rounding, direct 2-D otherwise;
+//               (3) fused into the convolution's output loop, the five
+//                   weighted sums A_ll, A_ls, A_ss, b_l, b_s in double-float
+//                   (exact FMA products, compensated sums), promoted to FP64
+//                   for the warp / block reduction;
+//               (4) one thread: 2-column NNLS or fixed amplitudes, chi^2,
+//                   log L in FP64.
+// The model-image entry points run the same kernel on one vector with the
+// intermediate images written out.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tll.h"
+#include "tll_device.cuh"
+
+using namespace tll;
+
+namespace {
+
+constexpr int kThreads = 512;      // CTA size of k_loglike
+constexpr int kHMax = 8;           // in-place row pass holds nx <= 32*kHMax
+constexpr int kRedBytes = 32 * 5 * 8;
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (expr);                                              \
+        if (e_ != cudaSuccess)                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? TLL_ENOMEM          \
+                                                        : TLL_ECUDA,          \
+                        "%s: %s", #expr, cudaGetErrorString(e_));             \
+    } while (0)
+
+struct LensDev {
+    int nx, ny, npix, sub, K, h, sep, mode;
+    float XC, YC;     // coordinate of the grid centre (between subpixels)
+    float JCX, JCY;   // subpixel index of the grid centre, (n*s - 1)/2
+    float dsh, dsl;   // subpixel step dpix/s as a float pair
+    float inv_s2;
+    const float *psf;    // [K*K] unit sum (direct path)
+    const float *pu;     // [K] column factor over PSF rows (separable path)
+    const float *pv;     // [K] row factor over PSF columns
+    const float4 *wpack; // [npix] (w_hi, w_lo, wd_hi, wd_lo)
+    double dWd, lognorm;
+};
+
+struct RunArgs {
+    const float *kc;     // [B][NCONST]
+    int B;
+    double *out;         // [B]
+    float *gscr;         // global image scratch, 4*npix floats per CTA
+    float *wr_unblurred; // WRITE: [2][npix]
+    float *wr_blurred;   // WRITE: [2][npix]
+    double *wr_res;      // WRITE: [8] All Als Ass bl bs sl ss logL
+};
+
+// -------------------------------------------------------------- kernels
+__global__ void k_prologue(const float *__restrict__ params, int B,
+                           float *__restrict__ kc, double X0, double Y0)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B)
+        decode_vector(params + (size_t)b * NPAR, kc + (size_t)b * NCONST, X0, Y0);
+}
+
+// One term of the five weighted sums (Sec. 2.3: A = M^T W M, b = M^T W d)
+// for one pixel with blurred column values ml, ms; wp = (w_hi, w_lo,
+// wd_hi, wd_lo).  Products are formed exactly as float pairs and added
+// with TwoSum into double-float accumulators a[0..9].
+__device__ __forceinline__ void accum_pixel(float ml, float ms, float4 wp, float *a)
+{
+    float p1 = wp.x * ml, e1 = fmaf(wp.x, ml, -p1);
+    e1 = fmaf(wp.y, ml, e1);
+    float p2 = wp.x * ms, e2 = fmaf(wp.x, ms, -p2);
+    e2 = fmaf(wp.y, ms, e2);
+    float p, e;
+    p = p1 * ml; e = fmaf(p1, ml, -p); e = fmaf(e1, ml, e); df_acc(a[0], a[1], p, e);
+    p = p1 * ms; e = fmaf(p1, ms, -p); e = fmaf(e1, ms, e); df_acc(a[2], a[3], p, e);
+    p = p2 * ms; e = fmaf(p2, ms, -p); e = fmaf(e2, ms, e); df_acc(a[4], a[5], p, e);
+    p = wp.z * ml; e = fmaf(wp.z, ml, -p); e = fmaf(wp.w, ml, e); df_acc(a[6], a[7], p, e);
+    p = wp.z * ms; e = fmaf(wp.z, ms, -p); e = fmaf(wp.w, ms, e); df_acc(a[8], a[9], p, e);
+}
+
+// Amplitudes and log L from the five sums (thread-local, FP64).
+// NNLS over two columns: the optimum is the unconstrained minimiser of one
+// face {none, lens only, source only, both} that is feasible; chi^2 of a
+// face's minimiser s is dWd - s^T b.  Fixed mode: s = (I_e^L, I_e^S) and
+// chi^2 = dWd - 2 s^T b + s^T A s.
+__device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
+                                              float IeL, float IeS, double *sl_o,
+                                              double *ss_o, double *ll_o)
+{
+    const double All = S[0], Als = S[1], Ass = S[2], bl = S[3], bs = S[4];
+    double sl, ss, chi2;
+    if (L.mode == TLL_AMP_FIXED) {
+        sl = IeL;
+        ss = IeS;
+        chi2 = L.dWd - 2.0 * (sl * bl + ss * bs) + sl * sl * All +
+               2.0 * sl * ss * Als + ss * ss * Ass;
+    } else {
+        sl = 0.0; ss = 0.0; chi2 = L.dWd;
+        if (All > 0.0 && bl > 0.0) {
+            const double c = L.dWd - bl * (bl / All);
+            if (c < chi2) { chi2 = c; sl = bl / All; ss = 0.0; }
+        }
+        if (Ass > 0.0 && bs > 0.0) {
+            const double c = L.dWd - bs * (bs / Ass);
+            if (c < chi2) { chi2 = c; sl = 0.0; ss = bs / Ass; }
+        }
+        // Both columns free only when they are not collinear to rounding:
+        // det / (A_ll A_ss) = 1 - rho^2 must exceed the sums' rounding
+        // (~1e-14) by a wide margin; collinear columns reach their optimum
+        // on a single-column face.  The candidate's chi^2 is the full
+        // quadratic form, exact for any s given A and b.
+        const double det = All * Ass - Als * Als;
+        if (det > 1e-9 * All * Ass) {
+            const double tl = (Ass * bl - Als * bs) / det;
+            const double ts = (All * bs - Als * bl) / det;
+            if (tl > 0.0 && ts > 0.0) {
+                const double c = L.dWd - 2.0 * (tl * bl + ts * bs) + tl * tl * All +
+                                 2.0 * tl * ts * Als + ts * ts * Ass;
+                if (c < chi2) { chi2 = c; sl = tl; ss = ts; }
+            }
+        }
+    }
+    *sl_o = sl;
+    *ss_o = ss;
+    *ll_o = -0.5 * chi2 + L.lognorm;
+}
+
+template <bool SMEM_IMG, bool WRITE>
+__global__ void __launch_bounds__(kThreads)
+k_loglike(const LensDev L, const RunArgs R)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    double *sred = reinterpret_cast<double *>(smem);
+    float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
+    const int K = L.K, h = L.h, nx = L.nx, ny = L.ny, npix = L.npix;
+    const int psf_floats = L.sep ? 2 * K : K * K;
+    float *Il, *Is, *Hl, *Hs;
+    if (SMEM_IMG) {
+        Il = spsf + ((psf_floats + 3) & ~3);
+        Is = Il + npix;
+        Hl = Il;   // the row pass runs in place
+        Hs = Is;
+    } else {
+        Il = R.gscr + (size_t)blockIdx.x * 4 * npix;
+        Is = Il + npix;
+        Hl = Is + npix;
+        Hs = Hl + npix;
+    }
+    for (int t = tid; t < psf_floats; t += nthr)
+        spsf[t] = L.sep ? (t < K ? L.pu[t] : L.pv[t - K]) : L.psf[t];
+    __syncthreads();
+    const float *su = spsf, *sv = spsf + K;
+
+    for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
+        const float *kc = R.kc + (size_t)b * NCONST;
+        if (kc[K_VALID] == 0.0f) {
+            if (tid == 0) {
+                R.out[b] = -INFINITY;
+                if (WRITE) R.wr_res[7] = -INFINITY;
+            }
+            continue;
+        }
+        const Mass m = load_mass(kc);
+        const Ellipse el = load_ellipse(kc, K_OXL);
+        const Ellipse es = load_ellipse(kc, K_OXS);
+
+        // (1) ray-trace + light on the subpixels, mean-binned per pixel.
+        // A subpixel at offset (jx, iy) from the grid centre (J - JC exact,
+        // one rounding for the product) has offset (O + jx, O + iy) from each
+        // model centre, O = grid centre - model centre (small numbers, so
+        // small rounding).
+        for (int pix = tid; pix < npix; pix += nthr) {
+            const int i = pix / nx, j = pix - i * nx;
+            float accl = 0.0f, accs = 0.0f;
+            for (int a = 0; a < L.sub; ++a) {
+                const float fi = (float)(i * L.sub + a) - L.JCY;
+                const float iy = fmaf(fi, L.dsh, fi * L.dsl);
+                const float y = L.YC + iy;
+#pragma unroll 2
+                for (int c = 0; c < L.sub; ++c) {
+                    const float fj = (float)(j * L.sub + c) - L.JCX;
+                    const float jx = fmaf(fj, L.dsh, fj * L.dsl);
+                    const float x = L.XC + jx;
+                    float ax, ay;
+                    deflection(m, m.ox + jx, m.oy + iy, x, y, ax, ay);
+                    accl += sersic_unit(el, el.ox + jx, el.oy + iy);
+                    accs += sersic_unit(es, (es.ox + jx) - ax, (es.oy + iy) - ay);
+                }
+            }
+            Il[pix] = accl * L.inv_s2;
+            Is[pix] = accs * L.inv_s2;
+        }
+        __syncthreads();
+        if (WRITE) {
+            for (int t = tid; t < npix; t += nthr) {
+                R.wr_unblurred[t] = Il[t];
+                R.wr_unblurred[npix + t] = Is[t];
+            }
+            __syncthreads();
+        }
+
+        // (2)+(3) convolution with the fused weighted sums
+        float acc[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+        if (L.sep) {
+            // row pass: H(i, j) = sum_c v[c] I(i, j + h - c)
+            for (int row = warp; row < 2 * ny; row += nwarp) {
+                const float *src = row < ny ? Il + row * nx : Is + (row - ny) * nx;
+                float *dst = row < ny ? Hl + row * nx : Hs + (row - ny) * nx;
+                if (SMEM_IMG) {
+                    float o[kHMax];
+#pragma unroll
+                    for (int q = 0; q < kHMax; ++q) {
+                        const int j = lane + 32 * q;
+                        float s = 0.0f;
+                        if (j < nx) {
+                            const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                            for (int c = c0; c <= c1; ++c) s = fmaf(sv[c], src[j + h - c], s);
+                        }
+                        o[q] = s;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < kHMax; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < nx) dst[j] = o[q];
+                    }
+                    __syncwarp();
+                } else {
+                    for (int j = lane; j < nx; j += 32) {
+                        const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                        float s = 0.0f;
+                        for (int c = c0; c <= c1; ++c) s = fmaf(sv[c], src[j + h - c], s);
+                        dst[j] = s;
+                    }
+                }
+            }
+            __syncthreads();
+            // column pass: m(i, j) = sum_r u[r] H(i + h - r, j), fused sums
+            const int nb = max(1, nthr / nx);
+            const int rb = (ny + nb - 1) / nb;
+            for (int it = tid; it < nx * nb; it += nthr) {
+                const int j = it % nx, band = it / nx;
+                const int r0 = band * rb, r1 = min(ny, r0 + rb);
+                for (int i = r0; i < r1; ++i) {
+                    const int q0 = max(0, i + h - ny + 1), q1 = min(K - 1, i + h);
+                    float ml = 0.0f, ms = 0.0f;
+                    for (int r = q0; r <= q1; ++r) {
+                        const int off = (i + h - r) * nx + j;
+                        ml = fmaf(su[r], Hl[off], ml);
+                        ms = fmaf(su[r], Hs[off], ms);
+                    }
+                    const int pix = i * nx + j;
+                    if (WRITE) {
+                        R.wr_blurred[pix] = ml;
+                        R.wr_blurred[npix + pix] = ms;
+                    }
+                    accum_pixel(ml, ms, L.wpack[pix], acc);
+                }
+            }
+        } else {
+            // direct 2-D convolution, one output pixel per thread, summed
+            // per PSF row then across rows
+            for (int pix = tid; pix < npix; pix += nthr) {
+                const int i = pix / nx, j = pix - i * nx;
+                const int r0 = max(0, i + h - ny + 1), r1 = min(K - 1, i + h);
+                const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                float ml = 0.0f, ms = 0.0f;
+                for (int r = r0; r <= r1; ++r) {
+                    const float *kr = spsf + r * K;
+                    const int base = (i + h - r) * nx + j + h;
+                    float rl = 0.0f, rs = 0.0f;
+                    for (int c = c0; c <= c1; ++c) {
+                        rl = fmaf(kr[c], Il[base - c], rl);
+                        rs = fmaf(kr[c], Is[base - c], rs);
+                    }
+                    ml += rl;
+                    ms += rs;
+                }
+                if (WRITE) {
+                    R.wr_blurred[pix] = ml;
+                    R.wr_blurred[npix + pix] = ms;
+                }
+                accum_pixel(ml, ms, L.wpack[pix], acc);
+            }
+        }
+
+        // (3) warp reduction in double-float, block reduction in FP64
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], off);
+                df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                sred[warp * 5 + k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double s = 0.0;
+            if (lane < 5)
+                for (int w = 0; w < nwarp; ++w) s += sred[w * 5 + lane];
+            double S[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, s, k);
+            if (lane == 0) {
+                double sl, ss, ll;
+                finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
+                R.out[b] = ll;
+                if (WRITE) {
+                    for (int k = 0; k < 5; ++k) R.wr_res[k] = S[k];
+                    R.wr_res[5] = sl;
+                    R.wr_res[6] = ss;
+                    R.wr_res[7] = ll;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Model image of one vector: I^m = s_l m_l + s_s m_s (Eq. 7), FP64 then
+// rounded.
+__global__ void k_combine(const float *__restrict__ blurred,
+                          const double *__restrict__ res, int npix,
+                          float *__restrict__ img)
+{
+    const double sl = res[5], ss = res[6];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npix;
+         t += gridDim.x * blockDim.x)
+        img[t] = (float)(sl * (double)blurred[t] + ss * (double)blurred[npix + t]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ lens object
+struct tll_lens {
+    int dev = 0;
+    int nx = 0, ny = 0, npix = 0, sub = 0, K = 0, flags = 0, mode = 0, sep = 0;
+    float dpix = 0, x0 = 0, y0 = 0;
+    double dWd = 0, lognorm = 0, psf_sum = 0;
+    float *d_psf = nullptr, *d_pu = nullptr, *d_pv = nullptr;
+    float4 *d_wpack = nullptr;
+    float *d_kc = nullptr;
+    int kc_cap = 0;
+    float *d_gscr = nullptr;
+    float *d_stage_p = nullptr;
+    double *d_stage_o = nullptr;
+    int stage_cap = 0;
+    float *d_p1 = nullptr, *d_kc1 = nullptr, *d_unb = nullptr, *d_blur = nullptr,
+          *d_img = nullptr;
+    double *d_res = nullptr, *d_out1 = nullptr;
+    bool smem_img = false;
+    int grid_cap = 0;
+    size_t smem_bytes = 0;
+    cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
+    bool prof_on = false, prof_recorded = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Coordinate of the grid centre, x0 + (nx - 1) dpix / 2: subpixel J sits at
+// centre + (J - (nx s - 1)/2) dpix/s.
+void grid_centre(const tll_lens *L, double *xc, double *yc)
+{
+    *xc = (double)L->x0 + 0.5 * (L->nx - 1) * (double)L->dpix;
+    *yc = (double)L->y0 + 0.5 * (L->ny - 1) * (double)L->dpix;
+}
+
+LensDev lens_dev(const tll_lens *L)
+{
+    LensDev d;
+    d.nx = L->nx; d.ny = L->ny; d.npix = L->npix; d.sub = L->sub;
+    d.K = L->K; d.h = (L->K - 1) / 2; d.sep = L->sep; d.mode = L->mode;
+    {
+        const double st = (double)L->dpix / L->sub;
+        d.dsh = (float)st;
+        d.dsl = (float)(st - (double)d.dsh);
+    }
+    double xc, yc;
+    grid_centre(L, &xc, &yc);
+    d.XC = (float)xc;
+    d.YC = (float)yc;
+    d.JCX = 0.5f * (float)(L->nx * L->sub - 1);
+    d.JCY = 0.5f * (float)(L->ny * L->sub - 1);
+    d.inv_s2 = 1.0f / (float)(L->sub * L->sub);
+    d.psf = L->d_psf; d.pu = L->d_pu; d.pv = L->d_pv; d.wpack = L->d_wpack;
+    d.dWd = L->dWd; d.lognorm = L->lognorm;
+    return d;
+}
+
+template <bool SMEM_IMG, bool WRITE>
+int launch_main(const tll_lens *L, const RunArgs &R, int grid, cudaStream_t st)
+{
+    k_loglike<SMEM_IMG, WRITE><<<grid, kThreads, L->smem_bytes, st>>>(lens_dev(L), R);
+    CUDA_TRY(cudaGetLastError());
+    return TLL_OK;
+}
+
+int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t st,
+              bool write, float *kc)
+{
+    const bool prof = L->prof_on && !write;
+    if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
+    double xc, yc;
+    grid_centre(L, &xc, &yc);
+    k_prologue<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, xc, yc);
+    CUDA_TRY(cudaGetLastError());
+    if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
+    RunArgs R;
+    R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr;
+    R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
+    const int grid = std::min(B, L->grid_cap);
+    if (write) {
+        return L->smem_img ? launch_main<true, true>(L, R, 1, st)
+                           : launch_main<false, true>(L, R, 1, st);
+    }
+    const int rc = L->smem_img ? launch_main<true, false>(L, R, grid, st)
+                               : launch_main<false, false>(L, R, grid, st);
+    if (rc == TLL_OK && prof) {
+        CUDA_TRY(cudaEventRecord(L->prof_ev[2], st));
+        L->prof_recorded = true;
+    }
+    return rc;
+}
+
+int ensure_kc(tll_lens *L, int B)
+{
+    if (B <= L->kc_cap) return TLL_OK;
+    int cap = std::max(B, 2 * L->kc_cap);
+    float *p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, (size_t)cap * NCONST * sizeof(float)));
+    if (L->d_kc) cudaFree(L->d_kc);
+    L->d_kc = p;
+    L->kc_cap = cap;
+    return TLL_OK;
+}
+
+int configure(tll_lens *L)
+{
+    int nsm = 0, optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, L->dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, L->dev));
+    const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
+    const size_t fixed = kRedBytes + (size_t)((psf_floats + 3) & ~3) * sizeof(float);
+    const size_t img = (size_t)2 * L->npix * sizeof(float);
+    L->smem_img = (fixed + img <= (size_t)optin) && (L->nx <= 32 * kHMax);
+    L->smem_bytes = L->smem_img ? fixed + img : fixed;
+    int per_sm = 0;
+    // allow every instantiation the device's full opt-in shared memory once,
+    // so lenses of different sizes can share the kernels
+    CUDA_TRY(cudaFuncSetAttribute(k_loglike<true, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(cudaFuncSetAttribute(k_loglike<true, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    if (L->smem_img) {
+        auto kern = k_loglike<true, false>;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
+                                                               L->smem_bytes));
+    } else {
+        auto kern = k_loglike<false, false>;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
+                                                               L->smem_bytes));
+    }
+    if (per_sm < 1) return fail(TLL_ECUDA, "k_loglike cannot be resident on an SM");
+    L->grid_cap = nsm * per_sm;
+    if (!L->smem_img) {
+        const size_t n = (size_t)L->grid_cap * 4 * L->npix;
+        CUDA_TRY(cudaMalloc(&L->d_gscr, n * sizeof(float)));
+    }
+    return TLL_OK;
+}
+
+void free_lens(tll_lens *L)
+{
+    if (!L) return;
+    void *ptrs[] = {L->d_psf, L->d_pu, L->d_pv, L->d_wpack, L->d_kc, L->d_gscr,
+                    L->d_stage_p, L->d_stage_o, L->d_p1, L->d_kc1, L->d_unb,
+                    L->d_blur, L->d_img, L->d_res, L->d_out1};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t ev : L->prof_ev)
+        if (ev) cudaEventDestroy(ev);
+    delete L;
+}
+
+// Run one vector through the WRITE kernel; outputs stay on the device.
+int run_one(tll_lens *L, const float *params_host)
+{
+    if (!params_host) return fail(TLL_EINVAL, "params is NULL");
+    CUDA_TRY(cudaMemcpy(L->d_p1, params_host, NPAR * sizeof(float), cudaMemcpyHostToDevice));
+    int rc = run_batch(L, L->d_p1, 1, L->d_out1, 0, true, L->d_kc1);
+    if (rc) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());
+    float valid = 0.0f;
+    CUDA_TRY(cudaMemcpy(&valid, L->d_kc1 + K_VALID, sizeof(float), cudaMemcpyDeviceToHost));
+    if (valid == 0.0f) return fail(TLL_EINVAL, "invalid parameter vector");
+    return TLL_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *tll_last_error(void) { return g_err; }
+
+int tll_version(void) { return 100; }
+
+int tll_create_lens(const float *image, const float *noise, const float *psf,
+                    int psf_size, const tll_grid_t *grid, int flags, tll_lens **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(TLL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!image || !noise || !psf || !grid) return fail(TLL_EINVAL, "NULL input pointer");
+    const tll_grid_t g = *grid;
+    if (g.nx < 1 || g.ny < 1 || g.nx > TLL_MAX_SIDE || g.ny > TLL_MAX_SIDE)
+        return fail(TLL_EINVAL, "image size %d x %d out of range", g.ny, g.nx);
+    if (g.sub < 1 || g.sub > TLL_MAX_SUB)
+        return fail(TLL_EINVAL, "supersampling %d out of range", g.sub);
+    if (!(g.pixel_scale > 0.0f) || !isfinite(g.pixel_scale) || !isfinite(g.x0) ||
+        !isfinite(g.y0))
+        return fail(TLL_EINVAL, "bad grid geometry");
+    if (psf_size < 1 || psf_size > TLL_MAX_PSF || psf_size % 2 == 0)
+        return fail(TLL_EINVAL, "PSF side %d must be odd and <= %d", psf_size, TLL_MAX_PSF);
+    const int mode = flags & 0xff;
+    if (mode != TLL_AMP_LINEAR && mode != TLL_AMP_FIXED)
+        return fail(TLL_EINVAL, "unknown amplitude mode %d", mode);
+    const int K = psf_size, npix = g.nx * g.ny;
+    double psum = 0.0;
+    for (int t = 0; t < K * K; ++t) {
+        if (!isfinite(psf[t])) return fail(TLL_EINVAL, "non-finite PSF entry");
+        psum += psf[t];
+    }
+    if (!(psum > 0.0)) return fail(TLL_EINVAL, "PSF sum must be > 0");
+
+    int dev = 0;
+    {
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || ndev < 1)
+            return fail(TLL_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+        CUDA_TRY(cudaGetDevice(&dev));
+    }
+    tll_lens *L = new (std::nothrow) tll_lens;
+    if (!L) return fail(TLL_ENOMEM, "host allocation failed");
+    L->dev = dev;
+    L->nx = g.nx; L->ny = g.ny; L->npix = npix; L->sub = g.sub; L->K = K;
+    L->flags = flags; L->mode = mode;
+    L->dpix = g.pixel_scale; L->x0 = g.x0; L->y0 = g.y0; L->psf_sum = psum;
+
+    // PSF, unit sum (Eq. 3); separable if it is an outer product to rounding
+    std::vector<float> pn(K * K), pu(K), pv(K);
+    for (int t = 0; t < K * K; ++t) pn[t] = (float)((double)psf[t] / psum);
+    int sep = 0;
+    if (!(flags & TLL_FLAG_DIRECT_CONV)) {
+        int r0 = 0, c0 = 0;
+        float best = -1.0f;
+        for (int r = 0; r < K; ++r)
+            for (int c = 0; c < K; ++c)
+                if (fabsf(pn[r * K + c]) > best) { best = fabsf(pn[r * K + c]); r0 = r; c0 = c; }
+        if (best > 0.0f) {
+            sep = 1;
+            std::vector<double> u(K), v(K);
+            for (int r = 0; r < K; ++r) u[r] = pn[r * K + c0];
+            for (int c = 0; c < K; ++c) v[c] = (double)pn[r0 * K + c] / (double)pn[r0 * K + c0];
+            for (int r = 0; r < K && sep; ++r)
+                for (int c = 0; c < K; ++c) {
+                    const double kv = pn[r * K + c], uv = u[r] * v[c];
+                    if (fabs(kv - uv) > 4.8e-7 * fabs(kv) + 1e-37) { sep = 0; break; }
+                }
+            for (int r = 0; r < K; ++r) pu[r] = (float)u[r];
+            for (int c = 0; c < K; ++c) pv[c] = (float)v[c];
+        }
+    }
+    L->sep = sep;
+
+    // weights (Eq. 5): w = 1/sigma^2 as a float pair, w*d likewise; masked
+    // pixels get 0.  dWd = sum w d^2, lognorm = -sum log(2 pi sigma^2)/2.
+    std::vector<float4> wp(npix);
+    double dWd = 0.0, lognorm = 0.0;
+    for (int t = 0; t < npix; ++t) {
+        const double s = noise[t], d = image[t];
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (isfinite(s) && s > 0.0 && isfinite(d)) {
+            const double w = 1.0 / (s * s), wd = w * d;
+            q.x = (float)w; q.y = (float)(w - (double)q.x);
+            q.z = (float)wd; q.w = (float)(wd - (double)q.z);
+            dWd += wd * d;
+            lognorm -= 0.5 * log(2.0 * M_PI * s * s);
+        }
+        wp[t] = q;
+    }
+    L->dWd = dWd;
+    L->lognorm = lognorm;
+
+    int rc = TLL_OK;
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? TLL_ENOMEM : TLL_ECUDA,
+                        "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        return TLL_OK;
+    };
+    if ((rc = alloc((void **)&L->d_psf, K * K * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_pu, K * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_pv, K * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_wpack, npix * sizeof(float4))) ||
+        (rc = alloc((void **)&L->d_p1, NPAR * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_kc1, NCONST * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_unb, 2 * npix * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_blur, 2 * npix * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_img, npix * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_res, 8 * sizeof(double))) ||
+        (rc = alloc((void **)&L->d_out1, sizeof(double)))) {
+        free_lens(L);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(L->d_psf, pn.data(), K * K * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->d_pu, pu.data(), K * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->d_pv, pv.data(), K * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->d_wpack, wp.data(), npix * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_lens(L);
+        return fail(TLL_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    if ((rc = configure(L)) || (rc = ensure_kc(L, 1024))) {
+        free_lens(L);
+        return rc;
+    }
+    *out = L;
+    return TLL_OK;
+}
+
+void tll_destroy_lens(tll_lens *L)
+{
+    if (!L) return;
+    DeviceGuard gd(L->dev);
+    free_lens(L);
+}
+
+int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
+                  int *flags, int *separable)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (nx) *nx = L->nx;
+    if (ny) *ny = L->ny;
+    if (sub) *sub = L->sub;
+    if (psf_size) *psf_size = L->K;
+    if (flags) *flags = L->flags;
+    if (separable) *separable = L->sep;
+    return TLL_OK;
+}
+
+int tll_profile_enable(tll_lens *L, int on)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    DeviceGuard gd(L->dev);
+    if (on && !L->prof_ev[0])
+        for (auto &ev : L->prof_ev) CUDA_TRY(cudaEventCreate(&ev));
+    L->prof_on = on != 0;
+    L->prof_recorded = false;
+    return TLL_OK;
+}
+
+int tll_profile_last(tll_lens *L, float *prologue_ms, float *main_ms)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (!L->prof_on || !L->prof_recorded)
+        return fail(TLL_EINVAL, "profiling not enabled or no batch recorded");
+    DeviceGuard gd(L->dev);
+    CUDA_TRY(cudaEventSynchronize(L->prof_ev[2]));
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, L->prof_ev[0], L->prof_ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, L->prof_ev[1], L->prof_ev[2]));
+    if (prologue_ms) *prologue_ms = a;
+    if (main_ms) *main_ms = b;
+    return TLL_OK;
+}
+
+int tll_loglike_batch(tll_lens *L, const float *params, int B, double *out, void *stream)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (B < 0) return fail(TLL_EINVAL, "negative batch size");
+    if (B == 0) return TLL_OK;
+    if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
+    DeviceGuard gd(L->dev);
+    int rc = ensure_kc(L, B);
+    if (rc) return rc;
+    return run_batch(L, params, B, out, (cudaStream_t)stream, false, L->d_kc);
+}
+
+int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
+                           void *stream)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (B < 0) return fail(TLL_EINVAL, "negative batch size");
+    if (B == 0) return TLL_OK;
+    if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
+    DeviceGuard gd(L->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B > L->stage_cap) {
+        const int cap = std::max(B, 2 * L->stage_cap);
+        float *p = nullptr;
+        double *o = nullptr;
+        CUDA_TRY(cudaMalloc(&p, (size_t)cap * NPAR * sizeof(float)));
+        cudaError_t e = cudaMalloc(&o, (size_t)cap * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return fail(TLL_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+        }
+        if (L->d_stage_p) cudaFree(L->d_stage_p);
+        if (L->d_stage_o) cudaFree(L->d_stage_o);
+        L->d_stage_p = p;
+        L->d_stage_o = o;
+        L->stage_cap = cap;
+    }
+    int rc = ensure_kc(L, B);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(L->d_stage_p, params, (size_t)B * NPAR * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    rc = run_batch(L, L->d_stage_p, B, L->d_stage_o, st, false, L->d_kc);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out, L->d_stage_o, (size_t)B * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TLL_OK;
+}
+
+int tll_model_columns(tll_lens *L, const float *params, float *lens_out, float *src_out,
+                      int blurred)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (!lens_out || !src_out) return fail(TLL_EINVAL, "NULL output");
+    DeviceGuard gd(L->dev);
+    int rc = run_one(L, params);
+    if (rc) return rc;
+    const float *src = blurred ? L->d_blur : L->d_unb;
+    const size_t n = (size_t)L->npix * sizeof(float);
+    CUDA_TRY(cudaMemcpy(lens_out, src, n, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(src_out, src + L->npix, n, cudaMemcpyDeviceToHost));
+    return TLL_OK;
+}
+
+int tll_model_image(tll_lens *L, const float *params, float *image_out, float *amps_out,
+                    double *loglike_out)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (!image_out) return fail(TLL_EINVAL, "NULL output");
+    DeviceGuard gd(L->dev);
+    int rc = run_one(L, params);
+    if (rc) return rc;
+    k_combine<<<std::max(1, std::min(1024, (L->npix + 255) / 256)), 256>>>(
+        L->d_blur, L->d_res, L->npix, L->d_img);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpy(image_out, L->d_img, (size_t)L->npix * sizeof(float),
+                        cudaMemcpyDeviceToHost));
+    double res[8];
+    CUDA_TRY(cudaMemcpy(res, L->d_res, sizeof res, cudaMemcpyDeviceToHost));
+    if (amps_out) {
+        amps_out[0] = (float)res[5];
+        amps_out[1] = (float)res[6];
+    }
+    if (loglike_out) *loglike_out = res[7];
+    return TLL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Python binding of libtll.so (ctypes).  Argument marshalling only: every
+step of the likelihood runs in the library's CUDA kernels.  There is no
+fallback -- if the library is missing or no GPU is usable, calls raise.
+
+Device tensors are torch tensors (torch provides memory and streams);
+host arrays are numpy arrays or CPU tensors (pinned ones copy faster).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtll.so")
+
+NPARAM = 21
+AMP_LINEAR = 0
+AMP_FIXED = 1
+FLAG_DIRECT_CONV = 0x100
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(6)
+_CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY"}
+
+# Every entry point include/tll.h declares (checked by the ABI test).
+SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
+           "tll_model_image", "tll_model_columns", "tll_lens_info",
+           "tll_profile_enable", "tll_profile_last",
+           "tll_destroy_lens", "tll_last_error", "tll_version")
+
+
+class TLLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("pixel_scale", ctypes.c_float), ("sub", ctypes.c_int),
+                ("x0", ctypes.c_float), ("y0", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtll.so (built in-tree by paper_2503_08586_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with "
+                           "`python -m paper_2503_08586_gb300.build`")
+    lib = ctypes.CDLL(p)
+    vp, i, fp, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+    lib.tll_create_lens.argtypes = [fp, fp, fp, i, ctypes.POINTER(Grid), i,
+                                    ctypes.POINTER(vp)]
+    lib.tll_create_lens.restype = i
+    lib.tll_loglike_batch.argtypes = [vp, fp, i, dp, vp]
+    lib.tll_loglike_batch.restype = i
+    lib.tll_loglike_batch_host.argtypes = [vp, fp, i, dp, vp]
+    lib.tll_loglike_batch_host.restype = i
+    lib.tll_model_image.argtypes = [vp, fp, fp, fp, dp]
+    lib.tll_model_image.restype = i
+    lib.tll_model_columns.argtypes = [vp, fp, fp, fp, i]
+    lib.tll_model_columns.restype = i
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.tll_lens_info.argtypes = [vp, ip, ip, ip, ip, ip, ip]
+    lib.tll_lens_info.restype = i
+    lib.tll_profile_enable.argtypes = [vp, i]
+    lib.tll_profile_enable.restype = i
+    lib.tll_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_float)]
+    lib.tll_profile_last.restype = i
+    lib.tll_destroy_lens.argtypes = [vp]
+    lib.tll_destroy_lens.restype = None
+    lib.tll_last_error.argtypes = []
+    lib.tll_last_error.restype = ctypes.c_char_p
+    lib.tll_version.argtypes = []
+    lib.tll_version.restype = i
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise TLLError(rc, load().tll_last_error().decode(errors="replace"))
+
+
+def _host_ptr(a, dtype):
+    """(pointer, keep-alive) for a contiguous host array of dtype."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                raise ValueError("expected a host tensor")
+            want = torch.float32 if dtype == np.float32 else torch.float64
+            if a.dtype != want or not a.is_contiguous():
+                raise ValueError(f"expected a contiguous {want} host tensor")
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Lens:
+    """One observed lens resident on the current CUDA device."""
+
+    def __init__(self, image, noise, psf, pixel_scale: float, sub: int,
+                 x0: float | None = None, y0: float | None = None,
+                 mode: int = AMP_LINEAR, direct_conv: bool = False):
+        lib = load()
+        img = np.ascontiguousarray(image, dtype=np.float32)
+        nse = np.ascontiguousarray(noise, dtype=np.float32)
+        k = np.ascontiguousarray(psf, dtype=np.float32)
+        if img.ndim != 2 or nse.shape != img.shape or k.ndim != 2 \
+                or k.shape[0] != k.shape[1]:
+            raise ValueError("image/noise must be [ny, nx], psf square")
+        ny, nx = img.shape
+        if x0 is None:
+            x0 = -(nx - 1) * pixel_scale / 2.0
+        if y0 is None:
+            y0 = -(ny - 1) * pixel_scale / 2.0
+        g = Grid(nx, ny, pixel_scale, sub, x0, y0)
+        h = ctypes.c_void_p()
+        flags = mode | (FLAG_DIRECT_CONV if direct_conv else 0)
+        _check(lib.tll_create_lens(img.ctypes.data, nse.ctypes.data,
+                                   k.ctypes.data, k.shape[0], ctypes.byref(g),
+                                   flags, ctypes.byref(h)))
+        self._h = h
+        self.ny, self.nx, self.sub, self.psf_size = ny, nx, sub, k.shape[0]
+        self.mode = mode
+        self.pixel_scale, self.x0, self.y0 = pixel_scale, x0, y0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        v = [ctypes.c_int() for _ in range(6)]
+        _check(load().tll_lens_info(self._h, *[ctypes.byref(x) for x in v]))
+        keys = ("nx", "ny", "sub", "psf_size", "flags", "separable")
+        return {k: x.value for k, x in zip(keys, v)}
+
+    # -- device batch
+    def loglike_batch(self, params, out=None, stream=None):
+        """params: CUDA float32 tensor [B, 21]; returns CUDA float64 [B]
+        (asynchronous on `stream`, default torch's current stream)."""
+        import torch
+        if not (params.is_cuda and params.dtype == torch.float32
+                and params.dim() == 2 and params.shape[1] == NPARAM
+                and params.is_contiguous()):
+            raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+        B = params.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device=params.device)
+        elif not (out.is_cuda and out.dtype == torch.float64
+                  and out.numel() >= B and out.is_contiguous()):
+            raise ValueError("out must be a contiguous CUDA float64 [B]")
+        _check(load().tll_loglike_batch(self._h, params.data_ptr(), B,
+                                        out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    # -- host batch (copies inside the call)
+    def loglike_batch_host(self, params, out=None, stream=None):
+        """params: host float32 [B, 21] (numpy or CPU tensor, pinned is
+        best); returns host float64 [B] (numpy unless `out` is given)."""
+        p, keep = _host_ptr(params, np.float32)
+        B = int(np.prod(keep.shape)) // NPARAM
+        if out is None:
+            out = np.empty(B, dtype=np.float64)
+        o, okeep = _host_ptr(out, np.float64)
+        if okeep is not out:
+            raise ValueError("out must be a contiguous float64 host array")
+        _check(load().tll_loglike_batch_host(self._h, p, B, o,
+                                             _stream_handle(stream)))
+        return out
+
+    # -- single vector
+    def model_image(self, params):
+        """(blurred model image [ny, nx] float32, amplitudes (2,), log L)."""
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(NPARAM)
+        img = np.empty((self.ny, self.nx), dtype=np.float32)
+        amps = np.empty(2, dtype=np.float32)
+        ll = ctypes.c_double()
+        _check(load().tll_model_image(self._h, p.ctypes.data, img.ctypes.data,
+                                      amps.ctypes.data, ctypes.byref(ll)))
+        return img, amps, ll.value
+
+    def model_columns(self, params, blurred: bool = True):
+        """Unit-amplitude (lens, source) columns [ny, nx] float32."""
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(NPARAM)
+        a = np.empty((self.ny, self.nx), dtype=np.float32)
+        b = np.empty((self.ny, self.nx), dtype=np.float32)
+        _check(load().tll_model_columns(self._h, p.ctypes.data, a.ctypes.data,
+                                        b.ctypes.data, 1 if blurred else 0))
+        return a, b
+
+    # -- profiling hook
+    def profile(self, on: bool = True):
+        """Record events around the two launches of each batch call."""
+        _check(load().tll_profile_enable(self._h, 1 if on else 0))
+
+    def profile_last(self):
+        """(prologue ms, main-kernel ms) of the last batch call (waits)."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(load().tll_profile_last(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().tll_destroy_lens(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def columns_renderer(pixel_scale, sub, psf, ny, nx):
+    """Render function for the input generator backed by this library
+    (blurred unit columns of the truth vector)."""
+    dummy = np.zeros((ny, nx), dtype=np.float32)
+    lens = Lens(dummy, np.ones((ny, nx), dtype=np.float32), psf, pixel_scale,
+                sub)
+
+    def render(params):
+        return lens.model_columns(params, blurred=True)
+
+    render.lens = lens
+    return render

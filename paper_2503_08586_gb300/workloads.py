@@ -180,9 +180,16 @@ class SynthLens:
     extra: dict = field(default_factory=dict)
 
 
+def f32(v: float) -> float:
+    """The float32 value nearest v, as a Python float (the library's grid
+    geometry is float32, so inputs are made exactly representable)."""
+    return float(np.float32(v))
+
+
 def centred_origin(n: int, pixel_scale: float) -> float:
-    """Coordinate of pixel 0's centre for an image centred on the origin."""
-    return -(n - 1) * pixel_scale / 2.0
+    """Coordinate of pixel 0's centre for an image centred on the origin
+    (float32-representable)."""
+    return f32(-(n - 1) * f32(pixel_scale) / 2.0)
 
 
 def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
@@ -211,7 +218,7 @@ def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
         var = sky_sigma ** 2 + np.maximum(model, 0.0) / g
     sigma = np.sqrt(var)
     data = model + rng.normal(size=model.shape) * sigma
-    return SynthLens(ny, nx, pixel_scale, sub, psf.astype(np.float32),
+    return SynthLens(ny, nx, f32(pixel_scale), sub, psf.astype(np.float32),
                      data.astype(np.float32), sigma.astype(np.float32), truth,
                      centred_origin(nx, pixel_scale),
                      centred_origin(ny, pixel_scale))
@@ -223,7 +230,7 @@ def workload(name: str, render_factory, batch: int | None = None):
     spec = WORKLOADS[name]
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + spec.seed_offset))
     psf = make_psf(spec)
-    render = render_factory(spec.pixel_scale, spec.sub, psf, spec.ny, spec.nx)
+    render = render_factory(f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx)
     lens = synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf,
                       render, spec.noise_kind)
     B = spec.batch if batch is None else batch
@@ -252,7 +259,7 @@ def ragged_workload(n_lenses: int, per_lens: int, render_factory,
     out = []
     for side, k in specs:
         psf = gaussian_psf(k, k / 7.0)
-        render = render_factory(pixel_scale, sub, psf, side, side)
+        render = render_factory(f32(pixel_scale), sub, psf, side, side)
         lens = synth_lens(rng, side, side, pixel_scale, sub, psf, render,
                           "sky+poisson")
         params = shrinking_draws(rng, lens.truth, per_lens)

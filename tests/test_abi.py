@@ -1,0 +1,81 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry
+point include/tll.h declares; argument errors come back as codes.  No
+compute call is made here (CPU-only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2503_08586_gb300 import build, tll
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tll_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return tll.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = _declared()
+    assert decl, "no declarations found"
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert decl == set(tll.SYMBOLS) | (decl - set(tll.SYMBOLS))
+    assert set(tll.SYMBOLS) <= decl
+
+
+def test_version_and_error_string(lib):
+    assert lib.tll_version() >= 100
+    assert isinstance(lib.tll_last_error(), bytes)
+
+
+def test_argument_validation_without_gpu(lib):
+    g = tll.Grid(4, 4, 0.1, 2, 0.0, 0.0)
+    h = ctypes.c_void_p()
+    img = np.zeros(16, np.float32)
+    psf = np.ones(9, np.float32)
+    # NULL pointers, even PSF, bad supersampling, zero PSF sum, bad mode
+    assert lib.tll_create_lens(None, img.ctypes.data, psf.ctypes.data, 3,
+                               ctypes.byref(g), 0, ctypes.byref(h)) == tll.EINVAL
+    assert lib.tll_create_lens(img.ctypes.data, img.ctypes.data,
+                               psf.ctypes.data, 2, ctypes.byref(g), 0,
+                               ctypes.byref(h)) == tll.EINVAL
+    bad = tll.Grid(4, 4, 0.1, 0, 0.0, 0.0)
+    assert lib.tll_create_lens(img.ctypes.data, img.ctypes.data,
+                               psf.ctypes.data, 3, ctypes.byref(bad), 0,
+                               ctypes.byref(h)) == tll.EINVAL
+    z = np.zeros(9, np.float32)
+    assert lib.tll_create_lens(img.ctypes.data, img.ctypes.data, z.ctypes.data,
+                               3, ctypes.byref(g), 0, ctypes.byref(h)) == tll.EINVAL
+    assert lib.tll_create_lens(img.ctypes.data, img.ctypes.data,
+                               psf.ctypes.data, 3, ctypes.byref(g), 7,
+                               ctypes.byref(h)) == tll.EINVAL
+    assert b"mode" in lib.tll_last_error()
+    # NULL lens
+    assert lib.tll_loglike_batch(None, None, 4, None, None) == tll.EINVAL
+    assert lib.tll_model_image(None, None, None, None, None) == tll.EINVAL
+    lib.tll_destroy_lens(None)
+
+
+def test_no_silent_cpu_fallback(lib):
+    """Without a usable GPU the library refuses instead of computing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tll.TLLError) as ei:
+        tll.Lens(np.zeros((4, 4)), np.ones((4, 4)), np.ones((3, 3)), 0.1, 2)
+    assert ei.value.code == tll.ECUDA

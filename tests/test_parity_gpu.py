@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 forward model, FP64 likelihood):
+  model pixels  |m_gpu - m_ora| <= 1e-5 |m_ora| + 1e-7 max|m_ora|, per column.
+                The floor covers Sersic tails, where the FP32 exponent's
+                rounding (|argument| * 2^-24) exceeds 1e-5 relative.
+  log L         vectors that fit the data at the noise level
+                (chi^2 <= 2 N_unmasked): |dlogL| <= 1e-3.
+                Every vector: |dlogL| <= max(1e-3, EPS_M sqrt(chi2)
+                (sqrt(dWd) + sqrt(chi2))) with EPS_M = 1e-6.  This is the
+                first-order effect of a relative model error <= EPS_M on
+                every pixel: dchi2 = 2 sum w (m - d) dm <= 2 EPS_M
+                sqrt(chi2) sqrt(sum w m^2) (Cauchy-Schwarz) and
+                sqrt(sum w m^2) <= sqrt(dWd) + sqrt(chi2).  chi2 and dWd
+                are the oracle's.  EPS_M = 1e-6 (about 8 float ulps) is ten
+                times tighter than the per-pixel gate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2503_08586_gb300 import build, tll
+from paper_2503_08586_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PIX_REL, PIX_FLOOR = 1e-5, 1e-7
+LL_ABS, EPS_M = 1e-3, 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    tll.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _pix_ok(gpu, ora):
+    ora = np.asarray(ora, np.float64)
+    gpu = np.asarray(gpu, np.float64)
+    tol = PIX_REL * np.abs(ora) + PIX_FLOOR * np.abs(ora).max()
+    err = np.abs(gpu - ora)
+    return bool(np.all(err <= tol)), float((err / np.maximum(tol, 1e-300)).max())
+
+
+def _lens_consts(lens):
+    """(dWd, lognorm, N_unmasked) with the masking rule of the likelihood."""
+    d = np.asarray(lens.data, np.float64)
+    s = np.asarray(lens.noise, np.float64)
+    ok = np.isfinite(s) & (s > 0) & np.isfinite(d)
+    w = np.where(ok, 1.0 / np.where(ok, s, 1.0) ** 2, 0.0)
+    dd = np.where(ok, d, 0.0)
+    return (float(np.sum(w * dd * dd)),
+            float(-0.5 * np.sum(np.log(2 * math.pi * s[ok] ** 2))), int(ok.sum()))
+
+
+def _ll_ok(gpu, ora, lens):
+    """Check log L against the gates above; returns the |dlogL| array."""
+    gpu, ora = np.asarray(gpu), np.asarray(ora)
+    assert np.array_equal(np.isneginf(gpu), np.isneginf(ora)), "validity differs"
+    fin = ~np.isneginf(ora)
+    assert np.all(np.isfinite(gpu[fin])), "non-finite log L"
+    dWd, lognorm, nun = _lens_consts(lens)
+    chi2 = np.maximum(-2.0 * (ora[fin] - lognorm), 0.0)
+    d = np.abs(gpu[fin] - ora[fin])
+    tol = np.maximum(LL_ABS, EPS_M * np.sqrt(chi2) * (np.sqrt(dWd) + np.sqrt(chi2)))
+    near = chi2 <= 2.0 * nun
+    tol = np.where(near, LL_ABS, tol)
+    k = int(np.argmax(d / tol))
+    assert np.all(d <= tol), (
+        f"|dlogL| {d[k]:.3e} > tol {tol[k]:.3e} (chi2 {chi2[k]:.4g}, near {near[k]}); "
+        f"max |dlogL| {d.max():.3e}, max rel {(d / np.abs(ora[fin])).max():.2e}")
+    return d
+
+
+def _pair(sl: W.SynthLens, mode=0, direct=False):
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0,
+                 mode=mode, direct_conv=direct)
+    o = oracle.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+    return g, o
+
+
+def _gpu_ll(g, params):
+    p = torch.from_numpy(np.ascontiguousarray(params, np.float32)).cuda()
+    out = g.loglike_batch(p)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _workload(name, batch=None):
+    return W.workload(name, oracle.columns_renderer, batch=batch)
+
+
+def _synth(ny, nx, dpix, sub, psf, seed, noise_kind="sky+poisson"):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    render = oracle.columns_renderer(dpix, sub, psf, ny, nx)
+    return W.synth_lens(rng, ny, nx, dpix, sub, psf, render, noise_kind), rng
+
+
+# ------------------------------------------------------------ columns
+def test_columns_parity_plain64():
+    lens, params = _workload("plain64", batch=8)
+    g, o = _pair(lens)
+    vecs = np.concatenate([lens.truth[None], params[:7]])
+    for p in vecs:
+        il, is_ = o.unblurred(p.astype(np.float64))
+        gl, gs = g.model_columns(p, blurred=False)
+        for gg, oo, nm in ((gl, il, "lens"), (gs, is_, "src")):
+            ok, worst = _pix_ok(gg, oo)
+            assert ok, f"unblurred {nm}: worst error / tol = {worst:.3f}"
+        _, ml, ms, _, _ = o.model(p.astype(np.float64), mode=1)
+        bl, bs = g.model_columns(p, blurred=True)
+        for gg, oo, nm in ((bl, ml, "lens"), (bs, ms, "src")):
+            ok, worst = _pix_ok(gg, oo)
+            assert ok, f"blurred {nm}: worst error / tol = {worst:.3f}"
+
+
+def test_model_image_and_amplitudes():
+    lens, params = _workload("plain64", batch=4)
+    g, o = _pair(lens)
+    for p in np.concatenate([lens.truth[None], params]):
+        ll_o, _, _, mod_o, amps_o = o.model(p.astype(np.float64), mode=0)
+        img, amps, ll = g.model_image(p)
+        ok, worst = _pix_ok(img, mod_o)
+        assert ok, f"model image worst error / tol {worst:.3f}"
+        assert np.allclose(amps, amps_o, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(amps_o).max()))
+        _ll_ok(np.array([ll]), np.array([ll_o]), lens)
+
+
+# ------------------------------------------------------------- log L
+def test_loglike_plain64_full_batch():
+    lens, params = _workload("plain64")
+    g, o = _pair(lens)
+    P = np.concatenate([lens.truth[None], params])
+    ref = o.loglike_batch(P.astype(np.float64))
+    got = _gpu_ll(g, P)
+    d = _ll_ok(got, ref, lens)
+    assert d[0] <= LL_ABS
+
+
+def test_near_truth_strict():
+    """Vectors around the truth (a converged sampler's region): the last
+    draws of a shrinking Gaussian, |dlogL| <= 1e-3 where they fit at the
+    noise level."""
+    lens, _ = _workload("plain64", batch=1)
+    g, o = _pair(lens)
+    rng = np.random.Generator(np.random.PCG64(77))
+    P = W.shrinking_draws(rng, lens.truth, 256, lo_frac=1e-4)[192:]
+    ref = o.loglike_batch(P.astype(np.float64))
+    got = _gpu_ll(g, P)
+    _, lognorm, nun = _lens_consts(lens)
+    near = -2.0 * (ref - lognorm) <= 2.0 * nun
+    assert near.sum() >= 16
+    _ll_ok(got, ref, lens)
+
+
+SHAPES = [
+    # ny, nx, dpix, sub, psf (kind, size), mode, direct
+    (37, 53, 0.06, 3, ("gauss", 7), 0, False),
+    (37, 53, 0.06, 3, ("gauss", 7), 0, True),
+    (29, 41, 0.07, 2, ("moffat", 9), 1, False),
+    (1, 1, 0.1, 1, ("gauss", 1), 0, False),
+    (3, 2, 0.2, 4, ("gauss", 5), 0, False),
+    (6, 300, 0.03, 1, ("gauss", 5), 0, False),       # nx > 256: global path
+    (180, 170, 0.05, 1, ("moffat", 11), 0, False),   # > shared memory
+    (64, 64, 0.05, 5, ("gauss", 31), 0, False),      # PSF wider than halo
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{s[0]}x{s[1]}s{s[3]}{s[4][0]}{s[4][1]}m{s[5]}{'d' if s[6] else ''}" for s in SHAPES])
+def test_loglike_shapes(shape):
+    ny, nx, dpix, sub, (kind, k), mode, direct = shape
+    psf = W.gaussian_psf(k, 1.7) if kind == "gauss" else W.moffat_psf(k, 2.0, 3.0)
+    lens, rng = _synth(ny, nx, dpix, sub, psf, seed=1000 + ny * 7 + nx)
+    g, o = _pair(lens, mode=mode, direct=direct)
+    info = g.info()
+    if kind == "moffat" or direct:
+        assert info["separable"] == 0
+    elif k > 1:
+        assert info["separable"] == 1
+    P = W.draw_prior(rng, 40)
+    P[:, 7] = lens.truth[7]
+    P[:, 14] = lens.truth[14]
+    P[0] = lens.truth
+    P[5, 1] = 0.9      # |eps| >= 1: invalid
+    P[5, 2] = 0.5
+    P[9, 8] = -0.2     # r_e < 0: invalid
+    P[13, 16] = 11.0   # n > 10: invalid
+    P[17, 3] = np.nan  # non-finite: invalid
+    ref = o.loglike_batch(P.astype(np.float64), mode=mode)
+    got = _gpu_ll(g, P)
+    _ll_ok(got, ref, lens)
+    assert np.isneginf(got[[5, 9, 13, 17]]).all()
+
+
+def test_masked_pixels():
+    psf = W.gaussian_psf(9, 2.0)
+    lens, rng = _synth(40, 44, 0.05, 2, psf, seed=5)
+    lens.noise[3, 4] = 0.0
+    lens.noise[10, 11] = np.inf
+    lens.noise[20, 5] = -1.0
+    lens.data[7, 30] = np.nan
+    lens.noise[30:33, 0:44] = np.nan
+    g, o = _pair(lens)
+    P = np.concatenate([lens.truth[None], W.draw_prior(rng, 15)])
+    _ll_ok(_gpu_ll(g, P), o.loglike_batch(P.astype(np.float64)), lens)
+
+
+def test_fixed_amplitudes():
+    lens, params = _workload("plain64", batch=32)
+    g, o = _pair(lens, mode=tll.AMP_FIXED)
+    P = np.concatenate([lens.truth[None], params])
+    P[1:, 7] = lens.truth[7] * np.linspace(0.5, 1.5, 32)
+    P[1:, 14] = lens.truth[14]
+    ref = o.loglike_batch(P.astype(np.float64), mode=1)
+    _ll_ok(_gpu_ll(g, P), ref, lens)
+
+
+def test_empty_batch_and_host_entry():
+    lens, params = _workload("plain64", batch=64)
+    g, _ = _pair(lens)
+    out = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    g.loglike_batch(torch.empty((0, 21), dtype=torch.float32, device="cuda"), out=out)
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == 7.0).all()
+    dev = _gpu_ll(g, params)
+    pinned = torch.from_numpy(params).pin_memory()
+    host = g.loglike_batch_host(pinned)
+    assert np.array_equal(dev, host)
+    assert np.array_equal(dev, _gpu_ll(g, params))   # deterministic
+
+
+# ----------------------------------------- full sizes, bench launch shape
+def test_csst100_full_batch_sampled():
+    """The benchmark's workload and launch (B = 4096 in one call); 48
+    sampled vectors compared with the oracle one by one, all finite."""
+    lens, params = _workload("csst100")
+    g, o = _pair(lens)
+    got = _gpu_ll(g, params)
+    assert np.all(np.isfinite(got))
+    idx = np.random.default_rng(3).choice(len(params), 48, replace=False)
+    ref = o.loglike_batch(params[idx].astype(np.float64))
+    _ll_ok(got[idx], ref, lens)
+    ll_t = g.model_image(lens.truth)[2]
+    assert abs(ll_t - o.loglike(lens.truth.astype(np.float64))) <= LL_ABS
+
+
+def test_hst200_full_batch_sampled():
+    """200x200, 5x5 subpixels, 31x31 Moffat (direct convolution, images in
+    global scratch), B = 2048 in one call; 6 sampled vectors vs the oracle."""
+    lens, params = _workload("hst200")
+    g, o = _pair(lens)
+    assert g.info()["separable"] == 0
+    got = _gpu_ll(g, params)
+    assert np.all(np.isfinite(got))
+    idx = np.array([0, 1, 777, 1500, 2046, 2047])
+    ref = o.loglike_batch(params[idx].astype(np.float64))
+    _ll_ok(got[idx], ref, lens)

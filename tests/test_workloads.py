@@ -47,7 +47,7 @@ def test_synth_lens_uses_render_and_noise_model():
     lens, params = W.workload("csst100", fac, batch=16)
     assert len(calls) == 1 and params.shape == (16, 21)
     assert lens.data.shape == (100, 100) and lens.noise.min() >= 1.0
-    assert abs(lens.x0 + 99 * 0.074 / 2) < 1e-12
+    assert lens.x0 == W.f32(-99 * W.f32(0.074) / 2) and lens.pixel_scale == W.f32(0.074)
     lens2, _ = W.workload("csst100", fac, batch=16)
     assert np.array_equal(lens.data, lens2.data)
 
