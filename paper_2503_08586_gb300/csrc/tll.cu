@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -38,7 +39,7 @@ using namespace tll;
 
 namespace {
 
-constexpr int kThreads = 512;      // CTA size of k_loglike
+constexpr int kThreads = 1024;     // CTA size of k_loglike (64 registers, 32 warps per SM)
 constexpr int kHMax = 8;           // in-place row pass holds nx <= 32*kHMax
 constexpr int kRedBytes = 32 * 5 * 8;
 
@@ -62,17 +63,26 @@ int fail(int code, const char *fmt, ...)
                         "%s: %s", #expr, cudaGetErrorString(e_));             \
     } while (0)
 
+constexpr int kMaxTaps = 32;   // separable PSF factors carried in the parameter block
+
 struct LensDev {
     int nx, ny, npix, sub, K, h, sep, mode;
-    float XC, YC;     // coordinate of the grid centre (between subpixels)
     float JCX, JCY;   // subpixel index of the grid centre, (n*s - 1)/2
-    float dsh, dsl;   // subpixel step dpix/s as a float pair
     float inv_s2;
+    int W, HL;        // padded layout: row stride, left zero columns
     const float *psf;    // [K*K] unit sum (direct path)
     const float *pu;     // [K] column factor over PSF rows (separable path)
     const float *pv;     // [K] row factor over PSF columns
     const float4 *wpack; // [npix] (w_hi, w_lo, wd_hi, wd_lo)
     double dWd, lognorm;
+    float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
+};
+
+// Image placement in k_loglike.
+enum : int {
+    IMG_GLOBAL = 0,   // per-CTA global scratch slot (L2), generic convolution
+    IMG_SMEM = 1,     // shared memory, unpadded, generic convolution
+    IMG_PADDED = 2    // shared memory with zero halos, convolution compiled per K
 };
 
 struct RunArgs {
@@ -87,11 +97,22 @@ struct RunArgs {
 
 // -------------------------------------------------------------- kernels
 __global__ void k_prologue(const float *__restrict__ params, int B,
-                           float *__restrict__ kc, double X0, double Y0)
+                           float *__restrict__ kc, double XC, double YC, double d,
+                           const double *__restrict__ bn_tab)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B)
-        decode_vector(params + (size_t)b * NPAR, kc + (size_t)b * NCONST, X0, Y0);
+        decode_vector(params + (size_t)b * NPAR, kc + (size_t)b * NCONST, XC, YC, d,
+                      bn_tab);
+}
+
+// One thread per node of the b_n table (run once per device).
+__global__ void k_bn_table(double *__restrict__ tab)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * BN_SEG) return;
+    const int seg = t / BN_SEG, k = t - seg * BN_SEG - 1;
+    tab[t] = sersic_bn_dev(bn_node(seg, k));
 }
 
 // One term of the five weighted sums (Sec. 2.3: A = M^T W M, b = M^T W d)
@@ -159,19 +180,305 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
     *ll_o = -0.5 * chi2 + L.lognorm;
 }
 
-template <bool SMEM_IMG, bool WRITE>
+// --------------------------------------------------------- trace phase
+// Ray-trace + light on the s x s subpixels of every pixel, mean-binned:
+// pixel (i, j) of the lens / source image goes to Il / Is [i*stride + off + j].
+// Subpixel (J, I) of the supersampled grid has exact integer-or-half
+// offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
+// coordinate is an affine function of them (see decode_vector).
+template <int SUB>
+__device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
+                                            float *Il, float *Is, int stride, int off,
+                                            int tid, int nthr)
+{
+    const int sub = SUB > 0 ? SUB : L.sub;
+    const int nx = L.nx;
+    for (int pix = tid; pix < L.npix; pix += nthr) {
+        const int i = pix / nx, j = pix - i * nx;
+        const float fj0 = (float)(j * sub) - L.JCX;
+        const float fi0 = (float)(i * sub) - L.JCY;
+        float accl = 0.0f, accs = 0.0f;
+#pragma unroll 1
+        for (int a = 0; a < sub; ++a) {
+            const RowTerms r = row_terms(v, fi0 + (float)a);
+#pragma unroll
+            for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
+                for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
+                    float il, is;
+                    subpixel(v, r, fj0 + (float)(SUB > 0 ? c : cr), il, is);
+                    accl += il;
+                    accs += is;
+                }
+            }
+        }
+        Il[i * stride + off + j] = accl * L.inv_s2;
+        Is[i * stride + off + j] = accs * L.inv_s2;
+    }
+}
+
+// ------------------------------------------------ generic convolution
+// Any PSF side, images unpadded with row stride nx (in shared memory, with
+// the row pass in place, or in a global scratch slot with separate H
+// buffers).  Separable: H(i,j) = sum_c v[c] I(i, j+h-c), then
+// m(i,j) = sum_r u[r] H(i+h-r, j); direct: m = sum_{r,c} K[r][c] I(i+h-r, j+h-c);
+// zero outside the image (Eq. 3).  Each output pixel's (m_l, m_s) goes to
+// accum_pixel.
+template <bool INPLACE, bool WRITE>
+__device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
+                                             const float *spsf, float *Il, float *Is,
+                                             float *Hl, float *Hs, float *acc, int tid,
+                                             int nthr)
+{
+    const int K = L.K, h = L.h, nx = L.nx, ny = L.ny, npix = L.npix;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    if (L.sep) {
+        const float *su = spsf, *sv = spsf + K;
+        for (int row = warp; row < 2 * ny; row += nwarp) {
+            const float *src = row < ny ? Il + row * nx : Is + (row - ny) * nx;
+            float *dst = row < ny ? Hl + row * nx : Hs + (row - ny) * nx;
+            if (INPLACE) {
+                float o[kHMax];
+#pragma unroll
+                for (int q = 0; q < kHMax; ++q) {
+                    const int j = lane + 32 * q;
+                    float sacc = 0.0f;
+                    if (j < nx) {
+                        const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                        for (int c = c0; c <= c1; ++c) sacc = fmaf(sv[c], src[j + h - c], sacc);
+                    }
+                    o[q] = sacc;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < kHMax; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < nx) dst[j] = o[q];
+                }
+                __syncwarp();
+            } else {
+                for (int j = lane; j < nx; j += 32) {
+                    const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                    float sacc = 0.0f;
+                    for (int c = c0; c <= c1; ++c) sacc = fmaf(sv[c], src[j + h - c], sacc);
+                    dst[j] = sacc;
+                }
+            }
+        }
+        __syncthreads();
+        const int nb = max(1, nthr / nx);
+        const int rb = (ny + nb - 1) / nb;
+        for (int it = tid; it < nx * nb; it += nthr) {
+            const int j = it % nx, band = it / nx;
+            const int r0 = band * rb, r1 = min(ny, r0 + rb);
+            for (int i = r0; i < r1; ++i) {
+                const int q0 = max(0, i + h - ny + 1), q1 = min(K - 1, i + h);
+                float ml = 0.0f, ms = 0.0f;
+                for (int r = q0; r <= q1; ++r) {
+                    const int o = (i + h - r) * nx + j;
+                    ml = fmaf(su[r], Hl[o], ml);
+                    ms = fmaf(su[r], Hs[o], ms);
+                }
+                const int pix = i * nx + j;
+                if (WRITE) {
+                    R.wr_blurred[pix] = ml;
+                    R.wr_blurred[npix + pix] = ms;
+                }
+                accum_pixel(ml, ms, L.wpack[pix], acc);
+            }
+        }
+    } else {
+        for (int pix = tid; pix < npix; pix += nthr) {
+            const int i = pix / nx, j = pix - i * nx;
+            const int r0 = max(0, i + h - ny + 1), r1 = min(K - 1, i + h);
+            const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+            float ml = 0.0f, ms = 0.0f;
+            for (int r = r0; r <= r1; ++r) {
+                const float *kr = spsf + r * K;
+                const int base = (i + h - r) * nx + j + h;
+                float rl = 0.0f, rs = 0.0f;
+                for (int c = c0; c <= c1; ++c) {
+                    rl = fmaf(kr[c], Il[base - c], rl);
+                    rs = fmaf(kr[c], Is[base - c], rs);
+                }
+                ml += rl;
+                ms += rs;
+            }
+            if (WRITE) {
+                R.wr_blurred[pix] = ml;
+                R.wr_blurred[npix + pix] = ms;
+            }
+            accum_pixel(ml, ms, L.wpack[pix], acc);
+        }
+    }
+}
+
+// --------------------------------------------------- padded convolution
+// Separable PSF with compile-time side K on the zero-padded shared-memory
+// layout: image pixel (i, j) at P[(h + i) W + HL + j], HL = h rounded up to
+// a multiple of 4; rows [0, h) and [h + ny, ...) and the columns outside
+// [HL, HL + nx) hold zeros, so no tap needs a bounds check.
+//  Row pass (in place, one warp per row): a lane computes 4 adjacent
+//  outputs from one window of K + 3 values read as float4s.
+//  Column pass: a warp takes 32 adjacent columns x CR rows; a lane reads
+//  CR + K - 1 values of its column and computes CR outputs per channel.
+// Taps come from the parameter block (compile-time indices).
+constexpr int kCR = 4;
+
+template <int K>
+struct PadGeom {
+    static constexpr int h = (K - 1) / 2;
+    static constexpr int HL = (h + 3) & ~3;
+    static constexpr int D = HL - h;                 // window offset in a group
+    static constexpr int NW = (D + K + 3 + 3) / 4;   // float4 reads per window
+};
+
+// Padded row stride for an image of nx columns and PSF side K (host and
+// device): covers every float4 window read of the row pass and the right
+// zero halo.
+__host__ __device__ inline int padded_stride(int nx, int K)
+{
+    const int h = (K - 1) / 2, HL = (h + 3) & ~3, D = HL - h;
+    const int NW = (D + K + 6) / 4;
+    const int W = 4 * ((nx + 3) / 4) + 4 * NW;
+    return (W + 3) & ~3;
+}
+
+struct Acc10 {
+    float a[10];
+};
+
+template <int K, bool WRITE>
+__device__ __noinline__ Acc10 conv_padded(const LensDev &L, const RunArgs &R, float *Pl,
+                                          float *Ps, int tid, int nthr)
+{
+    Acc10 out;
+    float *acc = out.a;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+    using G = PadGeom<K>;
+    const int nx = L.nx, ny = L.ny, W = L.W;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int ngroups = (nx + 3) >> 2;
+    // row pass, in place; each lane holds at most 2 groups (nx <= 256)
+    for (int row = warp; row < 2 * ny; row += nwarp) {
+        float *P = (row < ny ? Pl + (G::h + row) * W : Ps + (G::h + row - ny) * W);
+        float o[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = lane + 32 * q;
+            if (g < ngroups) {
+                float win[4 * G::NW];
+                const float4 *src = reinterpret_cast<const float4 *>(P + 4 * g);
+#pragma unroll
+                for (int k = 0; k < G::NW; ++k) {
+                    const float4 v4 = src[k];
+                    win[4 * k] = v4.x; win[4 * k + 1] = v4.y;
+                    win[4 * k + 2] = v4.z; win[4 * k + 3] = v4.w;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < K; ++c) a = fmaf(L.tv[c], win[G::D + K - 1 + r - c], a);
+                    o[q][r] = a;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = lane + 32 * q;
+            if (g < ngroups) {
+                float *dst = P + G::HL + 4 * g;
+                if (4 * g + 3 < nx) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(o[q][0], o[q][1], o[q][2], o[q][3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (4 * g + r < nx) dst[r] = o[q][r];
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // column pass with the fused weighted sums
+    const int ncg = (nx + 31) >> 5, nrb = (ny + kCR - 1) / kCR;
+    for (int item = warp; item < ncg * nrb; item += nwarp) {
+        const int cg = item % ncg, rb = item / ncg;
+        const int j = 32 * cg + lane, i0 = rb * kCR;
+        const int jc = min(j, nx - 1);
+        float ml[kCR], ms[kCR];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const float *col = (ch == 0 ? Pl : Ps) + i0 * W + G::HL + jc;
+            float win[kCR + K - 1];
+#pragma unroll
+            for (int t = 0; t < kCR + K - 1; ++t) win[t] = col[t * W];
+#pragma unroll
+            for (int r = 0; r < kCR; ++r) {
+                float a = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) a = fmaf(L.tu[c], win[r + K - 1 - c], a);
+                if (ch == 0) ml[r] = a; else ms[r] = a;
+            }
+        }
+        if (j < nx) {
+#pragma unroll
+            for (int r = 0; r < kCR; ++r) {
+                const int i = i0 + r;
+                if (i < ny) {
+                    const int pix = i * nx + j;
+                    if (WRITE) {
+                        R.wr_blurred[pix] = ml[r];
+                        R.wr_blurred[L.npix + pix] = ms[r];
+                    }
+                    accum_pixel(ml[r], ms[r], L.wpack[pix], acc);
+                }
+            }
+        }
+    }
+    return out;
+}
+
+template <bool WRITE>
+__device__ __forceinline__ void conv_padded_dispatch(const LensDev &L, const RunArgs &R,
+                                                     float *Pl, float *Ps, float *acc,
+                                                     int tid, int nthr)
+{
+    switch (L.K) {
+#define TLL_K(k) case k: { const Acc10 r = conv_padded<k, WRITE>(L, R, Pl, Ps, tid, nthr); \
+        for (int q = 0; q < 10; ++q) acc[q] = r.a[q]; } break;
+        TLL_K(1) TLL_K(3) TLL_K(5) TLL_K(7) TLL_K(9) TLL_K(11) TLL_K(13) TLL_K(15)
+        TLL_K(17) TLL_K(19) TLL_K(21) TLL_K(23) TLL_K(25) TLL_K(27) TLL_K(29) TLL_K(31)
+#undef TLL_K
+        default: break;   // the host selects IMG_PADDED only for odd K <= 31
+    }
+}
+
+// ------------------------------------------------------------- kernel
+template <int SUB, int IMG, bool WRITE>
 __global__ void __launch_bounds__(kThreads)
-k_loglike(const LensDev L, const RunArgs R)
+k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
-    const int K = L.K, h = L.h, nx = L.nx, ny = L.ny, npix = L.npix;
-    const int psf_floats = L.sep ? 2 * K : K * K;
+    const int K = L.K, nx = L.nx, ny = L.ny, npix = L.npix;
+    const int psf_floats = IMG == IMG_PADDED ? 0 : (L.sep ? 2 * K : K * K);
     float *Il, *Is, *Hl, *Hs;
-    if (SMEM_IMG) {
+    int stride = nx, off = 0;
+    if (IMG == IMG_PADDED) {
+        const int rows = ny + 2 * L.h + kCR;   // zero rows above, below, and for the last row block
+        Il = spsf;
+        Is = Il + rows * L.W;
+        Hl = Il; Hs = Is;
+        stride = L.W;
+        off = L.h * L.W + L.HL;
+        for (int t = tid; t < 2 * rows * L.W; t += nthr) Il[t] = 0.0f;
+    } else if (IMG == IMG_SMEM) {
         Il = spsf + ((psf_floats + 3) & ~3);
         Is = Il + npix;
         Hl = Il;   // the row pass runs in place
@@ -185,7 +492,6 @@ k_loglike(const LensDev L, const RunArgs R)
     for (int t = tid; t < psf_floats; t += nthr)
         spsf[t] = L.sep ? (t < K ? L.pu[t] : L.pv[t - K]) : L.psf[t];
     __syncthreads();
-    const float *su = spsf, *sv = spsf + K;
 
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
@@ -196,41 +502,16 @@ k_loglike(const LensDev L, const RunArgs R)
             }
             continue;
         }
-        const Mass m = load_mass(kc);
-        const Ellipse el = load_ellipse(kc, K_OXL);
-        const Ellipse es = load_ellipse(kc, K_OXS);
-
-        // (1) ray-trace + light on the subpixels, mean-binned per pixel.
-        // A subpixel at offset (jx, iy) from the grid centre (J - JC exact,
-        // one rounding for the product) has offset (O + jx, O + iy) from each
-        // model centre, O = grid centre - model centre (small numbers, so
-        // small rounding).
-        for (int pix = tid; pix < npix; pix += nthr) {
-            const int i = pix / nx, j = pix - i * nx;
-            float accl = 0.0f, accs = 0.0f;
-            for (int a = 0; a < L.sub; ++a) {
-                const float fi = (float)(i * L.sub + a) - L.JCY;
-                const float iy = fmaf(fi, L.dsh, fi * L.dsl);
-                const float y = L.YC + iy;
-#pragma unroll 2
-                for (int c = 0; c < L.sub; ++c) {
-                    const float fj = (float)(j * L.sub + c) - L.JCX;
-                    const float jx = fmaf(fj, L.dsh, fj * L.dsl);
-                    const float x = L.XC + jx;
-                    float ax, ay;
-                    deflection(m, m.ox + jx, m.oy + iy, x, y, ax, ay);
-                    accl += sersic_unit(el, el.ox + jx, el.oy + iy);
-                    accs += sersic_unit(es, (es.ox + jx) - ax, (es.oy + iy) - ay);
-                }
-            }
-            Il[pix] = accl * L.inv_s2;
-            Is[pix] = accs * L.inv_s2;
+        {
+            const VecConst v = load_consts(kc);
+            trace_image<SUB>(L, v, Il, Is, stride, off, tid, nthr);
         }
         __syncthreads();
         if (WRITE) {
             for (int t = tid; t < npix; t += nthr) {
-                R.wr_unblurred[t] = Il[t];
-                R.wr_unblurred[npix + t] = Is[t];
+                const int i = t / nx, j = t - i * nx;
+                R.wr_unblurred[t] = Il[i * stride + off + j];
+                R.wr_unblurred[npix + t] = Is[i * stride + off + j];
             }
             __syncthreads();
         }
@@ -239,96 +520,18 @@ k_loglike(const LensDev L, const RunArgs R)
         float acc[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
-        if (L.sep) {
-            // row pass: H(i, j) = sum_c v[c] I(i, j + h - c)
-            for (int row = warp; row < 2 * ny; row += nwarp) {
-                const float *src = row < ny ? Il + row * nx : Is + (row - ny) * nx;
-                float *dst = row < ny ? Hl + row * nx : Hs + (row - ny) * nx;
-                if (SMEM_IMG) {
-                    float o[kHMax];
-#pragma unroll
-                    for (int q = 0; q < kHMax; ++q) {
-                        const int j = lane + 32 * q;
-                        float s = 0.0f;
-                        if (j < nx) {
-                            const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
-                            for (int c = c0; c <= c1; ++c) s = fmaf(sv[c], src[j + h - c], s);
-                        }
-                        o[q] = s;
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int q = 0; q < kHMax; ++q) {
-                        const int j = lane + 32 * q;
-                        if (j < nx) dst[j] = o[q];
-                    }
-                    __syncwarp();
-                } else {
-                    for (int j = lane; j < nx; j += 32) {
-                        const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
-                        float s = 0.0f;
-                        for (int c = c0; c <= c1; ++c) s = fmaf(sv[c], src[j + h - c], s);
-                        dst[j] = s;
-                    }
-                }
-            }
-            __syncthreads();
-            // column pass: m(i, j) = sum_r u[r] H(i + h - r, j), fused sums
-            const int nb = max(1, nthr / nx);
-            const int rb = (ny + nb - 1) / nb;
-            for (int it = tid; it < nx * nb; it += nthr) {
-                const int j = it % nx, band = it / nx;
-                const int r0 = band * rb, r1 = min(ny, r0 + rb);
-                for (int i = r0; i < r1; ++i) {
-                    const int q0 = max(0, i + h - ny + 1), q1 = min(K - 1, i + h);
-                    float ml = 0.0f, ms = 0.0f;
-                    for (int r = q0; r <= q1; ++r) {
-                        const int off = (i + h - r) * nx + j;
-                        ml = fmaf(su[r], Hl[off], ml);
-                        ms = fmaf(su[r], Hs[off], ms);
-                    }
-                    const int pix = i * nx + j;
-                    if (WRITE) {
-                        R.wr_blurred[pix] = ml;
-                        R.wr_blurred[npix + pix] = ms;
-                    }
-                    accum_pixel(ml, ms, L.wpack[pix], acc);
-                }
-            }
-        } else {
-            // direct 2-D convolution, one output pixel per thread, summed
-            // per PSF row then across rows
-            for (int pix = tid; pix < npix; pix += nthr) {
-                const int i = pix / nx, j = pix - i * nx;
-                const int r0 = max(0, i + h - ny + 1), r1 = min(K - 1, i + h);
-                const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
-                float ml = 0.0f, ms = 0.0f;
-                for (int r = r0; r <= r1; ++r) {
-                    const float *kr = spsf + r * K;
-                    const int base = (i + h - r) * nx + j + h;
-                    float rl = 0.0f, rs = 0.0f;
-                    for (int c = c0; c <= c1; ++c) {
-                        rl = fmaf(kr[c], Il[base - c], rl);
-                        rs = fmaf(kr[c], Is[base - c], rs);
-                    }
-                    ml += rl;
-                    ms += rs;
-                }
-                if (WRITE) {
-                    R.wr_blurred[pix] = ml;
-                    R.wr_blurred[npix + pix] = ms;
-                }
-                accum_pixel(ml, ms, L.wpack[pix], acc);
-            }
-        }
+        if (IMG == IMG_PADDED)
+            conv_padded_dispatch<WRITE>(L, R, Il, Is, acc, tid, nthr);
+        else
+            conv_generic<IMG == IMG_SMEM, WRITE>(L, R, spsf, Il, Is, Hl, Hs, acc, tid, nthr);
 
         // (3) warp reduction in double-float, block reduction in FP64
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], off);
-                const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], off);
+                const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
                 df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
             }
         }
@@ -339,12 +542,12 @@ k_loglike(const LensDev L, const RunArgs R)
         }
         __syncthreads();
         if (warp == 0) {
-            double s = 0.0;
+            double sacc = 0.0;
             if (lane < 5)
-                for (int w = 0; w < nwarp; ++w) s += sred[w * 5 + lane];
+                for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
             double S[5];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, s, k);
+            for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, sacc, k);
             if (lane == 0) {
                 double sl, ss, ll;
                 finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
@@ -392,14 +595,42 @@ struct tll_lens {
     float *d_p1 = nullptr, *d_kc1 = nullptr, *d_unb = nullptr, *d_blur = nullptr,
           *d_img = nullptr;
     double *d_res = nullptr, *d_out1 = nullptr;
-    bool smem_img = false;
+    int img = 0;          // IMG_GLOBAL / IMG_SMEM / IMG_PADDED
+    int W = 0, HL = 0;    // padded layout geometry
+    std::vector<float> taps_u, taps_v;
     int grid_cap = 0;
     size_t smem_bytes = 0;
+    const double *bn_tab = nullptr;   // per-device b_n table (not owned)
     cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
     bool prof_on = false, prof_recorded = false;
 };
 
 namespace {
+
+// Per-device b_n table, built on first use and kept for the process.
+constexpr int kMaxDevices = 64;
+double *g_bn_tab[kMaxDevices] = {};
+std::mutex g_bn_mu;
+
+int bn_table(int dev, const double **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(TLL_ECUDA, "device id %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_bn_mu);
+    if (!g_bn_tab[dev]) {
+        double *p = nullptr;
+        CUDA_TRY(cudaMalloc(&p, 2 * BN_SEG * sizeof(double)));
+        k_bn_table<<<(2 * BN_SEG + 127) / 128, 128>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return fail(TLL_ECUDA, "b_n table: %s", cudaGetErrorString(e));
+        }
+        g_bn_tab[dev] = p;
+    }
+    *out = g_bn_tab[dev];
+    return TLL_OK;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -427,27 +658,41 @@ LensDev lens_dev(const tll_lens *L)
     LensDev d;
     d.nx = L->nx; d.ny = L->ny; d.npix = L->npix; d.sub = L->sub;
     d.K = L->K; d.h = (L->K - 1) / 2; d.sep = L->sep; d.mode = L->mode;
-    {
-        const double st = (double)L->dpix / L->sub;
-        d.dsh = (float)st;
-        d.dsl = (float)(st - (double)d.dsh);
-    }
-    double xc, yc;
-    grid_centre(L, &xc, &yc);
-    d.XC = (float)xc;
-    d.YC = (float)yc;
     d.JCX = 0.5f * (float)(L->nx * L->sub - 1);
     d.JCY = 0.5f * (float)(L->ny * L->sub - 1);
     d.inv_s2 = 1.0f / (float)(L->sub * L->sub);
     d.psf = L->d_psf; d.pu = L->d_pu; d.pv = L->d_pv; d.wpack = L->d_wpack;
     d.dWd = L->dWd; d.lognorm = L->lognorm;
+    d.W = L->W; d.HL = L->HL;
+    for (int k = 0; k < kMaxTaps; ++k) {
+        d.tu[k] = k < (int)L->taps_u.size() ? L->taps_u[k] : 0.0f;
+        d.tv[k] = k < (int)L->taps_v.size() ? L->taps_v[k] : 0.0f;
+    }
     return d;
 }
 
-template <bool SMEM_IMG, bool WRITE>
-int launch_main(const tll_lens *L, const RunArgs &R, int grid, cudaStream_t st)
+// Kernel variant for (supersampling, image placement, write-out):
+// s = 4 and s = 5 are compiled with the subpixel loop unrolled.
+template <int IMG, bool WRITE>
+void (*pick_kernel(int sub))(const LensDev, const RunArgs)
 {
-    k_loglike<SMEM_IMG, WRITE><<<grid, kThreads, L->smem_bytes, st>>>(lens_dev(L), R);
+    if (sub == 4) return k_loglike<4, IMG, WRITE>;
+    if (sub == 5) return k_loglike<5, IMG, WRITE>;
+    return k_loglike<0, IMG, WRITE>;
+}
+
+template <bool WRITE>
+void (*pick_kernel(int img, int sub))(const LensDev, const RunArgs)
+{
+    if (img == IMG_PADDED) return pick_kernel<IMG_PADDED, WRITE>(sub);
+    if (img == IMG_SMEM) return pick_kernel<IMG_SMEM, WRITE>(sub);
+    return pick_kernel<IMG_GLOBAL, WRITE>(sub);
+}
+
+int launch_main(const tll_lens *L, const RunArgs &R, int grid, bool write, cudaStream_t st)
+{
+    auto kern = write ? pick_kernel<true>(L->img, L->sub) : pick_kernel<false>(L->img, L->sub);
+    kern<<<grid, kThreads, L->smem_bytes, st>>>(lens_dev(L), R);
     CUDA_TRY(cudaGetLastError());
     return TLL_OK;
 }
@@ -459,19 +704,16 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
     double xc, yc;
     grid_centre(L, &xc, &yc);
-    k_prologue<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, xc, yc);
+    k_prologue<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, xc, yc,
+                                                (double)L->dpix / L->sub, L->bn_tab);
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
     RunArgs R;
     R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr;
     R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
     const int grid = std::min(B, L->grid_cap);
-    if (write) {
-        return L->smem_img ? launch_main<true, true>(L, R, 1, st)
-                           : launch_main<false, true>(L, R, 1, st);
-    }
-    const int rc = L->smem_img ? launch_main<true, false>(L, R, grid, st)
-                               : launch_main<false, false>(L, R, grid, st);
+    if (write) return launch_main(L, R, 1, true, st);
+    const int rc = launch_main(L, R, grid, false, st);
     if (rc == TLL_OK && prof) {
         CUDA_TRY(cudaEventRecord(L->prof_ev[2], st));
         L->prof_recorded = true;
@@ -496,30 +738,41 @@ int configure(tll_lens *L)
     int nsm = 0, optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, L->dev));
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, L->dev));
+    // placement: padded shared memory (separable PSF, K <= 31, nx <= 256),
+    // else unpadded shared memory, else a global scratch slot per CTA
+    const int h = (L->K - 1) / 2;
+    const int Wp = padded_stride(L->nx, L->K);
+    const size_t padded = kRedBytes + (size_t)2 * (L->ny + 2 * h + kCR) * Wp * sizeof(float);
     const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
     const size_t fixed = kRedBytes + (size_t)((psf_floats + 3) & ~3) * sizeof(float);
-    const size_t img = (size_t)2 * L->npix * sizeof(float);
-    L->smem_img = (fixed + img <= (size_t)optin) && (L->nx <= 32 * kHMax);
-    L->smem_bytes = L->smem_img ? fixed + img : fixed;
-    int per_sm = 0;
-    // allow every instantiation the device's full opt-in shared memory once,
-    // so lenses of different sizes can share the kernels
-    CUDA_TRY(cudaFuncSetAttribute(k_loglike<true, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    CUDA_TRY(cudaFuncSetAttribute(k_loglike<true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    if (L->smem_img) {
-        auto kern = k_loglike<true, false>;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
-                                                               L->smem_bytes));
+    const size_t plain = fixed + (size_t)2 * L->npix * sizeof(float);
+    if (L->sep && L->K <= kMaxTaps - 1 && L->nx <= 256 && padded <= (size_t)optin) {
+        L->img = IMG_PADDED;
+        L->smem_bytes = padded;
+        L->W = Wp;
+        L->HL = (h + 3) & ~3;
+    } else if (plain <= (size_t)optin && L->nx <= 32 * kHMax) {
+        L->img = IMG_SMEM;
+        L->smem_bytes = plain;
     } else {
-        auto kern = k_loglike<false, false>;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
-                                                               L->smem_bytes));
+        L->img = IMG_GLOBAL;
+        L->smem_bytes = fixed;
     }
+    // allow every shared-memory instantiation the device's full opt-in
+    // shared memory, so lenses of different sizes can share the kernels
+    for (int sb : {0, 4, 5})
+        for (int im : {IMG_SMEM, IMG_PADDED}) {
+            CUDA_TRY(cudaFuncSetAttribute(pick_kernel<false>(im, sb),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+            CUDA_TRY(cudaFuncSetAttribute(pick_kernel<true>(im, sb),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        }
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, pick_kernel<false>(L->img, L->sub), kThreads, L->smem_bytes));
     if (per_sm < 1) return fail(TLL_ECUDA, "k_loglike cannot be resident on an SM");
     L->grid_cap = nsm * per_sm;
-    if (!L->smem_img) {
+    if (L->img == IMG_GLOBAL) {
         const size_t n = (size_t)L->grid_cap * 4 * L->npix;
         CUDA_TRY(cudaMalloc(&L->d_gscr, n * sizeof(float)));
     }
@@ -630,6 +883,10 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         }
     }
     L->sep = sep;
+    if (sep) {
+        L->taps_u = pu;
+        L->taps_v = pv;
+    }
 
     // weights (Eq. 5): w = 1/sigma^2 as a float pair, w*d likewise; masked
     // pixels get 0.  dWd = sum w d^2, lognorm = -sum log(2 pi sigma^2)/2.
@@ -681,7 +938,7 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         free_lens(L);
         return fail(TLL_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
     }
-    if ((rc = configure(L)) || (rc = ensure_kc(L, 1024))) {
+    if ((rc = configure(L)) || (rc = ensure_kc(L, 1024)) || (rc = bn_table(dev, &L->bn_tab))) {
         free_lens(L);
         return rc;
     }

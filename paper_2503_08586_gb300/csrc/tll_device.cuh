@@ -16,24 +16,27 @@ namespace tll {
 constexpr int NPAR = 21;
 
 // Per-vector constants written by the prologue, NCONST floats per vector.
-// Offsets O* are (grid origin - centre) so that a subpixel's coordinate
-// relative to a centre is one add from its grid offset.  *H / *L pairs are
-// the high and low float parts of a constant (double-float).
+// Every coordinate a subpixel needs is an affine function of its integer
+// offsets (fj, fi) from the grid centre: C0 + CJ fj + CI fi.  *H / *L pairs
+// are the high and low float parts of a constant (double-float).
 enum : int {
     K_VALID = 0,
-    // mass: offsets to the SIE centre, rotation, q, prefactor A/f (hi, lo),
-    // f = sqrt(1 - q^2), q = 1 flag, shear
-    K_OXM, K_OYM, K_CM, K_SM, K_QM, K_AFH, K_AFL, K_F, K_SIS, K_G1, K_G2,
-    // lens light: offsets, rotation, q/r_e^2, 1/(q r_e^2), 1/(2n) (hi, lo),
-    // b log2(e) (hi, lo)
-    K_OXL, K_OYL, K_CL, K_SL, K_A1L, K_A2L, K_KHL, K_KLL, K_BHL, K_BLL,
-    // source, same fields
-    K_OXS, K_OYS, K_CS, K_SS, K_A1S, K_A2S, K_KHS, K_KLS, K_BHS, K_BLS,
+    // mass frame: x' = PX0 + PXJ fj + PXI fi, y' = PY0 + PYJ fj + PYI fi;
+    // q, f = sqrt(1 - q^2), 1/f, fast-path flag
+    K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_F, K_IF, K_FAST,
+    // lens light, scaled frame (x1 sqrt(q)/r_e, x2/(sqrt(q) r_e)):
+    // affine coefficients, 1/(2n) (hi, lo), b log2(e) (hi, lo)
+    K_LX0, K_LXJ, K_LXI, K_LY0, K_LYJ, K_LYI, K_KHL, K_KLL, K_BHL, K_BLL,
+    // source, scaled frame at theta minus shear (linear part) ...
+    K_SX0, K_SXJ, K_SXI, K_SY0, K_SYJ, K_SYI, K_KHS, K_KLS, K_BHS, K_BLS,
+    // ... minus the SIE deflection A (ux, uy) mapped from the mass frame:
+    // [Q11 Q12; Q21 Q22] (hi, lo)
+    K_Q11H, K_Q11L, K_Q12H, K_Q12L, K_Q21H, K_Q21L, K_Q22H, K_Q22L,
     // fixed amplitudes
     K_IEL, K_IES,
     NCONST_USED
 };
-constexpr int NCONST = 40;
+constexpr int NCONST = 48;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
 
 // ------------------------------------------------------------------ b_n
@@ -72,6 +75,53 @@ __device__ inline double sersic_bn_dev(double n)
     return b;
 }
 
+// b_n table: two uniform segments, n in [0.2, 1] and [1, 10], BN_NT nodes
+// each plus one guard node below and two above, filled once per device by
+// k_bn_table (sersic_bn_dev at each node) and read by cubic Lagrange
+// interpolation through the four nearest nodes (relative error < 3e-12).
+constexpr int BN_NT = 2048;
+constexpr int BN_SEG = BN_NT + 3;
+__host__ __device__ __forceinline__ double bn_lo(int seg) { return seg ? 1.0 : 0.2; }
+__host__ __device__ __forceinline__ double bn_hi(int seg) { return seg ? 10.0 : 1.0; }
+
+__device__ __forceinline__ double bn_node(int seg, int k)   // k = -1 .. BN_NT + 1
+{
+    const double h = (bn_hi(seg) - bn_lo(seg)) / (BN_NT - 1);
+    return bn_lo(seg) + h * k;
+}
+
+__device__ inline double sersic_bn_lookup(const double *__restrict__ tab, double n)
+{
+    const int seg = n < 1.0 ? 0 : 1;
+    const double h = (bn_hi(seg) - bn_lo(seg)) / (BN_NT - 1);
+    const double u = (n - bn_lo(seg)) * (1.0 / h);
+    int i = (int)floor(u);
+    i = max(0, min(i, BN_NT - 2));
+    const double t = u - i;
+    const double *p = tab + seg * BN_SEG + i;   // nodes i-1 .. i+2
+    const double tm1 = t - 1.0, tm2 = t - 2.0, tp1 = t + 1.0;
+    return (-t * tm1 * tm2 * (1.0 / 6.0)) * p[0] + (tp1 * tm1 * tm2 * 0.5) * p[1]
+           - (tp1 * t * tm2 * 0.5) * p[2] + (tp1 * t * tm1 * (1.0 / 6.0)) * p[3];
+}
+
+// (cos phi, sin phi) of phi = atan2(e2, e1)/2 (Eq. 11's position angle) by
+// the half-angle formulas, without trigonometric calls.
+__device__ __forceinline__ void half_angle(double e1, double e2, double e,
+                                           double *c, double *s)
+{
+    if (!(e > 0.0)) { *c = 1.0; *s = 0.0; return; }
+    const double c2 = e1 / e, s2 = e2 / e;
+    if (c2 >= 0.0) {
+        const double cc = sqrt(0.5 * (1.0 + c2));
+        *c = cc;
+        *s = s2 / (2.0 * cc);
+    } else {
+        const double ss = copysign(sqrt(0.5 * (1.0 - c2)), s2);
+        *s = ss;
+        *c = s2 / (2.0 * ss);
+    }
+}
+
 __device__ __forceinline__ void split2(double v, float *o_hi, float *o_lo)
 {
     const float h = (float)v;
@@ -82,10 +132,23 @@ __device__ __forceinline__ void split2(double v, float *o_hi, float *o_lo)
 // --------------------------------------------------------------- prologue
 // Decode one parameter vector into its constant block.  Validity: finite
 // entries, theta_E >= 0, |eps| < 1 for the three ellipses, r_e > 0, Sersic
-// index in [0.2, 10]; an invalid vector gets K_VALID = 0.  (X0, Y0) is the
-// coordinate of the grid centre, the origin of subpixel offsets (FP64).
+// index in [0.2, 10]; an invalid vector gets K_VALID = 0.  (XC, YC) is the
+// grid centre and d the subpixel step: subpixel (fj, fi) sits at
+// (XC + fj d, YC + fi d).  All arithmetic here is FP64, rounded once.
+//
+// Derivation of the folded coefficients (R(phi) = rotation by +phi):
+//   mass frame        x' = R(-phi_m) (theta - c_m)                  (Eq. 10)
+//   SIE deflection    alpha = R(phi_m) A (ux, uy), A = theta_E sqrt(q_m)
+//   shear             alpha_sh = G theta, G = [[g1, g2], [g2, -g1]] (Eq. 13/14)
+//   source position   beta = theta - alpha - G theta                 (Eq. 1)
+//   source frame      (x1, x2) = R(-phi_s) (beta - c_s), scaled by
+//                     (sqrt(q_s)/r_e, 1/(sqrt(q_s) r_e)) so (R_p/r_e)^2 =
+//                     x1^2 + x2^2                                    (Eq. 10)
+// so the scaled source coordinates are an affine map of theta minus
+// S R(phi_m - phi_s) A (ux, uy), S = diag of the scales.
 __device__ inline void decode_vector(const float *__restrict__ p, float *__restrict__ o,
-                                     double X0, double Y0)
+                                     double XC, double YC, double d,
+                                     const double *__restrict__ bn_tab)
 {
     bool ok = true;
     double v[NPAR];
@@ -106,86 +169,185 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     if (!ok) return;
     o[K_VALID] = 1.0f;
     const double LOG2E = 1.4426950408889634;
-    {   // mass: q = (1-e)/(1+e), angle = atan2(e2, e1)/2, f = 2 sqrt(e)/(1+e)
-        const double q = (1.0 - e_m) / (1.0 + e_m);
-        const double ang = 0.5 * atan2(v[2], v[1]);
-        const double f = 2.0 * sqrt(e_m) / (1.0 + e_m);
-        const double A = v[0] * sqrt(q);
-        o[K_OXM] = (float)(X0 - v[3]);
-        o[K_OYM] = (float)(Y0 - v[4]);
-        o[K_CM] = (float)cos(ang);
-        o[K_SM] = (float)sin(ang);
-        o[K_QM] = (float)q;
+
+    // mass: q = (1-e)/(1+e), f = sqrt(1 - q^2) = 2 sqrt(e)/(1+e)
+    const double qm = (1.0 - e_m) / (1.0 + e_m);
+    const double f = 2.0 * sqrt(e_m) / (1.0 + e_m);
+    const double A = v[0] * sqrt(qm);
+    double cm, sm;
+    half_angle(v[1], v[2], e_m, &cm, &sm);
+    {
+        const double dx = XC - v[3], dy = YC - v[4];
+        o[K_PX0] = (float)(dx * cm + dy * sm);
+        o[K_PXJ] = (float)(d * cm);
+        o[K_PXI] = (float)(d * sm);
+        o[K_PY0] = (float)(-dx * sm + dy * cm);
+        o[K_PYJ] = (float)(-d * sm);
+        o[K_PYI] = (float)(d * cm);
+        o[K_QM] = (float)qm;
         o[K_F] = (float)f;
-        if (f < 1e-6) { o[K_SIS] = 1.0f; split2(A, &o[K_AFH], &o[K_AFL]); }
-        else { o[K_SIS] = 0.0f; split2(A / f, &o[K_AFH], &o[K_AFL]); }
-        o[K_G1] = (float)v[5];
-        o[K_G2] = (float)v[6];
+        o[K_IF] = f > 0.0 ? (float)(1.0 / f) : 0.0f;
+        // fast path when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
+        // for every point: no atan range reduction, no atanh logarithm
+        o[K_FAST] = (f <= qm && f <= 0.5) ? 1.0f : 0.0f;
     }
-    // Sersic components: lens light (centre in slots 12, 13) and source
-    const int base[2] = {K_OXL, K_OXS};
-    const int par[2] = {8, 15};   // r_e, n, eps1, eps2, x, y follow r_e's slot
-    const double e_c[2] = {e_l, e_s};
-#pragma unroll
-    for (int comp = 0; comp < 2; ++comp) {
-        const int P0 = par[comp], B0 = base[comp];
-        const double re = v[P0], n = v[P0 + 1];
-        const double q = (1.0 - e_c[comp]) / (1.0 + e_c[comp]);
-        const double ang = 0.5 * atan2(v[P0 + 3], v[P0 + 2]);
-        o[B0 + 0] = (float)(X0 - v[P0 + 4]);
-        o[B0 + 1] = (float)(Y0 - v[P0 + 5]);
-        o[B0 + 2] = (float)cos(ang);
-        o[B0 + 3] = (float)sin(ang);
-        o[B0 + 4] = (float)(q / (re * re));
-        o[B0 + 5] = (float)(1.0 / (q * re * re));
-        split2(0.5 / n, &o[B0 + 6], &o[B0 + 7]);
-        split2(sersic_bn_dev(n) * LOG2E, &o[B0 + 8], &o[B0 + 9]);
+    const double g1 = v[5], g2 = v[6];
+
+    // lens light (centre in slots 12, 13)
+    {
+        const double re = v[8], n = v[9];
+        const double q = (1.0 - e_l) / (1.0 + e_l);
+        double c, s;
+        half_angle(v[10], v[11], e_l, &c, &s);
+        const double s1 = sqrt(q) / re, s2 = 1.0 / (sqrt(q) * re);
+        const double dx = XC - v[12], dy = YC - v[13];
+        o[K_LX0] = (float)(s1 * (dx * c + dy * s));
+        o[K_LXJ] = (float)(s1 * d * c);
+        o[K_LXI] = (float)(s1 * d * s);
+        o[K_LY0] = (float)(s2 * (-dx * s + dy * c));
+        o[K_LYJ] = (float)(-s2 * d * s);
+        o[K_LYI] = (float)(s2 * d * c);
+        split2(0.5 / n, &o[K_KHL], &o[K_KLL]);
+        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHL], &o[K_BLL]);
+    }
+    // source
+    {
+        const double re = v[15], n = v[16];
+        const double q = (1.0 - e_s) / (1.0 + e_s);
+        double c, s;
+        half_angle(v[17], v[18], e_s, &c, &s);
+        const double s1 = sqrt(q) / re, s2 = 1.0 / (sqrt(q) * re);
+        // linear part: beta_lin = (I - G) theta - c_s, theta = (XC + fj d, YC + fi d)
+        const double bx0 = (1.0 - g1) * XC - g2 * YC - v[19];
+        const double by0 = -g2 * XC + (1.0 + g1) * YC - v[20];
+        const double bxj = (1.0 - g1) * d, bxi = -g2 * d;
+        const double byj = -g2 * d, byi = (1.0 + g1) * d;
+        o[K_SX0] = (float)(s1 * (c * bx0 + s * by0));
+        o[K_SXJ] = (float)(s1 * (c * bxj + s * byj));
+        o[K_SXI] = (float)(s1 * (c * bxi + s * byi));
+        o[K_SY0] = (float)(s2 * (-s * bx0 + c * by0));
+        o[K_SYJ] = (float)(s2 * (-s * bxj + c * byj));
+        o[K_SYI] = (float)(s2 * (-s * bxi + c * byi));
+        split2(0.5 / n, &o[K_KHS], &o[K_KLS]);
+        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &o[K_BLS]);
+        // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
+        const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
+        const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
+        split2(s1 * A * cd, &o[K_Q11H], &o[K_Q11L]);
+        split2(-s1 * A * sd, &o[K_Q12H], &o[K_Q12L]);
+        split2(s2 * A * sd, &o[K_Q21H], &o[K_Q21L]);
+        split2(s2 * A * cd, &o[K_Q22H], &o[K_Q22L]);
     }
     o[K_IEL] = (float)v[7];
     o[K_IES] = (float)v[14];
 }
 
 // ------------------------------------------------------------ subpixel
-struct Ellipse {   // one Sersic component in registers
-    float ox, oy, c, s, a1, a2, kh, kl, bh, bl;
+// Per-vector constants in registers.
+struct Affine {    // v = c0 + cj fj + ci fi
+    float c0, cj, ci;
 };
-struct Mass {
-    float ox, oy, c, s, q, afh, afl, f, g1, g2;
-    bool sis;
+struct VecConst {
+    Affine px, py, lx, ly, sx, sy;
+    float q, f, invf;
+    bool fast;
+    float khl, kll, bhl, bll, khs, kls, bhs, bls;
+    float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
 };
 
-__device__ __forceinline__ Ellipse load_ellipse(const float *kc, int b)
+__device__ __forceinline__ Affine load_affine(const float *kc, int b)
 {
-    Ellipse e;
-    e.ox = kc[b + 0]; e.oy = kc[b + 1]; e.c = kc[b + 2]; e.s = kc[b + 3];
-    e.a1 = kc[b + 4]; e.a2 = kc[b + 5]; e.kh = kc[b + 6]; e.kl = kc[b + 7];
-    e.bh = kc[b + 8]; e.bl = kc[b + 9];
-    return e;
+    return Affine{kc[b], kc[b + 1], kc[b + 2]};
 }
 
-__device__ __forceinline__ Mass load_mass(const float *kc)
+__device__ __forceinline__ VecConst load_consts(const float *kc)
 {
-    Mass m;
-    m.ox = kc[K_OXM]; m.oy = kc[K_OYM]; m.c = kc[K_CM]; m.s = kc[K_SM];
-    m.q = kc[K_QM]; m.afh = kc[K_AFH]; m.afl = kc[K_AFL]; m.f = kc[K_F];
-    m.g1 = kc[K_G1]; m.g2 = kc[K_G2];
-    m.sis = kc[K_SIS] != 0.0f;
-    return m;
+    VecConst v;
+    v.px = load_affine(kc, K_PX0); v.py = load_affine(kc, K_PY0);
+    v.lx = load_affine(kc, K_LX0); v.ly = load_affine(kc, K_LY0);
+    v.sx = load_affine(kc, K_SX0); v.sy = load_affine(kc, K_SY0);
+    v.q = kc[K_QM]; v.f = kc[K_F]; v.invf = kc[K_IF];
+    v.fast = kc[K_FAST] != 0.0f;
+    v.khl = kc[K_KHL]; v.kll = kc[K_KLL]; v.bhl = kc[K_BHL]; v.bll = kc[K_BLL];
+    v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
+    v.q11h = kc[K_Q11H]; v.q11l = kc[K_Q11L]; v.q12h = kc[K_Q12H]; v.q12l = kc[K_Q12L];
+    v.q21h = kc[K_Q21H]; v.q21l = kc[K_Q21L]; v.q22h = kc[K_Q22H]; v.q22l = kc[K_Q22L];
+    return v;
 }
 
-// Unit-amplitude elliptical Sersic at offset (u, v) from its centre:
-// rotate (Eq. 10), (R_p/r_e)^2 = q x1^2/r_e^2 + x2^2/(q r_e^2),
+// SFU instructions (PTX ISA: ex2.approx, lg2.approx, rcp.approx).
+__device__ __forceinline__ float sfu_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 2^x for x <= 30 by range reduction x = k + f, k = rint(x), |f| <= 1/2:
+// ex2.approx on f (unbiased on that interval, unlike on wide arguments),
+// times 2^k added into the exponent field.  rint: adding 1.5 * 2^23 leaves
+// k in the low mantissa bits of kf, and kf's bits << 23 are k << 23.
+// x is clamped below at -125 so the result stays a normal float (smaller
+// values only enter pixel sums far below the model's rounding); a NaN x
+// (only from 0 * inf at r = 0, where 2^x -> 0 is wanted) also becomes -125.
+__device__ __forceinline__ float exp2_rr(float x)
+{
+    x = fmaxf(x, -125.0f);
+    const float kf = x + 12582912.0f;
+    const float f = x - (kf - 12582912.0f);
+    const float y = sfu_ex2(f);
+    return __int_as_float(__float_as_int(y) + (__float_as_int(kf) << 23));
+}
+
+// Horner in s for the Q(s) polynomials of tll_poly.cuh.
+__device__ __forceinline__ float poly_atan_q(float s)
+{
+    float q = -1.753930119e-03f;
+    q = fmaf(q, s, 1.072694361e-02f);
+    q = fmaf(q, s, -3.080459684e-02f);
+    q = fmaf(q, s, 5.755210295e-02f);
+    q = fmaf(q, s, -8.377315104e-02f);
+    q = fmaf(q, s, 1.094203070e-01f);
+    q = fmaf(q, s, -1.426193267e-01f);
+    q = fmaf(q, s, 1.999826580e-01f);
+    return fmaf(q, s, -3.333328366e-01f);
+}
+__device__ __forceinline__ float poly_atanh_q(float s)
+{
+    float q = 1.785548776e-01f;
+    q = fmaf(q, s, 4.985036701e-02f);
+    q = fmaf(q, s, 1.187057048e-01f);
+    q = fmaf(q, s, 1.421579868e-01f);
+    q = fmaf(q, s, 2.000301927e-01f);
+    return fmaf(q, s, 3.333328366e-01f);
+}
+
+// Unit-amplitude Sersic (Eq. 8) at scaled-frame coordinates (x1, x2), i.e.
+// (R_p/r_e)^2 = x1^2 + x2^2 (Eq. 10 folded into the coordinates):
 // t = (R_p/r_e)^{1/n} = 2^{log2((R_p/r_e)^2)/(2n)},
-// I = exp(-b (t - 1)) = 2^{b log2(e) (1 - t)} (Eq. 8).
-__device__ __forceinline__ float sersic_unit(const Ellipse &e, float u, float v)
+// I = exp(-b (t - 1)) = 2^{b log2(e) (1 - t)}.  The pow's exponential is
+// range-reduced (its bias would scale with b t); the outer one is not (a
+// bias there is a near-uniform relative scale).
+__device__ __forceinline__ float sersic_scaled(float x1, float x2, float kh, float kl,
+                                               float bh, float bl)
 {
-    const float x1 = fmaf(u, e.c, v * e.s);
-    const float x2 = fmaf(v, e.c, -u * e.s);
-    const float r2 = fmaf(x1 * x1, e.a1, x2 * x2 * e.a2);
-    const float L = log2f(r2);
-    const float t = exp2f(fmaf(e.kh, L, e.kl * L));
+    const float r2 = fmaf(x1, x1, x2 * x2);
+    const float L = sfu_lg2(r2);
+    const float t = exp2_rr(fmaf(kh, L, kl * L));
     const float omt = 1.0f - t;
-    return exp2f(fmaf(e.bh, omt, e.bl * omt));
+    return sfu_ex2(fmaf(bh, omt, bl * omt));
 }
 
 // 1/sqrt(a) to about 1 ulp: the hardware estimate plus one Newton step.
@@ -196,35 +358,72 @@ __device__ __forceinline__ float rsqrt_nr(float a)
     return fmaf(y, fmaf(-hy, y, 0.5f), y);
 }
 
-// Deflection of SIE (Eq. 12 at gamma = 2, elliptical radius of Eq. 10) at
-// offset (dx, dy) from the mass centre, plus external shear (Eqs. 13, 14) at
-// the absolute position (x, y).  SIE in the frame rotated by the mass angle:
-// with psi = sqrt(q^2 x'^2 + y'^2),
-//   alpha_x' = A/f atan(f x'/psi),  alpha_y' = A/f atanh(f y'/psi),
-// A = theta_E sqrt(q), f = sqrt(1 - q^2); for f -> 0 the q = 1 limit
-// alpha' = A (x', y')/psi.  Shear: alpha = (g1 x + g2 y, g2 x - g1 y).
-__device__ __forceinline__ void deflection(const Mass &m, float dx, float dy,
-                                           float x, float y, float &ax, float &ay)
+// SIE deflection (Eq. 12 at gamma = 2, elliptical radius of Eq. 10) in the
+// mass frame at (xp, yp), as alpha' = A (ux, uy): with psi = sqrt(q^2 xp^2 +
+// yp^2), zx = f xp/psi, zy = f yp/psi (f = sqrt(1 - q^2), A = theta_E sqrt(q)),
+//   ux = atan(zx)/f = (xp/psi) P_atan(zx^2),
+//   uy = atanh(zy)/f = (yp/psi) P_atanh(zy^2),
+// with atan(w) = w P_atan(w^2), atanh(w) = w P_atanh(w^2) (tll_poly.cuh); the
+// q = 1 limit needs no special case.  Vectors whose |zx| can exceed 1 or
+// |zy| exceed 1/2 take the general branch: atan(z) = sign(z) pi/2 -
+// atan(1/z) and atanh(z) = ln((1+z)/(1-z))/2 where needed, per point.
+__device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
+                                         float &ux, float &uy)
 {
-    const float xp = fmaf(dx, m.c, dy * m.s);
-    const float yp = fmaf(dy, m.c, -dx * m.s);
-    const float qx = m.q * xp;
-    const float psi2 = fmaxf(fmaf(qx, qx, yp * yp), 1e-24f);
-    const float rpsi = rsqrt_nr(psi2);
-    float axp, ayp;
-    if (m.sis) {
-        const float tx = xp * rpsi, ty = yp * rpsi;
-        axp = fmaf(m.afh, tx, m.afl * tx);
-        ayp = fmaf(m.afh, ty, m.afl * ty);
+    const float qx = v.q * xp;
+    const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
+    const float xr = xp * rpsi, yr = yp * rpsi;
+    const float zx = v.f * xr, zy = v.f * yr;
+    const float sx = zx * zx, sy = zy * zy;
+    if (v.fast) {
+        ux = fmaf(xr * sx, poly_atan_q(sx), xr);
+        uy = fmaf(yr * sy, poly_atanh_q(sy), yr);
     } else {
-        const float fr = m.f * rpsi;
-        const float zy = fminf(fmaxf(yp * fr, -0.99999994f), 0.99999994f);
-        const float at = atanf(xp * fr), ah = atanhf(zy);
-        axp = fmaf(m.afh, at, m.afl * at);
-        ayp = fmaf(m.afh, ah, m.afl * ah);
+        // atan: reduce |z| > 1 to 1/|z|
+        const float ax = fabsf(zx);
+        const bool big = ax > 1.0f;
+        const float w = big ? sfu_rcp(ax) : ax;
+        const float sw = w * w;
+        const float pw = fmaf(w * sw, poly_atan_q(sw), w);
+        float at = big ? (1.57079637f - pw) - 4.37113883e-08f : pw;
+        at = copysignf(at, zx);
+        // atanh: polynomial for |z| <= 1/2, logarithm above
+        const float ay = fminf(fabsf(zy), 0.99999994f);   // |zy| < f < 1
+        const float ph = fmaf(zy * sy, poly_atanh_q(sy), zy);
+        const float lg = 0.34657359f * sfu_lg2((1.0f + ay) * sfu_rcp(1.0f - ay));
+        const float ah = ay <= 0.5f ? ph : copysignf(lg, zy);
+        ux = at * v.invf;
+        uy = ah * v.invf;
     }
-    ax = fmaf(axp, m.c, -ayp * m.s) + fmaf(m.g1, x, m.g2 * y);
-    ay = fmaf(axp, m.s, ayp * m.c) + fmaf(m.g2, x, -m.g1 * y);
+}
+
+// The two unit columns at one subpixel (fj, fi), given the row terms
+// r* = c0 + ci fi of the six affine coordinates.
+struct RowTerms {
+    float px, py, lx, ly, sx, sy;
+};
+
+__device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
+{
+    return RowTerms{fmaf(v.px.ci, fi, v.px.c0), fmaf(v.py.ci, fi, v.py.c0),
+                    fmaf(v.lx.ci, fi, v.lx.c0), fmaf(v.ly.ci, fi, v.ly.c0),
+                    fmaf(v.sx.ci, fi, v.sx.c0), fmaf(v.sy.ci, fi, v.sy.c0)};
+}
+
+__device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
+                                         float &il, float &is)
+{
+    // SIE in its frame (lens equation's deflection, Eq. 1)
+    float ux, uy;
+    sie_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
+    // lens light at theta (Eq. 2, first term)
+    il = sersic_scaled(fmaf(v.lx.cj, fj, r.lx), fmaf(v.ly.cj, fj, r.ly), v.khl, v.kll,
+                       v.bhl, v.bll);
+    // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
+    const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux, fmaf(v.q12h, uy, v.q12l * uy)));
+    const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux, fmaf(v.q22h, uy, v.q22l * uy)));
+    is = sersic_scaled(fmaf(v.sx.cj, fj, r.sx) - t1, fmaf(v.sy.cj, fj, r.sy) - t2, v.khs,
+                       v.kls, v.bhs, v.bls);
 }
 
 // ------------------------------------------------------ double-float
