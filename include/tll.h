@@ -121,6 +121,33 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B,
                            double *out, void *stream);
 
 /*
+ * tll_loglike_batch_noalloc -- tll_loglike_batch for callers that must not
+ * allocate device memory during the call: for example a process whose
+ * device memory is entirely reserved by another allocator (a framework's
+ * caching allocator, a fixed per-job budget), where cudaMalloc would fail,
+ * or a latency-critical sampler loop that cannot accept cudaMalloc/cudaFree
+ * stalls.  (tll_loglike_batch grows a lens-owned scratch buffer with
+ * cudaMalloc when B exceeds what it has seen.)  There is no counterpart in
+ * the paper; this is a deployment variant of the same computation.
+ *   Same arguments, results and asynchrony as tll_loglike_batch.
+ *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
+ *     them into several calls).
+ *   Scratch: a fixed 3 MiB array compiled into the library, held on every
+ *     GPU that loads it until the process exits.  All calls share it and it
+ *     keeps the last call's contents; each call rewrites the part it reads
+ *     before reading it.  Calls that overlap on the GPU (different streams,
+ *     different lenses) race on it: order them on one stream or synchronise.
+ *   Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   The call itself makes no cudaMalloc, cudaFree or other allocating call;
+ *   the lens must already exist (tll_create_lens allocates).
+ */
+#define TLL_NOALLOC_MAX_B 16384
+int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B,
+                              double *out, void *stream);
+
+/*
  * tll_model_image -- the blurred model image I^m (Eq. 3) of one vector with
  * its amplitudes: linear (NNLS) or fixed, per the lens's mode.
  *   params     host float32 [TLL_NPARAM]

@@ -808,8 +808,60 @@ int run_one(tll_lens *L, const float *params_host)
 
 }  // namespace
 
+// ------------------------------------------- no-allocation entry point
+// Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
+// that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
+// array in the module instead, so the call itself allocates nothing; every
+// GPU that loads this library holds it (3 MiB) until the process exits.
+constexpr int kNoAllocMaxB = 16384;
+static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
+
+namespace {
+float *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_kc on device `dev` (current), looked up once
+// per device: host code sees only a host-side stand-in for the symbol.
+int noalloc_scratch(int dev, float **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(TLL_ECUDA, "device id %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_kc);
+        if (e != cudaSuccess || !p)
+            return fail(TLL_ECUDA, "cudaGetSymbolAddress(no-allocation scratch): %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return TLL_OK;
+}
+}  // namespace
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *out,
+                              void *stream)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (B < 0) return fail(TLL_EINVAL, "negative batch size");
+    if (B > kNoAllocMaxB)
+        return fail(TLL_EINVAL,
+                    "batch of %d vectors exceeds the no-allocation limit of %d per call",
+                    B, kNoAllocMaxB);
+    if (B == 0) return TLL_OK;
+    if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
+    DeviceGuard gd(L->dev);
+    float *kc = nullptr;
+    const int rc = noalloc_scratch(L->dev, &kc);
+    if (rc) return rc;
+    // k_prologue writes all NCONST entries of each of the B blocks before
+    // k_loglike reads them on the same stream, so nothing needs clearing.
+    return run_batch(L, params, B, out, (cudaStream_t)stream, false, kc);
+}
+
 
 const char *tll_last_error(void) { return g_err; }
 

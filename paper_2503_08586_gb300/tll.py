@@ -19,12 +19,14 @@ NPARAM = 21
 AMP_LINEAR = 0
 AMP_FIXED = 1
 FLAG_DIRECT_CONV = 0x100
+NOALLOC_MAX_B = 16384
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(6)
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY"}
 
 # Every entry point include/tll.h declares (checked by the ABI test).
 SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
+           "tll_loglike_batch_noalloc",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last",
            "tll_destroy_lens", "tll_last_error", "tll_version")
@@ -63,6 +65,8 @@ def load(path: str | None = None):
     lib.tll_loglike_batch.restype = i
     lib.tll_loglike_batch_host.argtypes = [vp, fp, i, dp, vp]
     lib.tll_loglike_batch_host.restype = i
+    lib.tll_loglike_batch_noalloc.argtypes = [vp, fp, i, dp, vp]
+    lib.tll_loglike_batch_noalloc.restype = i
     lib.tll_model_image.argtypes = [vp, fp, fp, fp, dp]
     lib.tll_model_image.restype = i
     lib.tll_model_columns.argtypes = [vp, fp, fp, fp, i]
@@ -173,6 +177,25 @@ class Lens:
             raise ValueError("out must be a contiguous CUDA float64 [B]")
         _check(load().tll_loglike_batch(self._h, params.data_ptr(), B,
                                         out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def loglike_batch_noalloc(self, params, out, stream=None):
+        """As loglike_batch, but the call allocates no device memory: the
+        library's fixed scratch array is used (B <= NOALLOC_MAX_B; calls
+        that overlap on the GPU race on that array).  `out` must be given,
+        since creating it would allocate."""
+        import torch
+        if not (params.is_cuda and params.dtype == torch.float32
+                and params.dim() == 2 and params.shape[1] == NPARAM
+                and params.is_contiguous()):
+            raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+        B = params.shape[0]
+        if not (out.is_cuda and out.dtype == torch.float64
+                and out.numel() >= B and out.is_contiguous()):
+            raise ValueError("out must be a contiguous CUDA float64 [B]")
+        _check(load().tll_loglike_batch_noalloc(self._h, params.data_ptr(), B,
+                                                out.data_ptr(),
+                                                _stream_handle(stream)))
         return out
 
     # -- host batch (copies inside the call)
