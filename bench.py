@@ -57,6 +57,34 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
     return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def source_hash() -> str:
+    """Hash of the kernel sources (csrc/*.cu*, include/*.h)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2503_08586_gb300", "csrc", "*.cu"))
+                   + glob.glob(os.path.join(ROOT, "paper_2503_08586_gb300", "csrc", "*.cuh"))
+                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload: str):
+    """DRAM bytes per launch of k_loglike from the committed ncu summary,
+    or None if there is none or the kernel sources changed since."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_loglike_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+) source_hash: (\w+)", open(path).read())
+    if not m or m.group(2) != source_hash():
+        return None
+    return float(m.group(1))
+
+
 # ------------------------------------------------------------ helpers
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
@@ -256,7 +284,8 @@ def run_ours(args):
         "subpixel_evals_per_s": value * lens.ny * lens.nx * lens.sub ** 2,
         "kernel_ms": {"k_prologue": statistics.mean(pro_ms), "k_loglike": main_avg},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": captured_traffic(args.workload),
                      "kernel": "k_loglike",
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                                    f"x {SM_MAX_MHZ:.0f} MHz"},
