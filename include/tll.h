@@ -121,6 +121,37 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B,
                            double *out, void *stream);
 
 /*
+ * tll_batcher -- one launch over parameter batches of several lenses.
+ * A ragged multi-lens batch (lenses of different sizes, supersampling and
+ * PSFs, each with its own number of vectors) runs as one persistent launch:
+ * CTAs take vectors from a shared work counter, largest lenses first, and
+ * switch lens descriptors on the fly.  This is the batching of Sec. 3.1.4
+ * ("batched likelihood evaluations") extended across lenses.
+ *
+ * tll_batcher_create -- a reusable context on the current device.
+ *   use_graph  != 0: each run replays a captured CUDA graph (descriptor
+ *              uploads, counter reset, prologue, kernel) on a non-default
+ *              stream; the graph is re-captured when buffers grow or the
+ *              stream changes.  0: plain launches.
+ * tll_batcher_run -- enqueue n (lens, params, count, out) entries on stream.
+ *   lenses  n lens handles (repeats allowed), all on the batcher's device
+ *   params  n DEVICE pointers, float32 [count_k][21]
+ *   counts  n batch sizes (0 allowed)
+ *   outs    n DEVICE pointers, float64 [count_k]
+ *   Asynchronous; results as tll_loglike_batch for each entry.  The lens
+ *   handles' scratch is not used (the batcher owns its own), but the
+ *   params/out buffers must stay valid until the stream reaches the work.
+ *   Runs on one batcher are ordered by its internal staging fence.
+ * Errors: TLL_EINVAL, TLL_ENOMEM, TLL_ECUDA.
+ */
+typedef struct tll_batcher tll_batcher;
+int tll_batcher_create(int use_graph, tll_batcher **out);
+int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses,
+                    const float *const *params, const int *counts,
+                    double *const *outs, int n, void *stream);
+void tll_batcher_destroy(tll_batcher *b);
+
+/*
  * tll_loglike_batch_noalloc -- tll_loglike_batch for callers that must not
  * allocate device memory during the call: for example a process whose
  * device memory is entirely reserved by another allocator (a framework's

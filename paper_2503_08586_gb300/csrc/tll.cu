@@ -70,6 +70,8 @@ struct LensDev {
     float JCX, JCY;   // subpixel index of the grid centre, (n*s - 1)/2
     float inv_s2;
     int W, HL;        // padded layout: row stride, left zero columns
+    int img;          // image placement (IMG_*)
+    double XC, YC, d; // grid centre and subpixel step (for the prologue)
     const float *psf;    // [K*K] unit sum (direct path)
     const float *pu;     // [K] column factor over PSF rows (separable path)
     const float *pv;     // [K] row factor over PSF columns
@@ -456,43 +458,146 @@ __device__ __forceinline__ void conv_padded_dispatch(const LensDev &L, const Run
     }
 }
 
-// ------------------------------------------------------------- kernel
+// ------------------------------------------------------ per-vector body
+// Where the two images of lens L live in a CTA: lens / source images Il, Is
+// with pixel (i, j) at [i*stride + off + j], row-pass outputs Hl, Hs.
+struct ImgPtrs {
+    float *Il, *Is, *Hl, *Hs;
+    int stride, off;
+};
+
+__device__ __forceinline__ int psf_smem_floats(const LensDev &L, int img)
+{
+    return img == IMG_PADDED ? 0 : (L.sep ? 2 * L.K : L.K * L.K);
+}
+
+template <int IMG>
+__device__ __forceinline__ ImgPtrs img_ptrs(const LensDev &L, float *spsf, float *gslot)
+{
+    ImgPtrs P;
+    if (IMG == IMG_PADDED) {
+        const int rows = L.ny + 2 * L.h + kCR;   // zero rows above, below, last row block
+        P.Il = spsf;
+        P.Is = P.Il + rows * L.W;
+        P.Hl = P.Il; P.Hs = P.Is;
+        P.stride = L.W;
+        P.off = L.h * L.W + L.HL;
+    } else if (IMG == IMG_SMEM) {
+        P.Il = spsf + ((psf_smem_floats(L, IMG) + 3) & ~3);
+        P.Is = P.Il + L.npix;
+        P.Hl = P.Il;   // the row pass runs in place
+        P.Hs = P.Is;
+        P.stride = L.nx; P.off = 0;
+    } else {
+        P.Il = gslot;
+        P.Is = P.Il + L.npix;
+        P.Hl = P.Is + L.npix;
+        P.Hs = P.Hl + L.npix;
+        P.stride = L.nx; P.off = 0;
+    }
+    return P;
+}
+
+// Prepare a CTA's memory for lens L: zero the padded layout's halos (they
+// stay zero: only interior pixels are ever written) or stage the PSF.
+template <int IMG>
+__device__ __forceinline__ void setup_lens(const LensDev &L, float *spsf, int tid, int nthr)
+{
+    if (IMG == IMG_PADDED) {
+        const int n = 2 * (L.ny + 2 * L.h + kCR) * L.W;
+        for (int t = tid; t < n; t += nthr) spsf[t] = 0.0f;
+    } else {
+        const int K = L.K, nf = psf_smem_floats(L, IMG);
+        for (int t = tid; t < nf; t += nthr)
+            spsf[t] = L.sep ? (t < K ? L.pu[t] : L.pv[t - K]) : L.psf[t];
+    }
+}
+
+// One parameter vector (its constant block kc is valid): trace, convolve
+// with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
+// block barrier.
+template <int SUB, int IMG, bool WRITE>
+__device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
+                                            const float *kc, double *outp, const ImgPtrs &P,
+                                            const float *spsf, double *sred, int tid, int nthr)
+{
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int nx = L.nx, npix = L.npix;
+    {
+        const VecConst v = load_consts(kc);
+        trace_image<SUB>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
+    }
+    __syncthreads();
+    if (WRITE) {
+        for (int t = tid; t < npix; t += nthr) {
+            const int i = t / nx, j = t - i * nx;
+            R.wr_unblurred[t] = P.Il[i * P.stride + P.off + j];
+            R.wr_unblurred[npix + t] = P.Is[i * P.stride + P.off + j];
+        }
+        __syncthreads();
+    }
+
+    // (2)+(3) convolution with the fused weighted sums
+    float acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+    if (IMG == IMG_PADDED)
+        conv_padded_dispatch<WRITE>(L, R, P.Il, P.Is, acc, tid, nthr);
+    else
+        conv_generic<IMG == IMG_SMEM, WRITE>(L, R, spsf, P.Il, P.Is, P.Hl, P.Hs, acc, tid,
+                                             nthr);
+
+    // (3) warp reduction in double-float, block reduction in FP64
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
+            df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            sred[warp * 5 + k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double sacc = 0.0;
+        if (lane < 5)
+            for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
+        double S[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, sacc, k);
+        if (lane == 0) {
+            double sl, ss, ll;
+            finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
+            *outp = ll;
+            if (WRITE) {
+                for (int k = 0; k < 5; ++k) R.wr_res[k] = S[k];
+                R.wr_res[5] = sl;
+                R.wr_res[6] = ss;
+                R.wr_res[7] = ll;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------- one-lens kernel
 template <int SUB, int IMG, bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
-    const int K = L.K, nx = L.nx, ny = L.ny, npix = L.npix;
-    const int psf_floats = IMG == IMG_PADDED ? 0 : (L.sep ? 2 * K : K * K);
-    float *Il, *Is, *Hl, *Hs;
-    int stride = nx, off = 0;
-    if (IMG == IMG_PADDED) {
-        const int rows = ny + 2 * L.h + kCR;   // zero rows above, below, and for the last row block
-        Il = spsf;
-        Is = Il + rows * L.W;
-        Hl = Il; Hs = Is;
-        stride = L.W;
-        off = L.h * L.W + L.HL;
-        for (int t = tid; t < 2 * rows * L.W; t += nthr) Il[t] = 0.0f;
-    } else if (IMG == IMG_SMEM) {
-        Il = spsf + ((psf_floats + 3) & ~3);
-        Is = Il + npix;
-        Hl = Il;   // the row pass runs in place
-        Hs = Is;
-    } else {
-        Il = R.gscr + (size_t)blockIdx.x * 4 * npix;
-        Is = Il + npix;
-        Hl = Is + npix;
-        Hs = Hl + npix;
-    }
-    for (int t = tid; t < psf_floats; t += nthr)
-        spsf[t] = L.sep ? (t < K ? L.pu[t] : L.pv[t - K]) : L.psf[t];
+    const ImgPtrs P =
+        img_ptrs<IMG>(L, spsf, IMG == IMG_GLOBAL ? R.gscr + (size_t)blockIdx.x * 4 * L.npix : nullptr);
+    setup_lens<IMG>(L, spsf, tid, nthr);
     __syncthreads();
-
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
         if (kc[K_VALID] == 0.0f) {
@@ -502,65 +607,121 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
             }
             continue;
         }
-        {
-            const VecConst v = load_consts(kc);
-            trace_image<SUB>(L, v, Il, Is, stride, off, tid, nthr);
+        vector_body<SUB, IMG, WRITE>(L, R, kc, R.out + b, P, spsf, sred, tid, nthr);
+    }
+}
+
+// ----------------------------------------------------- multi-lens kernel
+// One launch over a work list of B_1 + ... + B_n vectors of n lenses
+// (different sizes, supersampling, PSFs).  Segment s covers items
+// [first, first + count) of lens `lens`, reading params[k] and writing
+// out[k].  CTAs take items from an atomic counter (largest lenses first, as
+// the host orders them) and copy a lens's descriptor into shared memory when
+// they switch lens.
+struct Segment {
+    int lens, first, count, pad;
+    const float *params;
+    double *out;
+};
+struct MultiHdr {
+    int total, nseg;
+};
+struct MultiArgs {
+    const LensDev *lenses;
+    const Segment *segs;
+    const MultiHdr *hdr;
+    float *kc;                 // [total][NCONST]
+    float *gscr;               // per-CTA global image slots (IMG_GLOBAL lenses)
+    long long gslot_floats;
+    int *counter;              // work counter, zero at launch
+    const double *bn_tab;
+};
+
+__device__ __forceinline__ int find_segment(const Segment *segs, int nseg, int t)
+{
+    int lo = 0, hi = nseg - 1;     // largest s with segs[s].first <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_prologue_multi(const __grid_constant__ MultiArgs A)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.hdr->total) return;
+    const Segment &sg = A.segs[find_segment(A.segs, A.hdr->nseg, t)];
+    const LensDev &L = A.lenses[sg.lens];
+    decode_vector(sg.params + (size_t)(t - sg.first) * NPAR, A.kc + (size_t)t * NCONST, L.XC,
+                  L.YC, L.d, A.bn_tab);
+}
+
+template <int SUB, int IMG>
+__device__ __noinline__ void vector_body_multi(const LensDev &L, const float *kc, double *outp,
+                                               float *spsf, float *gslot, double *sred,
+                                               int tid, int nthr)
+{
+    RunArgs R = {};
+    const ImgPtrs P = img_ptrs<IMG>(L, spsf, gslot);
+    vector_body<SUB, IMG, false>(L, R, kc, outp, P, spsf, sred, tid, nthr);
+}
+
+template <int IMG>
+__device__ __forceinline__ void body_multi_sub(const LensDev &L, const float *kc, double *outp,
+                                               float *spsf, float *gslot, double *sred,
+                                               int tid, int nthr)
+{
+    if (L.sub == 4) vector_body_multi<4, IMG>(L, kc, outp, spsf, gslot, sred, tid, nthr);
+    else if (L.sub == 5) vector_body_multi<5, IMG>(L, kc, outp, spsf, gslot, sred, tid, nthr);
+    else vector_body_multi<0, IMG>(L, kc, outp, spsf, gslot, sred, tid, nthr);
+}
+
+__global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constant__ MultiArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LensDev sL;
+    __shared__ int s_t, s_seg;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double *sred = reinterpret_cast<double *>(smem);
+    float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
+    float *gslot = A.gscr ? A.gscr + (size_t)blockIdx.x * A.gslot_floats : nullptr;
+    const int total = A.hdr->total, nseg = A.hdr->nseg;
+    int cur = -1;
+    for (;;) {
+        if (tid == 0) {
+            const int t = atomicAdd(A.counter, 1);
+            s_t = t;
+            s_seg = t < total ? find_segment(A.segs, nseg, t) : 0;
         }
         __syncthreads();
-        if (WRITE) {
-            for (int t = tid; t < npix; t += nthr) {
-                const int i = t / nx, j = t - i * nx;
-                R.wr_unblurred[t] = Il[i * stride + off + j];
-                R.wr_unblurred[npix + t] = Is[i * stride + off + j];
-            }
+        const int t = s_t;
+        if (t >= total) break;
+        const Segment sg = A.segs[s_seg];
+        if (sg.lens != cur) {
+            const unsigned *src = reinterpret_cast<const unsigned *>(A.lenses + sg.lens);
+            unsigned *dst = reinterpret_cast<unsigned *>(&sL);
+            for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
             __syncthreads();
+            if (sL.img == IMG_PADDED) setup_lens<IMG_PADDED>(sL, spsf, tid, nthr);
+            else if (sL.img == IMG_SMEM) setup_lens<IMG_SMEM>(sL, spsf, tid, nthr);
+            else setup_lens<IMG_GLOBAL>(sL, spsf, tid, nthr);
+            __syncthreads();
+            cur = sg.lens;
         }
-
-        // (2)+(3) convolution with the fused weighted sums
-        float acc[10];
-#pragma unroll
-        for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
-        if (IMG == IMG_PADDED)
-            conv_padded_dispatch<WRITE>(L, R, Il, Is, acc, tid, nthr);
+        const float *kc = A.kc + (size_t)t * NCONST;
+        double *outp = sg.out + (t - sg.first);
+        if (kc[K_VALID] == 0.0f) {
+            if (tid == 0) *outp = -INFINITY;
+            __syncthreads();
+            continue;
+        }
+        if (sL.img == IMG_PADDED)
+            body_multi_sub<IMG_PADDED>(sL, kc, outp, spsf, gslot, sred, tid, nthr);
+        else if (sL.img == IMG_SMEM)
+            body_multi_sub<IMG_SMEM>(sL, kc, outp, spsf, gslot, sred, tid, nthr);
         else
-            conv_generic<IMG == IMG_SMEM, WRITE>(L, R, spsf, Il, Is, Hl, Hs, acc, tid, nthr);
-
-        // (3) warp reduction in double-float, block reduction in FP64
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
-                const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
-                df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
-            }
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                sred[warp * 5 + k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double sacc = 0.0;
-            if (lane < 5)
-                for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
-            double S[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, sacc, k);
-            if (lane == 0) {
-                double sl, ss, ll;
-                finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
-                R.out[b] = ll;
-                if (WRITE) {
-                    for (int k = 0; k < 5; ++k) R.wr_res[k] = S[k];
-                    R.wr_res[5] = sl;
-                    R.wr_res[6] = ss;
-                    R.wr_res[7] = ll;
-                }
-            }
-        }
-        __syncthreads();
+            body_multi_sub<IMG_GLOBAL>(sL, kc, outp, spsf, gslot, sred, tid, nthr);
     }
 }
 
@@ -663,7 +824,9 @@ LensDev lens_dev(const tll_lens *L)
     d.inv_s2 = 1.0f / (float)(L->sub * L->sub);
     d.psf = L->d_psf; d.pu = L->d_pu; d.pv = L->d_pv; d.wpack = L->d_wpack;
     d.dWd = L->dWd; d.lognorm = L->lognorm;
-    d.W = L->W; d.HL = L->HL;
+    d.W = L->W; d.HL = L->HL; d.img = L->img;
+    grid_centre(L, &d.XC, &d.YC);
+    d.d = (double)L->dpix / L->sub;
     for (int k = 0; k < kMaxTaps; ++k) {
         d.tu[k] = k < (int)L->taps_u.size() ? L->taps_u[k] : 0.0f;
         d.tv[k] = k < (int)L->taps_v.size() ? L->taps_v[k] : 0.0f;
@@ -808,6 +971,114 @@ int run_one(tll_lens *L, const float *params_host)
 
 }  // namespace
 
+// ------------------------------------------------------- batch context
+// Reusable buffers for multi-lens launches (and their CUDA graph).
+struct tll_batcher {
+    int dev = 0, nsm = 0, optin = 0, dyn_smem = 0;
+    bool use_graph = false;
+    int cap_lenses = 0, cap_segs = 0, cap_items = 0;
+    long long gslot_floats = 0;
+    LensDev *d_lenses = nullptr, *h_lenses = nullptr;   // h_*: pinned staging
+    Segment *d_segs = nullptr, *h_segs = nullptr;
+    MultiHdr *d_hdr = nullptr, *h_hdr = nullptr;
+    float *d_kc = nullptr, *d_gscr = nullptr;
+    int *d_counter = nullptr;
+    const double *bn_tab = nullptr;
+    cudaEvent_t staged = nullptr;      // staging may be refilled after this
+    bool staged_pending = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;    // stream the graph was captured on
+    long long launches = 0;
+};
+
+namespace {
+
+void batcher_free_buffers(tll_batcher *b)
+{
+    void *dev[] = {b->d_lenses, b->d_segs, b->d_hdr, b->d_kc, b->d_gscr, b->d_counter};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    void *host[] = {b->h_lenses, b->h_segs, b->h_hdr};
+    for (void *p : host)
+        if (p) cudaFreeHost(p);
+    b->d_lenses = b->h_lenses = nullptr;
+    b->d_segs = b->h_segs = nullptr;
+    b->d_hdr = b->h_hdr = nullptr;
+    b->d_kc = b->d_gscr = nullptr;
+    b->d_counter = nullptr;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+}
+
+// Grow every buffer to hold (lenses, segs, items, gslot); the graph (which
+// bakes in the buffer addresses and copy sizes) is dropped when anything grows.
+int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long gslot)
+{
+    if (lenses <= b->cap_lenses && segs <= b->cap_segs && items <= b->cap_items &&
+        gslot <= b->gslot_floats && b->d_kc)
+        return TLL_OK;
+    if (b->staged_pending) CUDA_TRY(cudaEventSynchronize(b->staged));
+    CUDA_TRY(cudaDeviceSynchronize());
+    const int cl = std::max(lenses, std::max(2 * b->cap_lenses, 16));
+    const int cs = std::max(segs, std::max(2 * b->cap_segs, 64));
+    const int ci = std::max(items, std::max(2 * b->cap_items, 4096));
+    const long long cg = std::max(gslot, b->gslot_floats);
+    batcher_free_buffers(b);
+    CUDA_TRY(cudaMalloc(&b->d_lenses, cl * sizeof(LensDev)));
+    CUDA_TRY(cudaMalloc(&b->d_segs, cs * sizeof(Segment)));
+    CUDA_TRY(cudaMalloc(&b->d_hdr, sizeof(MultiHdr)));
+    CUDA_TRY(cudaMalloc(&b->d_kc, (size_t)ci * NCONST * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&b->d_counter, sizeof(int)));
+    if (cg > 0) CUDA_TRY(cudaMalloc(&b->d_gscr, (size_t)b->nsm * cg * sizeof(float)));
+    CUDA_TRY(cudaMallocHost(&b->h_lenses, cl * sizeof(LensDev)));
+    CUDA_TRY(cudaMallocHost(&b->h_segs, cs * sizeof(Segment)));
+    CUDA_TRY(cudaMallocHost(&b->h_hdr, sizeof(MultiHdr)));
+    b->cap_lenses = cl;
+    b->cap_segs = cs;
+    b->cap_items = ci;
+    b->gslot_floats = cg;
+    return TLL_OK;
+}
+
+MultiArgs batcher_args(const tll_batcher *b)
+{
+    MultiArgs A;
+    A.lenses = b->d_lenses;
+    A.segs = b->d_segs;
+    A.hdr = b->d_hdr;
+    A.kc = b->d_kc;
+    A.gscr = b->d_gscr;
+    A.gslot_floats = b->gslot_floats;
+    A.counter = b->d_counter;
+    A.bn_tab = b->bn_tab;
+    return A;
+}
+
+// The launch sequence: stage descriptors, reset the counter, prologue,
+// multi-lens kernel.  `full` copies whole staging buffers (graph form,
+// fixed sizes); otherwise only what this call uses.
+int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaStream_t st)
+{
+    const int cl = full ? b->cap_lenses : nl, cs = full ? b->cap_segs : ns;
+    const int items = full ? b->cap_items : total;
+    CUDA_TRY(cudaMemcpyAsync(b->d_lenses, b->h_lenses, cl * sizeof(LensDev),
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_segs, b->h_segs, cs * sizeof(Segment),
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(MultiHdr), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    const MultiArgs A = batcher_args(b);
+    k_prologue_multi<<<(items + 127) / 128, 128, 0, st>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    k_loglike_multi<<<b->nsm, kThreads, b->dyn_smem, st>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    return TLL_OK;
+}
+
+}  // namespace
+
 // ------------------------------------------- no-allocation entry point
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
@@ -841,6 +1112,138 @@ int noalloc_scratch(int dev, float **out)
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+int tll_batcher_create(int use_graph, tll_batcher **out)
+{
+    if (!out) return fail(TLL_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1)
+        return fail(TLL_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    tll_batcher *b = new (std::nothrow) tll_batcher;
+    if (!b) return fail(TLL_ENOMEM, "host allocation failed");
+    int rc = TLL_OK;
+    auto bad = [&](int code) { delete b; return code; };
+    if (cudaGetDevice(&b->dev) != cudaSuccess) return bad(fail(TLL_ECUDA, "cudaGetDevice"));
+    if (cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev) !=
+            cudaSuccess)
+        return bad(fail(TLL_ECUDA, "device attributes"));
+    {   // dynamic shared memory = the opt-in maximum minus the static part
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_loglike_multi) != cudaSuccess)
+            return bad(fail(TLL_ECUDA, "k_loglike_multi attributes"));
+        b->dyn_smem = b->optin - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(k_loglike_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 b->dyn_smem) != cudaSuccess)
+            return bad(fail(TLL_ECUDA, "k_loglike_multi shared memory"));
+    }
+    if ((rc = bn_table(b->dev, &b->bn_tab))) return bad(rc);
+    if (cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess)
+        return bad(fail(TLL_ECUDA, "cudaEventCreate"));
+    b->use_graph = use_graph != 0;
+    *out = b;
+    return TLL_OK;
+}
+
+void tll_batcher_destroy(tll_batcher *b)
+{
+    if (!b) return;
+    DeviceGuard gd(b->dev);
+    if (b->staged_pending) cudaEventSynchronize(b->staged);
+    batcher_free_buffers(b);
+    if (b->staged) cudaEventDestroy(b->staged);
+    delete b;
+}
+
+int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const *params,
+                    const int *counts, double *const *outs, int n, void *stream)
+{
+    if (!b) return fail(TLL_EINVAL, "batcher is NULL");
+    if (n < 0) return fail(TLL_EINVAL, "negative lens count");
+    if (n == 0) return TLL_OK;
+    if (!lenses || !params || !counts || !outs) return fail(TLL_EINVAL, "NULL array");
+    DeviceGuard gd(b->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    // distinct lenses, segments ordered by cost (largest lenses first)
+    std::vector<tll_lens *> uniq;
+    std::vector<int> lid(n), order(n);
+    long long total = 0, gslot = 0;
+    for (int k = 0; k < n; ++k) {
+        tll_lens *L = lenses[k];
+        if (!L) return fail(TLL_EINVAL, "lens %d is NULL", k);
+        if (L->dev != b->dev) return fail(TLL_EINVAL, "lens %d is on another device", k);
+        if (counts[k] < 0) return fail(TLL_EINVAL, "negative count for lens %d", k);
+        if (counts[k] > 0 && (!params[k] || !outs[k]))
+            return fail(TLL_EINVAL, "NULL params/out for lens %d", k);
+        int u = 0;
+        while (u < (int)uniq.size() && uniq[u] != L) ++u;
+        if (u == (int)uniq.size()) uniq.push_back(L);
+        lid[k] = u;
+        order[k] = k;
+        total += counts[k];
+        if (L->img == IMG_GLOBAL) gslot = std::max(gslot, (long long)4 * L->npix);
+        if (L->smem_bytes > (size_t)b->dyn_smem)
+            return fail(TLL_EINVAL, "lens %d needs more shared memory than the batch kernel has", k);
+    }
+    if (total == 0) return TLL_OK;
+    if (total > (1LL << 30)) return fail(TLL_EINVAL, "batch too large");
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const long long wa = (long long)lenses[a]->npix * lenses[a]->sub * lenses[a]->sub;
+        const long long wc = (long long)lenses[c]->npix * lenses[c]->sub * lenses[c]->sub;
+        return wa > wc;
+    });
+    int rc = batcher_reserve(b, (int)uniq.size(), n, (int)total, gslot);
+    if (rc) return rc;
+    if (b->staged_pending) CUDA_TRY(cudaEventSynchronize(b->staged));
+    for (size_t u = 0; u < uniq.size(); ++u) b->h_lenses[u] = lens_dev(uniq[u]);
+    int first = 0, ns = 0;
+    for (int k : order) {
+        if (counts[k] == 0) continue;
+        Segment &sg = b->h_segs[ns++];
+        sg.lens = lid[k];
+        sg.first = first;
+        sg.count = counts[k];
+        sg.pad = 0;
+        sg.params = params[k];
+        sg.out = outs[k];
+        first += counts[k];
+    }
+    b->h_hdr->total = (int)total;
+    b->h_hdr->nseg = ns;
+    const bool graph = b->use_graph && st != nullptr;
+    if (graph) {
+        if (!b->gexec || b->gstream != st) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = batcher_enqueue(b, 0, 0, 0, true, st);
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return fail(TLL_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess)
+                return fail(TLL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            b->gstream = st;
+        }
+        CUDA_TRY(cudaGraphLaunch(b->gexec, st));
+    } else {
+        rc = batcher_enqueue(b, (int)uniq.size(), ns, (int)total, false, st);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(b->staged, st));
+    b->staged_pending = true;
+    ++b->launches;
+    return TLL_OK;
+}
 
 int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *out,
                               void *stream)

@@ -26,7 +26,8 @@ _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY"}
 
 # Every entry point include/tll.h declares (checked by the ABI test).
 SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
-           "tll_loglike_batch_noalloc",
+           "tll_loglike_batch_noalloc", "tll_batcher_create", "tll_batcher_run",
+           "tll_batcher_destroy",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last",
            "tll_destroy_lens", "tll_last_error", "tll_version")
@@ -79,6 +80,14 @@ def load(path: str | None = None):
     lib.tll_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float)]
     lib.tll_profile_last.restype = i
+    lib.tll_batcher_create.argtypes = [i, ctypes.POINTER(vp)]
+    lib.tll_batcher_create.restype = i
+    lib.tll_batcher_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
+                                    i, vp]
+    lib.tll_batcher_run.restype = i
+    lib.tll_batcher_destroy.argtypes = [vp]
+    lib.tll_batcher_destroy.restype = None
     lib.tll_destroy_lens.argtypes = [vp]
     lib.tll_destroy_lens.restype = None
     lib.tll_last_error.argtypes = []
@@ -260,6 +269,52 @@ class Lens:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batcher:
+    """One persistent launch over the parameter batches of several lenses
+    (ragged sizes), optionally replayed as a CUDA graph."""
+
+    def __init__(self, use_graph: bool = True):
+        h = ctypes.c_void_p()
+        _check(load().tll_batcher_create(1 if use_graph else 0, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, lenses, params, outs=None, stream=None):
+        """lenses: list of Lens; params: list of CUDA float32 [B_k, 21];
+        returns the list of CUDA float64 [B_k] outputs (asynchronous)."""
+        import torch
+        n = len(lenses)
+        if len(params) != n:
+            raise ValueError("one params tensor per lens")
+        if outs is None:
+            outs = [torch.empty(p.shape[0], dtype=torch.float64, device=p.device)
+                    for p in params]
+        for p, o in zip(params, outs):
+            if not (p.is_cuda and p.dtype == torch.float32 and p.is_contiguous()
+                    and p.dim() == 2 and p.shape[1] == NPARAM):
+                raise ValueError("params must be contiguous CUDA float32 [B, 21]")
+            if not (o.is_cuda and o.dtype == torch.float64 and o.is_contiguous()
+                    and o.numel() >= p.shape[0]):
+                raise ValueError("outs must be contiguous CUDA float64 [B]")
+        arr_l = (ctypes.c_void_p * n)(*[L.handle.value for L in lenses])
+        arr_p = (ctypes.c_void_p * n)(*[p.data_ptr() for p in params])
+        arr_c = (ctypes.c_int * n)(*[p.shape[0] for p in params])
+        arr_o = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        _check(load().tll_batcher_run(self._h, arr_l, arr_p, arr_c, arr_o, n,
+                                      _stream_handle(stream)))
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().tll_batcher_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def columns_renderer(pixel_scale, sub, psf, ny, nx):
