@@ -42,6 +42,8 @@
 #ifndef TLL_H
 #define TLL_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -152,6 +154,66 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses,
 void tll_batcher_destroy(tll_batcher *b);
 
 /*
+ * Continuous-batching server.  The paper's sampler calls the likelihood in
+ * batches of proposals (Sec. 3.1.4) and names host-device transfers and
+ * one-lens-at-a-time GPU use as its bottleneck (Sec. 3.1.4, 4.2); serving
+ * many lenses at once on one GPU has no counterpart in the paper and is a
+ * deployment layer over tll_batcher.
+ *
+ * A job is one observed lens kept on the device; it is admitted if its
+ * device footprint fits the remaining budget (else TLL_EBUSY: retry after
+ * another job closes).  A request is one parameter batch of one job, from
+ * host memory.  A launcher thread merges all pending requests (of any job)
+ * into one multi-lens launch per free slot; up to max_inflight launches run
+ * on their own streams, so work that arrives while others run joins the
+ * next launch and overlaps on the GPU.  Each result is the same as the
+ * job's own tll_loglike_batch (one vector never depends on another).
+ */
+typedef struct tll_server tll_server;
+typedef struct {
+    size_t hbm_budget_bytes;    /* device bytes open jobs may hold; 0: no limit */
+    int max_jobs;               /* job slots */
+    int max_vectors_per_launch; /* merge cap per launch, and the largest request */
+    int max_inflight;           /* launches in flight, 1..4 */
+    int coalesce;               /* 1: merge pending requests; 0: one per launch */
+    int use_graph;              /* replay each launch as a CUDA graph */
+} tll_server_config_t;
+typedef struct {
+    long long launches, vectors, requests, admissions_refused, pending, inflight;
+    size_t hbm_used_bytes;
+    int open_jobs;
+    double latency_p50_ms, latency_p99_ms, latency_max_ms; /* submit -> result,
+                                                              last 65536 requests */
+} tll_server_stats_t;
+
+/* Create a server on the current device (starts two host threads). */
+int tll_server_create(const tll_server_config_t *cfg, tll_server **out);
+/* Admit a lens (arguments as tll_create_lens); *job_id >= 0 on success,
+ * TLL_EBUSY when the budget or the job slots are exhausted. */
+int tll_server_open_job(tll_server *S, const float *image, const float *noise,
+                        const float *psf, int psf_size, const tll_grid_t *grid,
+                        int flags, int *job_id);
+/* Release a job; TLL_EBUSY while it has requests not yet completed. */
+int tll_server_close_job(tll_server *S, int job_id);
+/* Queue B vectors (host float32 [B][21]) of a job; results go to out (host
+ * float64 [B]).  Both buffers must stay valid until the request completes.
+ * 1 <= B <= max_vectors_per_launch. */
+int tll_server_submit(tll_server *S, int job_id, const float *params, int B,
+                      double *out, long long *request_id);
+/* *done = 1 once the request's results are in out. */
+int tll_server_poll(tll_server *S, long long request_id, int *done);
+/* Wait for a request (timeout_ms < 0: no limit; TLL_ETIMEOUT when it runs
+ * out, the request stays valid); on success the request is released and
+ * *latency_ms (may be NULL) is its submit-to-result time. */
+int tll_server_wait(tll_server *S, long long request_id, int timeout_ms,
+                    double *latency_ms);
+int tll_server_stats(tll_server *S, tll_server_stats_t *st);
+/* Finish queued work, stop the threads, release every job. */
+void tll_server_destroy(tll_server *S);
+/* Message for the last server error on the calling thread. */
+const char *tll_server_last_error(void);
+
+/*
  * tll_loglike_batch_noalloc -- tll_loglike_batch for callers that must not
  * allocate device memory during the call: for example a process whose
  * device memory is entirely reserved by another allocator (a framework's
@@ -210,6 +272,10 @@ int tll_model_columns(tll_lens *L, const float *params, float *lens_out,
  */
 int tll_profile_enable(tll_lens *L, int on);
 int tll_profile_last(tll_lens *L, float *prologue_ms, float *main_ms);
+
+/* Device memory a lens currently holds, in bytes (its data, the model
+ * buffers, and the scratch it has grown). */
+int tll_lens_footprint(const tll_lens *L, size_t *bytes);
 
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,

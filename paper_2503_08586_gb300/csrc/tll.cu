@@ -762,6 +762,7 @@ struct tll_lens {
     int grid_cap = 0;
     size_t smem_bytes = 0;
     const double *bn_tab = nullptr;   // per-device b_n table (not owned)
+    size_t dev_bytes = 0;             // device memory this lens holds
     cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
     bool prof_on = false, prof_recorded = false;
 };
@@ -891,6 +892,7 @@ int ensure_kc(tll_lens *L, int B)
     float *p = nullptr;
     CUDA_TRY(cudaMalloc(&p, (size_t)cap * NCONST * sizeof(float)));
     if (L->d_kc) cudaFree(L->d_kc);
+    L->dev_bytes += ((size_t)cap - L->kc_cap) * NCONST * sizeof(float);
     L->d_kc = p;
     L->kc_cap = cap;
     return TLL_OK;
@@ -938,6 +940,7 @@ int configure(tll_lens *L)
     if (L->img == IMG_GLOBAL) {
         const size_t n = (size_t)L->grid_cap * 4 * L->npix;
         CUDA_TRY(cudaMalloc(&L->d_gscr, n * sizeof(float)));
+        L->dev_bytes += n * sizeof(float);
     }
     return TLL_OK;
 }
@@ -1368,6 +1371,7 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         if (e != cudaSuccess)
             return fail(e == cudaErrorMemoryAllocation ? TLL_ENOMEM : TLL_ECUDA,
                         "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        L->dev_bytes += bytes;
         return TLL_OK;
     };
     if ((rc = alloc((void **)&L->d_psf, K * K * sizeof(float))) ||
@@ -1406,6 +1410,13 @@ void tll_destroy_lens(tll_lens *L)
     if (!L) return;
     DeviceGuard gd(L->dev);
     free_lens(L);
+}
+
+int tll_lens_footprint(const tll_lens *L, size_t *bytes)
+{
+    if (!L || !bytes) return fail(TLL_EINVAL, "NULL argument");
+    *bytes = L->dev_bytes;
+    return TLL_OK;
 }
 
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
@@ -1480,6 +1491,7 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
         }
         if (L->d_stage_p) cudaFree(L->d_stage_p);
         if (L->d_stage_o) cudaFree(L->d_stage_o);
+        L->dev_bytes += ((size_t)cap - L->stage_cap) * (NPAR * sizeof(float) + sizeof(double));
         L->d_stage_p = p;
         L->d_stage_o = o;
         L->stage_cap = cap;

@@ -27,7 +27,10 @@ _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY"}
 # Every entry point include/tll.h declares (checked by the ABI test).
 SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_loglike_batch_noalloc", "tll_batcher_create", "tll_batcher_run",
-           "tll_batcher_destroy",
+           "tll_batcher_destroy", "tll_lens_footprint", "tll_server_create",
+           "tll_server_open_job", "tll_server_close_job", "tll_server_submit",
+           "tll_server_poll", "tll_server_wait", "tll_server_stats",
+           "tll_server_destroy", "tll_server_last_error",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last",
            "tll_destroy_lens", "tll_last_error", "tll_version")
@@ -43,6 +46,21 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("pixel_scale", ctypes.c_float), ("sub", ctypes.c_int),
                 ("x0", ctypes.c_float), ("y0", ctypes.c_float)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
+                ("max_vectors_per_launch", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("coalesce", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("vectors", ctypes.c_longlong),
+                ("requests", ctypes.c_longlong), ("admissions_refused", ctypes.c_longlong),
+                ("pending", ctypes.c_longlong), ("inflight", ctypes.c_longlong),
+                ("hbm_used_bytes", ctypes.c_size_t), ("open_jobs", ctypes.c_int),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -88,6 +106,28 @@ def load(path: str | None = None):
     lib.tll_batcher_run.restype = i
     lib.tll_batcher_destroy.argtypes = [vp]
     lib.tll_batcher_destroy.restype = None
+    sz = ctypes.c_size_t
+    lib.tll_lens_footprint.argtypes = [vp, ctypes.POINTER(sz)]
+    lib.tll_lens_footprint.restype = i
+    lib.tll_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.tll_server_create.restype = i
+    lib.tll_server_open_job.argtypes = [vp, fp, fp, fp, i, ctypes.POINTER(Grid), i,
+                                        ctypes.POINTER(ctypes.c_int)]
+    lib.tll_server_open_job.restype = i
+    lib.tll_server_close_job.argtypes = [vp, i]
+    lib.tll_server_close_job.restype = i
+    lib.tll_server_submit.argtypes = [vp, i, fp, i, dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.tll_server_submit.restype = i
+    lib.tll_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+    lib.tll_server_poll.restype = i
+    lib.tll_server_wait.argtypes = [vp, ctypes.c_longlong, i, ctypes.POINTER(ctypes.c_double)]
+    lib.tll_server_wait.restype = i
+    lib.tll_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.tll_server_stats.restype = i
+    lib.tll_server_destroy.argtypes = [vp]
+    lib.tll_server_destroy.restype = None
+    lib.tll_server_last_error.argtypes = []
+    lib.tll_server_last_error.restype = ctypes.c_char_p
     lib.tll_destroy_lens.argtypes = [vp]
     lib.tll_destroy_lens.restype = None
     lib.tll_last_error.argtypes = []
@@ -309,6 +349,98 @@ class Batcher:
         if getattr(self, "_h", None) is not None and self._h.value:
             load().tll_batcher_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scheck(rc: int):
+    if rc != OK:
+        raise TLLError(rc, load().tll_server_last_error().decode(errors="replace"))
+
+
+class Server:
+    """Continuous-batching server (see tll.h): jobs are lenses admitted by
+    device-memory footprint; requests are host parameter batches merged
+    across jobs into multi-lens launches."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_jobs: int = 256,
+                 max_vectors_per_launch: int = 16384, max_inflight: int = 2,
+                 coalesce: bool = True, use_graph: bool = True):
+        cfg = ServerConfig(hbm_budget_bytes, max_jobs, max_vectors_per_launch,
+                           max_inflight, 1 if coalesce else 0, 1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        _scheck(load().tll_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+        self.max_vectors = max_vectors_per_launch
+
+    def open_job(self, image, noise, psf, pixel_scale, sub, x0=None, y0=None,
+                 mode=AMP_LINEAR):
+        """Admit a lens; returns its job id, or None when it does not fit
+        the budget / slots now (TLL_EBUSY)."""
+        img = np.ascontiguousarray(image, dtype=np.float32)
+        nse = np.ascontiguousarray(noise, dtype=np.float32)
+        k = np.ascontiguousarray(psf, dtype=np.float32)
+        ny, nx = img.shape
+        x0 = -(nx - 1) * pixel_scale / 2.0 if x0 is None else x0
+        y0 = -(ny - 1) * pixel_scale / 2.0 if y0 is None else y0
+        g = Grid(nx, ny, pixel_scale, sub, x0, y0)
+        jid = ctypes.c_int(-1)
+        rc = load().tll_server_open_job(self._h, img.ctypes.data, nse.ctypes.data,
+                                        k.ctypes.data, k.shape[0], ctypes.byref(g),
+                                        mode, ctypes.byref(jid))
+        if rc == EBUSY:
+            return None
+        _scheck(rc)
+        return jid.value
+
+    def close_job(self, job: int) -> bool:
+        """True when closed; False while it still has requests in flight."""
+        rc = load().tll_server_close_job(self._h, job)
+        if rc == EBUSY:
+            return False
+        _scheck(rc)
+        return True
+
+    def submit(self, job: int, params, out=None) -> int:
+        """Queue a host batch; returns a request id.  params: float32
+        [B, 21] (numpy or pinned CPU tensor), kept alive until waited."""
+        p, keep = _host_ptr(params, np.float32)
+        B = int(np.prod(keep.shape)) // NPARAM
+        if out is None:
+            out = np.empty(B, dtype=np.float64)
+        o, okeep = _host_ptr(out, np.float64)
+        rid = ctypes.c_longlong()
+        _scheck(load().tll_server_submit(self._h, job, p, B, o, ctypes.byref(rid)))
+        self._keep[rid.value] = (keep, okeep, out)
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        d = ctypes.c_int()
+        _scheck(load().tll_server_poll(self._h, rid, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        """(out array, latency ms); raises TLLError(ETIMEOUT) on timeout."""
+        lat = ctypes.c_double()
+        _scheck(load().tll_server_wait(self._h, rid, timeout_ms, ctypes.byref(lat)))
+        keep = self._keep.pop(rid)
+        return keep[2], lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _scheck(load().tll_server_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().tll_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):  # pragma: no cover
         try:

@@ -79,3 +79,15 @@ def test_no_silent_cpu_fallback(lib):
     with pytest.raises(tll.TLLError) as ei:
         tll.Lens(np.zeros((4, 4)), np.ones((4, 4)), np.ones((3, 3)), 0.1, 2)
     assert ei.value.code == tll.ECUDA
+
+
+def test_server_refuses_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tll.TLLError) as ei:
+        tll.Server(max_jobs=2)
+    assert ei.value.code in (tll.ECUDA, tll.ENOMEM)
+    cfg = tll.ServerConfig(0, 0, 16, 1, 1, 0)          # max_jobs = 0
+    h = ctypes.c_void_p()
+    assert lib.tll_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tll.EINVAL

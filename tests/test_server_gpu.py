@@ -1,0 +1,144 @@
+"""The continuous-batching server (tll_server_*): each request's result is
+the same alone and when merged with other jobs' requests into shared
+launches, and equals the job's own one-lens evaluation; admission by
+device-memory budget; error codes."""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2503_08586_gb300 import build, tll
+from paper_2503_08586_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(64, 64, 0.05, 4, 11), (100, 100, 0.074, 4, 21), (80, 60, 0.06, 5, 15),
+          (48, 48, 0.05, 2, 9)]
+
+
+@pytest.fixture(scope="module")
+def lenses():
+    build.build()
+    tll.load()
+    assert torch.cuda.is_available()
+    out = []
+    for k, (ny, nx, dpix, sub, ks) in enumerate(SHAPES):
+        psf = W.gaussian_psf(ks, 1.9)
+        rng = np.random.Generator(np.random.PCG64(900 + k))
+        render = oracle.columns_renderer(dpix, sub, psf, ny, nx)
+        sl = W.synth_lens(rng, ny, nx, dpix, sub, psf, render, "sky+poisson")
+        batches = [W.shrinking_draws(rng, sl.truth, int(rng.integers(50, 400)))
+                   for _ in range(4)]
+        out.append((sl, batches))
+    return out
+
+
+def _open(S, sl):
+    return S.open_job(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+
+
+def _reference(sl, P):
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+    o = g.loglike_batch(torch.from_numpy(P).cuda())
+    torch.cuda.synchronize()
+    r = o.cpu().numpy()
+    g.close()
+    return r
+
+
+@pytest.mark.parametrize("coalesce,graph", [(True, True), (True, False), (False, False)])
+def test_same_alone_and_in_the_mix(lenses, coalesce, graph):
+    # alone: one job at a time, one request at a time
+    alone = []
+    for sl, batches in lenses:
+        S = tll.Server(max_jobs=4, coalesce=coalesce, use_graph=graph)
+        j = _open(S, sl)
+        res = []
+        for P in batches:
+            out, _ = S.wait(S.submit(j, P))
+            res.append(out.copy())
+        assert S.close_job(j)
+        S.close()
+        alone.append(res)
+    # mix: all jobs open, every job submitting from its own thread
+    S = tll.Server(max_jobs=8, coalesce=coalesce, use_graph=graph, max_inflight=2)
+    jobs = [_open(S, sl) for sl, _ in lenses]
+    mixed = [None] * len(lenses)
+    errors = []
+
+    def run(k):
+        try:
+            rids = [S.submit(jobs[k], P) for P in lenses[k][1]]
+            mixed[k] = [S.wait(r)[0].copy() for r in rids]
+        except Exception as e:  # pragma: no cover
+            errors.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(len(lenses))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    st = S.stats()
+    assert st["requests"] == sum(len(b) for _, b in lenses)
+    if coalesce:
+        assert st["launches"] <= st["requests"]
+    for k, (sl, batches) in enumerate(lenses):
+        for b, P in enumerate(batches):
+            a, m = alone[k][b], mixed[k][b]
+            fin = np.isfinite(a)
+            assert np.array_equal(np.isneginf(a), np.isneginf(m))
+            assert np.allclose(m[fin], a[fin], rtol=1e-12, atol=1e-9)
+        ref = _reference(sl, batches[0])
+        assert np.allclose(alone[k][0], ref, rtol=1e-12, atol=1e-9)
+    for j in jobs:
+        assert S.close_job(j)
+    S.close()
+
+
+def test_admission_by_footprint(lenses):
+    sl0, _ = lenses[0]
+    g = tll.Lens(sl0.data, sl0.noise, sl0.psf, sl0.pixel_scale, sl0.sub, sl0.x0, sl0.y0)
+    import ctypes
+    b = ctypes.c_size_t()
+    assert tll.load().tll_lens_footprint(g.handle, ctypes.byref(b)) == tll.OK
+    g.close()
+    one = b.value
+    assert one > 16 * 64 * 64
+    S = tll.Server(hbm_budget_bytes=int(one * 1.5), max_jobs=4)
+    j1 = _open(S, sl0)
+    assert j1 is not None
+    assert _open(S, sl0) is None                     # over budget: EBUSY
+    assert S.stats()["admissions_refused"] == 1
+    assert S.close_job(j1)
+    j2 = _open(S, sl0)                               # memory freed: admitted
+    assert j2 is not None
+    assert S.stats()["hbm_used_bytes"] == one
+    S.close()
+
+
+def test_errors_and_timeouts(lenses):
+    sl, batches = lenses[1]
+    S = tll.Server(max_jobs=2, max_vectors_per_launch=1024)
+    j = _open(S, sl)
+    with pytest.raises(tll.TLLError) as e:
+        S.submit(j + 1, batches[0])                  # no such job
+    assert e.value.code == tll.EINVAL
+    with pytest.raises(tll.TLLError) as e:
+        S.submit(j, np.zeros((2000, 21), np.float32))  # over the launch cap
+    assert e.value.code == tll.EINVAL
+    big = W.shrinking_draws(np.random.default_rng(1), sl.truth, 1024)
+    rid = S.submit(j, big)
+    closed_early = S.close_job(j)                    # outstanding -> False
+    try:
+        out, lat = S.wait(rid, timeout_ms=0)
+    except tll.TLLError as ex:
+        assert ex.code == tll.ETIMEOUT
+        out, lat = S.wait(rid)
+    assert np.all(np.isfinite(out)) and lat > 0
+    if not closed_early:
+        assert S.close_job(j)
+    S.close()
