@@ -166,6 +166,81 @@ def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096):
             "wall_s": wall}
 
 
+# ------------------------------------------------------------ request stream
+def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload: str,
+               seed_offset: int = 20):
+    """A Poisson stream of lens-modelling jobs through the server, each a
+    closed-loop synthetic sampler: `iters` batches of U{500..5000} vectors
+    drawn from a Gaussian shrinking around its lens's truth, each submitted
+    from host memory after the previous result came back.  coalesce=True is
+    the served path (requests of all jobs merged per launch, 2 launches in
+    flight, graph replay); False is the plain path (one request per launch,
+    one at a time).  Returns throughput and request latencies."""
+    import threading
+    from paper_2503_08586_gb300 import tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    spec = W.WORKLOADS[workload]
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + seed_offset))
+    psf = W.make_psf(spec)
+    render = tll.columns_renderer(W.f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx)
+    lenses = [W.synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf, render,
+                           spec.noise_kind) for _ in range(n_jobs)]
+    render.lens.close()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
+    seeds = rng.integers(0, 2 ** 31, n_jobs)
+    S = tll.Server(max_jobs=max(64, n_jobs), max_vectors_per_launch=16384,
+                   max_inflight=2 if coalesce else 1, coalesce=coalesce,
+                   use_graph=coalesce)
+    lat, vecs, errors = [], [0], []
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def job(k):
+        try:
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            sl = lenses[k]
+            r = np.random.Generator(np.random.PCG64(int(seeds[k])))
+            sizes = r.integers(500, 5001, iters)
+            frac = np.geomspace(1.0, 0.01, iters)
+            j = None
+            while j is None:
+                j = S.open_job(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub,
+                               sl.x0, sl.y0)
+                if j is None:
+                    time.sleep(0.001)
+            for it in range(iters):
+                P = W.shrinking_draws(r, sl.truth, int(sizes[it]), lo_frac=frac[it])
+                out, l = S.wait(S.submit(j, P))
+                with lock:
+                    lat.append(l)
+                    vecs[0] += len(P)
+            while not S.close_job(j):
+                time.sleep(0.001)
+        except Exception as e:  # pragma: no cover
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=job, args=(k,)) for k in range(n_jobs)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - t0
+    st = S.stats()
+    S.close()
+    if errors:
+        raise RuntimeError(errors[0])
+    mean_b = vecs[0] / max(1, len(lat))
+    return {"evals_per_s": vecs[0] / wall, "wall_s": wall, "requests": len(lat),
+            "vectors": vecs[0], "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "launches": st["launches"],
+            "vectors_per_launch": vecs[0] / max(1, st["launches"]),
+            "lenses_per_hour": n_jobs / wall * 3600.0, "mean_batch": mean_b,
+            "jobs": n_jobs, "iters_per_job": iters, "arrival_rate_hz": rate_hz}
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -254,6 +329,22 @@ def run_ours(args):
     e2e_value = B * ws / (e2e_total / args.steps / 1e3)
     assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
 
+    # ---- request stream: served (merged launches) vs plain (one per launch)
+    served = plain = None
+    if not args.skip_stream:
+        served = run_stream(True, args.stream_jobs, args.stream_iters, args.stream_rate,
+                            args.workload)
+        plain = run_stream(False, args.stream_jobs, args.stream_iters, args.stream_rate,
+                           args.workload)
+        vals = torch.tensor([served["evals_per_s"], plain["evals_per_s"]],
+                            dtype=torch.float64, device=dev)
+        if ws > 1:
+            import torch.distributed as dist
+            # replicas: whole-job throughput is the sum over ranks
+            dist.all_reduce(vals, op=dist.ReduceOp.SUM)
+        served["evals_per_s_all_ranks"] = float(vals[0])
+        plain["evals_per_s_all_ranks"] = float(vals[1])
+
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
@@ -289,8 +380,19 @@ def run_ours(args):
                      "kernel": "k_loglike",
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                                    f"x {SM_MAX_MHZ:.0f} MHz"},
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8},
+        "e2e": ({"value": served["evals_per_s_all_ranks"], "unit": UNIT,
+                 "path": "served request stream through tll_server (host buffers)",
+                 "h2d_bytes_per_step": int(served["mean_batch"] * 21 * 4),
+                 "d2h_bytes_per_step": int(served["mean_batch"] * 8)}
+                if served else
+                {"value": e2e_value, "unit": UNIT,
+                 "path": "tll_loglike_batch_host, pinned host buffers",
+                 "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8}),
+        "e2e_batch_host": {"value": e2e_value, "unit": UNIT,
+                           "path": "tll_loglike_batch_host, pinned host buffers, B per step",
+                           "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8},
+        "served": served,
+        "plain": plain,
         "clocks": clk,
         "gpu_launches": launches,
         "impl": "ours",
@@ -357,6 +459,10 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--ref-sample", type=int, default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-stream", action="store_true")
+    ap.add_argument("--stream-jobs", type=int, default=32)
+    ap.add_argument("--stream-iters", type=int, default=100)
+    ap.add_argument("--stream-rate", type=float, default=20.0)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
