@@ -406,6 +406,75 @@ def run_ours(args):
     return line
 
 
+# ------------------------------------------------------------ ragged batch
+def run_ragged(args):
+    """Many lenses of different sizes (sides {64..200}, PSF 11..31 px, 4x4
+    subpixels), each with its own batch of vectors shrinking around its
+    truth, evaluated in ONE persistent multi-lens launch replayed as a CUDA
+    graph; one step = that launch."""
+    import torch
+    from paper_2503_08586_gb300 import build, tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    build.build()
+    tll.load()
+    t0 = time.perf_counter()
+    rng, specs = W.ragged_specs(args.ragged_lenses)
+    lenses, params = [], []
+    cache = {}
+    for side, k in specs:
+        key = (side, k)
+        if key not in cache:
+            psf = W.gaussian_psf(k, k / 7.0)
+            cache[key] = (psf, tll.columns_renderer(W.f32(0.074), 4, psf, side, side))
+        psf, render = cache[key]
+        sl = W.synth_lens(rng, side, side, 0.074, 4, psf, render, "sky+poisson")
+        lenses.append(tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0,
+                               sl.y0, batch_only=True))
+        params.append(torch.from_numpy(W.shrinking_draws(rng, sl.truth,
+                                                         args.ragged_vectors)).cuda())
+    for _, r in cache.values():
+        r.lens.close()
+    setup_s = time.perf_counter() - t0
+    outs = [torch.empty(p.shape[0], dtype=torch.float64, device="cuda") for p in params]
+    b = tll.Batcher(use_graph=True)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            b.run(lenses, params, outs, stream=stream)
+        stream.synchronize()
+        clocks = ClockSampler(0)
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(lenses, params, outs, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+    nvec = sum(p.shape[0] for p in params)
+    nsub = sum(p.shape[0] * L.nx * L.ny * L.sub ** 2 for p, L in zip(params, lenses))
+    allfin = all(bool(torch.isfinite(o).all()) for o in outs)
+    step = sum(ms) / len(ms)
+    return {
+        "metric": "log-likelihood evals/s (ragged multi-lens batch, one launch)",
+        "value": nvec / (step / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ragged: {len(lenses)} lenses, sides {{64..200}}, PSF 11..31, "
+                               f"4x4 subpixels, {args.ragged_vectors} vectors each, one "
+                               "multi-lens launch under a CUDA graph",
+                   "global_batch": nvec, "setup_s": setup_s,
+                   "l2": "flushed between timed steps"},
+        "subpixel_evals_per_s": nsub / (step / 1e3), "all_finite": allfin,
+        "clocks": clk, "gpu_launches": 2 * args.steps, "impl": "ours"}
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     """The FP64 oracle as it stands, on the host cores, same workload /
@@ -463,10 +532,17 @@ def main(argv=None):
     ap.add_argument("--stream-jobs", type=int, default=32)
     ap.add_argument("--stream-iters", type=int, default=100)
     ap.add_argument("--stream-rate", type=float, default=20.0)
+    ap.add_argument("--ragged-lenses", type=int, default=1000)
+    ap.add_argument("--ragged-vectors", type=int, default=2048)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "ragged":
+        line = run_ragged(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -69,6 +69,11 @@ enum {
 };
 /* Extra flag bit: never take the separable-PSF fast path (testing). */
 #define TLL_FLAG_DIRECT_CONV 0x100
+/* Extra flag bit: the lens is evaluated through a tll_batcher / tll_server;
+ * skip the one-lens kernel's image slots for large images (up to
+ * 152 x 16 B per pixel), allocated on first use by the allocating one-lens
+ * entry points if it is evaluated alone after all. */
+#define TLL_FLAG_BATCH_ONLY 0x200
 
 typedef struct tll_lens tll_lens; /* opaque; owns device copies of its data */
 
@@ -87,6 +92,7 @@ typedef struct {
  *          positive sum; the library normalises it to unit sum (Eq. 3)
  *   grid   image geometry (see Grid)
  *   flags  TLL_AMP_LINEAR or TLL_AMP_FIXED, optionally | TLL_FLAG_DIRECT_CONV
+ *          | TLL_FLAG_BATCH_ONLY
  *   out    receives the new lens
  * The caller keeps ownership of all input buffers.  The lens owns its device
  * memory and per-launch scratch; destroy it with tll_destroy_lens.

@@ -38,21 +38,38 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library (parallel
-    device compilation via --threads)."""
+    """Compile every .cu under csrc/ in parallel (each kernel translation
+    unit is self-contained) and link them into one shared library."""
     if not force and not _stale():
         return LIB
-    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "--threads", "0",
-           "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE, "-I" + CSRC,
-           "-o", LIB + ".tmp", *sources()]
+    import concurrent.futures as cf
+    objdir = os.path.join(PKG, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
+        common.append("-Xptxas=-v")
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        r = subprocess.run(common + ["-c", src, "-o", obj], capture_output=True, text=True)
+        return src, obj, r
+
+    srcs = sources()
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(compile_one, srcs))
+    log = ""
+    for src, obj, r in results:
+        log += r.stdout + r.stderr
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n" + r.stdout + r.stderr)
+    link = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp"] + [o for _, o, _ in results]
+    r = subprocess.run(link, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(LIB + ".tmp", LIB)
     if verbose:
-        print(res.stdout + res.stderr)
+        print(log)
     return LIB
 
 

@@ -1,0 +1,143 @@
+// tll_core.cuh -- types and helpers shared by the likelihood kernels and
+// the compiled convolutions (separate translation units, relocatable
+// device code).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tll.h"
+#include "tll_device.cuh"
+
+namespace tll {
+
+constexpr int kThreads = 1024;     // CTA size of k_loglike (64 registers, 32 warps per SM)
+constexpr int kHMax = 8;           // in-place row pass holds nx <= 32*kHMax
+constexpr int kRedBytes = 32 * 5 * 8;
+
+constexpr int kMaxTaps = 32;   // separable PSF factors carried in the parameter block
+constexpr int kMaxK = 31;      // largest PSF side of the compiled convolutions
+
+struct LensDev {
+    int nx, ny, npix, sub, K, h, sep, mode;
+    float JCX, JCY;   // subpixel index of the grid centre, (n*s - 1)/2
+    float inv_s2;
+    int W, HL;        // padded layout: row stride, left zero columns
+    int img;          // image placement (IMG_*)
+    double XC, YC, d; // grid centre and subpixel step (for the prologue)
+    const float *psf;    // [K*K] unit sum (direct path)
+    const float *pu;     // [K] column factor over PSF rows (separable path)
+    const float *pv;     // [K] row factor over PSF columns
+    const float4 *wpack; // [npix] (w_hi, w_lo, wd_hi, wd_lo)
+    double dWd, lognorm;
+    int band_rows;    // IMG_BANDED: output rows per shared-memory band
+    float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
+    float tk[kMaxK * kMaxK];            // the full PSF (direct convolution)
+};
+
+// Image placement in k_loglike.
+enum : int {
+    IMG_GLOBAL = 0,   // per-CTA global scratch slot (L2), generic convolution
+    IMG_SMEM = 1,     // shared memory, unpadded, generic convolution
+    IMG_PADDED = 2,   // shared memory with zero halos, convolution compiled per K
+    IMG_BANDED = 3    // global slot, convolved band by band through a zero-padded
+                      // shared-memory buffer, convolution compiled per K
+};
+
+struct RunArgs {
+    const float *kc;     // [B][NCONST]
+    int B;
+    double *out;         // [B]
+    float *gscr;         // global image scratch, 4*npix floats per CTA
+    float *wr_unblurred; // WRITE: [2][npix]
+    float *wr_blurred;   // WRITE: [2][npix]
+    double *wr_res;      // WRITE: [8] All Als Ass bl bs sl ss logL
+};
+
+// One term of the five weighted sums (Sec. 2.3: A = M^T W M, b = M^T W d)
+// for one pixel with blurred column values ml, ms; wp = (w_hi, w_lo,
+// wd_hi, wd_lo).  Products are formed exactly as float pairs and added
+// with TwoSum into double-float accumulators a[0..9].
+__device__ __forceinline__ void accum_pixel(float ml, float ms, float4 wp, float *a)
+{
+    float p1 = wp.x * ml, e1 = fmaf(wp.x, ml, -p1);
+    e1 = fmaf(wp.y, ml, e1);
+    float p2 = wp.x * ms, e2 = fmaf(wp.x, ms, -p2);
+    e2 = fmaf(wp.y, ms, e2);
+    float p, e;
+    p = p1 * ml; e = fmaf(p1, ml, -p); e = fmaf(e1, ml, e); df_acc(a[0], a[1], p, e);
+    p = p1 * ms; e = fmaf(p1, ms, -p); e = fmaf(e1, ms, e); df_acc(a[2], a[3], p, e);
+    p = p2 * ms; e = fmaf(p2, ms, -p); e = fmaf(e2, ms, e); df_acc(a[4], a[5], p, e);
+    p = wp.z * ml; e = fmaf(wp.z, ml, -p); e = fmaf(wp.w, ml, e); df_acc(a[6], a[7], p, e);
+    p = wp.z * ms; e = fmaf(wp.z, ms, -p); e = fmaf(wp.w, ms, e); df_acc(a[8], a[9], p, e);
+}
+
+// --------------------------------------------------- padded convolution
+// Separable PSF with compile-time side K on the zero-padded shared-memory
+// layout: image pixel (i, j) at P[(h + i) W + HL + j], HL = h rounded up to
+// a multiple of 4; rows [0, h) and [h + ny, ...) and the columns outside
+// [HL, HL + nx) hold zeros, so no tap needs a bounds check.
+//  Row pass (in place, one warp per row): a lane computes 4 adjacent
+//  outputs from one window of K + 3 values read as float4s.
+//  Column pass: a warp takes 32 adjacent columns x CR rows; a lane reads
+//  CR + K - 1 values of its column and computes CR outputs per channel.
+// Taps come from the parameter block (compile-time indices).
+constexpr int kCR = 4;
+
+template <int K>
+struct PadGeom {
+    static constexpr int h = (K - 1) / 2;
+    static constexpr int HL = (h + 3) & ~3;
+    static constexpr int D = HL - h;                 // window offset in a group
+    static constexpr int NW = (D + K + 3 + 3) / 4;   // float4 reads per window
+};
+
+// Padded row stride for an image of nx columns and PSF side K (host and
+// device): covers every float4 window read of the row pass and the right
+// zero halo.
+__host__ __device__ inline int padded_stride(int nx, int K)
+{
+    const int h = (K - 1) / 2, HL = (h + 3) & ~3, D = HL - h;
+    const int NW = (D + K + 6) / 4;
+    const int W = 4 * ((nx + 3) / 4) + 4 * NW;
+    return (W + 3) & ~3;
+}
+
+struct Acc10 {
+    float a[10];
+};
+
+// Multi-lens work list: segment s covers items [first, first + count) of
+// lens `lens`, reading params[k] and writing out[k]; segments are grouped
+// (same supersampling and convolution class) and each group is one launch.
+struct Segment {
+    int lens, first, count, pad;
+    const float *params;
+    double *out;
+};
+struct MultiHdr {        // one group: items [first, first + total), segments [seg0, seg0 + nseg)
+    int first, total, seg0, nseg;
+};
+struct MultiArgs {
+    const LensDev *lenses;
+    const Segment *segs;
+    const MultiHdr *groups;
+    const MultiHdr *all;       // the whole work list (prologue)
+    float *kc;                 // [total][NCONST]
+    float *gscr;               // per-CTA global image slots
+    long long gslot_floats;
+    int *counter;              // one work counter per group, zero at launch
+    const double *bn_tab;
+};
+
+// Largest s in [s0, s0 + n) with segs[s].first <= t.
+__host__ __device__ inline int find_segment(const Segment *segs, int s0, int n, int t)
+{
+    int lo = s0, hi = s0 + n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace tll

@@ -1,0 +1,31 @@
+// tll_kern_k05.cu -- likelihood kernels with the compiled convolution
+// for PSF sides 5, 7 (one translation unit per pair, compiled in parallel).
+#include "tll_kernels.cuh"
+
+namespace tll {
+namespace {
+
+SingleKernel single_k(int sub, int K, bool write)
+{
+    if (write) return nullptr;
+    switch (K) {
+        case 5: return single_for<5>(sub);
+        case 7: return single_for<7>(sub);
+    }
+    return nullptr;
+}
+
+MultiKernel multi_k(int sub, int K)
+{
+    switch (K) {
+        case 5: return multi_for<5>(sub);
+        case 7: return multi_for<7>(sub);
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+extern const KernelSet kernel_set_k05 = {single_k, multi_k};
+
+}  // namespace tll

@@ -1,0 +1,640 @@
+// tll_kernels.cuh -- the likelihood kernels (templates).  Included by the
+// tll_kern_*.cu translation units, each of which instantiates the kernels
+// for a few PSF sides K (the compiled convolutions are specialised per K),
+// so the kernels compile in parallel; the host finds them through the
+// registry at the end of this file.
+#pragma once
+
+#include <math.h>
+
+#include "tll_core.cuh"
+
+namespace tll {
+
+// Amplitudes and log L from the five sums (thread-local, FP64).
+// NNLS over two columns: the optimum is the unconstrained minimiser of one
+// face {none, lens only, source only, both} that is feasible; chi^2 of a
+// face's minimiser s is dWd - s^T b.  Fixed mode: s = (I_e^L, I_e^S) and
+// chi^2 = dWd - 2 s^T b + s^T A s.
+__device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
+                                              float IeL, float IeS, double *sl_o,
+                                              double *ss_o, double *ll_o)
+{
+    const double All = S[0], Als = S[1], Ass = S[2], bl = S[3], bs = S[4];
+    double sl, ss, chi2;
+    if (L.mode == TLL_AMP_FIXED) {
+        sl = IeL;
+        ss = IeS;
+        chi2 = L.dWd - 2.0 * (sl * bl + ss * bs) + sl * sl * All +
+               2.0 * sl * ss * Als + ss * ss * Ass;
+    } else {
+        sl = 0.0; ss = 0.0; chi2 = L.dWd;
+        if (All > 0.0 && bl > 0.0) {
+            const double c = L.dWd - bl * (bl / All);
+            if (c < chi2) { chi2 = c; sl = bl / All; ss = 0.0; }
+        }
+        if (Ass > 0.0 && bs > 0.0) {
+            const double c = L.dWd - bs * (bs / Ass);
+            if (c < chi2) { chi2 = c; sl = 0.0; ss = bs / Ass; }
+        }
+        // Both columns free only when they are not collinear to rounding:
+        // det / (A_ll A_ss) = 1 - rho^2 must exceed the sums' rounding
+        // (~1e-14) by a wide margin; collinear columns reach their optimum
+        // on a single-column face.  The candidate's chi^2 is the full
+        // quadratic form, exact for any s given A and b.
+        const double det = All * Ass - Als * Als;
+        if (det > 1e-9 * All * Ass) {
+            const double tl = (Ass * bl - Als * bs) / det;
+            const double ts = (All * bs - Als * bl) / det;
+            if (tl > 0.0 && ts > 0.0) {
+                const double c = L.dWd - 2.0 * (tl * bl + ts * bs) + tl * tl * All +
+                                 2.0 * tl * ts * Als + ts * ts * Ass;
+                if (c < chi2) { chi2 = c; sl = tl; ss = ts; }
+            }
+        }
+    }
+    *sl_o = sl;
+    *ss_o = ss;
+    *ll_o = -0.5 * chi2 + L.lognorm;
+}
+
+// --------------------------------------------------------- trace phase
+// Ray-trace + light on the s x s subpixels of every pixel, mean-binned:
+// pixel (i, j) of the lens / source image goes to Il / Is [i*stride + off + j].
+// Subpixel (J, I) of the supersampled grid has exact integer-or-half
+// offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
+// coordinate is an affine function of them (see decode_vector).
+template <int SUB>
+__device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
+                                            float *Il, float *Is, int stride, int off,
+                                            int tid, int nthr)
+{
+    const int sub = SUB > 0 ? SUB : L.sub;
+    const int nx = L.nx;
+    for (int pix = tid; pix < L.npix; pix += nthr) {
+        const int i = pix / nx, j = pix - i * nx;
+        const float fj0 = (float)(j * sub) - L.JCX;
+        const float fi0 = (float)(i * sub) - L.JCY;
+        float accl = 0.0f, accs = 0.0f;
+#pragma unroll 1
+        for (int a = 0; a < sub; ++a) {
+            const RowTerms r = row_terms(v, fi0 + (float)a);
+#pragma unroll
+            for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
+                for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
+                    float il, is;
+                    subpixel(v, r, fj0 + (float)(SUB > 0 ? c : cr), il, is);
+                    accl += il;
+                    accs += is;
+                }
+            }
+        }
+        Il[i * stride + off + j] = accl * L.inv_s2;
+        Is[i * stride + off + j] = accs * L.inv_s2;
+    }
+}
+
+// ------------------------------------------------ generic convolution
+// Any PSF side, images unpadded with row stride nx (in shared memory, with
+// the row pass in place, or in a global scratch slot with separate H
+// buffers).  Separable: H(i,j) = sum_c v[c] I(i, j+h-c), then
+// m(i,j) = sum_r u[r] H(i+h-r, j); direct: m = sum_{r,c} K[r][c] I(i+h-r, j+h-c);
+// zero outside the image (Eq. 3).  Each output pixel's (m_l, m_s) goes to
+// accum_pixel.
+template <bool WRITE>
+__device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
+                                             const float *spsf, float *Il, float *Is,
+                                             float *Hl, float *Hs, float *acc, int tid,
+                                             int nthr, bool INPLACE)
+{
+    const int K = L.K, h = L.h, nx = L.nx, ny = L.ny, npix = L.npix;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    if (L.sep) {
+        const float *su = spsf, *sv = spsf + K;
+        for (int row = warp; row < 2 * ny; row += nwarp) {
+            const float *src = row < ny ? Il + row * nx : Is + (row - ny) * nx;
+            float *dst = row < ny ? Hl + row * nx : Hs + (row - ny) * nx;
+            if (INPLACE) {
+                float o[kHMax];
+#pragma unroll
+                for (int q = 0; q < kHMax; ++q) {
+                    const int j = lane + 32 * q;
+                    float sacc = 0.0f;
+                    if (j < nx) {
+                        const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                        for (int c = c0; c <= c1; ++c) sacc = fmaf(sv[c], src[j + h - c], sacc);
+                    }
+                    o[q] = sacc;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < kHMax; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < nx) dst[j] = o[q];
+                }
+                __syncwarp();
+            } else {
+                for (int j = lane; j < nx; j += 32) {
+                    const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+                    float sacc = 0.0f;
+                    for (int c = c0; c <= c1; ++c) sacc = fmaf(sv[c], src[j + h - c], sacc);
+                    dst[j] = sacc;
+                }
+            }
+        }
+        __syncthreads();
+        const int nb = max(1, nthr / nx);
+        const int rb = (ny + nb - 1) / nb;
+        for (int it = tid; it < nx * nb; it += nthr) {
+            const int j = it % nx, band = it / nx;
+            const int r0 = band * rb, r1 = min(ny, r0 + rb);
+            for (int i = r0; i < r1; ++i) {
+                const int q0 = max(0, i + h - ny + 1), q1 = min(K - 1, i + h);
+                float ml = 0.0f, ms = 0.0f;
+                for (int r = q0; r <= q1; ++r) {
+                    const int o = (i + h - r) * nx + j;
+                    ml = fmaf(su[r], Hl[o], ml);
+                    ms = fmaf(su[r], Hs[o], ms);
+                }
+                const int pix = i * nx + j;
+                if (WRITE) {
+                    R.wr_blurred[pix] = ml;
+                    R.wr_blurred[npix + pix] = ms;
+                }
+                accum_pixel(ml, ms, L.wpack[pix], acc);
+            }
+        }
+    } else {
+        for (int pix = tid; pix < npix; pix += nthr) {
+            const int i = pix / nx, j = pix - i * nx;
+            const int r0 = max(0, i + h - ny + 1), r1 = min(K - 1, i + h);
+            const int c0 = max(0, j + h - nx + 1), c1 = min(K - 1, j + h);
+            float ml = 0.0f, ms = 0.0f;
+            for (int r = r0; r <= r1; ++r) {
+                const float *kr = spsf + r * K;
+                const int base = (i + h - r) * nx + j + h;
+                float rl = 0.0f, rs = 0.0f;
+                for (int c = c0; c <= c1; ++c) {
+                    rl = fmaf(kr[c], Il[base - c], rl);
+                    rs = fmaf(kr[c], Is[base - c], rs);
+                }
+                ml += rl;
+                ms += rs;
+            }
+            if (WRITE) {
+                R.wr_blurred[pix] = ml;
+                R.wr_blurred[npix + pix] = ms;
+            }
+            accum_pixel(ml, ms, L.wpack[pix], acc);
+        }
+    }
+}
+
+// Both compiled convolutions work on a zero-padded band buffer: per
+// channel, buffer row br holds image row b0 - h + br (zeros outside the
+// image), interior column j at buffer column HL + j, zeros elsewhere; the
+// s channel follows the l channel at Ps.  Outputs are image rows
+// [b0, b0 + nrows); each output pixel's (m_l, m_s) goes to accum_pixel.
+
+// Separable: row pass in place over buffer rows [rlo, rhi) (a lane makes
+// 4 adjacent outputs from one float4 window), then the column pass (a lane
+// makes kCR rows of its column from one window) fused with the sums.
+template <int K>
+__device__ __forceinline__ Acc10 conv_sep_band(const LensDev &L, float *Pl, float *Ps,
+                                            int b0, int nrows, int rlo, int rhi, int tid,
+                                            int nthr)
+{
+    Acc10 out;
+    float *acc = out.a;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+    using G = PadGeom<K>;
+    const int nx = L.nx, W = L.W;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int ngroups = (nx + 3) >> 2;
+    const int nr = rhi - rlo;
+    // row pass, in place; each lane holds at most 2 groups (nx <= 256)
+    for (int row = warp; row < 2 * nr; row += nwarp) {
+        float *P = (row < nr ? Pl + (rlo + row) * W : Ps + (rlo + row - nr) * W);
+        float o[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = lane + 32 * q;
+            if (g < ngroups) {
+                float win[4 * G::NW];
+                const float4 *src = reinterpret_cast<const float4 *>(P + 4 * g);
+#pragma unroll
+                for (int k = 0; k < G::NW; ++k) {
+                    const float4 v4 = src[k];
+                    win[4 * k] = v4.x; win[4 * k + 1] = v4.y;
+                    win[4 * k + 2] = v4.z; win[4 * k + 3] = v4.w;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < K; ++c) a = fmaf(L.tv[c], win[G::D + K - 1 + r - c], a);
+                    o[q][r] = a;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = lane + 32 * q;
+            if (g < ngroups) {
+                float *dst = P + G::HL + 4 * g;
+                if (4 * g + 3 < nx) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(o[q][0], o[q][1], o[q][2], o[q][3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (4 * g + r < nx) dst[r] = o[q][r];
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // column pass with the fused weighted sums: output row ro (image row
+    // b0 + ro) reads buffer rows ro .. ro + K - 1
+    const int ncg = (nx + 31) >> 5, nrb = (nrows + kCR - 1) / kCR;
+    for (int item = warp; item < ncg * nrb; item += nwarp) {
+        const int cg = item % ncg, rb = item / ncg;
+        const int j = 32 * cg + lane, r0 = rb * kCR;
+        const int jc = min(j, nx - 1);
+        float ml[kCR], ms[kCR];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const float *col = (ch == 0 ? Pl : Ps) + r0 * W + G::HL + jc;
+            float win[kCR + K - 1];
+#pragma unroll
+            for (int t = 0; t < kCR + K - 1; ++t) win[t] = col[t * W];
+#pragma unroll
+            for (int r = 0; r < kCR; ++r) {
+                float a = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) a = fmaf(L.tu[c], win[r + K - 1 - c], a);
+                if (ch == 0) ml[r] = a; else ms[r] = a;
+            }
+        }
+        if (j < nx) {
+#pragma unroll
+            for (int r = 0; r < kCR; ++r) {
+                if (r0 + r < nrows) {
+                    const int pix = (b0 + r0 + r) * nx + j;
+                    accum_pixel(ml[r], ms[r], L.wpack[pix], acc);
+                }
+            }
+        }
+    }
+    return out;
+}
+
+// Direct K x K convolution (any PSF): a thread makes 4 adjacent outputs of
+// one row; for each channel and PSF row it reads one float4 window and
+// applies the row's K taps (each tap read once, used for the 4 outputs);
+// m(i,j) = sum_{r,c} K[r][c] I(i+h-r, j+h-c), summed per PSF row.  Kept to
+// one window and 8 accumulators so it fits the kernel's 64 registers.
+template <int K>
+__device__ __forceinline__ Acc10 conv_direct_band(const LensDev &L, const float *Pl,
+                                               const float *Ps, int b0, int nrows, int tid,
+                                               int nthr)
+{
+    Acc10 out;
+    float *acc = out.a;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+    using G = PadGeom<K>;
+    const int nx = L.nx, W = L.W;
+    const int ngroups = (nx + 3) >> 2;
+    for (int item = tid; item < nrows * ngroups; item += nthr) {
+        const int ro = item / ngroups, g = item - ro * ngroups;
+        float o[2][4];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const float *base = (ch == 0 ? Pl : Ps) + 4 * g;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[ch][q] = 0.0f;
+#pragma unroll 1
+            for (int r = 0; r < K; ++r) {
+                // PSF row r meets image row (b0 + ro) + h - r = buffer row ro + 2h - r
+                const float4 *src = reinterpret_cast<const float4 *>(base + (ro + 2 * G::h - r) * W);
+                float win[4 * G::NW];
+#pragma unroll
+                for (int k = 0; k < G::NW; ++k) {
+                    const float4 v4 = src[k];
+                    win[4 * k] = v4.x; win[4 * k + 1] = v4.y;
+                    win[4 * k + 2] = v4.z; win[4 * k + 3] = v4.w;
+                }
+                const float *tr = L.tk + r * K;
+                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float t = tr[c];
+                    a0 = fmaf(t, win[G::D + K - 1 - c], a0);
+                    a1 = fmaf(t, win[G::D + K - c], a1);
+                    a2 = fmaf(t, win[G::D + K + 1 - c], a2);
+                    a3 = fmaf(t, win[G::D + K + 2 - c], a3);
+                }
+                o[ch][0] += a0; o[ch][1] += a1; o[ch][2] += a2; o[ch][3] += a3;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * g + q;
+            if (j < nx) accum_pixel(o[0][q], o[1][q], L.wpack[(b0 + ro) * nx + j], acc);
+        }
+    }
+    return out;
+}
+
+// ------------------------------------------------------ per-vector body
+// Where the two images of lens L live in a CTA: lens / source images Il, Is
+// with pixel (i, j) at [i*stride + off + j], row-pass outputs Hl, Hs.
+struct ImgPtrs {
+    float *Il, *Is, *Hl, *Hs;
+    int stride, off;
+};
+
+__device__ __forceinline__ int psf_smem_floats(const LensDev &L, int img)
+{
+    return (img == IMG_PADDED || img == IMG_BANDED) ? 0 : (L.sep ? 2 * L.K : L.K * L.K);
+}
+
+__device__ __forceinline__ ImgPtrs img_ptrs(const LensDev &L, float *spsf, float *gslot)
+{
+    const int IMG = L.img;
+    ImgPtrs P;
+    if (IMG == IMG_BANDED) {
+        // images in the global slot (unpadded); the band buffer is spsf
+        P.Il = gslot;
+        P.Is = P.Il + L.npix;
+        P.Hl = spsf;
+        P.Hs = spsf + (L.band_rows + 2 * L.h + kCR) * L.W;
+        P.stride = L.nx; P.off = 0;
+    } else if (IMG == IMG_PADDED) {
+        const int rows = L.ny + 2 * L.h + kCR;   // zero rows above, below, last row block
+        P.Il = spsf;
+        P.Is = P.Il + rows * L.W;
+        P.Hl = P.Il; P.Hs = P.Is;
+        P.stride = L.W;
+        P.off = L.h * L.W + L.HL;
+    } else if (IMG == IMG_SMEM) {
+        P.Il = spsf + ((psf_smem_floats(L, IMG) + 3) & ~3);
+        P.Is = P.Il + L.npix;
+        P.Hl = P.Il;   // the row pass runs in place
+        P.Hs = P.Is;
+        P.stride = L.nx; P.off = 0;
+    } else {
+        P.Il = gslot;
+        P.Is = P.Il + L.npix;
+        P.Hl = P.Is + L.npix;
+        P.Hs = P.Hl + L.npix;
+        P.stride = L.nx; P.off = 0;
+    }
+    return P;
+}
+
+// Prepare a CTA's memory for lens L: zero the padded layout's halos (they
+// stay zero: only interior pixels are ever written) or stage the PSF.
+__device__ __forceinline__ void setup_lens(const LensDev &L, float *spsf, int tid, int nthr)
+{
+    const int IMG = L.img;
+    if (IMG == IMG_PADDED || IMG == IMG_BANDED) {
+        const int rows = (IMG == IMG_PADDED ? L.ny : L.band_rows) + 2 * L.h + kCR;
+        const int n = 2 * rows * L.W;
+        for (int t = tid; t < n; t += nthr) spsf[t] = 0.0f;
+    } else {
+        const int K = L.K, nf = psf_smem_floats(L, IMG);
+        for (int t = tid; t < nf; t += nthr)
+            spsf[t] = L.sep ? (t < K ? L.pu[t] : L.pv[t - K]) : L.psf[t];
+    }
+}
+
+// One parameter vector (its constant block kc is valid): trace, convolve
+// with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
+// block barrier.
+// Convolve the two images with the fused sums.  K > 0: the compiled
+// convolution of side K on zero-padded bands (IMG_PADDED: the whole image is
+// one band already in place; IMG_BANDED: bands filled from the global slot);
+// K == 0: the generic convolution (IMG_SMEM, IMG_GLOBAL).
+template <int K, bool WRITE>
+__device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, const ImgPtrs &P,
+                                         const float *spsf, float *acc, int tid, int nthr)
+{
+    if constexpr (K > 0) {
+        static_assert(!WRITE, "write-out runs on the generic placements");
+        const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
+        const bool banded = L.img == IMG_BANDED;
+        const int step = banded ? L.band_rows : ny;
+        float *Pl = banded ? P.Hl : P.Il, *Ps = banded ? P.Hs : P.Is;
+        for (int b0 = 0; b0 < ny; b0 += step) {
+            const int nrows = min(step, ny - b0);
+            int rlo = h, rhi = h + ny;   // padded: image rows in place, halos zero
+            if (banded) {
+                // buffer rows [0, nrows + 2h) <- image rows [b0 - h, b0 + nrows + h)
+                const int nbr = nrows + 2 * h;
+                for (int t = tid; t < 2 * nbr * nx; t += nthr) {
+                    const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
+                    const int br = rem / nx, j = rem - br * nx;
+                    const int ir = b0 - h + br;
+                    const float v = (ir >= 0 && ir < ny) ? (ch ? P.Is : P.Il)[ir * nx + j] : 0.0f;
+                    (ch ? Ps : Pl)[br * W + HL + j] = v;
+                }
+                __syncthreads();
+                rlo = max(0, h - b0);
+                rhi = min(nbr, ny - b0 + h);
+            }
+            const Acc10 r = L.sep ? conv_sep_band<K>(L, Pl, Ps, b0, nrows, rlo, rhi, tid, nthr)
+                                  : conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) acc[k] += r.a[k];
+            if (banded) __syncthreads();
+        }
+    } else {
+        conv_generic<WRITE>(L, R, spsf, P.Il, P.Is, P.Hl, P.Hs, acc, tid, nthr,
+                            L.img == IMG_SMEM);
+    }
+}
+
+// One parameter vector (its constant block kc is valid): trace, convolve
+// with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
+// block barrier.
+template <int SUB, int K, bool WRITE>
+__device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
+                                            const float *kc, double *outp, const ImgPtrs &P,
+                                            const float *spsf, double *sred, int tid, int nthr)
+{
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int nx = L.nx, npix = L.npix;
+    {
+        const VecConst v = load_consts(kc);
+        trace_image<SUB>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
+    }
+    __syncthreads();
+    if (WRITE) {
+        for (int t = tid; t < npix; t += nthr) {
+            const int i = t / nx, j = t - i * nx;
+            R.wr_unblurred[t] = P.Il[i * P.stride + P.off + j];
+            R.wr_unblurred[npix + t] = P.Is[i * P.stride + P.off + j];
+        }
+        __syncthreads();
+    }
+    float acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+    convolve<K, WRITE>(L, R, P, spsf, acc, tid, nthr);
+
+    // warp reduction in double-float, block reduction in FP64
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
+            df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            sred[warp * 5 + k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double sacc = 0.0;
+        if (lane < 5)
+            for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
+        double S[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, sacc, k);
+        if (lane == 0) {
+            double sl, ss, ll;
+            finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
+            *outp = ll;
+            if (WRITE) {
+                for (int k = 0; k < 5; ++k) R.wr_res[k] = S[k];
+                R.wr_res[5] = sl;
+                R.wr_res[6] = ss;
+                R.wr_res[7] = ll;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------- one-lens kernel
+// K > 0: compiled convolution of side K (placements IMG_PADDED, IMG_BANDED);
+// K == 0: generic convolution (IMG_SMEM, IMG_GLOBAL).
+template <int SUB, int K, bool WRITE>
+__global__ void __launch_bounds__(kThreads)
+k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double *sred = reinterpret_cast<double *>(smem);
+    float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
+    const bool gslot = L.img == IMG_GLOBAL || L.img == IMG_BANDED;
+    const ImgPtrs P =
+        img_ptrs(L, spsf, gslot ? R.gscr + (size_t)blockIdx.x * 4 * L.npix : nullptr);
+    setup_lens(L, spsf, tid, nthr);
+    __syncthreads();
+    for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
+        const float *kc = R.kc + (size_t)b * NCONST;
+        if (kc[K_VALID] == 0.0f) {
+            if (tid == 0) {
+                R.out[b] = -INFINITY;
+                if (WRITE) R.wr_res[7] = -INFINITY;
+            }
+            continue;
+        }
+        vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, tid, nthr);
+    }
+}
+
+// ----------------------------------------------------- multi-lens kernel
+// One launch over the vectors of one group of segments (lenses sharing the
+// supersampling class SUB and the convolution class K): CTAs take items from
+// the group's atomic counter and copy a lens's descriptor into shared memory
+// when they switch lens.
+template <int SUB, int K>
+__global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constant__ MultiArgs A,
+                                                            int group)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LensDev sL;
+    __shared__ int s_t, s_seg;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double *sred = reinterpret_cast<double *>(smem);
+    float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
+    float *gslot = A.gscr ? A.gscr + (size_t)blockIdx.x * A.gslot_floats : nullptr;
+    const MultiHdr hd = A.groups[group];
+    int *counter = A.counter + group;
+    int cur = -1;
+    for (;;) {
+        if (tid == 0) {
+            const int t = hd.first + atomicAdd(counter, 1);
+            s_t = t;
+            s_seg = t < hd.first + hd.total ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+        }
+        __syncthreads();
+        const int t = s_t;
+        if (t >= hd.first + hd.total) break;
+        const Segment sg = A.segs[s_seg];
+        if (sg.lens != cur) {
+            const unsigned *src = reinterpret_cast<const unsigned *>(A.lenses + sg.lens);
+            unsigned *dst = reinterpret_cast<unsigned *>(&sL);
+            for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
+            __syncthreads();
+            setup_lens(sL, spsf, tid, nthr);
+            __syncthreads();
+            cur = sg.lens;
+        }
+        const float *kc = A.kc + (size_t)t * NCONST;
+        double *outp = sg.out + (t - sg.first);
+        if (kc[K_VALID] == 0.0f) {
+            if (tid == 0) *outp = -INFINITY;
+            __syncthreads();
+            continue;
+        }
+        RunArgs R = {};
+        const ImgPtrs P = img_ptrs(sL, spsf, gslot);
+        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, tid, nthr);
+    }
+}
+
+// --------------------------------------------------------------- registry
+using SingleKernel = void (*)(const LensDev, const RunArgs);
+using MultiKernel = void (*)(const MultiArgs, int);
+
+// Supersampling classes with an unrolled subpixel loop.
+__host__ __device__ inline int sub_class(int sub) { return (sub == 4 || sub == 5) ? sub : 0; }
+
+// Kernels of one translation unit; nullptr when (sub, K) is not in it.
+struct KernelSet {
+    SingleKernel (*single)(int sub, int K, bool write);
+    MultiKernel (*multi)(int sub, int K);
+};
+
+template <int K>
+inline SingleKernel single_for(int sub)
+{
+    switch (sub_class(sub)) {
+        case 4: return k_loglike<4, K, false>;
+        case 5: return k_loglike<5, K, false>;
+        default: return k_loglike<0, K, false>;
+    }
+}
+
+template <int K>
+inline MultiKernel multi_for(int sub)
+{
+    switch (sub_class(sub)) {
+        case 4: return k_loglike_multi<4, K>;
+        case 5: return k_loglike_multi<5, K>;
+        default: return k_loglike_multi<0, K>;
+    }
+}
+
+}  // namespace tll

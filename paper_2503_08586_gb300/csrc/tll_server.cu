@@ -364,7 +364,7 @@ int tll_server_open_job(tll_server *S, const float *image, const float *noise,
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != S->dev) cudaSetDevice(S->dev);
-    int rc = tll_create_lens(image, noise, psf, psf_size, grid, flags, &L);
+    int rc = tll_create_lens(image, noise, psf, psf_size, grid, flags | TLL_FLAG_BATCH_ONLY, &L);
     if (prev >= 0 && prev != S->dev) cudaSetDevice(prev);
     size_t bytes = 0;
     if (rc == TLL_OK) rc = tll_lens_footprint(L, &bytes);

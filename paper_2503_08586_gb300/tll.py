@@ -19,6 +19,7 @@ NPARAM = 21
 AMP_LINEAR = 0
 AMP_FIXED = 1
 FLAG_DIRECT_CONV = 0x100
+FLAG_BATCH_ONLY = 0x200
 NOALLOC_MAX_B = 16384
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(6)
@@ -175,7 +176,8 @@ class Lens:
 
     def __init__(self, image, noise, psf, pixel_scale: float, sub: int,
                  x0: float | None = None, y0: float | None = None,
-                 mode: int = AMP_LINEAR, direct_conv: bool = False):
+                 mode: int = AMP_LINEAR, direct_conv: bool = False,
+                 batch_only: bool = False):
         lib = load()
         img = np.ascontiguousarray(image, dtype=np.float32)
         nse = np.ascontiguousarray(noise, dtype=np.float32)
@@ -190,7 +192,8 @@ class Lens:
             y0 = -(ny - 1) * pixel_scale / 2.0
         g = Grid(nx, ny, pixel_scale, sub, x0, y0)
         h = ctypes.c_void_p()
-        flags = mode | (FLAG_DIRECT_CONV if direct_conv else 0)
+        flags = (mode | (FLAG_DIRECT_CONV if direct_conv else 0)
+                 | (FLAG_BATCH_ONLY if batch_only else 0))
         _check(lib.tll_create_lens(img.ctypes.data, nse.ctypes.data,
                                    k.ctypes.data, k.shape[0], ctypes.byref(g),
                                    flags, ctypes.byref(h)))
