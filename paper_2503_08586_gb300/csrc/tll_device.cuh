@@ -174,6 +174,7 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     const double qm = (1.0 - e_m) / (1.0 + e_m);
     const double f = 2.0 * sqrt(e_m) / (1.0 + e_m);
     const double A = v[0] * sqrt(qm);
+    bool fast;
     double cm, sm;
     half_angle(v[1], v[2], e_m, &cm, &sm);
     {
@@ -190,6 +191,7 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         // fast path when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
         // for every point: no atan range reduction, no atanh logarithm
         o[K_FAST] = (f <= qm && f <= 0.5) ? 1.0f : 0.0f;
+        fast = f <= qm && f <= 0.5;
     }
     const double g1 = v[5], g2 = v[6];
 
@@ -233,10 +235,15 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
         const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
         const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
-        split2(s1 * A * cd, &o[K_Q11H], &o[K_Q11L]);
-        split2(-s1 * A * sd, &o[K_Q12H], &o[K_Q12L]);
-        split2(s2 * A * sd, &o[K_Q21H], &o[K_Q21L]);
-        split2(s2 * A * cd, &o[K_Q22H], &o[K_Q22L]);
+        // The fast path's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
+        // path's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
+        // so its columns carry 1/f and ln 2/(2f).
+        const double c1 = fast ? 1.0 : 1.0 / f;
+        const double c2 = fast ? 1.0 : 0.34657359027997264 / f;
+        split2(s1 * A * cd * c1, &o[K_Q11H], &o[K_Q11L]);
+        split2(-s1 * A * sd * c2, &o[K_Q12H], &o[K_Q12L]);
+        split2(s2 * A * sd * c1, &o[K_Q21H], &o[K_Q21L]);
+        split2(s2 * A * cd * c2, &o[K_Q22H], &o[K_Q22L]);
     }
     o[K_IEL] = (float)v[7];
     o[K_IES] = (float)v[14];
@@ -249,7 +256,7 @@ struct Affine {    // v = c0 + cj fj + ci fi
 };
 struct VecConst {
     Affine px, py, lx, ly, sx, sy;
-    float q, f, invf;
+    float q, f;
     bool fast;
     float khl, kll, bhl, bll, khs, kls, bhs, bls;
     float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
@@ -266,7 +273,7 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.px = load_affine(kc, K_PX0); v.py = load_affine(kc, K_PY0);
     v.lx = load_affine(kc, K_LX0); v.ly = load_affine(kc, K_LY0);
     v.sx = load_affine(kc, K_SX0); v.sy = load_affine(kc, K_SY0);
-    v.q = kc[K_QM]; v.f = kc[K_F]; v.invf = kc[K_IF];
+    v.q = kc[K_QM]; v.f = kc[K_F];
     v.fast = kc[K_FAST] != 0.0f;
     v.khl = kc[K_KHL]; v.kll = kc[K_KLL]; v.bhl = kc[K_BHL]; v.bll = kc[K_BLL];
     v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
@@ -350,50 +357,50 @@ __device__ __forceinline__ float sersic_scaled(float x1, float x2, float kh, flo
     return sfu_ex2(fmaf(bh, omt, bl * omt));
 }
 
-// 1/sqrt(a) to about 1 ulp: the hardware estimate plus one Newton step.
+// 1/sqrt(a) to about 1 ulp for normal a: the hardware estimate
+// (rsqrt.approx) plus one Newton step.
 __device__ __forceinline__ float rsqrt_nr(float a)
 {
-    const float y = rsqrtf(a);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
     const float hy = 0.5f * a * y;
     return fmaf(y, fmaf(-hy, y, 0.5f), y);
 }
 
 // SIE deflection (Eq. 12 at gamma = 2, elliptical radius of Eq. 10) in the
-// mass frame at (xp, yp), as alpha' = A (ux, uy): with psi = sqrt(q^2 xp^2 +
-// yp^2), zx = f xp/psi, zy = f yp/psi (f = sqrt(1 - q^2), A = theta_E sqrt(q)),
-//   ux = atan(zx)/f = (xp/psi) P_atan(zx^2),
-//   uy = atanh(zy)/f = (yp/psi) P_atanh(zy^2),
-// with atan(w) = w P_atan(w^2), atanh(w) = w P_atanh(w^2) (tll_poly.cuh); the
-// q = 1 limit needs no special case.  Vectors whose |zx| can exceed 1 or
-// |zy| exceed 1/2 take the general branch: atan(z) = sign(z) pi/2 -
-// atan(1/z) and atanh(z) = ln((1+z)/(1-z))/2 where needed, per point.
+// mass frame at (xp, yp), as alpha' = A (ux, uy) up to the column scales the
+// prologue folds into Q: with psi = sqrt(q^2 xp^2 + yp^2), zx = f xp/psi,
+// zy = f yp/psi (f = sqrt(1 - q^2), A = theta_E sqrt(q)):
+//  FAST (vectors with f/q <= 1 and f <= 1/2, so |zx| <= 1, |zy| <= 1/2):
+//   ux = atan(zx)/f = (xp/psi) P_atan(zx^2), uy = atanh(zy)/f = (yp/psi)
+//   P_atanh(zy^2), with atan(w) = w P_atan(w^2), atanh(w) = w P_atanh(w^2)
+//   (tll_poly.cuh); relative accuracy, and the q = 1 limit needs no special
+//   case.
+//  general (f > 1/2 here, so 1/f is bounded): ux = atan(zx), reduced to
+//   sign(z) pi/2 - atan(1/z) where |z| > 1; uy = log2(1 + zy) - log2(1 - zy)
+//   = 2 atanh(zy)/ln 2 (|zy| <= f < 1), accurate in absolute terms.
+template <bool FAST>
 __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
                                          float &ux, float &uy)
 {
     const float qx = v.q * xp;
     const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
     const float xr = xp * rpsi, yr = yp * rpsi;
-    const float zx = v.f * xr, zy = v.f * yr;
-    const float sx = zx * zx, sy = zy * zy;
-    if (v.fast) {
+    if (FAST) {
+        const float zx = v.f * xr, zy = v.f * yr;
+        const float sx = zx * zx, sy = zy * zy;
         ux = fmaf(xr * sx, poly_atan_q(sx), xr);
         uy = fmaf(yr * sy, poly_atanh_q(sy), yr);
     } else {
-        // atan: reduce |z| > 1 to 1/|z|
+        const float zx = v.f * xr, zy = v.f * yr;
         const float ax = fabsf(zx);
         const bool big = ax > 1.0f;
         const float w = big ? sfu_rcp(ax) : ax;
         const float sw = w * w;
         const float pw = fmaf(w * sw, poly_atan_q(sw), w);
-        float at = big ? (1.57079637f - pw) - 4.37113883e-08f : pw;
-        at = copysignf(at, zx);
-        // atanh: polynomial for |z| <= 1/2, logarithm above
-        const float ay = fminf(fabsf(zy), 0.99999994f);   // |zy| < f < 1
-        const float ph = fmaf(zy * sy, poly_atanh_q(sy), zy);
-        const float lg = 0.34657359f * sfu_lg2((1.0f + ay) * sfu_rcp(1.0f - ay));
-        const float ah = ay <= 0.5f ? ph : copysignf(lg, zy);
-        ux = at * v.invf;
-        uy = ah * v.invf;
+        const float at = big ? (1.57079637f - pw) - 4.37113883e-08f : pw;
+        ux = copysignf(at, zx);
+        uy = sfu_lg2(1.0f + zy) - sfu_lg2(1.0f - zy);
     }
 }
 
@@ -410,12 +417,13 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
                     fmaf(v.sx.ci, fi, v.sx.c0), fmaf(v.sy.ci, fi, v.sy.c0)};
 }
 
+template <bool FAST>
 __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
                                          float &il, float &is)
 {
     // SIE in its frame (lens equation's deflection, Eq. 1)
     float ux, uy;
-    sie_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
+    sie_unit<FAST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
     // lens light at theta (Eq. 2, first term)
     il = sersic_scaled(fmaf(v.lx.cj, fj, r.lx), fmaf(v.ly.cj, fj, r.ly), v.khl, v.kll,
                        v.bhl, v.bll);

@@ -64,7 +64,7 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
 // Subpixel (J, I) of the supersampled grid has exact integer-or-half
 // offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
 // coordinate is an affine function of them (see decode_vector).
-template <int SUB>
+template <int SUB, bool FAST>
 __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
                                             float *Il, float *Is, int stride, int off,
                                             int tid, int nthr)
@@ -83,7 +83,7 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
                     float il, is;
-                    subpixel(v, r, fj0 + (float)(SUB > 0 ? c : cr), il, is);
+                    subpixel<FAST>(v, r, fj0 + (float)(SUB > 0 ? c : cr), il, is);
                     accl += il;
                     accs += is;
                 }
@@ -412,23 +412,48 @@ __device__ __forceinline__ void setup_lens(const LensDev &L, float *spsf, int ti
     }
 }
 
-// One parameter vector (its constant block kc is valid): trace, convolve
-// with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
-// block barrier.
-// Convolve the two images with the fused sums.  K > 0: the compiled
-// convolution of side K on zero-padded bands (IMG_PADDED: the whole image is
-// one band already in place; IMG_BANDED: bands filled from the global slot);
-// K == 0: the generic convolution (IMG_SMEM, IMG_GLOBAL).
+// Warp reduction of a thread's five double-float sums; lane 0 stores the
+// warp's sums in FP64 to sred[warp*5 + k] (add: adds to what is there).
+__device__ __forceinline__ void warp_sums(float *acc, double *sred, int lane, int warp, bool add)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
+            df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double v = (double)acc[2 * k] + (double)acc[2 * k + 1];
+            sred[warp * 5 + k] = add ? sred[warp * 5 + k] + v : v;
+        }
+    }
+}
+
+// Convolve the two images with the fused sums; each warp's sums end in
+// sred[warp*5 + k] (FP64).  K > 0: the compiled convolution of side K on
+// zero-padded bands (IMG_PADDED: the whole image is one band already in
+// place; IMG_BANDED: bands filled from the global slot), each band's sums
+// reduced over the warp as it ends, so that no accumulator stays live
+// across bands; K == 0: the generic convolution (IMG_SMEM, IMG_GLOBAL).
 template <int K, bool WRITE>
 __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, const ImgPtrs &P,
-                                         const float *spsf, float *acc, int tid, int nthr)
+                                         float *spsf, double *sred, int tid, int nthr)
 {
+    const int lane = tid & 31, warp = tid >> 5;
     if constexpr (K > 0) {
         static_assert(!WRITE, "write-out runs on the generic placements");
         const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
         const bool banded = L.img == IMG_BANDED;
         const int step = banded ? L.band_rows : ny;
-        float *Pl = banded ? P.Hl : P.Il, *Ps = banded ? P.Hs : P.Is;
+        // Both placements convolve in the padded shared buffer at spsf (the
+        // same pointers img_ptrs gives), written here from spsf so that the
+        // compiler sees shared-memory addresses (32-bit, LDS/STS).
+        float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
         for (int b0 = 0; b0 < ny; b0 += step) {
             const int nrows = min(step, ny - b0);
             int rlo = h, rhi = h + ny;   // padded: image rows in place, halos zero
@@ -446,15 +471,18 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
                 rlo = max(0, h - b0);
                 rhi = min(nbr, ny - b0 + h);
             }
-            const Acc10 r = L.sep ? conv_sep_band<K>(L, Pl, Ps, b0, nrows, rlo, rhi, tid, nthr)
-                                  : conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr);
-#pragma unroll
-            for (int k = 0; k < 10; ++k) acc[k] += r.a[k];
+            Acc10 r = L.sep ? conv_sep_band<K>(L, Pl, Ps, b0, nrows, rlo, rhi, tid, nthr)
+                            : conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr);
+            warp_sums(r.a, sred, lane, warp, b0 > 0);
             if (banded) __syncthreads();
         }
     } else {
+        float acc[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
         conv_generic<WRITE>(L, R, spsf, P.Il, P.Is, P.Hl, P.Hs, acc, tid, nthr,
                             L.img == IMG_SMEM);
+        warp_sums(acc, sred, lane, warp, false);
     }
 }
 
@@ -464,13 +492,15 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
 template <int SUB, int K, bool WRITE>
 __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
                                             const float *kc, double *outp, const ImgPtrs &P,
-                                            const float *spsf, double *sred, int tid, int nthr)
+                                            float *spsf, double *sred, int tid, int nthr)
 {
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nx = L.nx, npix = L.npix;
     {
         const VecConst v = load_consts(kc);
-        trace_image<SUB>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
+        // the SIE branch is taken once per vector (uniform over the CTA)
+        if (v.fast) trace_image<SUB, true>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
+        else trace_image<SUB, false>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
     }
     __syncthreads();
     if (WRITE) {
@@ -481,26 +511,8 @@ __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
         }
         __syncthreads();
     }
-    float acc[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
-    convolve<K, WRITE>(L, R, P, spsf, acc, tid, nthr);
-
-    // warp reduction in double-float, block reduction in FP64
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
-            const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
-            df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k)
-            sred[warp * 5 + k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
-    }
+    // warp sums in double-float, then per warp in FP64, block sum in FP64
+    convolve<K, WRITE>(L, R, P, spsf, sred, tid, nthr);
     __syncthreads();
     if (warp == 0) {
         double sacc = 0.0;
