@@ -267,6 +267,10 @@ def run_ours(args):
     out = torch.empty(B, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
+    # launch shape: the autotuner times the candidate shapes on this batch
+    # (outside the timed region); lenses of the same signature created later
+    # in this process (the request stream's) start with the chosen shape
+    tune = None if args.no_autotune else L.autotune(p_dev)
 
     def barrier():
         if ws > 1:
@@ -369,7 +373,9 @@ def run_ours(args):
                          f"SIE+shear, Sersic lens+source, NNLS amplitudes"),
             "batch_per_gpu": B, "global_batch": B * ws, "path": "plain",
             "parallelism": f"replicas x{ws}",
-            "l2": "flushed between timed steps (256 MB write, outside the events)"},
+            "l2": "flushed between timed steps (256 MB write, outside the events)",
+            "launch_shape": L.shape(),
+            "autotune": tune["tried"] if tune else "off"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "subpixel_evals_per_s": value * lens.ny * lens.nx * lens.sub ** 2,
@@ -422,7 +428,7 @@ def run_ragged(args):
     t0 = time.perf_counter()
     rng, specs = W.ragged_specs(args.ragged_lenses)
     lenses, params = [], []
-    cache = {}
+    cache, tuned = {}, {}
     for side, k in specs:
         key = (side, k)
         if key not in cache:
@@ -434,6 +440,11 @@ def run_ragged(args):
                                sl.y0, batch_only=True))
         params.append(torch.from_numpy(W.shrinking_draws(rng, sl.truth,
                                                          args.ragged_vectors)).cuda())
+        if not args.no_autotune and key not in tuned:
+            # first lens of a signature: tune it; later ones start tuned
+            tuned[key] = lenses[-1].autotune(params[-1])["chosen"]
+        elif key in tuned:
+            assert lenses[-1].shape()["threads"] == tuned[key]["threads"]
     for _, r in cache.values():
         r.lens.close()
     setup_s = time.perf_counter() - t0
@@ -470,6 +481,8 @@ def run_ragged(args):
                                f"4x4 subpixels, {args.ragged_vectors} vectors each, one "
                                "multi-lens launch under a CUDA graph",
                    "global_batch": nvec, "setup_s": setup_s,
+                   "launch_shapes": sorted({(t["threads"], t["ctas_per_sm"], t["placement"])
+                                            for t in tuned.values()}) or "default",
                    "l2": "flushed between timed steps"},
         "subpixel_evals_per_s": nsub / (step / 1e3), "all_finite": allfin,
         "clocks": clk, "gpu_launches": 2 * args.steps, "impl": "ours"}
@@ -529,6 +542,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-stream", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--stream-jobs", type=int, default=32)
     ap.add_argument("--stream-iters", type=int, default=100)
     ap.add_argument("--stream-rate", type=float, default=20.0)

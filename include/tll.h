@@ -70,9 +70,10 @@ enum {
 /* Extra flag bit: never take the separable-PSF fast path (testing). */
 #define TLL_FLAG_DIRECT_CONV 0x100
 /* Extra flag bit: the lens is evaluated through a tll_batcher / tll_server;
- * skip the one-lens kernel's image slots for large images (up to
- * 152 x 16 B per pixel), allocated on first use by the allocating one-lens
- * entry points if it is evaluated alone after all. */
+ * skip the one-lens kernel's per-CTA image slots for images that do not fit
+ * shared memory (8 or 16 B per pixel per resident CTA), allocated on first
+ * use by the allocating one-lens entry points if it is evaluated alone
+ * after all. */
 #define TLL_FLAG_BATCH_ONLY 0x200
 
 typedef struct tll_lens tll_lens; /* opaque; owns device copies of its data */
@@ -183,6 +184,9 @@ typedef struct {
     int max_inflight;           /* launches in flight, 1..4 */
     int coalesce;               /* 1: merge pending requests; 0: one per launch */
     int use_graph;              /* replay each launch as a CUDA graph */
+    int autotune;               /* 1: tll_autotune (built-in vectors) each job
+                                   whose lens signature is not tuned yet, at
+                                   admission, on a stream of its own */
 } tll_server_config_t;
 typedef struct {
     long long launches, vectors, requests, admissions_refused, pending, inflight;
@@ -231,7 +235,7 @@ const char *tll_server_last_error(void);
  *   Same arguments, results and asynchrony as tll_loglike_batch.
  *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
  *     them into several calls).
- *   Scratch: a fixed 3 MiB array compiled into the library, held on every
+ *   Scratch: a fixed 3.5 MiB array compiled into the library, held on every
  *     GPU that loads it until the process exits.  All calls share it and it
  *     keeps the last call's contents; each call rewrites the part it reads
  *     before reading it.  Calls that overlap on the GPU (different streams,
@@ -282,6 +286,76 @@ int tll_profile_last(tll_lens *L, float *prologue_ms, float *main_ms);
 /* Device memory a lens currently holds, in bytes (its data, the model
  * buffers, and the scratch it has grown). */
 int tll_lens_footprint(const tll_lens *L, size_t *bytes);
+
+/*
+ * Launch shapes and the autotuner.
+ * A lens's batched likelihood kernels (tll_loglike_batch*, and the lens's
+ * group in tll_batcher_run / the server) run persistent CTAs, each taking
+ * one parameter vector at a time (ray-trace + light of every subpixel,
+ * binning, PSF convolution, weighted sums; Sec. 2.1-2.4).  Its shape is the
+ * CTA size, how many CTAs share an SM, and where each CTA keeps the two
+ * binned images:
+ *   TLL_PLACE_PADDED  whole zero-padded images in shared memory, convolution
+ *                     compiled for the PSF side (PSF side <= 31, nx <= 256)
+ *   TLL_PLACE_BANDED  images in a per-CTA global slot (L2-resident),
+ *                     convolved band by band through a padded shared buffer
+ *                     (same compiled convolution; images too large to pad)
+ *   TLL_PLACE_SMEM    unpadded images in shared memory, generic convolution
+ *   TLL_PLACE_GLOBAL  images in a per-CTA global slot, generic convolution
+ * A new lens takes 1024-thread CTAs, one per SM, and the first placement
+ * that fits -- or the tuned shape of an earlier lens with the same
+ * signature (device, nx, ny, s, PSF side, separable PSF) in this process.
+ */
+enum {
+    TLL_PLACE_GLOBAL = 0,
+    TLL_PLACE_SMEM = 1,
+    TLL_PLACE_PADDED = 2,
+    TLL_PLACE_BANDED = 3
+};
+typedef struct {
+    int threads;        /* CTA size */
+    int ctas_per_sm;    /* CTAs resident per SM; a launch has SMs x this CTAs */
+    int placement;      /* TLL_PLACE_* */
+    int band_rows;      /* output rows per band (TLL_PLACE_BANDED), else 0 */
+    size_t smem_bytes;  /* dynamic shared memory per CTA */
+    float ms;           /* mean time of one tuning batch (0: not timed) */
+    int tuned;          /* 1: chosen by tll_autotune (here or for an earlier
+                           lens of the same signature) */
+} tll_shape_t;
+
+/* The lens's current launch shape. Errors: TLL_EINVAL (NULL argument). */
+int tll_lens_shape(const tll_lens *L, tll_shape_t *out);
+
+/*
+ * tll_set_shape -- give the lens the shape of `threads`-thread CTAs (a
+ * multiple of 32, <= 1024) with ctas_per_sm of them per SM, and the
+ * placement that share of shared memory allows.  Waits for the device to
+ * be idle first.  Errors: TLL_EINVAL (no such shape fits), TLL_ENOMEM,
+ * TLL_ECUDA (the lens keeps its shape).
+ */
+int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm);
+
+/*
+ * tll_autotune -- time the candidate shapes (1 x 1024, 2 x 512 and 4 x 256
+ * threads per SM, each with the placement its shared-memory share allows)
+ * on the device and give the lens the fastest; later lenses with the same
+ * signature start with it.
+ *   params     DEVICE float32 [B][TLL_NPARAM] vectors to time with, repeated
+ *              to at least two per CTA; or NULL with B = 0 for a built-in
+ *              set covering both SIE branches and steep and shallow Sersics
+ *   stream     cudaStream_t the tuning launches run on (NULL: default)
+ *   chosen     receives the chosen shape (may be NULL)
+ *   tried      receives up to max_tried candidate shapes with their times
+ *   n_tried    receives the number of candidates timed (may be NULL)
+ * Blocks until the tuning launches end.  Allocates temporary device buffers;
+ * the lens's one-lens image slots are resized to the chosen shape.  Must
+ * not run while other calls use the same lens.  Results of the likelihood
+ * do not depend on the shape beyond rounding (the sums' order changes).
+ * Errors: TLL_EINVAL, TLL_ENOMEM, TLL_ECUDA (the lens keeps its shape).
+ */
+int tll_autotune(tll_lens *L, const float *params, int B, void *stream,
+                 tll_shape_t *chosen, tll_shape_t *tried, int max_tried,
+                 int *n_tried);
 
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,

@@ -28,7 +28,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -105,6 +107,21 @@ __global__ void k_combine(const float *__restrict__ blurred,
 }  // namespace
 
 // ------------------------------------------------------------ lens object
+namespace {
+// Launch shape of the likelihood kernels for one lens: CTA size, CTAs
+// resident per SM, where the two images live, and what that costs.
+struct Shape {
+    int threads = kThreads;   // CTA size (multiple of 32, <= kThreads)
+    int per_sm = 1;           // resident CTAs per SM at this shared memory
+    int img = IMG_GLOBAL;     // IMG_*
+    int band_rows = 0;        // IMG_BANDED output rows per band
+    size_t smem = 0;          // dynamic shared memory per CTA
+    int grid_cap = 0;         // nsm * per_sm: persistent CTAs of one launch
+    long long gslot = 0;      // floats of global image slot per CTA (0: none)
+    float ms = 0.0f;          // tuning time per launch (0: not timed)
+};
+}  // namespace
+
 struct tll_lens {
     int dev = 0;
     int nx = 0, ny = 0, npix = 0, sub = 0, K = 0, flags = 0, mode = 0, sep = 0;
@@ -121,14 +138,13 @@ struct tll_lens {
     float *d_p1 = nullptr, *d_kc1 = nullptr, *d_unb = nullptr, *d_blur = nullptr,
           *d_img = nullptr;
     double *d_res = nullptr, *d_out1 = nullptr;
-    int img = 0;          // IMG_GLOBAL / IMG_SMEM / IMG_PADDED / IMG_BANDED
+    Shape shape;          // launch shape of the batched likelihood kernels
+    bool tuned = false;   // shape chosen by tll_autotune (or its cache)
     int img_write = 0;    // placement of the write-out (model image) launches
     size_t smem_write = 0;
     int W = 0, HL = 0;    // padded layout geometry
-    int band_rows = 0;    // IMG_BANDED rows per band
     std::vector<float> taps_u, taps_v, psf_norm;
-    int grid_cap = 0;
-    size_t smem_bytes = 0;
+    long long gscr_floats = 0;   // size of d_gscr
     const double *bn_tab = nullptr;   // per-device b_n table (not owned)
     size_t dev_bytes = 0;             // device memory this lens holds
     cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
@@ -193,7 +209,7 @@ LensDev lens_dev(const tll_lens *L)
     d.inv_s2 = 1.0f / (float)(L->sub * L->sub);
     d.psf = L->d_psf; d.pu = L->d_pu; d.pv = L->d_pv; d.wpack = L->d_wpack;
     d.dWd = L->dWd; d.lognorm = L->lognorm;
-    d.W = L->W; d.HL = L->HL; d.img = L->img; d.band_rows = L->band_rows;
+    d.W = L->W; d.HL = L->HL; d.img = L->shape.img; d.band_rows = L->shape.band_rows;
     for (int k = 0; k < kMaxK * kMaxK; ++k)
         d.tk[k] = k < (int)L->psf_norm.size() && L->K <= kMaxK ? L->psf_norm[k] : 0.0f;
     grid_centre(L, &d.XC, &d.YC);
@@ -241,9 +257,10 @@ int launch_main(const tll_lens *L, const RunArgs &R, int grid, bool write, cudaS
     LensDev d = lens_dev(L);
     if (write) d.img = L->img_write;
     const SingleKernel kern = write ? find_single(L->sub, 0, true)
-                                    : find_single(L->sub, conv_class(L->img, L->K), false);
+                                    : find_single(L->sub, conv_class(L->shape.img, L->K), false);
     if (!kern) return fail(TLL_ECUDA, "no kernel for s=%d K=%d", L->sub, L->K);
-    kern<<<grid, kThreads, write ? L->smem_write : L->smem_bytes, st>>>(d, R);
+    kern<<<grid, write ? kThreads : L->shape.threads, write ? L->smem_write : L->shape.smem,
+           st>>>(d, R);
     CUDA_TRY(cudaGetLastError());
     return TLL_OK;
 }
@@ -260,9 +277,9 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
     RunArgs R;
-    R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr;
+    R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr; R.gslot = L->shape.gslot;
     R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
-    const int grid = std::min(B, L->grid_cap);
+    const int grid = std::min(B, L->shape.grid_cap);
     if (write) return launch_main(L, R, 1, true, st);
     const int rc = launch_main(L, R, grid, false, st);
     if (rc == TLL_OK && prof) {
@@ -289,39 +306,106 @@ int ensure_kc(tll_lens *L, int B)
 // copy of a lens descriptor), so every lens also fits that kernel.
 constexpr int kSmemReserve = 8192;
 
-int configure(tll_lens *L)
+struct DevLimits {
+    int nsm = 0, optin = 0, per_sm_smem = 0, reserved = 0;
+};
+
+int dev_limits(int dev, DevLimits *D)
 {
-    int nsm = 0, optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, L->dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, L->dev));
-    const size_t avail = (size_t)optin - kSmemReserve;
-    // placement: for PSF side <= 31 and nx <= 256 the compiled convolutions,
-    // on the whole zero-padded image in shared memory if it fits, else band
-    // by band from a global slot; otherwise the generic convolution on
-    // unpadded shared memory or a global slot.
+    CUDA_TRY(cudaDeviceGetAttribute(&D->nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&D->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&D->per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                    dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&D->reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    return TLL_OK;
+}
+
+// The shape of running lens L with CTAs of `threads` threads, `per_sm` of
+// them per SM: each CTA gets an equal share of the SM's shared memory (less
+// the multi-lens kernel's static part).  Placement: for PSF side <= 31 and
+// nx <= 256 the compiled convolutions, on the whole zero-padded image in
+// shared memory if it fits, else band by band (bands of equal height) from
+// a global slot; otherwise the generic convolution on unpadded shared
+// memory or a global slot.  S->per_sm is the occupancy actually reached.
+int make_shape(const tll_lens *L, const DevLimits &D, int threads, int per_sm, Shape *out)
+{
+    if (threads < 32 || threads > kThreads || threads % 32 || per_sm < 1)
+        return fail(TLL_EINVAL, "bad launch shape %d x %d", threads, per_sm);
+    Shape S;
+    S.threads = threads;
+    const long long share =
+        std::min<long long>(D.optin, D.per_sm_smem / per_sm - D.reserved);
+    const long long avail = share - kSmemReserve;
     const int h = (L->K - 1) / 2;
-    L->img = -1;
+    S.img = -1;
     if (L->K <= kMaxK && L->nx <= 256) {
-        const int Wp = padded_stride(L->nx, L->K);
-        const size_t row_bytes = (size_t)2 * Wp * sizeof(float);
+        const size_t row_bytes = (size_t)2 * L->W * sizeof(float);
         const size_t whole = kRedBytes + (size_t)(L->ny + 2 * h + kCR) * row_bytes;
-        const long long br = (long long)((avail - kRedBytes) / row_bytes) - 2 * h - kCR;
-        L->W = Wp;
-        L->HL = (h + 3) & ~3;
-        if (whole <= avail) {
-            L->img = IMG_PADDED;
-            L->smem_bytes = whole;
+        const long long br = (avail - kRedBytes) / (long long)row_bytes - 2 * h - kCR;
+        if ((long long)whole <= avail) {
+            S.img = IMG_PADDED;
+            S.smem = whole;
         } else if (br >= 8) {
-            L->img = IMG_BANDED;
-            L->band_rows = (int)std::min<long long>(br, L->ny);
-            L->smem_bytes = kRedBytes + (size_t)(L->band_rows + 2 * h + kCR) * row_bytes;
+            const long long nb = (L->ny + br - 1) / br;
+            S.img = IMG_BANDED;
+            S.band_rows = (int)((L->ny + nb - 1) / nb);
+            S.smem = kRedBytes + (size_t)(S.band_rows + 2 * h + kCR) * row_bytes;
+            S.gslot = 2LL * L->npix;
         }
     }
-    {   // the generic placement: for lenses without a compiled one, and
-        // for every lens's write-out launches
+    if (S.img < 0) {
         const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
         const size_t fixed = kRedBytes + (size_t)((psf_floats + 3) & ~3) * sizeof(float);
         const size_t plain = fixed + (size_t)2 * L->npix * sizeof(float);
+        if ((long long)plain <= avail && L->nx <= 32 * kHMax) {
+            S.img = IMG_SMEM;
+            S.smem = plain;
+        } else if ((long long)fixed <= avail) {
+            S.img = IMG_GLOBAL;
+            S.smem = fixed;
+            S.gslot = 4LL * L->npix;
+        } else {
+            return fail(TLL_EINVAL, "no placement for %d CTAs per SM", per_sm);
+        }
+    }
+    const SingleKernel k = find_single(L->sub, conv_class(S.img, L->K), false);
+    if (!k) return fail(TLL_ECUDA, "no kernel for s=%d K=%d", L->sub, L->K);
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, D.optin));
+    int n = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, S.smem));
+    if (n < 1) return fail(TLL_EINVAL, "k_loglike cannot be resident at %d threads", threads);
+    S.per_sm = n;
+    S.grid_cap = D.nsm * n;
+    *out = S;
+    return TLL_OK;
+}
+
+// Tuned shapes by lens signature (device, nx, ny, s, K, separable): lenses
+// created later with a tuned signature start with its shape.
+struct TuneKey {
+    int dev, nx, ny, sub, K, sep;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dev, nx, ny, sub, K, sep) < std::tie(o.dev, o.nx, o.ny, o.sub, o.K, o.sep);
+    }
+};
+std::map<TuneKey, std::pair<int, int>> g_tuned;   // -> (threads, CTAs per SM asked)
+std::mutex g_tune_mu;
+
+TuneKey tune_key(const tll_lens *L) { return TuneKey{L->dev, L->nx, L->ny, L->sub, L->K, L->sep}; }
+
+int configure(tll_lens *L)
+{
+    DevLimits D;
+    int rc = dev_limits(L->dev, &D);
+    if (rc) return rc;
+    L->W = padded_stride(L->nx, L->K);
+    L->HL = (((L->K - 1) / 2) + 3) & ~3;
+    {   // the write-out (model image) launches: generic placement, one CTA
+        const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
+        const size_t fixed = kRedBytes + (size_t)((psf_floats + 3) & ~3) * sizeof(float);
+        const size_t plain = fixed + (size_t)2 * L->npix * sizeof(float);
+        const size_t avail = (size_t)D.optin - kSmemReserve;
         if (plain <= avail && L->nx <= 32 * kHMax) {
             L->img_write = IMG_SMEM;
             L->smem_write = plain;
@@ -329,36 +413,55 @@ int configure(tll_lens *L)
             L->img_write = IMG_GLOBAL;
             L->smem_write = fixed;
         }
+        const SingleKernel kw = find_single(L->sub, 0, true);
+        if (!kw) return fail(TLL_ECUDA, "no kernel for s=%d", L->sub);
+        CUDA_TRY(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, D.optin));
     }
-    if (L->img < 0) {
-        L->img = L->img_write;
-        L->smem_bytes = L->smem_write;
+    int threads = kThreads, per_sm = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(L));
+        if (it != g_tuned.end()) {
+            threads = it->second.first;
+            per_sm = it->second.second;
+            L->tuned = true;
+        }
     }
-    // this lens's kernels may use the device's full opt-in shared memory
-    const SingleKernel kmain = find_single(L->sub, conv_class(L->img, L->K), false);
-    const SingleKernel kwrite = find_single(L->sub, 0, true);
-    if (!kmain || !kwrite) return fail(TLL_ECUDA, "no kernel for s=%d K=%d", L->sub, L->K);
-    CUDA_TRY(cudaFuncSetAttribute(kmain, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    CUDA_TRY(cudaFuncSetAttribute(kwrite, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmain, kThreads,
-                                                           L->smem_bytes));
-    if (per_sm < 1) return fail(TLL_ECUDA, "k_loglike cannot be resident on an SM");
-    L->grid_cap = nsm * per_sm;
-    return TLL_OK;
+    rc = make_shape(L, D, threads, per_sm, &L->shape);
+    if (rc && L->tuned) {
+        L->tuned = false;
+        rc = make_shape(L, D, kThreads, 1, &L->shape);
+    }
+    return rc;
 }
 
-// The one-lens kernel's per-CTA global image slots (IMG_GLOBAL lenses).
-// Allocated at creation, except for lenses created TLL_FLAG_BATCH_ONLY
-// (evaluated through a batcher, which has its own slots); for those the
-// allocating one-lens entry points allocate on first use.
+long long gscr_need(const tll_lens *L)
+{
+    long long n = (long long)L->shape.grid_cap * L->shape.gslot;
+    if (L->img_write == IMG_GLOBAL) n = std::max(n, 4LL * L->npix);
+    return n;
+}
+
+// The one-lens kernel's per-CTA global image slots (shapes that keep the
+// images in global memory, and the generic write-out).  Allocated at
+// creation, except for lenses created TLL_FLAG_BATCH_ONLY (evaluated
+// through a batcher, which has its own slots); for those the allocating
+// one-lens entry points allocate on first use.  Grows (never shrinks
+// here) when the shape changes.
 int ensure_gscr(tll_lens *L)
 {
-    const bool needs = L->img == IMG_GLOBAL || L->img == IMG_BANDED || L->img_write == IMG_GLOBAL;
-    if (!needs || L->d_gscr) return TLL_OK;
-    const size_t n = (size_t)L->grid_cap * 4 * L->npix;
-    CUDA_TRY(cudaMalloc(&L->d_gscr, n * sizeof(float)));
-    L->dev_bytes += n * sizeof(float);
+    const long long need = gscr_need(L);
+    if (need <= L->gscr_floats) return TLL_OK;
+    if (L->d_gscr) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(L->d_gscr);
+        L->d_gscr = nullptr;
+        L->dev_bytes -= (size_t)L->gscr_floats * sizeof(float);
+        L->gscr_floats = 0;
+    }
+    CUDA_TRY(cudaMalloc(&L->d_gscr, (size_t)need * sizeof(float)));
+    L->gscr_floats = need;
+    L->dev_bytes += (size_t)need * sizeof(float);
     return TLL_OK;
 }
 
@@ -401,10 +504,23 @@ int run_one(tll_lens *L, const float *params_host)
 // each group is one launch of its k_loglike_multi<SUB, K>.
 constexpr int kMaxGroups = 64;
 
+namespace {
+// One group's launch: kernel, CTA size, grid and dynamic shared memory.
+struct GroupLaunch {
+    MultiKernel kern = nullptr;
+    int threads = 0, grid = 0;
+    size_t smem = 0;
+    bool operator==(const GroupLaunch &o) const
+    {
+        return kern == o.kern && threads == o.threads && grid == o.grid && smem == o.smem;
+    }
+};
+}  // namespace
+
 struct tll_batcher {
     int dev = 0, nsm = 0, optin = 0, dyn_smem = 0;
     bool use_graph = false;
-    int cap_lenses = 0, cap_segs = 0, cap_items = 0;
+    int cap_lenses = 0, cap_segs = 0, cap_items = 0, cap_ctas = 0;
     long long gslot_floats = 0;
     LensDev *d_lenses = nullptr, *h_lenses = nullptr;   // h_*: pinned staging
     Segment *d_segs = nullptr, *h_segs = nullptr;
@@ -414,11 +530,11 @@ struct tll_batcher {
     const double *bn_tab = nullptr;
     cudaEvent_t staged = nullptr;      // staging may be refilled after this
     bool staged_pending = false;
-    std::vector<MultiKernel> kern;     // this run's group kernels
+    std::vector<GroupLaunch> glaunch;  // this run's group launches
     std::vector<MultiKernel> kern_ready;  // kernels whose shared-memory limit is set
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;    // stream the graph was captured on
-    std::vector<MultiKernel> gkern;    // group kernels baked into the graph
+    std::vector<GroupLaunch> gcaptured;   // group launches baked into the graph
     long long launches = 0;
 };
 
@@ -443,12 +559,13 @@ void batcher_free_buffers(tll_batcher *b)
     }
 }
 
-// Grow every buffer to hold (lenses, segs, items, gslot); the graph (which
-// bakes in the buffer addresses and copy sizes) is dropped when anything grows.
-int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long gslot)
+// Grow every buffer to hold (lenses, segs, items, gslot floats for each of
+// ctas CTAs); the graph (which bakes in the buffer addresses and copy
+// sizes) is dropped when anything grows.
+int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long gslot, int ctas)
 {
     if (lenses <= b->cap_lenses && segs <= b->cap_segs && items <= b->cap_items &&
-        gslot <= b->gslot_floats && b->d_kc)
+        gslot <= b->gslot_floats && (gslot == 0 || ctas <= b->cap_ctas) && b->d_kc)
         return TLL_OK;
     if (b->staged_pending) CUDA_TRY(cudaEventSynchronize(b->staged));
     CUDA_TRY(cudaDeviceSynchronize());
@@ -456,13 +573,14 @@ int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long g
     const int cs = std::max(segs, std::max(2 * b->cap_segs, 64));
     const int ci = std::max(items, std::max(2 * b->cap_items, 4096));
     const long long cg = std::max(gslot, b->gslot_floats);
+    const int cc = std::max(ctas, b->cap_ctas);
     batcher_free_buffers(b);
     CUDA_TRY(cudaMalloc(&b->d_lenses, cl * sizeof(LensDev)));
     CUDA_TRY(cudaMalloc(&b->d_segs, cs * sizeof(Segment)));
     CUDA_TRY(cudaMalloc(&b->d_groups, (kMaxGroups + 1) * sizeof(MultiHdr)));
     CUDA_TRY(cudaMalloc(&b->d_kc, (size_t)ci * NCONST * sizeof(float)));
     CUDA_TRY(cudaMalloc(&b->d_counter, kMaxGroups * sizeof(int)));
-    if (cg > 0) CUDA_TRY(cudaMalloc(&b->d_gscr, (size_t)b->nsm * cg * sizeof(float)));
+    if (cg > 0) CUDA_TRY(cudaMalloc(&b->d_gscr, (size_t)cc * cg * sizeof(float)));
     CUDA_TRY(cudaMallocHost(&b->h_lenses, cl * sizeof(LensDev)));
     CUDA_TRY(cudaMallocHost(&b->h_segs, cs * sizeof(Segment)));
     CUDA_TRY(cudaMallocHost(&b->h_groups, (kMaxGroups + 1) * sizeof(MultiHdr)));
@@ -470,6 +588,7 @@ int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long g
     b->cap_segs = cs;
     b->cap_items = ci;
     b->gslot_floats = cg;
+    b->cap_ctas = cc;
     return TLL_OK;
 }
 
@@ -505,8 +624,9 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
     const MultiArgs A = batcher_args(b);
     k_prologue_multi<<<(items + 127) / 128, 128, 0, st>>>(A);
     CUDA_TRY(cudaGetLastError());
-    for (int g = 0; g < (int)b->kern.size(); ++g) {
-        b->kern[g]<<<b->nsm, kThreads, b->dyn_smem, st>>>(A, g);
+    for (int g = 0; g < (int)b->glaunch.size(); ++g) {
+        const GroupLaunch &gl = b->glaunch[g];
+        gl.kern<<<gl.grid, gl.threads, gl.smem, st>>>(A, g);
         CUDA_TRY(cudaGetLastError());
     }
     return TLL_OK;
@@ -518,7 +638,7 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
 // array in the module instead, so the call itself allocates nothing; every
-// GPU that loads this library holds it (3 MiB) until the process exits.
+// GPU that loads this library holds it (3.5 MiB) until the process exits.
 constexpr int kNoAllocMaxB = 16384;
 static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
 
@@ -602,8 +722,10 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
     cudaStream_t st = (cudaStream_t)stream;
     // distinct lenses; entries ordered by group key, then cost (largest first)
     std::vector<tll_lens *> uniq;
-    std::vector<int> lid(n), order, key(n);
+    std::vector<int> lid(n), order;
+    std::vector<long long> key(n);
     long long total = 0, gslot = 0;
+    int ctas = 0;
     for (int k = 0; k < n; ++k) {
         tll_lens *L = lenses[k];
         if (!L) return fail(TLL_EINVAL, "lens %d is NULL", k);
@@ -611,17 +733,24 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         if (counts[k] < 0) return fail(TLL_EINVAL, "negative count for lens %d", k);
         if (counts[k] > 0 && (!params[k] || !outs[k]))
             return fail(TLL_EINVAL, "NULL params/out for lens %d", k);
-        if (L->smem_bytes > (size_t)b->dyn_smem)
+        const Shape &S = L->shape;
+        if (S.smem > (size_t)b->dyn_smem)
             return fail(TLL_EINVAL, "lens %d needs more shared memory than the batch kernel has", k);
         int u = 0;
         while (u < (int)uniq.size() && uniq[u] != L) ++u;
         if (u == (int)uniq.size()) uniq.push_back(L);
         lid[k] = u;
-        key[k] = sub_class(L->sub) * 1000 + conv_class(L->img, L->K);
-        if (counts[k] > 0) order.push_back(k);
+        // group key: supersampling class, convolution class, CTA size, CTAs per SM
+        key[k] = (((long long)sub_class(L->sub) * 1000 + conv_class(S.img, L->K)) * 2048 +
+                  S.threads) * 64 + std::min(S.per_sm, 63);
+        if (counts[k] > 0) {
+            order.push_back(k);
+            if (S.gslot > 0) {
+                gslot = std::max(gslot, S.gslot);
+                ctas = std::max(ctas, b->nsm * S.per_sm);
+            }
+        }
         total += counts[k];
-        if (L->img == IMG_GLOBAL || L->img == IMG_BANDED)
-            gslot = std::max(gslot, (long long)4 * L->npix);
     }
     if (total == 0) return TLL_OK;
     if (total > (1LL << 30)) return fail(TLL_EINVAL, "batch too large");
@@ -631,28 +760,35 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         const long long wc = (long long)lenses[c]->npix * lenses[c]->sub * lenses[c]->sub;
         return wa > wc;
     });
-    int rc = batcher_reserve(b, (int)uniq.size(), n, (int)total, gslot);
+    int rc = batcher_reserve(b, (int)uniq.size(), n, (int)total, gslot, ctas);
     if (rc) return rc;
     if (b->staged_pending) CUDA_TRY(cudaEventSynchronize(b->staged));
     for (size_t u = 0; u < uniq.size(); ++u) b->h_lenses[u] = lens_dev(uniq[u]);
-    b->kern.clear();
+    b->glaunch.clear();
     int first = 0, ns = 0, ng = 0;
     for (size_t q = 0; q < order.size(); ++q) {
         const int k = order[q];
+        const Shape &S = lenses[k]->shape;
         if (q == 0 || key[k] != key[order[q - 1]]) {
             if (ng == kMaxGroups) return fail(TLL_EINVAL, "more than %d kernel groups", kMaxGroups);
-            const MultiKernel mk = find_multi(lenses[k]->sub, key[k] % 1000);
+            const int Kc = conv_class(S.img, lenses[k]->K);
+            const MultiKernel mk = find_multi(lenses[k]->sub, Kc);
             if (!mk) return fail(TLL_ECUDA, "no multi-lens kernel for s=%d K=%d", lenses[k]->sub,
-                                 key[k] % 1000);
+                                 Kc);
             if (std::find(b->kern_ready.begin(), b->kern_ready.end(), mk) == b->kern_ready.end()) {
                 CUDA_TRY(cudaFuncSetAttribute(mk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               b->dyn_smem));
                 b->kern_ready.push_back(mk);
             }
-            b->kern.push_back(mk);
+            GroupLaunch gl;
+            gl.kern = mk;
+            gl.threads = S.threads;
+            gl.grid = b->nsm * S.per_sm;
+            b->glaunch.push_back(gl);
             b->h_groups[ng] = MultiHdr{first, 0, ns, 0};
             ++ng;
         }
+        b->glaunch.back().smem = std::max(b->glaunch.back().smem, S.smem);
         Segment &sg = b->h_segs[ns++];
         sg.lens = lid[k];
         sg.first = first;
@@ -667,7 +803,7 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
     b->h_groups[kMaxGroups] = MultiHdr{0, (int)total, 0, ns};
     const bool graph = b->use_graph && st != nullptr;
     if (graph) {
-        if (!b->gexec || b->gstream != st || b->gkern != b->kern) {
+        if (!b->gexec || b->gstream != st || !(b->gcaptured == b->glaunch)) {
             if (b->gexec) {
                 cudaGraphExecDestroy(b->gexec);
                 b->gexec = nullptr;
@@ -686,7 +822,7 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
             if (ie != cudaSuccess)
                 return fail(TLL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
             b->gstream = st;
-            b->gkern = b->kern;
+            b->gcaptured = b->glaunch;
         }
         CUDA_TRY(cudaGraphLaunch(b->gexec, st));
     } else {
@@ -710,7 +846,7 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *o
                     B, kNoAllocMaxB);
     if (B == 0) return TLL_OK;
     if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
-    if ((L->img == IMG_GLOBAL || L->img == IMG_BANDED) && !L->d_gscr)
+    if (L->gscr_floats < gscr_need(L))
         return fail(TLL_EINVAL, "lens was created TLL_FLAG_BATCH_ONLY and has no one-lens "
                                 "image slots; evaluate it with tll_loglike_batch once first");
     DeviceGuard gd(L->dev);
@@ -722,6 +858,182 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *o
     return run_batch(L, params, B, out, (cudaStream_t)stream, false, kc);
 }
 
+
+static_assert(TLL_PLACE_GLOBAL == IMG_GLOBAL && TLL_PLACE_SMEM == IMG_SMEM &&
+                  TLL_PLACE_PADDED == IMG_PADDED && TLL_PLACE_BANDED == IMG_BANDED,
+              "placement codes");
+
+namespace {
+void shape_out(const Shape &S, tll_shape_t *o)
+{
+    o->threads = S.threads;
+    o->ctas_per_sm = S.per_sm;
+    o->placement = S.img;
+    o->band_rows = S.band_rows;
+    o->smem_bytes = S.smem;
+    o->ms = S.ms;
+    o->tuned = 0;
+}
+
+// Parameter vectors for timing when the caller gives none: a fixed set
+// spanning both SIE forms (q near 1 and q well below it), both Sersic
+// extremes of the usual prior, and sources inside and outside the caustic.
+void default_tuning_vectors(int B, std::vector<float> &p)
+{
+    p.assign((size_t)B * NPAR, 0.0f);
+    for (int b = 0; b < B; ++b) {
+        float *v = &p[(size_t)b * NPAR];
+        const int k = b % 8;
+        v[0] = 0.7f + 0.1f * (float)k;              // theta_E
+        v[1] = (k & 1) ? 0.25f : 0.04f;             // e1 (q = 0.6 or 0.92)
+        v[2] = 0.02f;
+        v[3] = 0.01f; v[4] = -0.02f;                // centre
+        v[5] = 0.03f; v[6] = -0.02f;                // shear
+        v[7] = 1.0f; v[8] = 0.6f; v[9] = (k & 2) ? 4.0f : 1.0f;
+        v[10] = 0.1f; v[11] = -0.05f;
+        v[12] = v[3]; v[13] = v[4];
+        v[14] = 1.0f; v[15] = 0.25f; v[16] = (k & 4) ? 3.0f : 1.2f;
+        v[17] = -0.1f; v[18] = 0.08f;
+        v[19] = (k & 1) ? 0.05f : 0.2f; v[20] = -0.03f;
+    }
+}
+}  // namespace
+
+extern "C" int tll_lens_shape(const tll_lens *L, tll_shape_t *out)
+{
+    if (!L || !out) return fail(TLL_EINVAL, "NULL argument");
+    shape_out(L->shape, out);
+    out->tuned = L->tuned ? 1 : 0;
+    return TLL_OK;
+}
+
+extern "C" int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    DeviceGuard gd(L->dev);
+    DevLimits D;
+    int rc = dev_limits(L->dev, &D);
+    if (rc) return rc;
+    Shape S;
+    if ((rc = make_shape(L, D, threads, ctas_per_sm, &S))) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());   // no launch of the old shape in flight
+    const Shape keep = L->shape;
+    L->shape = S;
+    if (!(L->flags & TLL_FLAG_BATCH_ONLY) && (rc = ensure_gscr(L))) {
+        L->shape = keep;
+        return rc;
+    }
+    return TLL_OK;
+}
+
+extern "C" int tll_autotune(tll_lens *L, const float *params, int B, void *stream,
+                            tll_shape_t *chosen, tll_shape_t *tried, int max_tried,
+                            int *n_tried)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (B < 0 || (B > 0 && !params)) return fail(TLL_EINVAL, "bad tuning batch");
+    if (max_tried < 0 || (max_tried > 0 && !tried)) return fail(TLL_EINVAL, "bad tried array");
+    DeviceGuard gd(L->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    DevLimits D;
+    int rc = dev_limits(L->dev, &D);
+    if (rc) return rc;
+    // candidates: 1024 threads resident per SM as 1 x 1024, 2 x 512, 4 x 256
+    static const int kCand[][2] = {{1024, 1}, {512, 2}, {256, 4}};
+    std::vector<Shape> cand;
+    std::vector<int> ask;   // CTAs per SM each candidate was made for
+    for (const auto &c : kCand) {
+        Shape S;
+        if (make_shape(L, D, c[0], c[1], &S) == TLL_OK) {
+            cand.push_back(S);
+            ask.push_back(c[1]);
+        }
+    }
+    g_err[0] = 0;
+    if (cand.empty()) return fail(TLL_ECUDA, "no launch shape fits this lens");
+    int grid_max = 0;
+    for (const Shape &S : cand) grid_max = std::max(grid_max, S.grid_cap);
+    // tuning batch: at least two vectors per CTA of the largest grid; the
+    // caller's vectors repeated, or the default set
+    const int Bt = std::max(B, 2 * grid_max);
+    float *d_p = nullptr;
+    double *d_o = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        if (d_p) cudaFree(d_p);
+        if (d_o) cudaFree(d_o);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    auto bail = [&](int code) { cleanup(); return code; };
+    if (cudaMalloc(&d_p, (size_t)Bt * NPAR * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&d_o, (size_t)Bt * sizeof(double)) != cudaSuccess)
+        return bail(fail(TLL_ENOMEM, "tuning buffers"));
+    if (B > 0) {
+        for (int off = 0; off < Bt; off += B) {
+            const int n = std::min(B, Bt - off);
+            if (cudaMemcpyAsync(d_p + (size_t)off * NPAR, params, (size_t)n * NPAR * sizeof(float),
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return bail(fail(TLL_ECUDA, "tuning batch copy"));
+        }
+    } else {
+        std::vector<float> hp;
+        default_tuning_vectors(Bt, hp);
+        if (cudaMemcpyAsync(d_p, hp.data(), hp.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return bail(fail(TLL_ECUDA, "tuning batch copy"));
+    }
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+        return bail(fail(TLL_ECUDA, "cudaEventCreate"));
+    if ((rc = ensure_kc(L, Bt))) return bail(rc);
+    const Shape keep = L->shape;
+    int best = -1;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        L->shape = cand[c];
+        if ((rc = ensure_gscr(L))) break;
+        // one warm-up launch, then three timed
+        if ((rc = run_batch(L, d_p, Bt, d_o, st, false, L->d_kc))) break;
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) { rc = fail(TLL_ECUDA, "event"); break; }
+        for (int r = 0; r < 3 && !rc; ++r) rc = run_batch(L, d_p, Bt, d_o, st, false, L->d_kc);
+        if (rc) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+            rc = fail(TLL_ECUDA, "tuning launch: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        cand[c].ms = ms / 3.0f;
+        if (best < 0 || cand[c].ms < cand[best].ms) best = (int)c;
+    }
+    if (rc) {
+        L->shape = keep;
+        return bail(rc);
+    }
+    L->shape = cand[best];
+    L->tuned = true;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(L)] = {cand[best].threads, ask[best]};
+    }
+    // keep the slots the chosen shape needs, no more
+    if (L->d_gscr && L->gscr_floats > gscr_need(L)) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(TLL_ECUDA, "sync"));
+        cudaFree(L->d_gscr);
+        L->d_gscr = nullptr;
+        L->dev_bytes -= (size_t)L->gscr_floats * sizeof(float);
+        L->gscr_floats = 0;
+        if (!(L->flags & TLL_FLAG_BATCH_ONLY) && (rc = ensure_gscr(L))) return bail(rc);
+    }
+    if (chosen) {
+        shape_out(L->shape, chosen);
+        chosen->tuned = 1;
+    }
+    if (n_tried) *n_tried = (int)cand.size();
+    for (int c = 0; c < (int)cand.size() && c < max_tried; ++c) shape_out(cand[c], &tried[c]);
+    cleanup();
+    return TLL_OK;
+}
 
 const char *tll_last_error(void) { return g_err; }
 

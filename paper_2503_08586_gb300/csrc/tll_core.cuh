@@ -47,7 +47,8 @@ struct RunArgs {
     const float *kc;     // [B][NCONST]
     int B;
     double *out;         // [B]
-    float *gscr;         // global image scratch, 4*npix floats per CTA
+    float *gscr;         // global image scratch, gslot floats per CTA
+    long long gslot;
     float *wr_unblurred; // WRITE: [2][npix]
     float *wr_blurred;   // WRITE: [2][npix]
     double *wr_res;      // WRITE: [8] All Als Ass bl bs sl ss logL

@@ -22,13 +22,15 @@ constexpr int NPAR = 21;
 enum : int {
     K_VALID = 0,
     // mass frame: x' = PX0 + PXJ fj + PXI fi, y' = PY0 + PYJ fj + PYI fi;
-    // q, f = sqrt(1 - q^2), 1/f, fast-path flag
-    K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_F, K_IF, K_FAST,
+    // q, f = sqrt(1 - q^2) (hi, lo), fast-path flag
+    K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_QML, K_F, K_FL, K_FAST,
     // lens light, scaled frame (x1 sqrt(q)/r_e, x2/(sqrt(q) r_e)):
     // affine coefficients, 1/(2n) (hi, lo), b log2(e) (hi, lo)
     K_LX0, K_LXJ, K_LXI, K_LY0, K_LYJ, K_LYI, K_KHL, K_KLL, K_BHL, K_BLL,
-    // source, scaled frame at theta minus shear (linear part) ...
+    // source, scaled frame at theta minus shear (linear part; hi parts,
+    // then lo parts) ...
     K_SX0, K_SXJ, K_SXI, K_SY0, K_SYJ, K_SYI, K_KHS, K_KLS, K_BHS, K_BLS,
+    K_SX0L, K_SXJL, K_SXIL, K_SY0L, K_SYJL, K_SYIL,
     // ... minus the SIE deflection A (ux, uy) mapped from the mass frame:
     // [Q11 Q12; Q21 Q22] (hi, lo)
     K_Q11H, K_Q11L, K_Q12H, K_Q12L, K_Q21H, K_Q21L, K_Q22H, K_Q22L,
@@ -36,7 +38,7 @@ enum : int {
     K_IEL, K_IES,
     NCONST_USED
 };
-constexpr int NCONST = 48;
+constexpr int NCONST = 56;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
 
 // ------------------------------------------------------------------ b_n
@@ -185,9 +187,8 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         o[K_PY0] = (float)(-dx * sm + dy * cm);
         o[K_PYJ] = (float)(-d * sm);
         o[K_PYI] = (float)(d * cm);
-        o[K_QM] = (float)qm;
-        o[K_F] = (float)f;
-        o[K_IF] = f > 0.0 ? (float)(1.0 / f) : 0.0f;
+        split2(qm, &o[K_QM], &o[K_QML]);
+        split2(f, &o[K_F], &o[K_FL]);
         // fast path when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
         // for every point: no atan range reduction, no atanh logarithm
         o[K_FAST] = (f <= qm && f <= 0.5) ? 1.0f : 0.0f;
@@ -224,12 +225,15 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         const double by0 = -g2 * XC + (1.0 + g1) * YC - v[20];
         const double bxj = (1.0 - g1) * d, bxi = -g2 * d;
         const double byj = -g2 * d, byi = (1.0 + g1) * d;
-        o[K_SX0] = (float)(s1 * (c * bx0 + s * by0));
-        o[K_SXJ] = (float)(s1 * (c * bxj + s * byj));
-        o[K_SXI] = (float)(s1 * (c * bxi + s * byi));
-        o[K_SY0] = (float)(s2 * (-s * bx0 + c * by0));
-        o[K_SYJ] = (float)(s2 * (-s * bxj + c * byj));
-        o[K_SYI] = (float)(s2 * (-s * bxi + c * byi));
+        // double-float: rounding these to float alone would move the whole
+        // source plane coherently (a shift and scale near 1e-7), which the
+        // likelihood near its optimum resolves
+        split2(s1 * (c * bx0 + s * by0), &o[K_SX0], &o[K_SX0L]);
+        split2(s1 * (c * bxj + s * byj), &o[K_SXJ], &o[K_SXJL]);
+        split2(s1 * (c * bxi + s * byi), &o[K_SXI], &o[K_SXIL]);
+        split2(s2 * (-s * bx0 + c * by0), &o[K_SY0], &o[K_SY0L]);
+        split2(s2 * (-s * bxj + c * byj), &o[K_SYJ], &o[K_SYJL]);
+        split2(s2 * (-s * bxi + c * byi), &o[K_SYI], &o[K_SYIL]);
         split2(0.5 / n, &o[K_KHS], &o[K_KLS]);
         split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &o[K_BLS]);
         // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
@@ -256,7 +260,8 @@ struct Affine {    // v = c0 + cj fj + ci fi
 };
 struct VecConst {
     Affine px, py, lx, ly, sx, sy;
-    float q, f;
+    Affine sxl, syl;      // lo parts of sx, sy
+    float q, ql, f, fl;   // q, f (hi, lo)
     bool fast;
     float khl, kll, bhl, bll, khs, kls, bhs, bls;
     float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
@@ -273,7 +278,8 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.px = load_affine(kc, K_PX0); v.py = load_affine(kc, K_PY0);
     v.lx = load_affine(kc, K_LX0); v.ly = load_affine(kc, K_LY0);
     v.sx = load_affine(kc, K_SX0); v.sy = load_affine(kc, K_SY0);
-    v.q = kc[K_QM]; v.f = kc[K_F];
+    v.sxl = load_affine(kc, K_SX0L); v.syl = load_affine(kc, K_SY0L);
+    v.q = kc[K_QM]; v.ql = kc[K_QML]; v.f = kc[K_F]; v.fl = kc[K_FL];
     v.fast = kc[K_FAST] != 0.0f;
     v.khl = kc[K_KHL]; v.kll = kc[K_KLL]; v.bhl = kc[K_BHL]; v.bll = kc[K_BLL];
     v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
@@ -383,16 +389,17 @@ template <bool FAST>
 __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
                                          float &ux, float &uy)
 {
-    const float qx = v.q * xp;
+    // q and f enter as double-float constants (their rounding would change
+    // the profile coherently); the products are rounded once
+    const float qx = fmaf(v.ql, xp, v.q * xp);
     const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
     const float xr = xp * rpsi, yr = yp * rpsi;
+    const float zx = fmaf(v.fl, xr, v.f * xr), zy = fmaf(v.fl, yr, v.f * yr);
     if (FAST) {
-        const float zx = v.f * xr, zy = v.f * yr;
         const float sx = zx * zx, sy = zy * zy;
         ux = fmaf(xr * sx, poly_atan_q(sx), xr);
         uy = fmaf(yr * sy, poly_atanh_q(sy), yr);
     } else {
-        const float zx = v.f * xr, zy = v.f * yr;
         const float ax = fabsf(zx);
         const bool big = ax > 1.0f;
         const float w = big ? sfu_rcp(ax) : ax;
@@ -417,9 +424,12 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
                     fmaf(v.sx.ci, fi, v.sx.c0), fmaf(v.sy.ci, fi, v.sy.c0)};
 }
 
+// nlx, nly: minus the lo parts of the source coordinates at this pixel
+// (c0 + cj fj + ci fi of the lo constants, at the pixel's first subpixel;
+// they change by far less than a float ulp across a pixel).
 template <bool FAST>
 __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
-                                         float &il, float &is)
+                                         float nlx, float nly, float &il, float &is)
 {
     // SIE in its frame (lens equation's deflection, Eq. 1)
     float ux, uy;
@@ -428,8 +438,8 @@ __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, f
     il = sersic_scaled(fmaf(v.lx.cj, fj, r.lx), fmaf(v.ly.cj, fj, r.ly), v.khl, v.kll,
                        v.bhl, v.bll);
     // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
-    const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux, fmaf(v.q12h, uy, v.q12l * uy)));
-    const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux, fmaf(v.q22h, uy, v.q22l * uy)));
+    const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux, fmaf(v.q12h, uy, fmaf(v.q12l, uy, nlx))));
+    const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux, fmaf(v.q22h, uy, fmaf(v.q22l, uy, nly))));
     is = sersic_scaled(fmaf(v.sx.cj, fj, r.sx) - t1, fmaf(v.sy.cj, fj, r.sy) - t2, v.khs,
                        v.kls, v.bhs, v.bls);
 }

@@ -75,6 +75,8 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
+        const float nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
+        const float nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
         float accl = 0.0f, accs = 0.0f;
 #pragma unroll 1
         for (int a = 0; a < sub; ++a) {
@@ -83,7 +85,7 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
                     float il, is;
-                    subpixel<FAST>(v, r, fj0 + (float)(SUB > 0 ? c : cr), il, is);
+                    subpixel<FAST>(v, r, fj0 + (float)(SUB > 0 ? c : cr), nlx, nly, il, is);
                     accl += il;
                     accs += is;
                 }
@@ -549,7 +551,7 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
     const bool gslot = L.img == IMG_GLOBAL || L.img == IMG_BANDED;
     const ImgPtrs P =
-        img_ptrs(L, spsf, gslot ? R.gscr + (size_t)blockIdx.x * 4 * L.npix : nullptr);
+        img_ptrs(L, spsf, gslot ? R.gscr + (size_t)blockIdx.x * R.gslot : nullptr);
     setup_lens(L, spsf, tid, nthr);
     __syncthreads();
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {

@@ -365,6 +365,24 @@ int tll_server_open_job(tll_server *S, const float *image, const float *noise,
     cudaGetDevice(&prev);
     if (prev != S->dev) cudaSetDevice(S->dev);
     int rc = tll_create_lens(image, noise, psf, psf_size, grid, flags | TLL_FLAG_BATCH_ONLY, &L);
+    if (rc == TLL_OK && S->cfg.autotune) {
+        // first job of its signature: time the launch shapes (later jobs
+        // of the same signature start with the result)
+        tll_shape_t sh;
+        if (tll_lens_shape(L, &sh) == TLL_OK && !sh.tuned) {
+            cudaStream_t ts = nullptr;
+            if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+                rc = TLL_ECUDA;
+            } else {
+                rc = tll_autotune(L, nullptr, 0, ts, nullptr, nullptr, 0, nullptr);
+                cudaStreamDestroy(ts);
+            }
+            if (rc != TLL_OK) {
+                tll_destroy_lens(L);
+                L = nullptr;
+            }
+        }
+    }
     if (prev >= 0 && prev != S->dev) cudaSetDevice(prev);
     size_t bytes = 0;
     if (rc == TLL_OK) rc = tll_lens_footprint(L, &bytes);

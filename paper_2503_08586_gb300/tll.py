@@ -33,7 +33,8 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_server_poll", "tll_server_wait", "tll_server_stats",
            "tll_server_destroy", "tll_server_last_error",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
-           "tll_profile_enable", "tll_profile_last",
+           "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
+           "tll_autotune",
            "tll_destroy_lens", "tll_last_error", "tll_version")
 
 
@@ -49,10 +50,27 @@ class Grid(ctypes.Structure):
                 ("x0", ctypes.c_float), ("y0", ctypes.c_float)]
 
 
+PLACEMENTS = {0: "global", 1: "smem", 2: "padded", 3: "banded"}
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("placement", ctypes.c_int), ("band_rows", ctypes.c_int),
+                ("smem_bytes", ctypes.c_size_t), ("ms", ctypes.c_float),
+                ("tuned", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"threads": self.threads, "ctas_per_sm": self.ctas_per_sm,
+                "placement": PLACEMENTS.get(self.placement, self.placement),
+                "band_rows": self.band_rows, "smem_bytes": int(self.smem_bytes),
+                "ms": float(self.ms), "tuned": bool(self.tuned)}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
                 ("max_vectors_per_launch", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("coalesce", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("coalesce", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -99,6 +117,13 @@ def load(path: str | None = None):
     lib.tll_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float)]
     lib.tll_profile_last.restype = i
+    lib.tll_lens_shape.argtypes = [vp, ctypes.POINTER(Shape)]
+    lib.tll_lens_shape.restype = i
+    lib.tll_set_shape.argtypes = [vp, i, i]
+    lib.tll_set_shape.restype = i
+    lib.tll_autotune.argtypes = [vp, fp, i, vp, ctypes.POINTER(Shape), ctypes.POINTER(Shape), i,
+                                 ctypes.POINTER(ctypes.c_int)]
+    lib.tll_autotune.restype = i
     lib.tll_batcher_create.argtypes = [i, ctypes.POINTER(vp)]
     lib.tll_batcher_create.restype = i
     lib.tll_batcher_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -285,6 +310,39 @@ class Lens:
                                         b.ctypes.data, 1 if blurred else 0))
         return a, b
 
+    # -- launch shape
+    def shape(self) -> dict:
+        """The batched kernels' launch shape (CTA size, CTAs per SM,
+        image placement, band rows, shared memory)."""
+        sh = Shape()
+        _check(load().tll_lens_shape(self._h, ctypes.byref(sh)))
+        return sh.as_dict()
+
+    def set_shape(self, threads: int, ctas_per_sm: int) -> dict:
+        """Use `threads`-thread CTAs, ctas_per_sm per SM; returns the shape."""
+        _check(load().tll_set_shape(self._h, int(threads), int(ctas_per_sm)))
+        return self.shape()
+
+    def autotune(self, params=None, stream=None) -> dict:
+        """Time the candidate launch shapes on the device and keep the
+        fastest.  params: CUDA float32 [B, 21] to time with, or None for the
+        library's built-in set.  Returns {"chosen": shape, "tried": [shapes]}
+        (each with its mean time per tuning batch, ms)."""
+        p, B = None, 0
+        if params is not None:
+            import torch
+            if not (params.is_cuda and params.dtype == torch.float32
+                    and params.dim() == 2 and params.shape[1] == NPARAM
+                    and params.is_contiguous()):
+                raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+            p, B = ctypes.c_void_p(params.data_ptr()), int(params.shape[0])
+        chosen = Shape()
+        tried = (Shape * 8)()
+        n = ctypes.c_int()
+        _check(load().tll_autotune(self._h, p, B, _stream_handle(stream), ctypes.byref(chosen),
+                                   tried, 8, ctypes.byref(n)))
+        return {"chosen": chosen.as_dict(), "tried": [tried[k].as_dict() for k in range(n.value)]}
+
     # -- profiling hook
     def profile(self, on: bool = True):
         """Record events around the two launches of each batch call."""
@@ -372,9 +430,10 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 0, max_jobs: int = 256,
                  max_vectors_per_launch: int = 16384, max_inflight: int = 2,
-                 coalesce: bool = True, use_graph: bool = True):
+                 coalesce: bool = True, use_graph: bool = True, autotune: bool = False):
         cfg = ServerConfig(hbm_budget_bytes, max_jobs, max_vectors_per_launch,
-                           max_inflight, 1 if coalesce else 0, 1 if use_graph else 0)
+                           max_inflight, 1 if coalesce else 0, 1 if use_graph else 0,
+                           1 if autotune else 0)
         h = ctypes.c_void_p()
         _scheck(load().tll_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

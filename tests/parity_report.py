@@ -1,0 +1,84 @@
+"""Error of the CUDA path against the FP64 oracle, per workload (run on a GPU):
+
+    python tests/parity_report.py > parity.md
+
+For each workload: the worst per-pixel error of the model columns (lens and
+source light, before and after the PSF) relative to the pixel gate
+1e-5 |m| + 1e-7 max|m|, over the true vector and prior draws; and |dlogL| by
+region -- the posterior bulk (chi^2 within 50 of the truth's), the rest of
+chi^2 <= 2N, and prior draws -- plus the error of log L differences between
+bulk vectors (what a sampler compares).  Inputs are the seeded synthetic
+workloads; nothing is stored.
+"""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import torch  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2503_08586_gb300 import build, tll  # noqa: E402
+from paper_2503_08586_gb300 import workloads as W  # noqa: E402
+from test_parity_gpu import BULK_DCHI2, _chi2_truth, _lens_consts  # noqa: E402
+
+
+def pix_ratio(gpu, ora):
+    ora = np.asarray(ora, np.float64)
+    tol = 1e-5 * np.abs(ora) + 1e-7 * np.abs(ora).max()
+    return float((np.abs(np.asarray(gpu, np.float64) - ora) / np.maximum(tol, 1e-300)).max())
+
+
+def report(name, n_prior=24, n_conv=64):
+    lens, prior = W.workload(name, oracle.columns_renderer, batch=n_prior)
+    g = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    worst = 0.0
+    for p in np.concatenate([lens.truth[None], prior[:4]]):
+        il, is_ = o.unblurred(p.astype(np.float64))
+        _, ml, ms, _, _ = o.model(p.astype(np.float64), mode=1)
+        for blurred, refs in ((False, (il, is_)), (True, (ml, ms))):
+            cols = g.model_columns(p, blurred=blurred)
+            for c, r in zip(cols, refs):
+                worst = max(worst, pix_ratio(np.asarray(c).reshape(r.shape), r))
+    rng = np.random.Generator(np.random.PCG64(2024))
+    conv = W.shrinking_draws(rng, lens.truth, n_conv, lo_frac=1e-6)
+    P = np.concatenate([conv, prior]).astype(np.float32)
+    ref = o.loglike_batch(P.astype(np.float64))
+    got = g.loglike_batch(torch.from_numpy(P).cuda())
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    _, lognorm, nun = _lens_consts(lens)
+    fin = np.isfinite(ref)
+    chi2 = -2.0 * (ref - lognorm)
+    bulk = fin & (chi2 <= _chi2_truth(lens) + BULK_DCHI2)
+    near = fin & ~bulk & (chi2 <= 2 * nun)
+    far = fin & ~bulk & ~near
+    d = np.abs(got - ref)
+
+    def mx(m):
+        return f"{d[m].max():.2e} ({int(m.sum())})" if m.any() else "-"
+    pair = "-"
+    if bulk.sum() >= 2:
+        gb, rb = got[bulk], ref[bulk]
+        pair = f"{np.abs((gb[:, None] - gb[None]) - (rb[:, None] - rb[None])).max():.2e}"
+    g.close()
+    return (f"| {name} | {lens.ny}x{lens.nx}, s={lens.sub}, K={lens.psf.shape[0]} | {worst:.3f} | "
+            f"{mx(bulk)} | {pair} | {mx(near)} | {mx(far)} |")
+
+
+def main():
+    build.build()
+    tll.load()
+    print("| workload | image | worst pixel error / gate | bulk max abs dlogL (n) | "
+          "bulk pairwise d(dlogL) | near max (n) | prior max (n) |")
+    print("|---|---|---|---|---|---|---|")
+    for name in ("plain64", "csst100", "hst200"):
+        print(report(name), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -142,3 +142,19 @@ def test_errors_and_timeouts(lenses):
     if not closed_early:
         assert S.close_job(j)
     S.close()
+
+
+def test_autotune_at_admission(lenses):
+    # the first job of a signature is tuned at admission; results match the
+    # job's own one-lens evaluation up to FP64 summation order
+    S = tll.Server(max_jobs=4, autotune=True)
+    for sl, batches in lenses[:2]:
+        j = _open(S, sl)
+        assert j is not None
+        out, _ = S.wait(S.submit(j, batches[0]))
+        ref = _reference(sl, batches[0])
+        fin = np.isfinite(ref)
+        assert np.array_equal(fin, np.isfinite(out))
+        assert np.allclose(out[fin], ref[fin], rtol=1e-10, atol=1e-8)
+        assert S.close_job(j)
+    S.close()
