@@ -271,6 +271,10 @@ def run_ours(args):
     # (outside the timed region); lenses of the same signature created later
     # in this process (the request stream's) start with the chosen shape
     tune = None if args.no_autotune else L.autotune(p_dev)
+    conv_variant = {"fused": tll.CONV_FUSED, "split-direct": tll.CONV_SPLIT_DIRECT,
+                    "split-tc": tll.CONV_SPLIT_TOEPLITZ_TC}[args.conv]
+    if conv_variant != tll.CONV_FUSED:
+        L.set_conv(conv_variant, chunk=args.split_chunk)
 
     def barrier():
         if ws > 1:
@@ -300,7 +304,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     L.profile(False)
-    launches = 2 * args.steps
+    per_step = 2 if args.conv == "fused" else 1 + 3 * -(-B // args.split_chunk)
+    launches = per_step * args.steps
     total = sum(step_ms)
     if ws > 1:
         import torch.distributed as dist
@@ -375,6 +380,7 @@ def run_ours(args):
             "parallelism": f"replicas x{ws}",
             "l2": "flushed between timed steps (256 MB write, outside the events)",
             "launch_shape": L.shape(),
+            "conv": args.conv,
             "autotune": tune["tried"] if tune else "off"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
@@ -383,7 +389,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": captured_traffic(args.workload),
-                     "kernel": "k_loglike",
+                     "kernel": ("k_loglike" if args.conv == "fused" else
+                                "k_trace_split + conv + k_sums_split"),
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                                    f"x {SM_MAX_MHZ:.0f} MHz"},
         "e2e": ({"value": served["evals_per_s_all_ranks"], "unit": UNIT,
@@ -543,6 +550,8 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-stream", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--conv", choices=["fused", "split-direct", "split-tc"], default="fused")
+    ap.add_argument("--split-chunk", type=int, default=1024)
     ap.add_argument("--stream-jobs", type=int, default=32)
     ap.add_argument("--stream-iters", type=int, default=100)
     ap.add_argument("--stream-rate", type=float, default=20.0)

@@ -327,6 +327,39 @@ typedef struct {
 int tll_lens_shape(const tll_lens *L, tll_shape_t *out);
 
 /*
+ * Convolution variants (Eq. 3) of a lens's one-lens batched entry points
+ * (tll_loglike_batch*, tll_model_columns); the batcher and the server always
+ * use the fused kernels.
+ *   TLL_CONV_FUSED        the default: trace, convolution and sums in one
+ *                         kernel (separable or direct FP32 FMAs)
+ *   TLL_CONV_SPLIT_DIRECT a split pipeline -- trace kernel, convolution
+ *                         kernel, sums kernel, images of `chunk` vectors in
+ *                         device memory -- with a direct FP32 convolution
+ *                         (whole padded image in shared memory)
+ *   TLL_CONV_SPLIT_TOEPLITZ_TC  the same pipeline with the convolution of
+ *                         each PSF row as a GEMM with a banded Toeplitz
+ *                         matrix on the tensor cores (tcgen05, TF32 with
+ *                         three products per term for FP32-level accuracy);
+ *                         PSF side <= 33
+ * The split variants exist to compare the two convolutions on the same
+ * inputs.  chunk: vectors per pass of the split pipeline (0: 1024); it holds
+ * 16 B per pixel per vector of device memory.  Waits for the device first.
+ * Errors: TLL_EINVAL (unknown variant, image or PSF too large), TLL_ENOMEM,
+ * TLL_ECUDA.
+ */
+enum {
+    TLL_CONV_FUSED = 0,
+    TLL_CONV_SPLIT_DIRECT = 1,
+    TLL_CONV_SPLIT_TOEPLITZ_TC = 2
+};
+int tll_set_conv(tll_lens *L, int variant, int chunk);
+
+/* Wait for the device and report whether the tensor-core convolution's
+ * bounded waits ran out since the last check (TLL_ETIMEOUT: the affected
+ * outputs are not valid), else TLL_OK. */
+int tll_conv_check(tll_lens *L);
+
+/*
  * tll_set_shape -- give the lens the shape of `threads`-thread CTAs (a
  * multiple of 32, <= 1024) with ctas_per_sm of them per SM, and the
  * placement that share of shared memory allows.  Waits for the device to

@@ -36,6 +36,7 @@
 
 #include "tll.h"
 #include "tll_kernels.cuh"
+#include "tll_split.cuh"
 
 using namespace tll;
 
@@ -145,6 +146,15 @@ struct tll_lens {
     int W = 0, HL = 0;    // padded layout geometry
     std::vector<float> taps_u, taps_v, psf_norm;
     long long gscr_floats = 0;   // size of d_gscr
+    // split pipeline (tll_set_conv): image buffers for split_cap vectors,
+    // Toeplitz tiles, the tensor-core kernel's status word
+    int conv_variant = TLL_CONV_FUSED;
+    float *d_unbl = nullptr, *d_sblur = nullptr, *d_tiles = nullptr;
+    float *d_thi = nullptr, *d_tlo = nullptr;   // TF32 parts, chunk-major (Toeplitz)
+    CUtensorMap tm_hi, tm_lo;                   // their tensor maps
+    int *d_tc_status = nullptr;
+    int split_cap = 0;
+    size_t tc_part_bytes = 0;
     const double *bn_tab = nullptr;   // per-device b_n table (not owned)
     size_t dev_bytes = 0;             // device memory this lens holds
     cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
@@ -265,6 +275,29 @@ int launch_main(const tll_lens *L, const RunArgs &R, int grid, bool write, cudaS
     return TLL_OK;
 }
 
+// The split pipeline for B vectors whose constants are in kc: in chunks of
+// split_cap vectors, trace -> convolution (direct or Toeplitz on the tensor
+// cores) -> sums, with the images in the lens's split buffers.
+int run_split(tll_lens *L, const float *kc, int B, double *out, cudaStream_t st)
+{
+    int nsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, L->dev));
+    const LensDev d = lens_dev(L);
+    for (int b0 = 0; b0 < B; b0 += L->split_cap) {
+        const int nb = std::min(L->split_cap, B - b0);
+        const float *k = kc + (size_t)b0 * NCONST;
+        CUDA_TRY(launch_trace_split(d, k, nb, L->d_unbl, std::min(nb, nsm), st));
+        if (L->conv_variant == TLL_CONV_SPLIT_TOEPLITZ_TC)
+            CUDA_TRY(launch_conv_tc(d, L->d_unbl, nb, L->d_thi, L->d_tlo, L->tm_hi, L->tm_lo,
+                                    L->d_sblur, L->d_tiles, L->d_tc_status, nsm, st));
+        else
+            CUDA_TRY(launch_conv_direct_split(d, L->d_unbl, nb, L->d_sblur,
+                                              std::min(2 * nb, nsm), st));
+        CUDA_TRY(launch_sums_split(d, k, L->d_sblur, nb, out + b0, std::min(nb, nsm), st));
+    }
+    return TLL_OK;
+}
+
 int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t st,
               bool write, float *kc)
 {
@@ -281,7 +314,8 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
     const int grid = std::min(B, L->shape.grid_cap);
     if (write) return launch_main(L, R, 1, true, st);
-    const int rc = launch_main(L, R, grid, false, st);
+    const int rc = L->conv_variant == TLL_CONV_FUSED ? launch_main(L, R, grid, false, st)
+                                                     : run_split(L, kc, B, out, st);
     if (rc == TLL_OK && prof) {
         CUDA_TRY(cudaEventRecord(L->prof_ev[2], st));
         L->prof_recorded = true;
@@ -470,7 +504,8 @@ void free_lens(tll_lens *L)
     if (!L) return;
     void *ptrs[] = {L->d_psf, L->d_pu, L->d_pv, L->d_wpack, L->d_kc, L->d_gscr,
                     L->d_stage_p, L->d_stage_o, L->d_p1, L->d_kc1, L->d_unb,
-                    L->d_blur, L->d_img, L->d_res, L->d_out1};
+                    L->d_blur, L->d_img, L->d_res, L->d_out1, L->d_unbl, L->d_sblur,
+                    L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : L->prof_ev)
@@ -859,8 +894,9 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *o
 }
 
 
-static_assert(TLL_PLACE_GLOBAL == IMG_GLOBAL && TLL_PLACE_SMEM == IMG_SMEM &&
-                  TLL_PLACE_PADDED == IMG_PADDED && TLL_PLACE_BANDED == IMG_BANDED,
+static_assert((int)TLL_PLACE_GLOBAL == (int)IMG_GLOBAL && (int)TLL_PLACE_SMEM == (int)IMG_SMEM &&
+                  (int)TLL_PLACE_PADDED == (int)IMG_PADDED &&
+                  (int)TLL_PLACE_BANDED == (int)IMG_BANDED,
               "placement codes");
 
 namespace {
@@ -905,6 +941,94 @@ extern "C" int tll_lens_shape(const tll_lens *L, tll_shape_t *out)
     shape_out(L->shape, out);
     out->tuned = L->tuned ? 1 : 0;
     return TLL_OK;
+}
+
+extern "C" int tll_set_conv(tll_lens *L, int variant, int chunk)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (variant != TLL_CONV_FUSED && variant != TLL_CONV_SPLIT_DIRECT &&
+        variant != TLL_CONV_SPLIT_TOEPLITZ_TC)
+        return fail(TLL_EINVAL, "unknown convolution variant %d", variant);
+    if (chunk < 0 || chunk > (1 << 20)) return fail(TLL_EINVAL, "chunk %d out of range", chunk);
+    DeviceGuard gd(L->dev);
+    CUDA_TRY(cudaDeviceSynchronize());   // no launch using the old buffers in flight
+    if (variant == TLL_CONV_FUSED) {
+        L->conv_variant = variant;
+        return TLL_OK;
+    }
+    DevLimits D;
+    int rc = dev_limits(L->dev, &D);
+    if (rc) return rc;
+    const LensDev d = lens_dev(L);
+    if (variant == TLL_CONV_SPLIT_DIRECT && conv_direct_split_smem(d) > (size_t)D.optin)
+        return fail(TLL_EINVAL, "padded %d x %d image does not fit shared memory", L->ny, L->nx);
+    if (variant == TLL_CONV_SPLIT_TOEPLITZ_TC && L->K > kTcMaxK)
+        return fail(TLL_EINVAL, "Toeplitz tiles hold PSF sides up to %d", kTcMaxK);
+    const int cap = chunk > 0 ? chunk : 1024;
+    const bool regrow = cap != L->split_cap || !L->d_unbl;
+    if (regrow) {
+        const size_t bytes = (size_t)cap * 2 * L->npix * sizeof(float);
+        float *u = nullptr, *b = nullptr;
+        cudaError_t e = cudaMalloc(&u, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b, bytes);
+        if (e != cudaSuccess) {
+            if (u) cudaFree(u);
+            return fail(TLL_ENOMEM, "split image buffers (%zu bytes): %s", 2 * bytes,
+                        cudaGetErrorString(e));
+        }
+        if (L->d_unbl) {
+            cudaFree(L->d_unbl);
+            cudaFree(L->d_sblur);
+            L->dev_bytes -= (size_t)L->split_cap * 2 * L->npix * sizeof(float) * 2;
+        }
+        L->d_unbl = u;
+        L->d_sblur = b;
+        L->split_cap = cap;
+        L->dev_bytes += 2 * bytes;
+    }
+    if (variant == TLL_CONV_SPLIT_TOEPLITZ_TC && (regrow || !L->d_thi)) {
+        const size_t pf = tc_part_floats(2 * cap, L->ny, L->nx);
+        if (L->d_thi) {
+            cudaFree(L->d_thi);
+            cudaFree(L->d_tlo);
+            L->d_thi = L->d_tlo = nullptr;
+            L->dev_bytes -= L->tc_part_bytes * 2;
+            L->tc_part_bytes = 0;
+        }
+        CUDA_TRY(cudaMalloc(&L->d_thi, pf * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&L->d_tlo, pf * sizeof(float)));
+        L->tc_part_bytes = pf * sizeof(float);
+        L->dev_bytes += 2 * L->tc_part_bytes;
+        if (make_tc_maps(L->d_thi, L->d_tlo, 2 * cap, L->ny, L->nx, L->K, &L->tm_hi, &L->tm_lo))
+            return fail(TLL_ECUDA, "cuTensorMapEncodeTiled failed for the Toeplitz operands");
+    }
+    if (variant == TLL_CONV_SPLIT_TOEPLITZ_TC && !L->d_tiles) {
+        std::vector<float> t(tc_tile_floats(L->K));
+        build_tc_tiles(L->psf_norm.data(), L->K, t.data());
+        CUDA_TRY(cudaMalloc(&L->d_tiles, t.size() * sizeof(float)));
+        L->dev_bytes += t.size() * sizeof(float);
+        CUDA_TRY(cudaMemcpy(L->d_tiles, t.data(), t.size() * sizeof(float),
+                            cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMalloc(&L->d_tc_status, sizeof(int)));
+        L->dev_bytes += sizeof(int);
+        CUDA_TRY(cudaMemset(L->d_tc_status, 0, sizeof(int)));
+    }
+    L->conv_variant = variant;
+    return TLL_OK;
+}
+
+extern "C" int tll_conv_check(tll_lens *L)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (!L->d_tc_status) return TLL_OK;
+    DeviceGuard gd(L->dev);
+    CUDA_TRY(cudaDeviceSynchronize());
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, L->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == 0) return TLL_OK;
+    CUDA_TRY(cudaMemset(L->d_tc_status, 0, sizeof(int)));
+    return fail(TLL_ETIMEOUT, "tensor-core convolution: a bounded wait ran out (status %d); "
+                              "its outputs are not valid", st);
 }
 
 extern "C" int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm)
@@ -1287,6 +1411,14 @@ int tll_model_columns(tll_lens *L, const float *params, float *lens_out, float *
     int rc = run_one(L, params);
     if (rc) return rc;
     const float *src = blurred ? L->d_blur : L->d_unb;
+    if (L->conv_variant != TLL_CONV_FUSED) {
+        // the columns of the lens's split pipeline (its convolution variant)
+        rc = run_split(L, L->d_kc1, 1, L->d_out1, 0);
+        if (rc) return rc;
+        CUDA_TRY(cudaDeviceSynchronize());
+        if ((rc = tll_conv_check(L))) return rc;
+        src = blurred ? L->d_sblur : L->d_unbl;
+    }
     const size_t n = (size_t)L->npix * sizeof(float);
     CUDA_TRY(cudaMemcpy(lens_out, src, n, cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemcpy(src_out, src + L->npix, n, cudaMemcpyDeviceToHost));

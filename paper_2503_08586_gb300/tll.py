@@ -34,7 +34,7 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_server_destroy", "tll_server_last_error",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
-           "tll_autotune",
+           "tll_autotune", "tll_set_conv", "tll_conv_check",
            "tll_destroy_lens", "tll_last_error", "tll_version")
 
 
@@ -51,6 +51,7 @@ class Grid(ctypes.Structure):
 
 
 PLACEMENTS = {0: "global", 1: "smem", 2: "padded", 3: "banded"}
+CONV_FUSED, CONV_SPLIT_DIRECT, CONV_SPLIT_TOEPLITZ_TC = 0, 1, 2
 
 
 class Shape(ctypes.Structure):
@@ -119,6 +120,10 @@ def load(path: str | None = None):
     lib.tll_profile_last.restype = i
     lib.tll_lens_shape.argtypes = [vp, ctypes.POINTER(Shape)]
     lib.tll_lens_shape.restype = i
+    lib.tll_set_conv.argtypes = [vp, i, i]
+    lib.tll_set_conv.restype = i
+    lib.tll_conv_check.argtypes = [vp]
+    lib.tll_conv_check.restype = i
     lib.tll_set_shape.argtypes = [vp, i, i]
     lib.tll_set_shape.restype = i
     lib.tll_autotune.argtypes = [vp, fp, i, vp, ctypes.POINTER(Shape), ctypes.POINTER(Shape), i,
@@ -317,6 +322,17 @@ class Lens:
         sh = Shape()
         _check(load().tll_lens_shape(self._h, ctypes.byref(sh)))
         return sh.as_dict()
+
+    def set_conv(self, variant: int, chunk: int = 0):
+        """Convolution variant of the one-lens batched path: CONV_FUSED
+        (default), CONV_SPLIT_DIRECT or CONV_SPLIT_TOEPLITZ_TC (split
+        pipeline, chunk vectors per pass, 0: 1024)."""
+        _check(load().tll_set_conv(self._h, int(variant), int(chunk)))
+
+    def conv_check(self):
+        """Raise TLLError(ETIMEOUT) if the tensor-core convolution's
+        bounded waits ran out since the last check (waits for the device)."""
+        _check(load().tll_conv_check(self._h))
 
     def set_shape(self, threads: int, ctas_per_sm: int) -> dict:
         """Use `threads`-thread CTAs, ctas_per_sm per SM; returns the shape."""

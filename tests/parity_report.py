@@ -7,8 +7,10 @@ source light, before and after the PSF) relative to the pixel gate
 1e-5 |m| + 1e-7 max|m|, over the true vector and prior draws; and |dlogL| by
 region -- the posterior bulk (chi^2 within 50 of the truth's), the rest of
 chi^2 <= 2N, and prior draws -- plus the error of log L differences between
-bulk vectors (what a sampler compares).  Inputs are the seeded synthetic
-workloads; nothing is stored.
+bulk vectors (what a sampler compares).  hst200 is reported again with the
+split pipeline's two convolutions (direct FP32, and the banded-Toeplitz GEMM
+on the tensor cores).  Inputs are the seeded synthetic workloads; nothing is
+stored.
 """
 import os
 import sys
@@ -32,9 +34,13 @@ def pix_ratio(gpu, ora):
     return float((np.abs(np.asarray(gpu, np.float64) - ora) / np.maximum(tol, 1e-300)).max())
 
 
-def report(name, n_prior=24, n_conv=64):
+def report(name, n_prior=24, n_conv=64, conv=None):
     lens, prior = W.workload(name, oracle.columns_renderer, batch=n_prior)
     g = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    label = name
+    if conv is not None:
+        g.set_conv(conv[1])
+        label = f"{name} ({conv[0]})"
     o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
     worst = 0.0
     for p in np.concatenate([lens.truth[None], prior[:4]]):
@@ -50,6 +56,7 @@ def report(name, n_prior=24, n_conv=64):
     ref = o.loglike_batch(P.astype(np.float64))
     got = g.loglike_batch(torch.from_numpy(P).cuda())
     torch.cuda.synchronize()
+    g.conv_check()
     got = got.cpu().numpy()
     _, lognorm, nun = _lens_consts(lens)
     fin = np.isfinite(ref)
@@ -66,7 +73,7 @@ def report(name, n_prior=24, n_conv=64):
         gb, rb = got[bulk], ref[bulk]
         pair = f"{np.abs((gb[:, None] - gb[None]) - (rb[:, None] - rb[None])).max():.2e}"
     g.close()
-    return (f"| {name} | {lens.ny}x{lens.nx}, s={lens.sub}, K={lens.psf.shape[0]} | {worst:.3f} | "
+    return (f"| {label} | {lens.ny}x{lens.nx}, s={lens.sub}, K={lens.psf.shape[0]} | {worst:.3f} | "
             f"{mx(bulk)} | {pair} | {mx(near)} | {mx(far)} |")
 
 
@@ -78,6 +85,10 @@ def main():
     print("|---|---|---|---|---|---|---|")
     for name in ("plain64", "csst100", "hst200"):
         print(report(name), flush=True)
+    # the hst200 convolution (Eq. 3) run three ways
+    for conv in (("split, direct FP32", tll.CONV_SPLIT_DIRECT),
+                 ("split, Toeplitz 3xTF32 tensor cores", tll.CONV_SPLIT_TOEPLITZ_TC)):
+        print(report("hst200", conv=conv), flush=True)
 
 
 if __name__ == "__main__":
