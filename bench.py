@@ -58,13 +58,15 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
 
 
 def source_hash() -> str:
-    """Hash of the kernel sources (csrc/*.cu*, include/*.h)."""
+    """Hash of the sources that define k_loglike (the per-subpixel model, the
+    kernel templates and their per-K instantiations)."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2503_08586_gb300", "csrc", "*.cu"))
-                   + glob.glob(os.path.join(ROOT, "paper_2503_08586_gb300", "csrc", "*.cuh"))
-                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    c = os.path.join(ROOT, "paper_2503_08586_gb300", "csrc")
+    files = sorted([os.path.join(c, f) for f in ("tll_device.cuh", "tll_core.cuh",
+                                                 "tll_kernels.cuh", "tll_poly.cuh")]
+                   + glob.glob(os.path.join(c, "tll_kern_*.cu")))
     for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
