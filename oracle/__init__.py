@@ -26,6 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tll_oracle.c")
 _LIB = os.path.join(_HERE, "_liboracle.so")
 NPARAM = 21
+NPARAM_EPL = 22
+MASS = {"sie": 0, "epl": 1}
 
 _lib = None
 
@@ -53,7 +55,8 @@ class _Lens(ctypes.Structure):
                 ("y0", ctypes.c_double),
                 ("data", ctypes.POINTER(ctypes.c_double)),
                 ("sigma", ctypes.POINTER(ctypes.c_double)),
-                ("psf", ctypes.POINTER(ctypes.c_double))]
+                ("psf", ctypes.POINTER(ctypes.c_double)),
+                ("mass", ctypes.c_int)]
 
 
 def _load():
@@ -68,6 +71,7 @@ def _load():
         "ora_sersic_bn": (d, [d]),
         "ora_sersic": (d, [d] * 9),
         "ora_sie_alpha": (None, [d] * 7 + [pd, pd]),
+        "ora_epl_alpha": (None, [d] * 8 + [pd, pd]),
         "ora_shear_potential": (d, [d] * 4),
         "ora_shear_alpha": (None, [d] * 4 + [pd, pd]),
         "ora_trace_point": (i, [pd, d, d, pd, pd]),
@@ -128,6 +132,14 @@ def sie_alpha(x, y, thE, q, phi, xc=0.0, yc=0.0):
     return ax.value, ay.value
 
 
+def epl_alpha(x, y, thE, q, phi, gamma, xc=0.0, yc=0.0):
+    """EPL deflection (Eq. 12, any slope; Tessore & Metcalf closed form)."""
+    ax, ay = ctypes.c_double(), ctypes.c_double()
+    _load().ora_epl_alpha(x, y, thE, q, phi, xc, yc, gamma, ctypes.byref(ax),
+                          ctypes.byref(ay))
+    return ax.value, ay.value
+
+
 def shear_potential(x, y, g1, g2) -> float:
     return _load().ora_shear_potential(x, y, g1, g2)
 
@@ -181,7 +193,8 @@ def chi2(ml, ms, d, w, sl, ss) -> float:
 class Lens:
     """A lens as the oracle sees it: data, noise map, raw PSF and the grid."""
 
-    def __init__(self, data, noise, psf, pixel_scale, sub, x0=None, y0=None):
+    def __init__(self, data, noise, psf, pixel_scale, sub, x0=None, y0=None,
+                 mass: str = "sie"):
         self.data = _f64(data)
         self.noise = _f64(noise)
         self.psf = _f64(psf)
@@ -191,8 +204,11 @@ class Lens:
         self.sub = int(sub)
         self.x0 = -(self.nx - 1) * self.dpix / 2 if x0 is None else float(x0)
         self.y0 = -(self.ny - 1) * self.dpix / 2 if y0 is None else float(y0)
+        self.mass = mass
+        self.nparam = NPARAM_EPL if mass == "epl" else NPARAM
         self._s = _Lens(self.ny, self.nx, self.sub, self.k, self.dpix, self.x0,
-                        self.y0, _p(self.data), _p(self.noise), _p(self.psf))
+                        self.y0, _p(self.data), _p(self.noise), _p(self.psf),
+                        MASS[mass])
 
     def loglike(self, params, mode: int = 0) -> float:
         p = _f64(params)
@@ -220,7 +236,7 @@ class Lens:
         return il.reshape(self.ny, self.nx), is_.reshape(self.ny, self.nx)
 
     def loglike_batch(self, params, mode: int = 0, nthreads: int = 0):
-        p = _f64(params).reshape(-1, NPARAM)
+        p = _f64(params).reshape(-1, self.nparam)
         out = np.zeros(p.shape[0])
         _load().ora_loglike_batch(ctypes.byref(self._s), _p(p), p.shape[0],
                                   mode, _p(out), nthreads)
@@ -231,11 +247,11 @@ def max_threads() -> int:
     return _load().ora_max_threads()
 
 
-def columns_renderer(pixel_scale, sub, psf, ny, nx):
+def columns_renderer(pixel_scale, sub, psf, ny, nx, mass: str = "sie"):
     """A render function for the input generator: blurred unit columns from
     the oracle (used to synthesise data images in the tests)."""
     dummy = np.zeros((ny, nx))
-    lens = Lens(dummy, np.ones((ny, nx)), psf, pixel_scale, sub)
+    lens = Lens(dummy, np.ones((ny, nx)), psf, pixel_scale, sub, mass=mass)
 
     def render(params):
         _, ml, ms, _, _ = lens.model(params, mode=1)

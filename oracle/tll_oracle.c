@@ -20,7 +20,8 @@
  *   Sersic profile, b_n           Sec. 2.4, Eqs. (8), (9)
  *   elliptical coordinates        Sec. 2.4, Eq. (10)
  *   ellipticity components        Sec. 2.4, Eq. (11)
- *   power-law / SIE convergence   Sec. 2.4, Eq. (12), gamma = 2
+ *   power-law convergence         Sec. 2.4, Eq. (12): SIE (gamma = 2) and the
+ *                                 elliptical power law (EPL, any gamma)
  *   external shear                Sec. 2.4, Eqs. (13), (14)
  *
  * Readings taken where the paper is silent or ambiguous (each one is also
@@ -48,12 +49,20 @@
  *      whose sigma is not finite and > 0, or whose datum is not finite, is
  *      masked (weight 0, no normalisation term).
  *   R9 invalid parameter vectors (|eps| >= 1, r_e <= 0, n outside [0.2, 10],
- *      theta_E < 0, non-finite entries) give log L = -infinity.
+ *      theta_E < 0, non-finite entries; for the EPL a slope outside
+ *      (1, 3)) give log L = -infinity.
+ *   R12 EPL: Eq. (12) with R replaced by the elliptical radius of Eq. (10),
+ *      kappa = (3 - gamma)/2 (theta_E / R_p)^(gamma - 1); with t = gamma - 1,
+ *      b = theta_E sqrt(q) and R = sqrt(q^2 x'^2 + y'^2) = sqrt(q) R_p this is
+ *      kappa = (2 - t)/2 (b/R)^t, whose deflection is the closed form of
+ *      Tessore & Metcalf (2015), written out in epl_alpha().  gamma = 2 is the
+ *      SIE of R4.
  *
- * Parameter vector layout (21 doubles / floats):
+ * Parameter vector layout (21 doubles / floats; 22 for the EPL):
  *   [0] theta_E  [1] eps1_m [2] eps2_m [3] x_m [4] y_m [5] gamma_1 [6] gamma_2
  *   [7] I_e^L [8] r_e^L [9] n^L [10] eps1_L [11] eps2_L [12] x_L [13] y_L
  *   [14] I_e^S [15] r_e^S [16] n^S [17] eps1_S [18] eps2_S [19] x_S [20] y_S
+ *   [21] gamma (the mass slope; EPL lenses only)
  */
 #include <math.h>
 #include <stdlib.h>
@@ -63,6 +72,8 @@
 #endif
 
 #define ORA_NPAR 21
+#define ORA_MASS_SIE 0
+#define ORA_MASS_EPL 1
 
 /* ---------------------------------------------------------------- Eq. (11) */
 /* Ellipticity components -> (q, position angle).  Eq. (11):
@@ -150,6 +161,43 @@ void ora_sie_alpha(double x, double y, double thE, double q, double phi,
     *ay = axp * s + ayp * c;
 }
 
+/* EPL deflection (reading R12).  In the frame rotated by phi about
+ * (xc, yc), with t = gamma - 1, b = theta_E sqrt(q), R = sqrt(q^2 x'^2 + y'^2)
+ * and the elliptical angle R e^{i varphi} = q x' + i y', Tessore & Metcalf
+ * (2015) give, as a complex number alpha' = alpha_x' + i alpha_y',
+ *   alpha' = 2 b / (1 + q) (b/R)^(t - 1) e^{i varphi}
+ *            2F1(1, t/2; 2 - t/2; -(1 - q)/(1 + q) e^{2 i varphi}),
+ * the hypergeometric function summed as its power series (the ratio of term
+ * n to term n - 1 is z (2n - 2 + t)/(2n + 2 - t), |z| = (1-q)/(1+q) < 1),
+ * until a term is below 1e-17 of the sum.  Rotated back by +phi. */
+void ora_epl_alpha(double x, double y, double thE, double q, double phi,
+                   double xc, double yc, double gamma, double *ax, double *ay)
+{
+    double c = cos(phi), s = sin(phi);
+    double xp = (x - xc) * c + (y - yc) * s;
+    double yp = -(x - xc) * s + (y - yc) * c;
+    double R = sqrt(q * q * xp * xp + yp * yp);
+    if (R < 1e-12) R = 1e-12;
+    double t = gamma - 1.0, b = thE * sqrt(q);
+    double cv = q * xp / R, sv = yp / R;             /* e^{i varphi} */
+    double c2 = cv * cv - sv * sv, s2 = 2.0 * cv * sv;  /* e^{2 i varphi} */
+    double zf = -(1.0 - q) / (1.0 + q);
+    double tr = 1.0, ti = 0.0, sr = 1.0, si = 0.0;   /* term, sum */
+    for (int n = 1; n < 100000; ++n) {
+        double ratio = zf * (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+        double nr = (tr * c2 - ti * s2) * ratio;
+        double ni = (tr * s2 + ti * c2) * ratio;
+        tr = nr; ti = ni;
+        sr += tr; si += ti;
+        if (sqrt(tr * tr + ti * ti) < 1e-17 * sqrt(sr * sr + si * si)) break;
+    }
+    double pre = 2.0 * b / (1.0 + q) * pow(b / R, t - 1.0);
+    double axp = pre * (cv * sr - sv * si);
+    double ayp = pre * (cv * si + sv * sr);
+    *ax = axp * c - ayp * s;
+    *ay = axp * s + ayp * c;
+}
+
 /* ------------------------------------------------------ Eqs. (13), (14) */
 /* External shear potential (reading R5): psi = g1 (x^2 - y^2)/2 + g2 x y. */
 double ora_shear_potential(double x, double y, double g1, double g2)
@@ -167,16 +215,25 @@ void ora_shear_alpha(double x, double y, double g1, double g2,
 
 /* ------------------------------------------------------------ parameters */
 typedef struct {
-    double thE, qm, phim, xm, ym, g1, g2;
+    int mass;                       /* ORA_MASS_SIE or ORA_MASS_EPL */
+    double thE, qm, phim, xm, ym, g1, g2, gamma;
     double IeL, reL, nL, qL, phiL, xL, yL, bL;
     double IeS, reS, nS, qS, phiS, xS, yS, bS;
 } ora_model;
 
-/* Decode one parameter vector; returns -1 for an invalid vector (R9). */
-int ora_decode(const double *p, ora_model *m)
+/* Decode one parameter vector (21 entries, 22 for the EPL); returns -1 for
+ * an invalid vector (R9). */
+int ora_decode(const double *p, int mass, ora_model *m)
 {
-    for (int k = 0; k < ORA_NPAR; ++k)
+    const int np = mass == ORA_MASS_EPL ? ORA_NPAR + 1 : ORA_NPAR;
+    for (int k = 0; k < np; ++k)
         if (!isfinite(p[k])) return -1;
+    m->mass = mass;
+    m->gamma = 2.0;
+    if (mass == ORA_MASS_EPL) {
+        if (!(p[21] > 1.0 && p[21] < 3.0)) return -1;
+        m->gamma = p[21];
+    }
     if (p[0] < 0.0) return -1;
     if (ora_ellipse(p[1], p[2], &m->qm, &m->phim)) return -1;
     if (ora_ellipse(p[10], p[11], &m->qL, &m->phiL)) return -1;
@@ -196,7 +253,10 @@ int ora_decode(const double *p, ora_model *m)
 void ora_trace(const ora_model *m, double x, double y, double *bx, double *by)
 {
     double ax, ay, sx, sy;
-    ora_sie_alpha(x, y, m->thE, m->qm, m->phim, m->xm, m->ym, &ax, &ay);
+    if (m->mass == ORA_MASS_EPL)
+        ora_epl_alpha(x, y, m->thE, m->qm, m->phim, m->xm, m->ym, m->gamma, &ax, &ay);
+    else
+        ora_sie_alpha(x, y, m->thE, m->qm, m->phim, m->xm, m->ym, &ax, &ay);
     ora_shear_alpha(x, y, m->g1, m->g2, &sx, &sy);
     *bx = x - ax - sx;
     *by = y - ay - sy;
@@ -206,7 +266,7 @@ void ora_trace(const ora_model *m, double x, double y, double *bx, double *by)
 int ora_trace_point(const double *p, double x, double y, double *bx, double *by)
 {
     ora_model m;
-    if (ora_decode(p, &m)) return -1;
+    if (ora_decode(p, ORA_MASS_SIE, &m)) return -1;
     ora_trace(&m, x, y, bx, by);
     return 0;
 }
@@ -337,6 +397,7 @@ typedef struct {
     int ny, nx, sub, k;
     double dpix, x0, y0;
     const double *data, *sigma, *psf; /* psf: raw, normalised here */
+    int mass;                         /* ORA_MASS_SIE or ORA_MASS_EPL */
 } ora_lens;
 
 /* Everything for one parameter vector.  mode 0: NNLS amplitudes (R7);
@@ -349,7 +410,7 @@ double ora_loglike_full(const ora_lens *L, const double *p, int mode,
 {
     ora_model m;
     int npix = L->ny * L->nx;
-    if (ora_decode(p, &m)) return -INFINITY;
+    if (ora_decode(p, L->mass, &m)) return -INFINITY;
     double *il = malloc(sizeof(double) * npix), *is = malloc(sizeof(double) * npix);
     double *ml = malloc(sizeof(double) * npix), *ms = malloc(sizeof(double) * npix);
     double *w = malloc(sizeof(double) * npix);
@@ -384,13 +445,14 @@ done:
 int ora_unblurred_columns(const ora_lens *L, const double *p, double *il, double *is)
 {
     ora_model m;
-    if (ora_decode(p, &m)) return -1;
+    if (ora_decode(p, L->mass, &m)) return -1;
     ora_columns(&m, L->ny, L->nx, L->dpix, L->sub, L->x0, L->y0, il, is);
     return 0;
 }
 
-/* Batch of B vectors (params row-major [B][21]); parallel over vectors only
- * (each vector's arithmetic is unchanged).  nthreads <= 0: library default. */
+/* Batch of B vectors (params row-major [B][21], [B][22] for the EPL);
+ * parallel over vectors only (each vector's arithmetic is unchanged).
+ * nthreads <= 0: library default. */
 void ora_loglike_batch(const ora_lens *L, const double *params, int B, int mode,
                        double *out, int nthreads)
 {
@@ -399,8 +461,9 @@ void ora_loglike_batch(const ora_lens *L, const double *params, int B, int mode,
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int b = 0; b < B; ++b)
-        out[b] = ora_loglike_full(L, params + (size_t)b * ORA_NPAR, mode,
-                                  NULL, NULL, NULL, NULL);
+        out[b] = ora_loglike_full(L, params + (size_t)b * (L->mass == ORA_MASS_EPL
+                                                               ? ORA_NPAR + 1 : ORA_NPAR),
+                                  mode, NULL, NULL, NULL, NULL);
     (void)nthreads;
 }
 

@@ -11,6 +11,7 @@ import pytest
 from scipy import integrate, optimize, signal, special
 
 import oracle
+from paper_2503_08586_gb300 import workloads as W
 
 rng_global = np.random.default_rng(12345)
 
@@ -225,6 +226,116 @@ def test_sie_sis_limit():
         q = (1 - 1e-9) / (1 + 1e-9)
         ax, ay = oracle.sie_alpha(x, y, 1.3, q, 0.7)
         assert abs(ax - 1.3 * x / r) < 1e-8 and abs(ay - 1.3 * y / r) < 1e-8
+
+
+# ---------------------------------------------- Eq. (12), any gamma (EPL)
+def _alpha_homoeoid_kappa(x, y, q, kap):
+    """The homoeoid integrals above for any elliptical convergence kappa(xi),
+    xi^2 = x^2 + y^2/q^2, with u = s^4 so that kappa ~ u^(-t/2) (t < 2) leaves
+    a smooth integrand."""
+    def xi(u):
+        return math.sqrt(u * (x * x + y * y / (1 - (1 - q * q) * u)))
+
+    def jx_f(s_):
+        u = s_ ** 4
+        return 4 * s_ ** 3 * kap(xi(u)) / math.sqrt(1 - (1 - q * q) * u)
+
+    def jy_f(s_):
+        u = s_ ** 4
+        return 4 * s_ ** 3 * kap(xi(u)) / (1 - (1 - q * q) * u) ** 1.5
+
+    jx = integrate.quad(jx_f, 0, 1, epsabs=1e-15, epsrel=1e-13, limit=400)[0]
+    jy = integrate.quad(jy_f, 0, 1, epsabs=1e-15, epsrel=1e-13, limit=400)[0]
+    return q * x * jx, q * y * jy
+
+
+def _kappa_epl(thE, q, gamma):
+    """Eq. (12) with the Eq. (10) radius R_p = sqrt(q) xi."""
+    return lambda xi: (3 - gamma) / 2 * (thE / (math.sqrt(q) * xi)) ** (gamma - 1)
+
+
+def test_epl_vs_homoeoid_quadrature():
+    r = np.random.default_rng(17)
+    for _ in range(60):
+        thE = r.uniform(0.3, 2.0)
+        q = r.uniform(0.3, 0.999)
+        gamma = r.uniform(1.3, 2.7)
+        phi = r.uniform(-math.pi / 2, math.pi / 2)
+        xc, yc = r.normal(0, 0.1, 2)
+        x, y = r.uniform(-2.5, 2.5, 2)
+        ax, ay = oracle.epl_alpha(x, y, thE, q, phi, gamma, xc, yc)
+        c, s = math.cos(phi), math.sin(phi)
+        xp = (x - xc) * c + (y - yc) * s
+        yp = -(x - xc) * s + (y - yc) * c
+        hx, hy = _alpha_homoeoid_kappa(xp, yp, q, _kappa_epl(thE, q, gamma))
+        rx, ry = hx * c - hy * s, hx * s + hy * c
+        scale = thE + math.hypot(rx, ry)
+        assert abs(ax - rx) < 1e-9 * scale and abs(ay - ry) < 1e-9 * scale, (gamma, q)
+
+
+def test_epl_circular_closed_form():
+    """q = 1: alpha = theta_E (theta_E/r)^(gamma-2) theta/|theta| (the
+    enclosed convergence of Eq. 12), so |theta| = theta_E maps to beta = 0."""
+    for gamma in (1.4, 2.0, 2.6):
+        for (x, y) in [(0.3, 0.4), (-1.2, 0.5), (2.0, -2.0)]:
+            r = math.hypot(x, y)
+            ax, ay = oracle.epl_alpha(x, y, 1.3, 1.0, 0.7, gamma)
+            a = 1.3 * (1.3 / r) ** (gamma - 2)
+            assert abs(ax - a * x / r) < 1e-13 and abs(ay - a * y / r) < 1e-13
+        ax, ay = oracle.epl_alpha(1.3 * 0.6, 1.3 * 0.8, 1.3, 1.0, 0.0, gamma)
+        assert abs(ax - 1.3 * 0.6) < 1e-13 and abs(ay - 1.3 * 0.8) < 1e-13
+
+
+def test_epl_is_sie_at_gamma_2():
+    r = np.random.default_rng(18)
+    for _ in range(50):
+        thE, q, phi = r.uniform(0.3, 2.0), r.uniform(0.3, 0.999), r.uniform(0, math.pi)
+        x, y = r.uniform(-2.5, 2.5, 2)
+        a = oracle.epl_alpha(x, y, thE, q, phi, 2.0)
+        b = oracle.sie_alpha(x, y, thE, q, phi)
+        assert abs(a[0] - b[0]) < 1e-12 * thE and abs(a[1] - b[1]) < 1e-12 * thE
+
+
+def test_epl_divergence_and_curl():
+    """div alpha = 2 kappa (Eq. 12, any gamma) and curl alpha = 0."""
+    r = np.random.default_rng(19)
+    h = 1e-5
+    for _ in range(50):
+        thE, q, gamma = r.uniform(0.5, 1.5), r.uniform(0.4, 0.98), r.uniform(1.4, 2.6)
+        phi = r.uniform(0, math.pi)
+        x, y = r.uniform(-2, 2, 2)
+        if math.hypot(x, y) < 0.2:
+            continue
+        f = lambda a, b: oracle.epl_alpha(a, b, thE, q, phi, gamma)
+        dax = (f(x + h, y)[0] - f(x - h, y)[0]) / (2 * h)
+        day = (f(x, y + h)[1] - f(x, y - h)[1]) / (2 * h)
+        curl = (f(x + h, y)[1] - f(x - h, y)[1]) / (2 * h) - (
+            f(x, y + h)[0] - f(x, y - h)[0]) / (2 * h)
+        c, s = math.cos(phi), math.sin(phi)
+        xp, yp = x * c + y * s, -x * s + y * c
+        kappa = (3 - gamma) / 2 * (thE / math.sqrt(q * xp * xp + yp * yp / q)) ** (gamma - 1)
+        assert abs(dax + day - 2 * kappa) < 1e-6 * (1 + kappa)
+        assert abs(curl) < 1e-6
+
+
+def test_epl_lens_validity_and_batch():
+    """EPL lenses take 22 entries (gamma last, valid in (1, 3)); the batch
+    equals single evaluations; gamma = 2 gives the SIE lens's log L."""
+    rng = np.random.default_rng(20)
+    ny = nx = 12
+    psf = W.gaussian_psf(5, 1.5)
+    data = rng.normal(size=(ny, nx))
+    sig = np.ones((ny, nx))
+    le = oracle.Lens(data, sig, psf, 0.1, 2, mass="epl")
+    ls = oracle.Lens(data, sig, psf, 0.1, 2)
+    P = W.draw_prior(rng, 6).astype(np.float64)
+    Pe = np.concatenate([P, np.full((6, 1), 2.0)], axis=1)
+    assert np.allclose(le.loglike_batch(Pe), ls.loglike_batch(P), rtol=1e-11, atol=1e-9)
+    Pe[:, 21] = [1.5, 2.5, 1.0, 3.0, np.nan, 2.2]
+    out = le.loglike_batch(Pe)
+    assert np.isneginf(out[[2, 3, 4]]).all() and np.isfinite(out[[0, 1, 5]]).all()
+    single = [le.loglike(Pe[k]) for k in range(6)]
+    assert np.array_equal(np.asarray(single), out)
 
 
 def test_einstein_ring():
