@@ -151,7 +151,7 @@ def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096):
     oracle.build()
     cores = os.cpu_count() or 1
     o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
-                    lens.x0, lens.y0)
+                    lens.x0, lens.y0, mass="epl" if params.shape[1] == 22 else "sie")
     P = params.astype(np.float64)
     n0 = min(2 * cores, len(P))
     t = time.perf_counter()
@@ -263,7 +263,7 @@ def run_ours(args):
     B = args.batch or spec.batch
     lens, params = W.workload(args.workload, tll.columns_renderer, batch=B)
     L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
-                 lens.x0, lens.y0)
+                 lens.x0, lens.y0, mass=spec.mass)
     info = L.info()
     p_dev = torch.from_numpy(params).to(dev)
     out = torch.empty(B, dtype=torch.float64, device=dev)
@@ -402,10 +402,10 @@ def run_ours(args):
                 if served else
                 {"value": e2e_value, "unit": UNIT,
                  "path": "tll_loglike_batch_host, pinned host buffers",
-                 "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8}),
+                 "h2d_bytes_per_step": B * L.nparam * 4, "d2h_bytes_per_step": B * 8}),
         "e2e_batch_host": {"value": e2e_value, "unit": UNIT,
                            "path": "tll_loglike_batch_host, pinned host buffers, B per step",
-                           "h2d_bytes_per_step": B * 21 * 4, "d2h_bytes_per_step": B * 8},
+                           "h2d_bytes_per_step": B * L.nparam * 4, "d2h_bytes_per_step": B * 8},
         "served": served,
         "plain": plain,
         "clocks": clk,
@@ -512,7 +512,7 @@ def run_reference(args):
     lens, params = W.workload(args.workload, oracle.columns_renderer, batch=B)
     cores = os.cpu_count() or 1
     o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
-                    lens.x0, lens.y0)
+                    lens.x0, lens.y0, mass=spec.mass)
     P = params.astype(np.float64)
     S = min(B, args.ref_sample or 4 * cores)
     for w in range(args.warmup):

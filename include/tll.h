@@ -5,7 +5,9 @@
  * observed strong-lens image, the forward model and Gaussian log-likelihood
  * of arXiv:2503.08586 (TinyLensGpu):
  *   - lens equation beta = theta - alpha(theta) (Sec. 2.1, Eq. 1) with an
- *     SIE (Sec. 2.4, Eq. 12 at gamma = 2) plus external shear (Eqs. 13, 14);
+ *     SIE (Sec. 2.4, Eq. 12 at gamma = 2) or, for lenses created with
+ *     TLL_MASS_EPL, the elliptical power law of Eq. 12 at any slope, plus
+ *     external shear (Eqs. 13, 14);
  *   - image formation I = I_L(theta) + I_S(beta) (Eq. 2) with elliptical
  *     Sersic light (Eqs. 8-11), on an s x s supersampled grid binned back to
  *     pixels (Sec. 2.1, text after Eq. 2);
@@ -26,13 +28,16 @@
  *     [6] gamma_2  [7] I_e^L [8] r_e^L [9] n^L [10] eps1_L [11] eps2_L
  *     [12] x_L [13] y_L [14] I_e^S [15] r_e^S [16] n^S [17] eps1_S
  *     [18] eps2_S [19] x_S [20] y_S
+ *     Lenses created with TLL_MASS_EPL take TLL_NPARAM_EPL = 22 entries,
+ *     [21] the mass slope gamma of Eq. 12 (valid in (1, 3); kappa =
+ *     (3 - gamma)/2 (theta_E/R_p)^(gamma - 1) with the Eq. 10 radius).
  *     (ellipticities as Eq. 11; shear components with
  *     psi_ext = gamma_1 (x^2 - y^2)/2 + gamma_2 x y about the origin, which is
  *     Eq. 13 on the branch gamma_1 = -gamma cos 2phi of Eq. 14; I_e slots
  *     are used only with TLL_AMP_FIXED.)
  *   Invalid vectors (|eps| >= 1, r_e <= 0, n outside [0.2, 10],
- *     theta_E < 0, a non-finite entry) give log L = -INFINITY; the rest of
- *     the batch is unaffected.
+ *     theta_E < 0, an EPL slope outside (1, 3), a non-finite entry) give
+ *     log L = -INFINITY; the rest of the batch is unaffected.
  *   Masking: a pixel whose noise sigma is not finite and > 0, or whose datum
  *     is not finite, has weight 0 and no normalisation term.
  *   log L = -chi^2/2 - sum_{unmasked} log(2 pi sigma_i^2)/2, in FP64.
@@ -49,6 +54,7 @@ extern "C" {
 #endif
 
 #define TLL_NPARAM 21
+#define TLL_NPARAM_EPL 22
 #define TLL_MAX_SUB 8      /* largest supersampling factor s */
 #define TLL_MAX_PSF 63     /* largest PSF side */
 #define TLL_MAX_SIDE 4096  /* largest image side */
@@ -75,6 +81,12 @@ enum {
  * use by the allocating one-lens entry points if it is evaluated alone
  * after all. */
 #define TLL_FLAG_BATCH_ONLY 0x200
+/* Extra flag bit: the mass is the elliptical power law of Eq. 12 with a free
+ * slope (parameter vectors of TLL_NPARAM_EPL entries) instead of the SIE.
+ * Its deflection is the closed form of Tessore & Metcalf (2015), a
+ * hypergeometric series summed per vector to 1e-9 of its leading term (at
+ * most 64 terms: axis ratios down to ~0.25 at that accuracy). */
+#define TLL_MASS_EPL 0x400
 
 typedef struct tll_lens tll_lens; /* opaque; owns device copies of its data */
 
@@ -106,7 +118,7 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
 
 /*
  * tll_loglike_batch -- log L of B parameter vectors (Eqs. 1-3, 5-12).
- *   params  DEVICE float32 [B][TLL_NPARAM] (see Parameter vector)
+ *   params  DEVICE float32 [B][tll_lens_nparam(L)] (see Parameter vector)
  *   B       number of vectors, >= 0 (0: no work, TLL_OK)
  *   out     DEVICE float64 [B]
  *   stream  cudaStream_t to launch on (NULL: the legacy default stream)
@@ -121,7 +133,7 @@ int tll_loglike_batch(tll_lens *L, const float *params, int B, double *out,
 
 /*
  * tll_loglike_batch_host -- tll_loglike_batch from HOST buffers: copies
- * params (host float32 [B][21]) to the device, runs the batch and copies the
+ * params (host float32 [B][tll_lens_nparam(L)]) to the device, runs the batch and copies the
  * log-likelihoods back to out (host float64 [B]), all on `stream`, and
  * waits for the stream.  Pinned host buffers make the copies asynchronous
  * DMA.  Errors: as tll_loglike_batch.
@@ -205,7 +217,7 @@ int tll_server_open_job(tll_server *S, const float *image, const float *noise,
                         int flags, int *job_id);
 /* Release a job; TLL_EBUSY while it has requests not yet completed. */
 int tll_server_close_job(tll_server *S, int job_id);
-/* Queue B vectors (host float32 [B][21]) of a job; results go to out (host
+/* Queue B vectors (host float32 [B][nparam of the job's lens]) of a job; results go to out (host
  * float64 [B]).  Both buffers must stay valid until the request completes.
  * 1 <= B <= max_vectors_per_launch. */
 int tll_server_submit(tll_server *S, int job_id, const float *params, int B,
@@ -235,7 +247,7 @@ const char *tll_server_last_error(void);
  *   Same arguments, results and asynchrony as tll_loglike_batch.
  *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
  *     them into several calls).
- *   Scratch: a fixed 3.5 MiB array compiled into the library, held on every
+ *   Scratch: a fixed 8 MiB array compiled into the library, held on every
  *     GPU that loads it until the process exits.  All calls share it and it
  *     keeps the last call's contents; each call rewrites the part it reads
  *     before reading it.  Calls that overlap on the GPU (different streams,
@@ -253,7 +265,7 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B,
 /*
  * tll_model_image -- the blurred model image I^m (Eq. 3) of one vector with
  * its amplitudes: linear (NNLS) or fixed, per the lens's mode.
- *   params     host float32 [TLL_NPARAM]
+ *   params     host float32 [tll_lens_nparam(L)]
  *   image_out  host float32 [ny][nx]
  *   amps_out   host float32 [2] (lens, source amplitude) or NULL
  *   loglike_out host float64 [1] or NULL
@@ -373,7 +385,7 @@ int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm);
  * threads per SM, each with the placement its shared-memory share allows)
  * on the device and give the lens the fastest; later lenses with the same
  * signature start with it.
- *   params     DEVICE float32 [B][TLL_NPARAM] vectors to time with, repeated
+ *   params     DEVICE float32 [B][tll_lens_nparam(L)] vectors to time with, repeated
  *              to at least two per CTA; or NULL with B = 0 for a built-in
  *              set covering both SIE branches and steep and shallow Sersics
  *   stream     cudaStream_t the tuning launches run on (NULL: default)
@@ -389,6 +401,10 @@ int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm);
 int tll_autotune(tll_lens *L, const float *params, int B, void *stream,
                  tll_shape_t *chosen, tll_shape_t *tried, int max_tried,
                  int *n_tried);
+
+/* Entries per parameter vector of this lens: TLL_NPARAM, or TLL_NPARAM_EPL
+ * for a TLL_MASS_EPL lens (-1 for NULL). */
+int tll_lens_nparam(const tll_lens *L);
 
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,

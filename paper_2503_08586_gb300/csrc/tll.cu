@@ -65,12 +65,12 @@ int fail(int code, const char *fmt, ...)
 // -------------------------------------------------------------- kernels
 __global__ void k_prologue(const float *__restrict__ params, int B,
                            float *__restrict__ kc, double XC, double YC, double d,
-                           const double *__restrict__ bn_tab)
+                           const double *__restrict__ bn_tab, int epl)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B)
-        decode_vector(params + (size_t)b * NPAR, kc + (size_t)b * NCONST, XC, YC, d,
-                      bn_tab);
+        decode_vector(params + (size_t)b * (epl ? NPAR_EPL : NPAR), kc + (size_t)b * NCONST,
+                      XC, YC, d, bn_tab, epl != 0);
 }
 
 // One thread per node of the b_n table (run once per device).
@@ -89,8 +89,8 @@ __global__ void k_prologue_multi(const __grid_constant__ MultiArgs A)
     if (t >= A.all->total) return;
     const Segment &sg = A.segs[find_segment(A.segs, 0, A.all->nseg, t)];
     const LensDev &L = A.lenses[sg.lens];
-    decode_vector(sg.params + (size_t)(t - sg.first) * NPAR, A.kc + (size_t)t * NCONST, L.XC,
-                  L.YC, L.d, A.bn_tab);
+    decode_vector(sg.params + (size_t)(t - sg.first) * (L.epl ? NPAR_EPL : NPAR),
+                  A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0);
 }
 
 // Model image of one vector: I^m = s_l m_l + s_s m_s (Eq. 7), FP64 then
@@ -126,6 +126,7 @@ struct Shape {
 struct tll_lens {
     int dev = 0;
     int nx = 0, ny = 0, npix = 0, sub = 0, K = 0, flags = 0, mode = 0, sep = 0;
+    int epl = 0, nparam = NPAR;   // mass model: SIE (21 parameters) or EPL (22)
     float dpix = 0, x0 = 0, y0 = 0;
     double dWd = 0, lognorm = 0, psf_sum = 0;
     float *d_psf = nullptr, *d_pu = nullptr, *d_pv = nullptr;
@@ -220,6 +221,7 @@ LensDev lens_dev(const tll_lens *L)
     d.psf = L->d_psf; d.pu = L->d_pu; d.pv = L->d_pv; d.wpack = L->d_wpack;
     d.dWd = L->dWd; d.lognorm = L->lognorm;
     d.W = L->W; d.HL = L->HL; d.img = L->shape.img; d.band_rows = L->shape.band_rows;
+    d.epl = L->epl;
     for (int k = 0; k < kMaxK * kMaxK; ++k)
         d.tk[k] = k < (int)L->psf_norm.size() && L->K <= kMaxK ? L->psf_norm[k] : 0.0f;
     grid_centre(L, &d.XC, &d.YC);
@@ -306,7 +308,7 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     double xc, yc;
     grid_centre(L, &xc, &yc);
     k_prologue<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, xc, yc,
-                                                (double)L->dpix / L->sub, L->bn_tab);
+                                                (double)L->dpix / L->sub, L->bn_tab, L->epl);
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
     RunArgs R;
@@ -336,9 +338,21 @@ int ensure_kc(tll_lens *L, int B)
     return TLL_OK;
 }
 
-// Shared memory kept free for the multi-lens kernel's static part (its
-// copy of a lens descriptor), so every lens also fits that kernel.
+// Shared memory kept free for the kernels' static part (the multi-lens
+// kernel's copy of a lens descriptor, the EPL series), so every lens also
+// fits that kernel.
 constexpr int kSmemReserve = 8192;
+
+// Let kernel k use all the dynamic shared memory the opt-in limit leaves
+// beside its static part.
+int allow_dynamic_smem(const void *k, int optin)
+{
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes));
+    return TLL_OK;
+}
 
 struct DevLimits {
     int nsm = 0, optin = 0, per_sm_smem = 0, reserved = 0;
@@ -404,7 +418,7 @@ int make_shape(const tll_lens *L, const DevLimits &D, int threads, int per_sm, S
     }
     const SingleKernel k = find_single(L->sub, conv_class(S.img, L->K), false);
     if (!k) return fail(TLL_ECUDA, "no kernel for s=%d K=%d", L->sub, L->K);
-    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, D.optin));
+    if (int rc = allow_dynamic_smem((const void *)k, D.optin)) return rc;
     int n = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, S.smem));
     if (n < 1) return fail(TLL_EINVAL, "k_loglike cannot be resident at %d threads", threads);
@@ -449,7 +463,7 @@ int configure(tll_lens *L)
         }
         const SingleKernel kw = find_single(L->sub, 0, true);
         if (!kw) return fail(TLL_ECUDA, "no kernel for s=%d", L->sub);
-        CUDA_TRY(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, D.optin));
+        if (int rc = allow_dynamic_smem((const void *)kw, D.optin)) return rc;
     }
     int threads = kThreads, per_sm = 1;
     {
@@ -521,7 +535,7 @@ int run_one(tll_lens *L, const float *params_host)
         const int rc = ensure_gscr(L);
         if (rc) return rc;
     }
-    CUDA_TRY(cudaMemcpy(L->d_p1, params_host, NPAR * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(L->d_p1, params_host, L->nparam * sizeof(float), cudaMemcpyHostToDevice));
     int rc = run_batch(L, L->d_p1, 1, L->d_out1, 0, true, L->d_kc1);
     if (rc) return rc;
     CUDA_TRY(cudaDeviceSynchronize());
@@ -673,7 +687,7 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
 // array in the module instead, so the call itself allocates nothing; every
-// GPU that loads this library holds it (3.5 MiB) until the process exits.
+// GPU that loads this library holds it (8 MiB) until the process exits.
 constexpr int kNoAllocMaxB = 16384;
 static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
 
@@ -914,11 +928,12 @@ void shape_out(const Shape &S, tll_shape_t *o)
 // Parameter vectors for timing when the caller gives none: a fixed set
 // spanning both SIE forms (q near 1 and q well below it), both Sersic
 // extremes of the usual prior, and sources inside and outside the caustic.
-void default_tuning_vectors(int B, std::vector<float> &p)
+void default_tuning_vectors(int B, int nparam, std::vector<float> &p)
 {
-    p.assign((size_t)B * NPAR, 0.0f);
+    p.assign((size_t)B * nparam, 0.0f);
     for (int b = 0; b < B; ++b) {
-        float *v = &p[(size_t)b * NPAR];
+        float *v = &p[(size_t)b * nparam];
+        if (nparam > NPAR) v[21] = (b & 1) ? 1.8f : 2.2f;   // EPL slope
         const int k = b % 8;
         v[0] = 0.7f + 0.1f * (float)k;              // theta_E
         v[1] = (k & 1) ? 0.25f : 0.04f;             // e1 (q = 0.6 or 0.92)
@@ -1090,19 +1105,20 @@ extern "C" int tll_autotune(tll_lens *L, const float *params, int B, void *strea
             if (e) cudaEventDestroy(e);
     };
     auto bail = [&](int code) { cleanup(); return code; };
-    if (cudaMalloc(&d_p, (size_t)Bt * NPAR * sizeof(float)) != cudaSuccess ||
+    if (cudaMalloc(&d_p, (size_t)Bt * L->nparam * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&d_o, (size_t)Bt * sizeof(double)) != cudaSuccess)
         return bail(fail(TLL_ENOMEM, "tuning buffers"));
     if (B > 0) {
         for (int off = 0; off < Bt; off += B) {
             const int n = std::min(B, Bt - off);
-            if (cudaMemcpyAsync(d_p + (size_t)off * NPAR, params, (size_t)n * NPAR * sizeof(float),
+            if (cudaMemcpyAsync(d_p + (size_t)off * L->nparam, params,
+                                (size_t)n * L->nparam * sizeof(float),
                                 cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return bail(fail(TLL_ECUDA, "tuning batch copy"));
         }
     } else {
         std::vector<float> hp;
-        default_tuning_vectors(Bt, hp);
+        default_tuning_vectors(Bt, L->nparam, hp);
         if (cudaMemcpyAsync(d_p, hp.data(), hp.size() * sizeof(float), cudaMemcpyHostToDevice,
                             st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
@@ -1204,6 +1220,8 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
     L->dev = dev;
     L->nx = g.nx; L->ny = g.ny; L->npix = npix; L->sub = g.sub; L->K = K;
     L->flags = flags; L->mode = mode;
+    L->epl = (flags & TLL_MASS_EPL) ? 1 : 0;
+    L->nparam = L->epl ? NPAR_EPL : NPAR;
     L->dpix = g.pixel_scale; L->x0 = g.x0; L->y0 = g.y0; L->psf_sum = psum;
 
     // PSF, unit sum (Eq. 3); separable if it is an outer product to rounding
@@ -1269,7 +1287,7 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         (rc = alloc((void **)&L->d_pu, K * sizeof(float))) ||
         (rc = alloc((void **)&L->d_pv, K * sizeof(float))) ||
         (rc = alloc((void **)&L->d_wpack, npix * sizeof(float4))) ||
-        (rc = alloc((void **)&L->d_p1, NPAR * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_p1, NPAR_EPL * sizeof(float))) ||
         (rc = alloc((void **)&L->d_kc1, NCONST * sizeof(float))) ||
         (rc = alloc((void **)&L->d_unb, 2 * npix * sizeof(float))) ||
         (rc = alloc((void **)&L->d_blur, 2 * npix * sizeof(float))) ||
@@ -1324,6 +1342,12 @@ int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
     return TLL_OK;
 }
 
+int tll_lens_nparam(const tll_lens *L)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL"), -1;
+    return L->nparam;
+}
+
 int tll_profile_enable(tll_lens *L, int on)
 {
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
@@ -1376,7 +1400,7 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
         const int cap = std::max(B, 2 * L->stage_cap);
         float *p = nullptr;
         double *o = nullptr;
-        CUDA_TRY(cudaMalloc(&p, (size_t)cap * NPAR * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&p, (size_t)cap * L->nparam * sizeof(float)));
         cudaError_t e = cudaMalloc(&o, (size_t)cap * sizeof(double));
         if (e != cudaSuccess) {
             cudaFree(p);
@@ -1384,7 +1408,7 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
         }
         if (L->d_stage_p) cudaFree(L->d_stage_p);
         if (L->d_stage_o) cudaFree(L->d_stage_o);
-        L->dev_bytes += ((size_t)cap - L->stage_cap) * (NPAR * sizeof(float) + sizeof(double));
+        L->dev_bytes += ((size_t)cap - L->stage_cap) * (L->nparam * sizeof(float) + sizeof(double));
         L->d_stage_p = p;
         L->d_stage_o = o;
         L->stage_cap = cap;
@@ -1392,7 +1416,7 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
     int rc = ensure_kc(L, B);
     if (!rc) rc = ensure_gscr(L);
     if (rc) return rc;
-    CUDA_TRY(cudaMemcpyAsync(L->d_stage_p, params, (size_t)B * NPAR * sizeof(float),
+    CUDA_TRY(cudaMemcpyAsync(L->d_stage_p, params, (size_t)B * L->nparam * sizeof(float),
                              cudaMemcpyHostToDevice, st));
     rc = run_batch(L, L->d_stage_p, B, L->d_stage_o, st, false, L->d_kc);
     if (rc) return rc;

@@ -30,6 +30,7 @@ struct LensDev {
     const float4 *wpack; // [npix] (w_hi, w_lo, wd_hi, wd_lo)
     double dWd, lognorm;
     int band_rows;    // IMG_BANDED: output rows per shared-memory band
+    int epl;          // elliptical power-law mass: 22 parameters per vector
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
     float tk[kMaxK * kMaxK];            // the full PSF (direct convolution)
 };

@@ -14,6 +14,8 @@
 namespace tll {
 
 constexpr int NPAR = 21;
+constexpr int NPAR_EPL = 22;     // elliptical power-law mass: slope gamma at [21]
+constexpr int kEplMaxN = 63;     // highest power of the EPL deflection series
 
 // Per-vector constants written by the prologue, NCONST floats per vector.
 // Every coordinate a subpixel needs is an affine function of its integer
@@ -36,9 +38,13 @@ enum : int {
     K_Q11H, K_Q11L, K_Q12H, K_Q12L, K_Q21H, K_Q21L, K_Q22H, K_Q22L,
     // fixed amplitudes
     K_IEL, K_IES,
-    NCONST_USED
+    // elliptical power law (Eq. 12 at any slope): flag, highest power N of
+    // the deflection series, the magnitude's exponent e0 + e1 log2(psi^2)
+    // (hi, lo each), the series coefficients c_0 .. c_N
+    K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L, K_EC0,
+    NCONST_USED = K_EC0 + kEplMaxN + 1
 };
-constexpr int NCONST = 56;
+constexpr int NCONST = 128;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
 
 // ------------------------------------------------------------------ b_n
@@ -150,15 +156,17 @@ __device__ __forceinline__ void split2(double v, float *o_hi, float *o_lo)
 // S R(phi_m - phi_s) A (ux, uy), S = diag of the scales.
 __device__ inline void decode_vector(const float *__restrict__ p, float *__restrict__ o,
                                      double XC, double YC, double d,
-                                     const double *__restrict__ bn_tab)
+                                     const double *__restrict__ bn_tab, bool epl = false)
 {
     bool ok = true;
-    double v[NPAR];
+    double v[NPAR_EPL];
 #pragma unroll
     for (int k = 0; k < NPAR; ++k) {
         v[k] = (double)p[k];
         ok = ok && isfinite(v[k]);
     }
+    v[21] = epl ? (double)p[21] : 2.0;
+    ok = ok && v[21] > 1.0 && v[21] < 3.0;   // slope (EPL), non-finite fails too
     ok = ok && v[0] >= 0.0;
     ok = ok && v[8] > 0.0 && v[15] > 0.0;
     ok = ok && v[9] >= 0.2 && v[9] <= 10.0 && v[16] >= 0.2 && v[16] <= 10.0;
@@ -242,12 +250,38 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         // The fast path's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
         // path's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
         // so its columns carry 1/f and ln 2/(2f).
-        const double c1 = fast ? 1.0 : 1.0 / f;
-        const double c2 = fast ? 1.0 : 0.34657359027997264 / f;
-        split2(s1 * A * cd * c1, &o[K_Q11H], &o[K_Q11L]);
-        split2(-s1 * A * sd * c2, &o[K_Q12H], &o[K_Q12L]);
-        split2(s2 * A * sd * c1, &o[K_Q21H], &o[K_Q21L]);
-        split2(s2 * A * cd * c2, &o[K_Q22H], &o[K_Q22L]);
+        double c1 = fast ? 1.0 : 1.0 / f;
+        double c2 = fast ? 1.0 : 0.34657359027997264 / f;
+        double Am = A;
+        if (epl) {
+            // EPL (Tessore & Metcalf 2015 in this normalisation): with
+            // t = gamma - 1, b = theta_E sqrt(q), psi^2 = q^2 x'^2 + y'^2 and
+            // psi e^{i vphi} = q x' + i y', the deflection in the mass frame
+            // is 2b/(1+q) (b/psi)^(t-1) e^{i vphi} sum_n c_n e^{2 i n vphi},
+            // c_n = prod_{k<=n} (2k - 2 + t)/(2k + 2 - t) (-(1-q)/(1+q))^n
+            // (the series of 2F1(1, t/2; 2 - t/2; .)).  (ux, uy) is that sum
+            // times (b/psi)^(t-1) = 2^(e0 + e1 log2 psi^2); Q carries 2b/(1+q).
+            const double t = v[21] - 1.0, fr = -(1.0 - qm) / (1.0 + qm);
+            o[K_EPL] = 1.0f;
+            split2((t - 1.0) * log2(A), &o[K_E0H], &o[K_E0L]);
+            split2(0.5 * (1.0 - t), &o[K_E1H], &o[K_E1L]);
+            double cn = 1.0;
+            int N = 0;
+            o[K_EC0] = 1.0f;
+            for (int n = 1; n <= kEplMaxN; ++n) {
+                cn *= fr * (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+                o[K_EC0 + n] = (float)cn;
+                N = n;
+                if (fabs(cn) < 1e-9) break;   // the rest of the series is below float rounding
+            }
+            o[K_EN] = (float)N;
+            c1 = c2 = 1.0;
+            Am = 2.0 * A / (1.0 + qm);
+        }
+        split2(s1 * Am * cd * c1, &o[K_Q11H], &o[K_Q11L]);
+        split2(-s1 * Am * sd * c2, &o[K_Q12H], &o[K_Q12L]);
+        split2(s2 * Am * sd * c1, &o[K_Q21H], &o[K_Q21L]);
+        split2(s2 * Am * cd * c2, &o[K_Q22H], &o[K_Q22L]);
     }
     o[K_IEL] = (float)v[7];
     o[K_IES] = (float)v[14];
@@ -265,6 +299,9 @@ struct VecConst {
     bool fast;
     float khl, kll, bhl, bll, khs, kls, bhs, bls;
     float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
+    bool epl;                       // elliptical power-law mass
+    int en;                         // highest power of its series
+    float e0h, e0l, e1h, e1l;       // its magnitude's exponent
 };
 
 __device__ __forceinline__ Affine load_affine(const float *kc, int b)
@@ -285,6 +322,9 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
     v.q11h = kc[K_Q11H]; v.q11l = kc[K_Q11L]; v.q12h = kc[K_Q12H]; v.q12l = kc[K_Q12L];
     v.q21h = kc[K_Q21H]; v.q21l = kc[K_Q21L]; v.q22h = kc[K_Q22H]; v.q22l = kc[K_Q22L];
+    v.epl = kc[K_EPL] != 0.0f;
+    v.en = (int)kc[K_EN];
+    v.e0h = kc[K_E0H]; v.e0l = kc[K_E0L]; v.e1h = kc[K_E1H]; v.e1l = kc[K_E1L];
     return v;
 }
 
@@ -411,6 +451,34 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
     }
 }
 
+// EPL deflection (Eq. 12 at slope gamma) in the mass frame at (xp, yp), as
+// alpha' = (2b/(1+q)) (ux, uy) with Q carrying 2b/(1+q):
+//   (ux + i uy) = (b/psi)^(t-1) e^{i vphi} sum_{n<=N} c_n w^n,
+//   psi e^{i vphi} = q xp + i yp, w = e^{2 i vphi},
+// the sum by Horner in complex arithmetic over the coefficients ec[0..N]
+// (staged in shared memory per vector), the magnitude as
+// 2^(e0 + e1 log2 psi^2) with a range-reduced exp2.
+__device__ __forceinline__ void epl_unit(const VecConst &v, float xp, float yp,
+                                         const float *ec, float &ux, float &uy)
+{
+    const float qx = fmaf(v.ql, xp, v.q * xp);
+    const float a = fmaxf(fmaf(qx, qx, yp * yp), 1e-24f);
+    const float rpsi = rsqrt_nr(a);
+    const float c = qx * rpsi, s = yp * rpsi;            // e^{i vphi}
+    const float wr = fmaf(c, c, -s * s), wi = 2.0f * c * s;
+    float ar = ec[v.en], ai = 0.0f;
+#pragma unroll 4
+    for (int n = v.en - 1; n >= 0; --n) {
+        const float nr = fmaf(ar, wr, fmaf(-ai, wi, ec[n]));
+        ai = fmaf(ar, wi, ai * wr);
+        ar = nr;
+    }
+    const float L = sfu_lg2(a);
+    const float m = exp2_rr(fmaf(v.e1h, L, fmaf(v.e1l, L, v.e0l)) + v.e0h);
+    ux = m * fmaf(c, ar, -s * ai);
+    uy = m * fmaf(c, ai, s * ar);
+}
+
 // The two unit columns at one subpixel (fj, fi), given the row terms
 // r* = c0 + ci fi of the six affine coordinates.
 struct RowTerms {
@@ -427,13 +495,18 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
 // nlx, nly: minus the lo parts of the source coordinates at this pixel
 // (c0 + cj fj + ci fi of the lo constants, at the pixel's first subpixel;
 // they change by far less than a float ulp across a pixel).
-template <bool FAST>
+// MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series ec).
+template <int MODE>
 __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
-                                         float nlx, float nly, float &il, float &is)
+                                         float nlx, float nly, const float *ec, float &il,
+                                         float &is)
 {
-    // SIE in its frame (lens equation's deflection, Eq. 1)
+    // mass deflection in its frame (the lens equation's alpha, Eq. 1)
     float ux, uy;
-    sie_unit<FAST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
+    if constexpr (MODE == 2)
+        epl_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, ux, uy);
+    else
+        sie_unit<MODE == 0>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
     // lens light at theta (Eq. 2, first term)
     il = sersic_scaled(fmaf(v.lx.cj, fj, r.lx), fmaf(v.ly.cj, fj, r.ly), v.khl, v.kll,
                        v.bhl, v.bll);

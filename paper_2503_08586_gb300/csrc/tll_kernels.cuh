@@ -64,10 +64,11 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
 // Subpixel (J, I) of the supersampled grid has exact integer-or-half
 // offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
 // coordinate is an affine function of them (see decode_vector).
-template <int SUB, bool FAST>
+// MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series coefficients ec).
+template <int SUB, int MODE>
 __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
                                             float *Il, float *Is, int stride, int off,
-                                            int tid, int nthr)
+                                            int tid, int nthr, const float *ec)
 {
     const int sub = SUB > 0 ? SUB : L.sub;
     const int nx = L.nx;
@@ -85,7 +86,7 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
                     float il, is;
-                    subpixel<FAST>(v, r, fj0 + (float)(SUB > 0 ? c : cr), nlx, nly, il, is);
+                    subpixel<MODE>(v, r, fj0 + (float)(SUB > 0 ? c : cr), nlx, nly, ec, il, is);
                     accl += il;
                     accs += is;
                 }
@@ -491,20 +492,36 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
 // One parameter vector (its constant block kc is valid): trace, convolve
 // with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
 // block barrier.
+// Trace one vector with the deflection form it needs (the branch is uniform
+// over the CTA); an EPL vector's series coefficients are first staged in
+// sepl (kEplMaxN + 1 floats of shared memory).  Ends with a block barrier.
+template <int SUB>
+__device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, float *Il,
+                                             float *Is, int stride, int off, float *sepl,
+                                             int tid, int nthr)
+{
+    const VecConst v = load_consts(kc);
+    if (v.epl) {
+        for (int t = tid; t <= v.en; t += nthr) sepl[t] = kc[K_EC0 + t];
+        __syncthreads();
+        trace_image<SUB, 2>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+    } else if (v.fast) {
+        trace_image<SUB, 0>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+    } else {
+        trace_image<SUB, 1>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+    }
+    __syncthreads();
+}
+
 template <int SUB, int K, bool WRITE>
 __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
                                             const float *kc, double *outp, const ImgPtrs &P,
-                                            float *spsf, double *sred, int tid, int nthr)
+                                            float *spsf, double *sred, float *sepl, int tid,
+                                            int nthr)
 {
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nx = L.nx, npix = L.npix;
-    {
-        const VecConst v = load_consts(kc);
-        // the SIE branch is taken once per vector (uniform over the CTA)
-        if (v.fast) trace_image<SUB, true>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
-        else trace_image<SUB, false>(L, v, P.Il, P.Is, P.stride, P.off, tid, nthr);
-    }
-    __syncthreads();
+    trace_vector<SUB>(L, kc, P.Il, P.Is, P.stride, P.off, sepl, tid, nthr);
     if (WRITE) {
         for (int t = tid; t < npix; t += nthr) {
             const int i = t / nx, j = t - i * nx;
@@ -546,6 +563,7 @@ __global__ void __launch_bounds__(kThreads)
 k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float sepl[kEplMaxN + 1];
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
@@ -563,7 +581,7 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
             }
             continue;
         }
-        vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, tid, nthr);
+        vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, sepl, tid, nthr);
     }
 }
 
@@ -579,6 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LensDev sL;
     __shared__ int s_t, s_seg;
+    __shared__ float sepl[kEplMaxN + 1];
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
@@ -614,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
         }
         RunArgs R = {};
         const ImgPtrs P = img_ptrs(sL, spsf, gslot);
-        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, tid, nthr);
+        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, sepl, tid, nthr);
     }
 }
 

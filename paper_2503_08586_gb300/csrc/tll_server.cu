@@ -52,7 +52,8 @@ constexpr size_t kLatencyWindow = 1 << 16;
 struct Request {
     long long id = 0;
     int job = 0, B = 0;
-    const float *hp = nullptr;   // caller's host params [B][21]
+    int nparam = TLL_NPARAM;     // entries per vector of the job's lens
+    const float *hp = nullptr;   // caller's host params [B][nparam]
     double *ho = nullptr;        // caller's host out [B]
     int state = 0;               // 0 pending, 1 in flight, 2 done, 3 failed
     double t_submit = 0, t_done = 0;
@@ -77,7 +78,8 @@ struct Slot {
 struct Flight {
     int slot = 0;
     std::vector<Request *> reqs;
-    std::vector<int> offsets;
+    std::vector<int> offsets;        // first vector of each request
+    std::vector<size_t> poffsets;    // first float of each request's parameters
 };
 
 }  // namespace
@@ -145,6 +147,7 @@ void launcher_loop(tll_server *S)
         Flight f;
         f.slot = slot;
         int total = 0;
+        size_t ptotal = 0;
         while (!S->pending.empty()) {
             Request *r = S->pending.front();
             if (!f.reqs.empty() && (!S->cfg.coalesce ||
@@ -152,9 +155,11 @@ void launcher_loop(tll_server *S)
                 break;
             S->pending.pop_front();
             f.offsets.push_back(total);
+            f.poffsets.push_back(ptotal);
             f.reqs.push_back(r);
             r->state = 1;
             total += r->B;
+            ptotal += (size_t)r->B * r->nparam;
             if (!S->cfg.coalesce) break;
         }
         Slot &sl = S->slots[slot];
@@ -165,20 +170,19 @@ void launcher_loop(tll_server *S)
 
         // stage: host params -> pinned -> device, one copy per launch
         for (size_t k = 0; k < f.reqs.size(); ++k)
-            memcpy(sl.h_params + (size_t)f.offsets[k] * TLL_NPARAM, f.reqs[k]->hp,
-                   (size_t)f.reqs[k]->B * TLL_NPARAM * sizeof(float));
+            memcpy(sl.h_params + f.poffsets[k], f.reqs[k]->hp,
+                   (size_t)f.reqs[k]->B * f.reqs[k]->nparam * sizeof(float));
         std::vector<const float *> pp(f.reqs.size());
         std::vector<double *> oo(f.reqs.size());
         std::vector<int> cnt(f.reqs.size());
         for (size_t k = 0; k < f.reqs.size(); ++k) {
-            pp[k] = sl.d_params + (size_t)f.offsets[k] * TLL_NPARAM;
+            pp[k] = sl.d_params + f.poffsets[k];
             oo[k] = sl.d_out + f.offsets[k];
             cnt[k] = f.reqs[k]->B;
         }
         int rc = TLL_OK;
         char msg[256] = "";
-        cudaError_t e = cudaMemcpyAsync(sl.d_params, sl.h_params,
-                                        (size_t)total * TLL_NPARAM * sizeof(float),
+        cudaError_t e = cudaMemcpyAsync(sl.d_params, sl.h_params, ptotal * sizeof(float),
                                         cudaMemcpyHostToDevice, sl.stream);
         if (e != cudaSuccess) {
             rc = TLL_ECUDA;
@@ -301,9 +305,9 @@ int tll_server_create(const tll_server_config_t *cfg, tll_server **out)
         Slot &sl = S->slots[k];
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_params, nv * TLL_NPARAM * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_params, nv * TLL_NPARAM_EPL * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, nv * sizeof(double));
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_params, nv * TLL_NPARAM * sizeof(float));
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_params, nv * TLL_NPARAM_EPL * sizeof(float));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, nv * sizeof(double));
         int rc = e == cudaSuccess ? tll_batcher_create(c.use_graph, &sl.bat) : TLL_ECUDA;
         if (rc != TLL_OK) {
@@ -448,6 +452,7 @@ int tll_server_submit(tll_server *S, int job_id, const float *params, int B, dou
     r->id = S->next_id++;
     r->job = job_id;
     r->B = B;
+    r->nparam = tll_lens_nparam(S->jobs[job_id].L);
     r->hp = params;
     r->ho = out;
     r->t_submit = now_ms();

@@ -21,14 +21,13 @@ __global__ void __launch_bounds__(kThreads)
 k_trace_split(const __grid_constant__ LensDev L, const float *__restrict__ kc, int nvec,
               float *__restrict__ unbl)
 {
+    __shared__ float sepl[kEplMaxN + 1];
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int b = blockIdx.x; b < nvec; b += gridDim.x) {
         const float *k = kc + (size_t)b * NCONST;
         if (k[K_VALID] == 0.0f) continue;
         float *Il = unbl + (size_t)b * 2 * L.npix, *Is = Il + L.npix;
-        const VecConst v = load_consts(k);
-        if (v.fast) trace_image<SUB, true>(L, v, Il, Is, L.nx, 0, tid, nthr);
-        else trace_image<SUB, false>(L, v, Il, Is, L.nx, 0, tid, nthr);
+        trace_vector<SUB>(L, k, Il, Is, L.nx, 0, sepl, tid, nthr);
     }
 }
 

@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtll.so")
 
 NPARAM = 21
+NPARAM_EPL = 22
+MASS_EPL = 0x400
 AMP_LINEAR = 0
 AMP_FIXED = 1
 FLAG_DIRECT_CONV = 0x100
@@ -34,7 +36,7 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_server_destroy", "tll_server_last_error",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
-           "tll_autotune", "tll_set_conv", "tll_conv_check",
+           "tll_autotune", "tll_set_conv", "tll_conv_check", "tll_lens_nparam",
            "tll_destroy_lens", "tll_last_error", "tll_version")
 
 
@@ -120,6 +122,8 @@ def load(path: str | None = None):
     lib.tll_profile_last.restype = i
     lib.tll_lens_shape.argtypes = [vp, ctypes.POINTER(Shape)]
     lib.tll_lens_shape.restype = i
+    lib.tll_lens_nparam.argtypes = [vp]
+    lib.tll_lens_nparam.restype = i
     lib.tll_set_conv.argtypes = [vp, i, i]
     lib.tll_set_conv.restype = i
     lib.tll_conv_check.argtypes = [vp]
@@ -207,8 +211,12 @@ class Lens:
     def __init__(self, image, noise, psf, pixel_scale: float, sub: int,
                  x0: float | None = None, y0: float | None = None,
                  mode: int = AMP_LINEAR, direct_conv: bool = False,
-                 batch_only: bool = False):
+                 batch_only: bool = False, mass: str = "sie"):
+        """mass: "sie" (21 parameters per vector) or "epl" (the elliptical
+        power law of Eq. 12, 22 parameters: the slope gamma last)."""
         lib = load()
+        if mass not in ("sie", "epl"):
+            raise ValueError("mass must be 'sie' or 'epl'")
         img = np.ascontiguousarray(image, dtype=np.float32)
         nse = np.ascontiguousarray(noise, dtype=np.float32)
         k = np.ascontiguousarray(psf, dtype=np.float32)
@@ -223,13 +231,16 @@ class Lens:
         g = Grid(nx, ny, pixel_scale, sub, x0, y0)
         h = ctypes.c_void_p()
         flags = (mode | (FLAG_DIRECT_CONV if direct_conv else 0)
-                 | (FLAG_BATCH_ONLY if batch_only else 0))
+                 | (FLAG_BATCH_ONLY if batch_only else 0)
+                 | (MASS_EPL if mass == "epl" else 0))
         _check(lib.tll_create_lens(img.ctypes.data, nse.ctypes.data,
                                    k.ctypes.data, k.shape[0], ctypes.byref(g),
                                    flags, ctypes.byref(h)))
         self._h = h
         self.ny, self.nx, self.sub, self.psf_size = ny, nx, sub, k.shape[0]
         self.mode = mode
+        self.mass = mass
+        self.nparam = lib.tll_lens_nparam(h)
         self.pixel_scale, self.x0, self.y0 = pixel_scale, x0, y0
 
     @property
@@ -248,9 +259,9 @@ class Lens:
         (asynchronous on `stream`, default torch's current stream)."""
         import torch
         if not (params.is_cuda and params.dtype == torch.float32
-                and params.dim() == 2 and params.shape[1] == NPARAM
+                and params.dim() == 2 and params.shape[1] == self.nparam
                 and params.is_contiguous()):
-            raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+            raise ValueError(f"params must be a contiguous CUDA float32 [B, {self.nparam}]")
         B = params.shape[0]
         if out is None:
             out = torch.empty(B, dtype=torch.float64, device=params.device)
@@ -268,9 +279,9 @@ class Lens:
         since creating it would allocate."""
         import torch
         if not (params.is_cuda and params.dtype == torch.float32
-                and params.dim() == 2 and params.shape[1] == NPARAM
+                and params.dim() == 2 and params.shape[1] == self.nparam
                 and params.is_contiguous()):
-            raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+            raise ValueError(f"params must be a contiguous CUDA float32 [B, {self.nparam}]")
         B = params.shape[0]
         if not (out.is_cuda and out.dtype == torch.float64
                 and out.numel() >= B and out.is_contiguous()):
@@ -282,10 +293,10 @@ class Lens:
 
     # -- host batch (copies inside the call)
     def loglike_batch_host(self, params, out=None, stream=None):
-        """params: host float32 [B, 21] (numpy or CPU tensor, pinned is
+        """params: host float32 [B, nparam] (numpy or CPU tensor, pinned is
         best); returns host float64 [B] (numpy unless `out` is given)."""
         p, keep = _host_ptr(params, np.float32)
-        B = int(np.prod(keep.shape)) // NPARAM
+        B = int(np.prod(keep.shape)) // self.nparam
         if out is None:
             out = np.empty(B, dtype=np.float64)
         o, okeep = _host_ptr(out, np.float64)
@@ -298,7 +309,7 @@ class Lens:
     # -- single vector
     def model_image(self, params):
         """(blurred model image [ny, nx] float32, amplitudes (2,), log L)."""
-        p = np.ascontiguousarray(params, dtype=np.float32).reshape(NPARAM)
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(self.nparam)
         img = np.empty((self.ny, self.nx), dtype=np.float32)
         amps = np.empty(2, dtype=np.float32)
         ll = ctypes.c_double()
@@ -308,7 +319,7 @@ class Lens:
 
     def model_columns(self, params, blurred: bool = True):
         """Unit-amplitude (lens, source) columns [ny, nx] float32."""
-        p = np.ascontiguousarray(params, dtype=np.float32).reshape(NPARAM)
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(self.nparam)
         a = np.empty((self.ny, self.nx), dtype=np.float32)
         b = np.empty((self.ny, self.nx), dtype=np.float32)
         _check(load().tll_model_columns(self._h, p.ctypes.data, a.ctypes.data,
@@ -348,9 +359,9 @@ class Lens:
         if params is not None:
             import torch
             if not (params.is_cuda and params.dtype == torch.float32
-                    and params.dim() == 2 and params.shape[1] == NPARAM
+                    and params.dim() == 2 and params.shape[1] == self.nparam
                     and params.is_contiguous()):
-                raise ValueError("params must be a contiguous CUDA float32 [B, 21]")
+                raise ValueError(f"params must be a contiguous CUDA float32 [B, {self.nparam}]")
             p, B = ctypes.c_void_p(params.data_ptr()), int(params.shape[0])
         chosen = Shape()
         tried = (Shape * 8)()
@@ -407,10 +418,10 @@ class Batcher:
         if outs is None:
             outs = [torch.empty(p.shape[0], dtype=torch.float64, device=p.device)
                     for p in params]
-        for p, o in zip(params, outs):
+        for L, p, o in zip(lenses, params, outs):
             if not (p.is_cuda and p.dtype == torch.float32 and p.is_contiguous()
-                    and p.dim() == 2 and p.shape[1] == NPARAM):
-                raise ValueError("params must be contiguous CUDA float32 [B, 21]")
+                    and p.dim() == 2 and p.shape[1] == L.nparam):
+                raise ValueError(f"params must be contiguous CUDA float32 [B, {L.nparam}]")
             if not (o.is_cuda and o.dtype == torch.float64 and o.is_contiguous()
                     and o.numel() >= p.shape[0]):
                 raise ValueError("outs must be contiguous CUDA float64 [B]")
@@ -454,10 +465,11 @@ class Server:
         _scheck(load().tll_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._keep = {}
+        self._nparam = {}
         self.max_vectors = max_vectors_per_launch
 
     def open_job(self, image, noise, psf, pixel_scale, sub, x0=None, y0=None,
-                 mode=AMP_LINEAR):
+                 mode=AMP_LINEAR, mass: str = "sie"):
         """Admit a lens; returns its job id, or None when it does not fit
         the budget / slots now (TLL_EBUSY)."""
         img = np.ascontiguousarray(image, dtype=np.float32)
@@ -468,12 +480,14 @@ class Server:
         y0 = -(ny - 1) * pixel_scale / 2.0 if y0 is None else y0
         g = Grid(nx, ny, pixel_scale, sub, x0, y0)
         jid = ctypes.c_int(-1)
+        flags = mode | (MASS_EPL if mass == "epl" else 0)
         rc = load().tll_server_open_job(self._h, img.ctypes.data, nse.ctypes.data,
                                         k.ctypes.data, k.shape[0], ctypes.byref(g),
-                                        mode, ctypes.byref(jid))
+                                        flags, ctypes.byref(jid))
         if rc == EBUSY:
             return None
         _scheck(rc)
+        self._nparam[jid.value] = NPARAM_EPL if mass == "epl" else NPARAM
         return jid.value
 
     def close_job(self, job: int) -> bool:
@@ -486,9 +500,9 @@ class Server:
 
     def submit(self, job: int, params, out=None) -> int:
         """Queue a host batch; returns a request id.  params: float32
-        [B, 21] (numpy or pinned CPU tensor), kept alive until waited."""
+        [B, nparam] (numpy or pinned CPU tensor), kept alive until waited."""
         p, keep = _host_ptr(params, np.float32)
-        B = int(np.prod(keep.shape)) // NPARAM
+        B = int(np.prod(keep.shape)) // self._nparam.get(job, NPARAM)
         if out is None:
             out = np.empty(B, dtype=np.float64)
         o, okeep = _host_ptr(out, np.float64)
@@ -527,12 +541,12 @@ class Server:
             pass
 
 
-def columns_renderer(pixel_scale, sub, psf, ny, nx):
+def columns_renderer(pixel_scale, sub, psf, ny, nx, mass: str = "sie"):
     """Render function for the input generator backed by this library
     (blurred unit columns of the truth vector)."""
     dummy = np.zeros((ny, nx), dtype=np.float32)
     lens = Lens(dummy, np.ones((ny, nx), dtype=np.float32), psf, pixel_scale,
-                sub)
+                sub, mass=mass)
 
     def render(params):
         return lens.model_columns(params, blurred=True)

@@ -31,6 +31,7 @@ import numpy as np
 
 SEED_BASE = 2503085860
 NPARAM = 21
+NPARAM_EPL = 22          # elliptical power-law mass: the slope gamma appended
 
 PARAM_NAMES = [
     "theta_E", "eps1_m", "eps2_m", "x_m", "y_m", "gamma_1", "gamma_2",
@@ -44,6 +45,7 @@ PRIOR_WIDTH = np.array([
     0.0, 0.26, 0.87, 0.10, 0.10, 0.05, 0.05,
     0.0, 0.26, 0.87, 0.10, 0.10, 0.15, 0.15,
 ])
+PRIOR_WIDTH_EPL = np.append(PRIOR_WIDTH, 0.23)   # gamma ~ U[1.6, 2.4]
 
 
 @dataclass
@@ -60,6 +62,7 @@ class WorkloadSpec:
     noise_kind: str        # "sky" | "sky+poisson"
     moffat_beta: float = 3.0
     seed_offset: int = 0
+    mass: str = "sie"      # "sie" | "epl"
 
 
 WORKLOADS = {
@@ -69,6 +72,9 @@ WORKLOADS = {
                             4096, "sky+poisson", seed_offset=2),
     "hst200": WorkloadSpec("hst200", 200, 200, 0.05, 5, 31, "moffat", 0.10,
                            2048, "sky+poisson", seed_offset=3),
+    # csst100 with the elliptical power-law mass of Eq. 12 (slope free)
+    "csst100_epl": WorkloadSpec("csst100_epl", 100, 100, 0.074, 4, 21, "gaussian", 0.15,
+                                4096, "sky+poisson", seed_offset=6, mass="epl"),
 }
 
 
@@ -112,12 +118,14 @@ def _eps(rng, n, qlo=0.5, qhi=1.0):
     return e * np.cos(2 * pa), e * np.sin(2 * pa)
 
 
-def draw_prior(rng: np.random.Generator, n: int) -> np.ndarray:
+def draw_prior(rng: np.random.Generator, n: int, mass: str = "sie") -> np.ndarray:
     """n parameter vectors from the workload priors, float32 [n, 21]:
     theta_E ~ U[0.5,1.5]"; mass q ~ U[0.5,1], PA ~ U[0,pi); centre ~ N(0,0.05");
     gamma_1,2 ~ N(0,0.05); lens and source Sersic n ~ U[1,4], r_e ~ U[0.1,1]",
     q ~ U[0.5,1], PA ~ U[0,pi); lens-light centre = mass centre (Table 1);
-    source centre uniform in a disc of radius 0.3"; I_e slots = 1."""
+    source centre uniform in a disc of radius 0.3"; I_e slots = 1.
+    mass "epl": [n, 22] with the mass slope gamma ~ U[1.6, 2.4] last (drawn
+    after the other entries, so the first 21 columns are the SIE draws)."""
     p = np.zeros((n, NPARAM), dtype=np.float64)
     p[:, 0] = rng.uniform(0.5, 1.5, n)
     p[:, 1], p[:, 2] = _eps(rng, n)
@@ -139,16 +147,23 @@ def draw_prior(rng: np.random.Generator, n: int) -> np.ndarray:
     ang = rng.uniform(0.0, 2 * math.pi, n)
     p[:, 19] = rad * np.cos(ang)
     p[:, 20] = rad * np.sin(ang)
+    if mass == "epl":
+        p = np.concatenate([p, rng.uniform(1.6, 2.4, (n, 1))], axis=1)
     return p.astype(np.float32)
 
 
 def shrinking_draws(rng, truth: np.ndarray, n: int, lo_frac: float = 0.01):
     """n vectors ~ N(truth, sigma_j), sigma_j shrinking geometrically from the
     prior width to lo_frac of it (a stand-in for a sampler converging);
-    entries clipped into the valid region.  float32 [n, 21]."""
+    entries clipped into the valid region.  float32 [n, 21] (or [n, 22] for
+    an EPL truth, gamma clipped to [1.2, 2.8])."""
     frac = np.geomspace(1.0, lo_frac, n)
-    p = truth[None, :].astype(np.float64) + rng.normal(size=(n, NPARAM)) * (
-        frac[:, None] * PRIOR_WIDTH[None, :])
+    npar = truth.shape[0]
+    width = PRIOR_WIDTH_EPL if npar == NPARAM_EPL else PRIOR_WIDTH
+    p = truth[None, :].astype(np.float64) + rng.normal(size=(n, npar)) * (
+        frac[:, None] * width[None, :])
+    if npar == NPARAM_EPL:
+        p[:, 21] = np.clip(p[:, 21], 1.2, 2.8)
     p[:, 0] = np.clip(p[:, 0], 0.05, 3.5)
     for a, b in ((1, 2), (10, 11), (17, 18)):
         e = np.hypot(p[:, a], p[:, b])
@@ -193,7 +208,7 @@ def centred_origin(n: int, pixel_scale: float) -> float:
 
 
 def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
-               peak_snr=50.0, sky_sigma=1.0, truth=None) -> SynthLens:
+               peak_snr=50.0, sky_sigma=1.0, truth=None, mass: str = "sie") -> SynthLens:
     """One lens: truth from the priors, noiseless image from render(truth)
     (blurred unit-amplitude lens and source columns), amplitudes set so that
     each component's brightest blurred pixel is peak_snr * sky_sigma, then
@@ -201,7 +216,7 @@ def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
     sigma^2 = sky^2 + max(model,0)/g with g chosen so the Poisson term equals
     sky^2 at the source peak."""
     if truth is None:
-        truth = draw_prior(rng, 1)[0]
+        truth = draw_prior(rng, 1, mass)[0]
     truth = truth.astype(np.float32).copy()
     ml, ms = render(truth)
     ml = np.asarray(ml, dtype=np.float64)
@@ -225,16 +240,18 @@ def synth_lens(rng, ny, nx, pixel_scale, sub, psf, render, noise_kind="sky",
 
 
 def workload(name: str, render_factory, batch: int | None = None):
-    """(lens, params[B, 21]) for a named single-lens workload.
-    render_factory(pixel_scale, sub, psf, ny, nx) -> render(params)."""
+    """(lens, params[B, 21] or [B, 22] for an EPL workload) for a named
+    single-lens workload.  render_factory(pixel_scale, sub, psf, ny, nx
+    [, mass=...]) -> render(params)."""
     spec = WORKLOADS[name]
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + spec.seed_offset))
     psf = make_psf(spec)
-    render = render_factory(f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx)
+    kw = {} if spec.mass == "sie" else {"mass": spec.mass}
+    render = render_factory(f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx, **kw)
     lens = synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf,
-                      render, spec.noise_kind)
+                      render, spec.noise_kind, mass=spec.mass)
     B = spec.batch if batch is None else batch
-    params = draw_prior(rng, B)
+    params = draw_prior(rng, B, spec.mass)
     return lens, params
 
 

@@ -25,31 +25,35 @@ import torch  # noqa: E402
 import oracle  # noqa: E402
 from paper_2503_08586_gb300 import build, tll  # noqa: E402
 from paper_2503_08586_gb300 import workloads as W  # noqa: E402
-from test_parity_gpu import BULK_DCHI2, _chi2_truth, _lens_consts  # noqa: E402
+from test_parity_gpu import BULK_DCHI2, _chi2_truth, _lens_consts, _pix_allowance  # noqa: E402
 
 
-def pix_ratio(gpu, ora):
+def pix_ratio(gpu, ora, allow):
     ora = np.asarray(ora, np.float64)
-    tol = 1e-5 * np.abs(ora) + 1e-7 * np.abs(ora).max()
+    tol = 1e-5 * np.abs(ora) + 1e-7 * np.abs(ora).max() + allow
     return float((np.abs(np.asarray(gpu, np.float64) - ora) / np.maximum(tol, 1e-300)).max())
 
 
 def report(name, n_prior=24, n_conv=64, conv=None):
     lens, prior = W.workload(name, oracle.columns_renderer, batch=n_prior)
-    g = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    mass = W.WORKLOADS[name].mass
+    g = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0,
+                 mass=mass)
     label = name
     if conv is not None:
         g.set_conv(conv[1])
         label = f"{name} ({conv[0]})"
-    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0,
+                    mass=mass)
     worst = 0.0
     for p in np.concatenate([lens.truth[None], prior[:4]]):
         il, is_ = o.unblurred(p.astype(np.float64))
         _, ml, ms, _, _ = o.model(p.astype(np.float64), mode=1)
         for blurred, refs in ((False, (il, is_)), (True, (ml, ms))):
             cols = g.model_columns(p, blurred=blurred)
-            for c, r in zip(cols, refs):
-                worst = max(worst, pix_ratio(np.asarray(c).reshape(r.shape), r))
+            allow = _pix_allowance(o, p, blurred)
+            for c, r, a in zip(cols, refs, allow):
+                worst = max(worst, pix_ratio(np.asarray(c).reshape(r.shape), r, a))
     rng = np.random.Generator(np.random.PCG64(2024))
     conv = W.shrinking_draws(rng, lens.truth, n_conv, lo_frac=1e-6)
     P = np.concatenate([conv, prior]).astype(np.float32)
@@ -83,7 +87,7 @@ def main():
     print("| workload | image | worst pixel error / gate | bulk max abs dlogL (n) | "
           "bulk pairwise d(dlogL) | near max (n) | prior max (n) |")
     print("|---|---|---|---|---|---|---|")
-    for name in ("plain64", "csst100", "hst200"):
+    for name in ("plain64", "csst100", "hst200", "csst100_epl"):
         print(report(name), flush=True)
     # the hst200 convolution (Eq. 3) run three ways
     for conv in (("split, direct FP32", tll.CONV_SPLIT_DIRECT),

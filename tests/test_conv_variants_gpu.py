@@ -12,7 +12,7 @@ import oracle
 from paper_2503_08586_gb300 import build, tll
 from paper_2503_08586_gb300 import workloads as W
 
-from test_parity_gpu import _ll_ok, _pix_ok
+from test_parity_gpu import _ll_ok, _pix_allowance, _pix_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -41,14 +41,15 @@ def cases():
         o = oracle.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
         ref = o.loglike_batch(P.astype(np.float64))
         cols = [o.model(P[j].astype(np.float64), mode=1)[1:3] for j in (0, 25, 45)]
-        out.append((sl, P, ref, cols))
+        allows = [_pix_allowance(o, P[j], blurred=True) for j in (0, 25, 45)]
+        out.append((sl, P, ref, cols, allows))
     return out
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=["fused", "split_direct", "split_tc"])
 @pytest.mark.parametrize("idx", range(len(LENSES)))
 def test_variant_against_oracle(cases, idx, variant):
-    sl, P, ref, cols = cases[idx]
+    sl, P, ref, cols, allows = cases[idx]
     g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0,
                  direct_conv=True)
     g.set_conv(variant, chunk=16)      # several passes of the split pipeline
@@ -58,17 +59,17 @@ def test_variant_against_oracle(cases, idx, variant):
     got = out.cpu().numpy()
     assert np.isneginf(got[3])
     _ll_ok(got, ref, sl)
-    for j, (ml, ms) in zip((0, 25, 45), cols):
+    for j, (ml, ms), ab in zip((0, 25, 45), cols, allows):
         bl, bs = g.model_columns(P[j], blurred=True)
-        for gg, oo, nm in ((bl, ml, "lens"), (bs, ms, "source")):
-            ok, worst = _pix_ok(np.asarray(gg).reshape(oo.shape), oo)
+        for gg, oo, aa, nm in ((bl, ml, ab[0], "lens"), (bs, ms, ab[1], "source")):
+            ok, worst = _pix_ok(np.asarray(gg).reshape(oo.shape), oo, aa)
             assert ok, f"vector {j} {nm}: worst pixel error / tol = {worst:.3f}"
     g.conv_check()
     g.close()
 
 
 def test_variants_agree(cases):
-    sl, P, ref, _ = cases[0]
+    sl, P, ref, _, _ = cases[0]
     g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
     Pd = torch.from_numpy(P).cuda()
     res = []

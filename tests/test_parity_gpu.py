@@ -2,9 +2,15 @@
 the same seeded inputs.
 
 Tolerances (FP32 forward model, FP64 likelihood):
-  model pixels  |m_gpu - m_ora| <= 1e-5 |m_ora| + 1e-7 max|m_ora|, per column.
-                The floor covers Sersic tails, where the FP32 exponent's
-                rounding (|argument| * 2^-24) exceeds 1e-5 relative.
+  model pixels  |m_gpu - m_ora| <= 1e-5 |m_ora| + 1e-7 max|m_ora| + a_i, per
+                column.  The floor covers Sersic tails, where the FP32
+                exponent's rounding (|argument| * 2^-24) exceeds 1e-5
+                relative.  a_i is the pixel's change in the oracle when the
+                light centres move by POS_ERR = 2e-7 arcsec (1-2 float ulps
+                of an image-plane coordinate, the scale of FP32 position
+                rounding): negligible except at a Sersic cusp (n > 1, where
+                dI/dr ~ r^(1/n - 1) diverges), whose pixel no FP32
+                evaluation can bring within a relative gate.
   log L         three regions, by the oracle's chi^2 and the chi^2 of the
                 lens's true parameters (chi2_t):
                 - posterior bulk, chi^2 <= chi2_t + 50, where a converged
@@ -38,7 +44,7 @@ from paper_2503_08586_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-PIX_REL, PIX_FLOOR = 1e-5, 1e-7
+PIX_REL, PIX_FLOOR, POS_ERR = 1e-5, 1e-7, 2e-7
 LL_ABS, EPS_M, EPS_NEAR, BULK_DCHI2 = 1e-3, 1e-6, 1e-7, 50.0
 
 
@@ -49,10 +55,34 @@ def _lib():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def _pix_ok(gpu, ora):
+def _pix_allowance(o, params, blurred, mode=1):
+    """Per-pixel allowance a_i for both columns (lens, source): the largest
+    change of the oracle's column when the lens-light centre ([12], [13]) and
+    the source centre ([19], [20]) move by +-POS_ERR in x and in y."""
+    p0 = np.asarray(params, np.float64)
+
+    def cols(p):
+        if blurred:
+            _, ml, ms, _, _ = o.model(p, mode=mode)
+            return ml, ms
+        return o.unblurred(p)
+
+    base = cols(p0)
+    allow = [np.zeros_like(base[0]), np.zeros_like(base[1])]
+    for dx, dy in ((POS_ERR, 0), (-POS_ERR, 0), (0, POS_ERR), (0, -POS_ERR)):
+        p = p0.copy()
+        p[12] += dx; p[13] += dy; p[19] += dx; p[20] += dy
+        for c, (a, b) in enumerate(zip(cols(p), base)):
+            allow[c] = np.maximum(allow[c], np.abs(a - b))
+    return allow
+
+
+def _pix_ok(gpu, ora, allow=None):
     ora = np.asarray(ora, np.float64)
     gpu = np.asarray(gpu, np.float64)
     tol = PIX_REL * np.abs(ora) + PIX_FLOOR * np.abs(ora).max()
+    if allow is not None:
+        tol = tol + allow
     err = np.abs(gpu - ora)
     return bool(np.all(err <= tol)), float((err / np.maximum(tol, 1e-300)).max())
 
@@ -75,8 +105,9 @@ def _chi2_truth(lens):
     """The oracle's chi^2 at the lens's true parameters (cached per lens)."""
     key = id(lens)
     if key not in _CHI2_TRUTH:
+        mass = "epl" if np.asarray(lens.truth).shape[0] == oracle.NPARAM_EPL else "sie"
         o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
-                        lens.x0, lens.y0)
+                        lens.x0, lens.y0, mass=mass)
         _, lognorm, _ = _lens_consts(lens)
         ll = o.loglike_batch(np.asarray(lens.truth, np.float64)[None])[0]
         _CHI2_TRUTH[key] = (lens, max(-2.0 * (ll - lognorm), 0.0))
@@ -140,13 +171,15 @@ def test_columns_parity_plain64():
     for p in vecs:
         il, is_ = o.unblurred(p.astype(np.float64))
         gl, gs = g.model_columns(p, blurred=False)
-        for gg, oo, nm in ((gl, il, "lens"), (gs, is_, "src")):
-            ok, worst = _pix_ok(gg, oo)
+        au = _pix_allowance(o, p, blurred=False)
+        for gg, oo, aa, nm in ((gl, il, au[0], "lens"), (gs, is_, au[1], "src")):
+            ok, worst = _pix_ok(gg, oo, aa)
             assert ok, f"unblurred {nm}: worst error / tol = {worst:.3f}"
         _, ml, ms, _, _ = o.model(p.astype(np.float64), mode=1)
         bl, bs = g.model_columns(p, blurred=True)
-        for gg, oo, nm in ((bl, ml, "lens"), (bs, ms, "src")):
-            ok, worst = _pix_ok(gg, oo)
+        ab = _pix_allowance(o, p, blurred=True)
+        for gg, oo, aa, nm in ((bl, ml, ab[0], "lens"), (bs, ms, ab[1], "src")):
+            ok, worst = _pix_ok(gg, oo, aa)
             assert ok, f"blurred {nm}: worst error / tol = {worst:.3f}"
 
 
@@ -156,7 +189,8 @@ def test_model_image_and_amplitudes():
     for p in np.concatenate([lens.truth[None], params]):
         ll_o, _, _, mod_o, amps_o = o.model(p.astype(np.float64), mode=0)
         img, amps, ll = g.model_image(p)
-        ok, worst = _pix_ok(img, mod_o)
+        ab = _pix_allowance(o, p, blurred=True)
+        ok, worst = _pix_ok(img, mod_o, amps_o[0] * ab[0] + amps_o[1] * ab[1])
         assert ok, f"model image worst error / tol {worst:.3f}"
         assert np.allclose(amps, amps_o, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(amps_o).max()))
         _ll_ok(np.array([ll]), np.array([ll_o]), lens)
