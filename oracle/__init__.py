@@ -59,6 +59,12 @@ class _Lens(ctypes.Structure):
                 ("mass", ctypes.c_int)]
 
 
+class _Comp(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("plane", ctypes.c_int),
+                ("flags", ctypes.c_int), ("scale", ctypes.c_double),
+                ("index", ctypes.c_double)]
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -83,6 +89,16 @@ def _load():
         "ora_unblurred_columns": (i, [ctypes.POINTER(_Lens), pd, pd, pd]),
         "ora_loglike_batch": (None, [ctypes.POINTER(_Lens), pd, i, i, pd, i]),
         "ora_max_threads": (i, []),
+        "ora_gauss": (d, [d] * 7),
+        "ora_multi_nparam": (i, [ctypes.POINTER(_Comp), i, i]),
+        "ora_chol_solve": (i, [pd, pd, i, pd]),
+        "ora_fnnls": (i, [pd, pd, i, pd]),
+        "ora_loglike_multi": (d, [ctypes.POINTER(_Lens), ctypes.POINTER(_Comp), i, pd,
+                                  pd, pd, pd]),
+        "ora_multi_unblurred": (i, [ctypes.POINTER(_Lens), ctypes.POINTER(_Comp), i,
+                                    pd, pd]),
+        "ora_loglike_multi_batch": (None, [ctypes.POINTER(_Lens), ctypes.POINTER(_Comp),
+                                           i, pd, i, pd, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,6 +257,107 @@ class Lens:
         _load().ora_loglike_batch(ctypes.byref(self._s), _p(p), p.shape[0],
                                   mode, _p(out), nthreads)
         return out
+
+
+# ------------------------------------------------- multi-component light
+# Sec. 2.3 (Eq. 7): N_l lens-light and N_s source profiles, one column each.
+COMP = {"sersic": 0, "gauss": 1}
+PLANE = {"lens": 0, "source": 1}
+FREE_SCALE = 1
+FREE_INDEX = 2
+MULTI_HEAD = 15    # mass (7), lens-light geometry (4), source geometry (4)
+
+
+def gauss(x, y, cx, cy, q, phi, sigma) -> float:
+    """Unit-central-intensity elliptical Gaussian (reading R13)."""
+    return _load().ora_gauss(x, y, cx, cy, q, phi, sigma)
+
+
+def fnnls(A, b):
+    """FNNLS (Bro & de Jong 1997) on A = Z^T Z, b = Z^T y: (x, steps)."""
+    A = _f64(A)
+    b = _f64(b)
+    n = b.size
+    x = np.zeros(n)
+    steps = _load().ora_fnnls(_p(A), _p(b), n, _p(x))
+    return x, steps
+
+
+def chol_solve(G, r):
+    G, r = _f64(G), _f64(r)
+    z = np.zeros(r.size)
+    if _load().ora_chol_solve(_p(G), _p(r), r.size, _p(z)):
+        return None
+    return z
+
+
+def comp_array(comps):
+    """comps: list of dicts {type, plane, free_scale, free_index, scale, index}
+    (names as in COMP / PLANE) -> a ctypes array for the C oracle."""
+    arr = (_Comp * len(comps))()
+    for k, c in enumerate(comps):
+        flags = (FREE_SCALE if c.get("free_scale", True) else 0) | (
+            FREE_INDEX if c.get("free_index", False) else 0)
+        arr[k] = _Comp(COMP[c["type"]], PLANE[c["plane"]], flags,
+                       float(c.get("scale", 1.0)), float(c.get("index", 1.0)))
+    return arr
+
+
+class MultiLens(Lens):
+    """A lens with a multi-component light model (readings R13-R15)."""
+
+    def __init__(self, data, noise, psf, pixel_scale, sub, comps, x0=None,
+                 y0=None, mass: str = "sie"):
+        super().__init__(data, noise, psf, pixel_scale, sub, x0, y0, mass)
+        self.comps = list(comps)
+        self._c = comp_array(self.comps)
+        self.nc = len(self.comps)
+        self.nparam = _load().ora_multi_nparam(self._c, self.nc, MASS[mass])
+        if self.nparam < 0:
+            raise ValueError("bad component list")
+
+    def loglike(self, params, mode: int = 0) -> float:
+        p = _f64(params)
+        return _load().ora_loglike_multi(ctypes.byref(self._s), self._c, self.nc,
+                                         _p(p), None, None, None)
+
+    def model(self, params, mode: int = 0):
+        """(log L, blurred columns [nc, ny, nx], model, amplitudes [nc])."""
+        p = _f64(params)
+        n = self.ny * self.nx
+        cols, amps, mod = np.zeros(n * self.nc), np.zeros(self.nc), np.zeros(n)
+        ll = _load().ora_loglike_multi(ctypes.byref(self._s), self._c, self.nc,
+                                       _p(p), _p(cols), _p(amps), _p(mod))
+        return (ll, cols.reshape(self.nc, self.ny, self.nx),
+                mod.reshape(self.ny, self.nx), amps)
+
+    def unblurred(self, params):
+        p = _f64(params)
+        cols = np.zeros(self.nc * self.ny * self.nx)
+        if _load().ora_multi_unblurred(ctypes.byref(self._s), self._c, self.nc,
+                                       _p(p), _p(cols)):
+            return None
+        return cols.reshape(self.nc, self.ny, self.nx)
+
+    def loglike_batch(self, params, mode: int = 0, nthreads: int = 0):
+        p = _f64(params).reshape(-1, self.nparam)
+        out = np.zeros(p.shape[0])
+        _load().ora_loglike_multi_batch(ctypes.byref(self._s), self._c, self.nc,
+                                        _p(p), p.shape[0], _p(out), nthreads)
+        return out
+
+
+def multi_columns_renderer(pixel_scale, sub, psf, ny, nx, comps, mass: str = "sie"):
+    """render(params) -> blurred unit columns [nc, ny, nx] of a
+    multi-component model (to synthesise data images in the tests)."""
+    dummy = np.zeros((ny, nx))
+    lens = MultiLens(dummy, np.ones((ny, nx)), psf, pixel_scale, sub, comps, mass=mass)
+
+    def render(params):
+        _, cols, _, _ = lens.model(params)
+        return cols
+
+    return render
 
 
 def max_threads() -> int:

@@ -476,3 +476,345 @@ int ora_max_threads(void)
     return 1;
 #endif
 }
+
+/* ================================================================
+ * Multi-component light and N-column non-negative least squares.
+ *
+ * Sec. 2.3, Eq. (7): the lens light and the source light are superpositions
+ * of N_l and N_s unit-amplitude profiles; each profile is one column of
+ * L = [L_l | L_s], M = B L, and the amplitudes s >= 0 minimise
+ * ||(M s - d)/n|| (the penalty after Eq. 7), solved by FNNLS (Bro & de Jong
+ * 1997).  Sec. 3.2 models SLACS lenses with two Sersic components per
+ * galaxy sharing one centre and one ellipticity, with the indices fixed at 1
+ * and 4; Sec. 4.3 names the multiple Gaussian expansion (MGE).  This part of
+ * the oracle therefore takes a list of components, each a Sersic (Eq. 8) or
+ * a Gaussian, in the lens plane (at theta) or the source plane (at beta of
+ * Eq. 1), all components of one plane sharing that plane's centre and
+ * ellipticity (Eq. 10, 11).
+ *
+ * Readings (listed with the others in the design notes):
+ *   R13 Gaussian component: unit central intensity, exp(-R_p^2 / (2 sigma^2))
+ *       with the R_p of Eq. (10) (the same elliptical radius as the Sersic);
+ *       the paper prints no formula for it.  Its scale is sigma (arcsec).
+ *   R14 parameter vector of a multi-component model:
+ *       [0] theta_E [1] eps1_m [2] eps2_m [3] x_m [4] y_m [5] gamma_1
+ *       [6] gamma_2 [7] eps1_L [8] eps2_L [9] x_L [10] y_L [11] eps1_S
+ *       [12] eps2_S [13] x_S [14] y_S, then, component by component, the
+ *       free values: its scale (r_e or sigma) if free, then its Sersic index
+ *       if free; an EPL mass appends its slope last.  Fixed values come from
+ *       the component list.  Invalid as R9 (scale <= 0, index outside
+ *       [0.2, 10], |eps| >= 1, theta_E < 0, non-finite).
+ *   R15 FNNLS tolerance: a column enters the passive set while its gradient
+ *       b_j - (A x)_j exceeds 10 eps ||A||_1 n (eps = 2^-52), and a
+ *       passive amplitude that reaches a non-positive value leaves it; the
+ *       step that would re-enter a column whose least-squares value is not
+ *       positive is skipped for that pass (the Lawson-Hanson safeguard).
+ * ================================================================ */
+#define ORA_COMP_SERSIC 0
+#define ORA_COMP_GAUSS 1
+#define ORA_PLANE_LENS 0
+#define ORA_PLANE_SOURCE 1
+#define ORA_FREE_SCALE 1
+#define ORA_FREE_INDEX 2
+#define ORA_MAXC 16
+#define ORA_MHEAD 15
+
+typedef struct {
+    int type, plane, flags;
+    double scale, index;
+} ora_comp_spec;
+
+typedef struct {
+    ora_model mass;                 /* mass and shear fields only */
+    double qL, phiL, xL, yL, qS, phiS, xS, yS;
+    int nc;
+    int type[ORA_MAXC], plane[ORA_MAXC];
+    double scale[ORA_MAXC], n[ORA_MAXC], bn[ORA_MAXC];
+} ora_mmodel;
+
+/* Entries of a multi-component parameter vector (R14), -1 for a bad list. */
+int ora_multi_nparam(const ora_comp_spec *c, int nc, int mass)
+{
+    if (nc < 1 || nc > ORA_MAXC) return -1;
+    int np = ORA_MHEAD;
+    for (int k = 0; k < nc; ++k) {
+        if (c[k].type != ORA_COMP_SERSIC && c[k].type != ORA_COMP_GAUSS) return -1;
+        if (c[k].plane != ORA_PLANE_LENS && c[k].plane != ORA_PLANE_SOURCE) return -1;
+        if (c[k].flags & ORA_FREE_SCALE) ++np;
+        if (c[k].type == ORA_COMP_SERSIC && (c[k].flags & ORA_FREE_INDEX)) ++np;
+    }
+    return np + (mass == ORA_MASS_EPL ? 1 : 0);
+}
+
+/* Decode a multi-component vector (R14); -1 if invalid (R9). */
+int ora_decode_multi(const double *p, const ora_comp_spec *c, int nc, int mass,
+                     ora_mmodel *m)
+{
+    int np = ora_multi_nparam(c, nc, mass);
+    if (np < 0) return -1;
+    for (int k = 0; k < np; ++k)
+        if (!isfinite(p[k])) return -1;
+    ora_model *mm = &m->mass;
+    memset(mm, 0, sizeof *mm);
+    mm->mass = mass;
+    mm->gamma = 2.0;
+    if (mass == ORA_MASS_EPL) {
+        if (!(p[np - 1] > 1.0 && p[np - 1] < 3.0)) return -1;
+        mm->gamma = p[np - 1];
+    }
+    if (p[0] < 0.0) return -1;
+    if (ora_ellipse(p[1], p[2], &mm->qm, &mm->phim)) return -1;
+    if (ora_ellipse(p[7], p[8], &m->qL, &m->phiL)) return -1;
+    if (ora_ellipse(p[11], p[12], &m->qS, &m->phiS)) return -1;
+    mm->thE = p[0]; mm->xm = p[3]; mm->ym = p[4]; mm->g1 = p[5]; mm->g2 = p[6];
+    m->xL = p[9]; m->yL = p[10]; m->xS = p[13]; m->yS = p[14];
+    m->nc = nc;
+    int slot = ORA_MHEAD;
+    for (int k = 0; k < nc; ++k) {
+        m->type[k] = c[k].type;
+        m->plane[k] = c[k].plane;
+        m->scale[k] = (c[k].flags & ORA_FREE_SCALE) ? p[slot++] : c[k].scale;
+        m->n[k] = 0.0;
+        m->bn[k] = 0.0;
+        if (!(m->scale[k] > 0.0) || !isfinite(m->scale[k])) return -1;
+        if (c[k].type == ORA_COMP_SERSIC) {
+            m->n[k] = (c[k].flags & ORA_FREE_INDEX) ? p[slot++] : c[k].index;
+            if (!(m->n[k] >= 0.2 && m->n[k] <= 10.0)) return -1;
+            m->bn[k] = ora_sersic_bn(m->n[k]);
+        }
+    }
+    return 0;
+}
+
+/* Unit-central-intensity elliptical Gaussian (R13) at (x, y): the R_p of
+ * Eq. (10) in the frame rotated by phi about (cx, cy). */
+double ora_gauss(double x, double y, double cx, double cy, double q,
+                 double phi, double sigma)
+{
+    double c = cos(phi), s = sin(phi);
+    double x1 = (x - cx) * c + (y - cy) * s;
+    double x2 = -(x - cx) * s + (y - cy) * c;
+    double R2 = x1 * x1 * q + x2 * x2 / q;
+    return exp(-R2 / (2.0 * sigma * sigma));
+}
+
+/* The nc unit columns of L (Eq. 7) before the PSF, cols[k][npix]: each
+ * subpixel of the s x s grid (R1) evaluates every component at theta (lens
+ * plane) or at beta(theta) of Eq. (1) (source plane); binned by the mean (R2). */
+void ora_multi_columns(const ora_mmodel *m, int ny, int nx, double dpix, int sub,
+                       double x0, double y0, double *cols)
+{
+    int npix = ny * nx;
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < nx; ++j) {
+            double acc[ORA_MAXC] = {0};
+            for (int a = 0; a < sub; ++a)
+                for (int c = 0; c < sub; ++c) {
+                    double x = x0 + j * dpix + ((c + 0.5) / sub - 0.5) * dpix;
+                    double y = y0 + i * dpix + ((a + 0.5) / sub - 0.5) * dpix;
+                    double bx, by;
+                    ora_trace(&m->mass, x, y, &bx, &by);
+                    for (int k = 0; k < m->nc; ++k) {
+                        int src = m->plane[k] == ORA_PLANE_SOURCE;
+                        double px = src ? bx : x, py = src ? by : y;
+                        double cx = src ? m->xS : m->xL, cy = src ? m->yS : m->yL;
+                        double q = src ? m->qS : m->qL, phi = src ? m->phiS : m->phiL;
+                        acc[k] += m->type[k] == ORA_COMP_SERSIC
+                                      ? ora_sersic(px, py, cx, cy, q, phi, m->scale[k],
+                                                   m->n[k], m->bn[k])
+                                      : ora_gauss(px, py, cx, cy, q, phi, m->scale[k]);
+                    }
+                }
+            for (int k = 0; k < m->nc; ++k)
+                cols[(size_t)k * npix + i * nx + j] = acc[k] / (double)(sub * sub);
+        }
+}
+
+/* Solve G z = r for the symmetric positive definite k x k matrix G
+ * (row-major) by the Cholesky factorisation G = R^T R; -1 if a pivot is
+ * not positive. */
+int ora_chol_solve(const double *G, const double *r, int k, double *z)
+{
+    double R[ORA_MAXC * ORA_MAXC], y[ORA_MAXC];
+    for (int i = 0; i < k; ++i)
+        for (int j = i; j < k; ++j) {
+            double v = G[i * k + j];
+            for (int t = 0; t < i; ++t) v -= R[t * k + i] * R[t * k + j];
+            if (i == j) {
+                if (!(v > 0.0)) return -1;
+                R[i * k + i] = sqrt(v);
+            } else {
+                R[i * k + j] = v / R[i * k + i];
+            }
+        }
+    for (int i = 0; i < k; ++i) {            /* R^T y = r */
+        double v = r[i];
+        for (int t = 0; t < i; ++t) v -= R[t * k + i] * y[t];
+        y[i] = v / R[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {       /* R z = y */
+        double v = y[i];
+        for (int t = i + 1; t < k; ++t) v -= R[i * k + t] * z[t];
+        z[i] = v / R[i * k + i];
+    }
+    return 0;
+}
+
+/* Least squares restricted to the passive set: s_P = A_PP^{-1} b_P, s = 0
+ * elsewhere.  -1 if A_PP is not positive definite. */
+static int ora_passive_solve(const double *A, const double *b, const int *P, int n,
+                             double *s)
+{
+    int idx[ORA_MAXC], k = 0;
+    double G[ORA_MAXC * ORA_MAXC], r[ORA_MAXC], z[ORA_MAXC];
+    for (int i = 0; i < n; ++i)
+        if (P[i]) idx[k++] = i;
+    for (int a = 0; a < k; ++a) {
+        r[a] = b[idx[a]];
+        for (int c = 0; c < k; ++c) G[a * k + c] = A[idx[a] * n + idx[c]];
+    }
+    for (int i = 0; i < n; ++i) s[i] = 0.0;
+    if (k == 0) return 0;
+    if (ora_chol_solve(G, r, k, z)) return -1;
+    for (int a = 0; a < k; ++a) s[idx[a]] = z[a];
+    return 0;
+}
+
+/* FNNLS (Bro & de Jong 1997): min ||Z x - y||^2 subject to x >= 0, given
+ * only A = Z^T Z (n x n, row-major, n <= ORA_MAXC) and b = Z^T y -- the
+ * Lawson-Hanson active-set method run on the normal equations (Sec. 2.3:
+ * the paper's linear solve).  Steps, with R15's tolerance:
+ *   start with every column active (held at zero): x = 0, gradient w = b;
+ *   while some active column has w_j > tol: make the one with the largest
+ *   w_j passive; solve the passive least-squares problem for s; while some
+ *   passive s_i <= 0, move x towards s as far as feasibility allows
+ *   (alpha = min x_i/(x_i - s_i) over those i), make the columns that reach
+ *   zero active, and solve again; then x = s and w = b - A x.
+ * Returns the number of outer steps, -1 if the step cap (30 n) ran out. */
+int ora_fnnls(const double *A, const double *b, int n, double *x)
+{
+    int P[ORA_MAXC] = {0}, blocked[ORA_MAXC] = {0};
+    double w[ORA_MAXC], s[ORA_MAXC];
+    double norm1 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double cs = 0.0;
+        for (int i = 0; i < n; ++i) cs += fabs(A[i * n + j]);
+        if (cs > norm1) norm1 = cs;
+    }
+    const double tol = 10.0 * 2.220446049250313e-16 * norm1 * n;
+    for (int i = 0; i < n; ++i) { x[i] = 0.0; w[i] = b[i]; }
+    for (int step = 0; step < 30 * n; ++step) {
+        int j = -1;
+        double wmax = tol;
+        for (int i = 0; i < n; ++i)
+            if (!P[i] && !blocked[i] && w[i] > wmax) { wmax = w[i]; j = i; }
+        if (j < 0) return step;
+        P[j] = 1;
+        if (ora_passive_solve(A, b, P, n, s) || !(s[j] > 0.0)) {
+            P[j] = 0;             /* Lawson-Hanson safeguard (R15) */
+            blocked[j] = 1;
+            continue;
+        }
+        for (int inner = 0; inner <= n; ++inner) {
+            double alpha = 2.0;
+            int kmin = -1;
+            for (int i = 0; i < n; ++i)
+                if (P[i] && s[i] <= 0.0) {
+                    double a = x[i] / (x[i] - s[i]);
+                    if (a < alpha) { alpha = a; kmin = i; }
+                }
+            if (kmin < 0) break;
+            for (int i = 0; i < n; ++i) x[i] += alpha * (s[i] - x[i]);
+            x[kmin] = 0.0;
+            for (int i = 0; i < n; ++i)
+                if (P[i] && x[i] <= 0.0) { P[i] = 0; x[i] = 0.0; }
+            if (ora_passive_solve(A, b, P, n, s)) return -1;
+        }
+        for (int i = 0; i < n; ++i) { x[i] = s[i]; blocked[i] = 0; }
+        for (int i = 0; i < n; ++i) {
+            double v = b[i];
+            for (int k = 0; k < n; ++k) v -= A[i * n + k] * x[k];
+            w[i] = v;
+        }
+    }
+    return -1;
+}
+
+/* One multi-component vector: columns, PSF (Eq. 3), weights (R8), the
+ * normal equations A = M^T W M, b = M^T W d, FNNLS amplitudes, then chi^2
+ * by a direct pass over the pixels and log L (Eq. 5).  Optional outputs:
+ * the blurred columns [nc][npix], the amplitudes [nc], the blurred model.
+ * Returns -INFINITY for an invalid vector. */
+double ora_loglike_multi(const ora_lens *L, const ora_comp_spec *c, int nc,
+                         const double *p, double *cols_out, double *amps_out,
+                         double *model_out)
+{
+    ora_mmodel m;
+    int npix = L->ny * L->nx;
+    if (ora_decode_multi(p, c, nc, L->mass, &m)) return -INFINITY;
+    double *u = malloc(sizeof(double) * npix * nc), *mc = malloc(sizeof(double) * npix * nc);
+    double *w = malloc(sizeof(double) * npix), *psf = malloc(sizeof(double) * L->k * L->k);
+    double *mod = malloc(sizeof(double) * npix);
+    double res = -INFINITY;
+    if (!u || !mc || !w || !psf || !mod) goto done;
+    if (ora_psf_normalise(L->psf, L->k, psf)) goto done;
+    ora_multi_columns(&m, L->ny, L->nx, L->dpix, L->sub, L->x0, L->y0, u);
+    for (int k = 0; k < nc; ++k)
+        ora_convolve(u + (size_t)k * npix, L->ny, L->nx, psf, L->k, mc + (size_t)k * npix);
+    ora_weights(L->data, L->sigma, npix, w);
+    double A[ORA_MAXC * ORA_MAXC] = {0}, b[ORA_MAXC] = {0}, x[ORA_MAXC];
+    for (int a = 0; a < nc; ++a) {
+        const double *ma = mc + (size_t)a * npix;
+        for (int t = 0; t < npix; ++t) b[a] += w[t] * ma[t] * L->data[t];
+        for (int e = 0; e < nc; ++e) {
+            const double *me = mc + (size_t)e * npix;
+            double v = 0.0;
+            for (int t = 0; t < npix; ++t) v += w[t] * ma[t] * me[t];
+            A[a * nc + e] = v;
+        }
+    }
+    ora_fnnls(A, b, nc, x);
+    double chi2 = 0.0, norm = 0.0;
+    for (int t = 0; t < npix; ++t) {
+        double mv = 0.0;
+        for (int k = 0; k < nc; ++k) mv += x[k] * mc[(size_t)k * npix + t];
+        mod[t] = mv;
+        if (w[t] == 0.0) continue;
+        double r = L->data[t] - mv;
+        chi2 += w[t] * r * r;
+        norm += log(2.0 * M_PI / w[t]);
+    }
+    res = -0.5 * chi2 - 0.5 * norm;
+    if (cols_out) memcpy(cols_out, mc, sizeof(double) * npix * nc);
+    if (amps_out) memcpy(amps_out, x, sizeof(double) * nc);
+    if (model_out) memcpy(model_out, mod, sizeof(double) * npix);
+done:
+    free(u); free(mc); free(w); free(psf); free(mod);
+    return res;
+}
+
+/* Unblurred multi-component columns [nc][npix]; -1 for an invalid vector. */
+int ora_multi_unblurred(const ora_lens *L, const ora_comp_spec *c, int nc,
+                        const double *p, double *cols)
+{
+    ora_mmodel m;
+    if (ora_decode_multi(p, c, nc, L->mass, &m)) return -1;
+    ora_multi_columns(&m, L->ny, L->nx, L->dpix, L->sub, L->x0, L->y0, cols);
+    return 0;
+}
+
+/* Batch of B multi-component vectors (row-major [B][nparam]); parallel over
+ * vectors only. */
+void ora_loglike_multi_batch(const ora_lens *L, const ora_comp_spec *c, int nc,
+                             const double *params, int B, double *out, int nthreads)
+{
+    const int np = ora_multi_nparam(c, nc, L->mass);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; ++b)
+        out[b] = np < 0 ? -INFINITY
+                        : ora_loglike_multi(L, c, nc, params + (size_t)b * np, NULL, NULL, NULL);
+    (void)nthreads;
+}
