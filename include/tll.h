@@ -247,7 +247,7 @@ const char *tll_server_last_error(void);
  *   Same arguments, results and asynchrony as tll_loglike_batch.
  *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
  *     them into several calls).
- *   Scratch: a fixed 8 MiB array compiled into the library, held on every
+ *   Scratch: a fixed 12 MiB array compiled into the library, held on every
  *     GPU that loads it until the process exits.  All calls share it and it
  *     keeps the last call's contents; each call rewrites the part it reads
  *     before reading it.  Calls that overlap on the GPU (different streams,
@@ -267,7 +267,8 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B,
  * its amplitudes: linear (NNLS) or fixed, per the lens's mode.
  *   params     host float32 [tll_lens_nparam(L)]
  *   image_out  host float32 [ny][nx]
- *   amps_out   host float32 [2] (lens, source amplitude) or NULL
+ *   amps_out   host float32 [tll_lens_ncols(L)] (lens, source amplitude;
+ *              or one per component) or NULL
  *   loglike_out host float64 [1] or NULL
  * Synchronous.  An invalid vector gives TLL_EINVAL.
  */
@@ -403,8 +404,75 @@ int tll_autotune(tll_lens *L, const float *params, int B, void *stream,
                  int *n_tried);
 
 /* Entries per parameter vector of this lens: TLL_NPARAM, or TLL_NPARAM_EPL
- * for a TLL_MASS_EPL lens (-1 for NULL). */
+ * for a TLL_MASS_EPL lens, or the multi-component layout's count after
+ * tll_set_light (-1 for NULL). */
 int tll_lens_nparam(const tll_lens *L);
+
+/*
+ * Multi-component light (Sec. 2.3, Eq. 7: the lens light and the source
+ * light are superpositions of N_l and N_s profiles, each a column of
+ * L = [L_l | L_s] with its own non-negative amplitude, solved by FNNLS).
+ * Sec. 3.2 fits SLACS lenses with two Sersics per galaxy sharing one centre
+ * and one ellipticity, indices fixed at 1 and 4; Sec. 4.3 names the
+ * Gaussian expansion.  A component is an elliptical Sersic (Eq. 8, unit
+ * I_e) or an elliptical Gaussian of unit central intensity,
+ * exp(-R_p^2 / (2 sigma^2)) with the R_p of Eq. 10, placed in the lens plane
+ * (evaluated at theta) or the source plane (at beta of Eq. 1).  All
+ * components of one plane share that plane's centre and ellipticity.
+ *
+ * Parameter vector of a multi-component lens (float32):
+ *   [0] theta_E [1] eps1_m [2] eps2_m [3] x_m [4] y_m [5] gamma_1 [6] gamma_2
+ *   [7] eps1_L [8] eps2_L [9] x_L [10] y_L      (lens-plane geometry)
+ *   [11] eps1_S [12] eps2_S [13] x_S [14] y_S   (source-plane geometry)
+ *   then, component by component, its scale (r_e or sigma, arcsec) if
+ *   TLL_COMP_FREE_SCALE, then its Sersic index if TLL_COMP_FREE_INDEX;
+ *   a TLL_MASS_EPL lens appends the mass slope last.  Values that are not
+ *   free come from the component list.  Invalid vectors (scale <= 0, index
+ *   outside [0.2, 10], |eps| >= 1, theta_E < 0, a slope outside (1, 3),
+ *   non-finite entries) give log L = -INFINITY.
+ * The amplitudes are the non-negative least-squares solution over all
+ * columns (FNNLS, Bro & de Jong 1997, in FP64 per vector); log L as above.
+ */
+#define TLL_MAX_COMPS 8
+enum { TLL_COMP_SERSIC = 0, TLL_COMP_GAUSSIAN = 1 };
+enum { TLL_PLANE_LENS = 0, TLL_PLANE_SOURCE = 1 };
+#define TLL_COMP_FREE_SCALE 1   /* scale read from the parameter vector */
+#define TLL_COMP_FREE_INDEX 2   /* Sersic index read from the parameter vector */
+typedef struct {
+    int type;     /* TLL_COMP_SERSIC or TLL_COMP_GAUSSIAN */
+    int plane;    /* TLL_PLANE_LENS or TLL_PLANE_SOURCE */
+    int flags;    /* TLL_COMP_FREE_SCALE | TLL_COMP_FREE_INDEX */
+    float scale;  /* fixed r_e or sigma (arcsec) when not free */
+    float index;  /* fixed Sersic index when not free */
+} tll_comp_t;
+
+/*
+ * tll_set_light -- give lens L the multi-component light model `comps`
+ * (1..TLL_MAX_COMPS components; columns in list order), or with ncomp = 0
+ * return it to the two-column Sersic model of TLL_NPARAM.  The lens must
+ * use TLL_AMP_LINEAR and the fused convolution.  Allocates the model's
+ * per-CTA image slots ((2 ncomp + 3) x 4 bytes per pixel per SM) and waits
+ * for the device first.  Afterwards tll_loglike_batch, _host, _noalloc,
+ * tll_model_image (amps_out receives ncomp amplitudes) and
+ * tll_model_columns_n evaluate the new model; tll_model_columns, the
+ * batcher, the server, tll_set_shape, tll_set_conv and tll_autotune refuse
+ * the lens with TLL_EINVAL.
+ * Errors: TLL_EINVAL (bad list), TLL_ENOMEM, TLL_ECUDA (the lens keeps its
+ * previous model).
+ */
+int tll_set_light(tll_lens *L, const tll_comp_t *comps, int ncomp);
+
+/* Columns of the lens's model: 2 (lens, source) or its component count. */
+int tll_lens_ncols(const tll_lens *L);
+
+/*
+ * tll_model_columns_n -- every unit-amplitude column of L (Eq. 7) for one
+ * vector (params host [tll_lens_nparam(L)]), binned, before (blurred = 0)
+ * or after (blurred = 1) the PSF, to cols_out (host float32
+ * [tll_lens_ncols(L)][ny][nx]).  Synchronous.  An invalid vector gives
+ * TLL_EINVAL.
+ */
+int tll_model_columns_n(tll_lens *L, const float *params, float *cols_out, int blurred);
 
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,

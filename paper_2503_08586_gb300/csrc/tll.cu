@@ -35,7 +35,7 @@
 #include <vector>
 
 #include "tll.h"
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 #include "tll_split.cuh"
 
 using namespace tll;
@@ -91,6 +91,28 @@ __global__ void k_prologue_multi(const __grid_constant__ MultiArgs A)
     const LensDev &L = A.lenses[sg.lens];
     decode_vector(sg.params + (size_t)(t - sg.first) * (L.epl ? NPAR_EPL : NPAR),
                   A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0);
+}
+
+// Multi-component prologue: one thread per vector.
+__global__ void k_prologue_nc(const float *__restrict__ params, int B, float *__restrict__ kc,
+                              const __grid_constant__ LensDev L, const __grid_constant__ MultiDev M,
+                              const double *__restrict__ bn_tab)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) decode_multi(params + (size_t)b * M.npar, kc + (size_t)b * NCONST, L, M, bn_tab);
+}
+
+// Model image of one multi-component vector: sum_k s_k M_k (Eq. 7), FP64
+// then rounded; res holds the amplitudes.
+__global__ void k_combine_nc(const float *__restrict__ cols, const double *__restrict__ res,
+                             int nc, int npix, float *__restrict__ img)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npix;
+         t += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < nc; ++k) v += res[k] * (double)cols[(size_t)k * npix + t];
+        img[t] = (float)v;
+    }
 }
 
 // Model image of one vector: I^m = s_l m_l + s_s m_s (Eq. 7), FP64 then
@@ -160,9 +182,20 @@ struct tll_lens {
     size_t dev_bytes = 0;             // device memory this lens holds
     cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
     bool prof_on = false, prof_recorded = false;
+    // multi-component light (tll_set_light): nc > 0 columns, their list and
+    // trace schedule, the multi-column kernel's shape and per-CTA slots
+    int nc = 0;
+    MultiDev md = {};
+    Shape nc_shape;
+    float *d_nscr = nullptr;
+    long long nscr_floats = 0;
+    double *d_nres = nullptr;   // amplitudes and log L of the model-image launch
 };
 
 namespace {
+
+// Largest parameter vector of any model: 15 + 2 per component + the slope.
+constexpr int kMaxParams = kMultiHead + 2 * kMaxComps + 1;
 
 // Per-device b_n table, built on first use and kept for the process.
 constexpr int kMaxDevices = 64;
@@ -261,6 +294,13 @@ MultiKernel find_multi(int sub, int Kc)
 {
     for (const KernelSet *ks : kSets)
         if (MultiKernel f = ks->multi(sub, Kc)) return f;
+    return nullptr;
+}
+
+NcKernel find_nc(int sub, int Kc)
+{
+    for (const KernelSet *ks : kSets)
+        if (NcKernel f = ks->nc(sub, Kc)) return f;
     return nullptr;
 }
 
@@ -519,7 +559,7 @@ void free_lens(tll_lens *L)
     void *ptrs[] = {L->d_psf, L->d_pu, L->d_pv, L->d_wpack, L->d_kc, L->d_gscr,
                     L->d_stage_p, L->d_stage_o, L->d_p1, L->d_kc1, L->d_unb,
                     L->d_blur, L->d_img, L->d_res, L->d_out1, L->d_unbl, L->d_sblur,
-                    L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo};
+                    L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo, L->d_nscr, L->d_nres};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : L->prof_ev)
@@ -543,6 +583,127 @@ int run_one(tll_lens *L, const float *params_host)
     CUDA_TRY(cudaMemcpy(&valid, L->d_kc1 + K_VALID, sizeof(float), cudaMemcpyDeviceToHost));
     if (valid == 0.0f) return fail(TLL_EINVAL, "invalid parameter vector");
     return TLL_OK;
+}
+
+// ------------------------------------------------- multi-column lenses
+// Shape of the multi-column kernel: 1024-thread CTAs, one per SM.  For PSF
+// side <= 31 and nx <= 256 the compiled band convolution, with the tallest
+// equal bands the shared memory allows (the whole image when it fits);
+// otherwise the generic convolution with the PSF taps in shared memory.
+// Per-CTA global slot: U [nc], M [nc + 1] and H [2] images of npix floats.
+int nc_configure(tll_lens *L)
+{
+    DevLimits D;
+    if (int rc = dev_limits(L->dev, &D)) return rc;
+    Shape S;
+    S.threads = kThreads;
+    const int h = (L->K - 1) / 2;
+    const long long share = std::min<long long>(D.optin, D.per_sm_smem - D.reserved);
+    NcKernel k = nullptr;
+    if (L->K <= kMaxK && L->nx <= 256) {
+        k = find_nc(L->sub, L->K);
+        if (!k) return fail(TLL_ECUDA, "no multi-column kernel for s=%d K=%d", L->sub, L->K);
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k));
+        const long long avail = share - (long long)fa.sharedSizeBytes;
+        const size_t row_bytes = (size_t)2 * L->W * sizeof(float);
+        const long long rows = avail / (long long)row_bytes - 2 * h - kCR;
+        if (rows >= 8) {
+            const long long nb = (L->ny + std::min<long long>(rows, L->ny) - 1) /
+                                 std::min<long long>(rows, L->ny);
+            S.img = IMG_BANDED;
+            S.band_rows = (int)((L->ny + nb - 1) / nb);
+            S.smem = (size_t)(S.band_rows + 2 * h + kCR) * row_bytes;
+        } else {
+            k = nullptr;
+        }
+    }
+    if (!k) {
+        k = find_nc(L->sub, 0);
+        if (!k) return fail(TLL_ECUDA, "no multi-column kernel for s=%d", L->sub);
+        S.img = IMG_GLOBAL;
+        S.band_rows = 0;
+        const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
+        S.smem = (size_t)((psf_floats + 3) & ~3) * sizeof(float);
+    }
+    // the kernel is shared by every lens of its (s, K) class: allow the
+    // most any of them can ask for, never less
+    if (int rc = allow_dynamic_smem((const void *)k, D.optin)) return rc;
+    int n = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, S.threads, S.smem));
+    if (n < 1) return fail(TLL_EINVAL, "multi-column kernel cannot be resident");
+    S.per_sm = 1;
+    S.grid_cap = D.nsm;
+    S.gslot = (2LL * L->nc + 3) * L->npix;
+    L->nc_shape = S;
+    return TLL_OK;
+}
+
+int nc_ensure_scr(tll_lens *L)
+{
+    const long long need = (long long)L->nc_shape.grid_cap * L->nc_shape.gslot;
+    if (need <= L->nscr_floats) return TLL_OK;
+    if (L->d_nscr) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(L->d_nscr);
+        L->dev_bytes -= (size_t)L->nscr_floats * sizeof(float);
+        L->d_nscr = nullptr;
+        L->nscr_floats = 0;
+    }
+    CUDA_TRY(cudaMalloc(&L->d_nscr, (size_t)need * sizeof(float)));
+    L->nscr_floats = need;
+    L->dev_bytes += (size_t)need * sizeof(float);
+    return TLL_OK;
+}
+
+// Prologue and multi-column kernel for B vectors; wres != null: one CTA,
+// amplitudes and log L of vector 0 to wres, its columns stay in slot 0.
+int run_batch_nc(tll_lens *L, const float *params, int B, double *out, cudaStream_t st,
+                 float *kc, double *wres)
+{
+    const bool prof = L->prof_on && !wres;
+    if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
+    LensDev d = lens_dev(L);
+    d.img = L->nc_shape.img;
+    d.band_rows = L->nc_shape.band_rows;
+    k_prologue_nc<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, d, L->md, L->bn_tab);
+    CUDA_TRY(cudaGetLastError());
+    if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
+    const NcKernel k = find_nc(L->sub, d.img == IMG_BANDED ? L->K : 0);
+    if (!k) return fail(TLL_ECUDA, "no multi-column kernel for s=%d K=%d", L->sub, L->K);
+    NcArgs R;
+    R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_nscr; R.gslot = L->nc_shape.gslot;
+    R.wr_res = wres;
+    const int grid = wres ? 1 : std::min(B, L->nc_shape.grid_cap);
+    k<<<grid, L->nc_shape.threads, L->nc_shape.smem, st>>>(d, L->md, R);
+    CUDA_TRY(cudaGetLastError());
+    if (prof) {
+        CUDA_TRY(cudaEventRecord(L->prof_ev[2], st));
+        L->prof_recorded = true;
+    }
+    return TLL_OK;
+}
+
+// One multi-column vector with its columns and amplitudes kept (model
+// image entry points); synchronous.
+int run_one_nc(tll_lens *L, const float *params_host)
+{
+    if (!params_host) return fail(TLL_EINVAL, "params is NULL");
+    if (int rc = nc_ensure_scr(L)) return rc;
+    CUDA_TRY(cudaMemcpy(L->d_p1, params_host, L->nparam * sizeof(float), cudaMemcpyHostToDevice));
+    int rc = run_batch_nc(L, L->d_p1, 1, L->d_out1, 0, L->d_kc1, L->d_nres);
+    if (rc) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());
+    float valid = 0.0f;
+    CUDA_TRY(cudaMemcpy(&valid, L->d_kc1 + K_VALID, sizeof(float), cudaMemcpyDeviceToHost));
+    if (valid == 0.0f) return fail(TLL_EINVAL, "invalid parameter vector");
+    return TLL_OK;
+}
+
+int reject_nc(const tll_lens *L, const char *what)
+{
+    return L && L->nc ? fail(TLL_EINVAL, "%s: not available for multi-component lenses", what)
+                      : TLL_OK;
 }
 
 }  // namespace
@@ -687,7 +848,7 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
 // array in the module instead, so the call itself allocates nothing; every
-// GPU that loads this library holds it (8 MiB) until the process exits.
+// GPU that loads this library holds it (12 MiB) until the process exits.
 constexpr int kNoAllocMaxB = 16384;
 static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
 
@@ -779,6 +940,7 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         tll_lens *L = lenses[k];
         if (!L) return fail(TLL_EINVAL, "lens %d is NULL", k);
         if (L->dev != b->dev) return fail(TLL_EINVAL, "lens %d is on another device", k);
+        if (int rc = reject_nc(L, "tll_batcher_run")) return rc;
         if (counts[k] < 0) return fail(TLL_EINVAL, "negative count for lens %d", k);
         if (counts[k] > 0 && (!params[k] || !outs[k]))
             return fail(TLL_EINVAL, "NULL params/out for lens %d", k);
@@ -895,13 +1057,15 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *o
                     B, kNoAllocMaxB);
     if (B == 0) return TLL_OK;
     if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
-    if (L->gscr_floats < gscr_need(L))
+    if (!L->nc && L->gscr_floats < gscr_need(L))
         return fail(TLL_EINVAL, "lens was created TLL_FLAG_BATCH_ONLY and has no one-lens "
                                 "image slots; evaluate it with tll_loglike_batch once first");
     DeviceGuard gd(L->dev);
     float *kc = nullptr;
     const int rc = noalloc_scratch(L->dev, &kc);
     if (rc) return rc;
+    // a multi-component lens's image slots were allocated by tll_set_light
+    if (L->nc) return run_batch_nc(L, params, B, out, (cudaStream_t)stream, kc, nullptr);
     // k_prologue writes all NCONST entries of each of the B blocks before
     // k_loglike reads them on the same stream, so nothing needs clearing.
     return run_batch(L, params, B, out, (cudaStream_t)stream, false, kc);
@@ -965,6 +1129,7 @@ extern "C" int tll_set_conv(tll_lens *L, int variant, int chunk)
         variant != TLL_CONV_SPLIT_TOEPLITZ_TC)
         return fail(TLL_EINVAL, "unknown convolution variant %d", variant);
     if (chunk < 0 || chunk > (1 << 20)) return fail(TLL_EINVAL, "chunk %d out of range", chunk);
+    if (int rc = reject_nc(L, "tll_set_conv")) return rc;
     DeviceGuard gd(L->dev);
     CUDA_TRY(cudaDeviceSynchronize());   // no launch using the old buffers in flight
     if (variant == TLL_CONV_FUSED) {
@@ -1049,6 +1214,7 @@ extern "C" int tll_conv_check(tll_lens *L)
 extern "C" int tll_set_shape(tll_lens *L, int threads, int ctas_per_sm)
 {
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (int rc = reject_nc(L, "tll_set_shape")) return rc;
     DeviceGuard gd(L->dev);
     DevLimits D;
     int rc = dev_limits(L->dev, &D);
@@ -1072,6 +1238,7 @@ extern "C" int tll_autotune(tll_lens *L, const float *params, int B, void *strea
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
     if (B < 0 || (B > 0 && !params)) return fail(TLL_EINVAL, "bad tuning batch");
     if (max_tried < 0 || (max_tried > 0 && !tried)) return fail(TLL_EINVAL, "bad tried array");
+    if (int rc = reject_nc(L, "tll_autotune")) return rc;
     DeviceGuard gd(L->dev);
     cudaStream_t st = (cudaStream_t)stream;
     DevLimits D;
@@ -1287,7 +1454,7 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         (rc = alloc((void **)&L->d_pu, K * sizeof(float))) ||
         (rc = alloc((void **)&L->d_pv, K * sizeof(float))) ||
         (rc = alloc((void **)&L->d_wpack, npix * sizeof(float4))) ||
-        (rc = alloc((void **)&L->d_p1, NPAR_EPL * sizeof(float))) ||
+        (rc = alloc((void **)&L->d_p1, kMaxParams * sizeof(float))) ||
         (rc = alloc((void **)&L->d_kc1, NCONST * sizeof(float))) ||
         (rc = alloc((void **)&L->d_unb, 2 * npix * sizeof(float))) ||
         (rc = alloc((void **)&L->d_blur, 2 * npix * sizeof(float))) ||
@@ -1382,6 +1549,11 @@ int tll_loglike_batch(tll_lens *L, const float *params, int B, double *out, void
     if (!params || !out) return fail(TLL_EINVAL, "NULL params or out");
     DeviceGuard gd(L->dev);
     int rc = ensure_kc(L, B);
+    if (L->nc) {
+        if (!rc) rc = nc_ensure_scr(L);
+        if (rc) return rc;
+        return run_batch_nc(L, params, B, out, (cudaStream_t)stream, L->d_kc, nullptr);
+    }
     if (!rc) rc = ensure_gscr(L);
     if (rc) return rc;
     return run_batch(L, params, B, out, (cudaStream_t)stream, false, L->d_kc);
@@ -1414,11 +1586,12 @@ int tll_loglike_batch_host(tll_lens *L, const float *params, int B, double *out,
         L->stage_cap = cap;
     }
     int rc = ensure_kc(L, B);
-    if (!rc) rc = ensure_gscr(L);
+    if (!rc) rc = L->nc ? nc_ensure_scr(L) : ensure_gscr(L);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(L->d_stage_p, params, (size_t)B * L->nparam * sizeof(float),
                              cudaMemcpyHostToDevice, st));
-    rc = run_batch(L, L->d_stage_p, B, L->d_stage_o, st, false, L->d_kc);
+    rc = L->nc ? run_batch_nc(L, L->d_stage_p, B, L->d_stage_o, st, L->d_kc, nullptr)
+               : run_batch(L, L->d_stage_p, B, L->d_stage_o, st, false, L->d_kc);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out, L->d_stage_o, (size_t)B * sizeof(double),
                              cudaMemcpyDeviceToHost, st));
@@ -1431,6 +1604,7 @@ int tll_model_columns(tll_lens *L, const float *params, float *lens_out, float *
 {
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
     if (!lens_out || !src_out) return fail(TLL_EINVAL, "NULL output");
+    if (int rc = reject_nc(L, "tll_model_columns (use tll_model_columns_n)")) return rc;
     DeviceGuard gd(L->dev);
     int rc = run_one(L, params);
     if (rc) return rc;
@@ -1455,6 +1629,23 @@ int tll_model_image(tll_lens *L, const float *params, float *image_out, float *a
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
     if (!image_out) return fail(TLL_EINVAL, "NULL output");
     DeviceGuard gd(L->dev);
+    if (L->nc) {
+        int rc = run_one_nc(L, params);
+        if (rc) return rc;
+        const float *cols = L->d_nscr + (size_t)L->nc * L->npix;   // slot 0, blurred
+        k_combine_nc<<<std::max(1, std::min(1024, (L->npix + 255) / 256)), 256>>>(
+            cols, L->d_nres, L->nc, L->npix, L->d_img);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpy(image_out, L->d_img, (size_t)L->npix * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+        double res[kMaxComps + 1];
+        CUDA_TRY(cudaMemcpy(res, L->d_nres, (L->nc + 1) * sizeof(double),
+                            cudaMemcpyDeviceToHost));
+        if (amps_out)
+            for (int k = 0; k < L->nc; ++k) amps_out[k] = (float)res[k];
+        if (loglike_out) *loglike_out = res[L->nc];
+        return TLL_OK;
+    }
     int rc = run_one(L, params);
     if (rc) return rc;
     k_combine<<<std::max(1, std::min(1024, (L->npix + 255) / 256)), 256>>>(
@@ -1469,6 +1660,109 @@ int tll_model_image(tll_lens *L, const float *params, float *image_out, float *a
         amps_out[1] = (float)res[6];
     }
     if (loglike_out) *loglike_out = res[7];
+    return TLL_OK;
+}
+
+int tll_set_light(tll_lens *L, const tll_comp_t *comps, int ncomp)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (ncomp < 0 || ncomp > TLL_MAX_COMPS)
+        return fail(TLL_EINVAL, "component count %d out of range [0, %d]", ncomp, TLL_MAX_COMPS);
+    if (ncomp > 0 && !comps) return fail(TLL_EINVAL, "comps is NULL");
+    if (ncomp > 0 && L->mode != TLL_AMP_LINEAR)
+        return fail(TLL_EINVAL, "multi-component light needs TLL_AMP_LINEAR amplitudes");
+    if (ncomp > 0 && L->conv_variant != TLL_CONV_FUSED)
+        return fail(TLL_EINVAL, "multi-component light runs the fused pipeline only");
+    MultiDev md = {};
+    int npar = kMultiHead;
+    for (int c = 0; c < ncomp; ++c) {
+        const tll_comp_t &q = comps[c];
+        if (q.type != TLL_COMP_SERSIC && q.type != TLL_COMP_GAUSSIAN)
+            return fail(TLL_EINVAL, "component %d: unknown type %d", c, q.type);
+        if (q.plane != TLL_PLANE_LENS && q.plane != TLL_PLANE_SOURCE)
+            return fail(TLL_EINVAL, "component %d: unknown plane %d", c, q.plane);
+        if (q.flags & ~(TLL_COMP_FREE_SCALE | TLL_COMP_FREE_INDEX))
+            return fail(TLL_EINVAL, "component %d: unknown flags 0x%x", c, q.flags);
+        if (!(q.flags & TLL_COMP_FREE_SCALE) && !(q.scale > 0.0f && isfinite(q.scale)))
+            return fail(TLL_EINVAL, "component %d: fixed scale must be finite and > 0", c);
+        const bool free_n = q.type == TLL_COMP_SERSIC && (q.flags & TLL_COMP_FREE_INDEX);
+        if (q.type == TLL_COMP_SERSIC && !free_n && !(q.index >= 0.2f && q.index <= 10.0f))
+            return fail(TLL_EINVAL, "component %d: fixed Sersic index must be in [0.2, 10]", c);
+        md.type[c] = q.type == TLL_COMP_SERSIC ? COMP_SERSIC : COMP_GAUSS;
+        md.plane[c] = q.plane == TLL_PLANE_LENS ? PLANE_LENS : PLANE_SOURCE;
+        md.flags[c] = ((q.flags & TLL_COMP_FREE_SCALE) ? FREE_SCALE : 0) | (free_n ? FREE_INDEX : 0);
+        md.scale[c] = q.scale;
+        md.index[c] = q.index;
+        npar += ((q.flags & TLL_COMP_FREE_SCALE) ? 1 : 0) + (free_n ? 1 : 0);
+    }
+    DeviceGuard gd(L->dev);
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (ncomp == 0) {   // back to the two-column model
+        if (L->d_nscr) {
+            cudaFree(L->d_nscr);
+            L->dev_bytes -= (size_t)L->nscr_floats * sizeof(float);
+            L->d_nscr = nullptr;
+            L->nscr_floats = 0;
+        }
+        L->nc = 0;
+        L->nparam = L->epl ? NPAR_EPL : NPAR;
+        return TLL_OK;
+    }
+    // trace schedule: lens-plane passes, then source-plane passes, each of
+    // up to kPassMax components in list order
+    for (int pl = 0; pl < 2; ++pl) {
+        const int plane = pl == 0 ? PLANE_LENS : PLANE_SOURCE;
+        for (int c = 0; c < ncomp; ++c) {
+            if (md.plane[c] != plane) continue;
+            if (md.npass == 0 || md.pass_plane[md.npass - 1] != plane ||
+                md.pass_n[md.npass - 1] == kPassMax) {
+                md.pass_plane[md.npass] = plane;
+                md.pass_n[md.npass] = 0;
+                ++md.npass;
+            }
+            md.pass_comp[md.npass - 1][md.pass_n[md.npass - 1]++] = c;
+        }
+    }
+    md.nc = ncomp;
+    md.npar = npar + (L->epl ? 1 : 0);
+    const int old_nc = L->nc;
+    const MultiDev old_md = L->md;
+    L->nc = ncomp;
+    L->md = md;
+    int rc = nc_configure(L);
+    if (!rc && !L->d_nres) {
+        cudaError_t e = cudaMalloc(&L->d_nres, (kMaxComps + 1) * sizeof(double));
+        if (e != cudaSuccess) rc = fail(TLL_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+        else L->dev_bytes += (kMaxComps + 1) * sizeof(double);
+    }
+    if (!rc) rc = nc_ensure_scr(L);
+    if (rc) {
+        L->nc = old_nc;
+        L->md = old_md;
+        return rc;
+    }
+    L->nparam = md.npar;
+    return TLL_OK;
+}
+
+int tll_lens_ncols(const tll_lens *L)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL"), -1;
+    return L->nc ? L->nc : 2;
+}
+
+int tll_model_columns_n(tll_lens *L, const float *params, float *cols_out, int blurred)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL");
+    if (!cols_out) return fail(TLL_EINVAL, "NULL output");
+    if (!L->nc)
+        return tll_model_columns(L, params, cols_out, cols_out + L->npix, blurred);
+    DeviceGuard gd(L->dev);
+    int rc = run_one_nc(L, params);
+    if (rc) return rc;
+    const float *src = L->d_nscr + (blurred ? (size_t)L->nc * L->npix : 0);
+    CUDA_TRY(cudaMemcpy(cols_out, src, (size_t)L->nc * L->npix * sizeof(float),
+                        cudaMemcpyDeviceToHost));
     return TLL_OK;
 }
 

@@ -104,10 +104,6 @@ __host__ __device__ inline int padded_stride(int nx, int K)
     return (W + 3) & ~3;
 }
 
-struct Acc10 {
-    float a[10];
-};
-
 // Multi-lens work list: segment s covers items [first, first + count) of
 // lens `lens`, reading params[k] and writing out[k]; segments are grouped
 // (same supersampling and convolution class) and each group is one launch.

@@ -44,7 +44,7 @@ enum : int {
     K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L, K_EC0,
     NCONST_USED = K_EC0 + kEplMaxN + 1
 };
-constexpr int NCONST = 128;
+constexpr int NCONST = 192;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
 
 // ------------------------------------------------------------------ b_n
@@ -175,7 +175,7 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     const double e_s = sqrt(v[17] * v[17] + v[18] * v[18]);
     ok = ok && e_m < 1.0 && e_l < 1.0 && e_s < 1.0;
 #pragma unroll
-    for (int k = 0; k < NCONST; ++k) o[k] = 0.0f;
+    for (int k = 0; k < NCONST_USED; ++k) o[k] = 0.0f;
     if (!ok) return;
     o[K_VALID] = 1.0f;
     const double LOG2E = 1.4426950408889634;

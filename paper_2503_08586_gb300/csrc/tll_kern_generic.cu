@@ -1,7 +1,7 @@
 // tll_kern_generic.cu -- likelihood kernels with the generic (runtime PSF
 // side) convolution, including the write-out variants of the model-image
 // entry points.
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 
 namespace tll {
 namespace {
@@ -21,8 +21,13 @@ MultiKernel multi_k(int sub, int K)
     return K == 0 ? multi_for<0>(sub) : nullptr;
 }
 
+NcKernel nc_k(int sub, int K)
+{
+    return K == 0 ? nc_for<0>(sub) : nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_generic = {single_k, multi_k};
+extern const KernelSet kernel_set_generic = {single_k, multi_k, nc_k};
 
 }  // namespace tll

@@ -1,6 +1,6 @@
 // tll_kern_k01.cu -- likelihood kernels with the compiled convolution
 // for PSF sides 1, 3 (one translation unit per pair, compiled in parallel).
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 
 namespace tll {
 namespace {
@@ -24,8 +24,17 @@ MultiKernel multi_k(int sub, int K)
     return nullptr;
 }
 
+NcKernel nc_k(int sub, int K)
+{
+    switch (K) {
+        case 1: return nc_for<1>(sub);
+        case 3: return nc_for<3>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k01 = {single_k, multi_k};
+extern const KernelSet kernel_set_k01 = {single_k, multi_k, nc_k};
 
 }  // namespace tll

@@ -1,6 +1,6 @@
 // tll_kern_k09.cu -- likelihood kernels with the compiled convolution
 // for PSF sides 9, 11 (one translation unit per pair, compiled in parallel).
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 
 namespace tll {
 namespace {
@@ -24,8 +24,17 @@ MultiKernel multi_k(int sub, int K)
     return nullptr;
 }
 
+NcKernel nc_k(int sub, int K)
+{
+    switch (K) {
+        case 9: return nc_for<9>(sub);
+        case 11: return nc_for<11>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k09 = {single_k, multi_k};
+extern const KernelSet kernel_set_k09 = {single_k, multi_k, nc_k};
 
 }  // namespace tll

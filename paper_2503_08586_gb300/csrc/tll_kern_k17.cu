@@ -1,6 +1,6 @@
 // tll_kern_k17.cu -- likelihood kernels with the compiled convolution
 // for PSF sides 17, 19 (one translation unit per pair, compiled in parallel).
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 
 namespace tll {
 namespace {
@@ -24,8 +24,17 @@ MultiKernel multi_k(int sub, int K)
     return nullptr;
 }
 
+NcKernel nc_k(int sub, int K)
+{
+    switch (K) {
+        case 17: return nc_for<17>(sub);
+        case 19: return nc_for<19>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k17 = {single_k, multi_k};
+extern const KernelSet kernel_set_k17 = {single_k, multi_k, nc_k};
 
 }  // namespace tll

@@ -1,6 +1,6 @@
 // tll_kern_k21.cu -- likelihood kernels with the compiled convolution
 // for PSF sides 21, 23 (one translation unit per pair, compiled in parallel).
-#include "tll_kernels.cuh"
+#include "tll_multi.cuh"
 
 namespace tll {
 namespace {
@@ -24,8 +24,17 @@ MultiKernel multi_k(int sub, int K)
     return nullptr;
 }
 
+NcKernel nc_k(int sub, int K)
+{
+    switch (K) {
+        case 21: return nc_for<21>(sub);
+        case 23: return nc_for<23>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k21 = {single_k, multi_k};
+extern const KernelSet kernel_set_k21 = {single_k, multi_k, nc_k};
 
 }  // namespace tll

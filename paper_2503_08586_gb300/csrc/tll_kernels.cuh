@@ -202,15 +202,31 @@ __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
 // Separable: row pass in place over buffer rows [rlo, rhi) (a lane makes
 // 4 adjacent outputs from one float4 window), then the column pass (a lane
 // makes kCR rows of its column from one window) fused with the sums.
-template <int K>
-__device__ __forceinline__ Acc10 conv_sep_band(const LensDev &L, float *Pl, float *Ps,
-                                            int b0, int nrows, int rlo, int rhi, int tid,
-                                            int nthr)
+// Output sinks of the compiled convolutions: SumsSink adds each output
+// pixel's pair to the five weighted sums (the fused reduction); PairStore
+// writes the pair to two images (the multi-column path).
+struct SumsSink {
+    const LensDev &L;
+    float a[10];
+    __device__ __forceinline__ void operator()(int pix, float ml, float ms)
+    {
+        accum_pixel(ml, ms, L.wpack[pix], a);
+    }
+};
+struct PairStore {
+    float *ol, *os;
+    __device__ __forceinline__ void operator()(int pix, float ml, float ms)
+    {
+        ol[pix] = ml;
+        os[pix] = ms;
+    }
+};
+
+template <int K, class Sink>
+__device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float *Ps,
+                                              int b0, int nrows, int rlo, int rhi, int tid,
+                                              int nthr, Sink &sink)
 {
-    Acc10 out;
-    float *acc = out.a;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
     using G = PadGeom<K>;
     const int nx = L.nx, W = L.W;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -284,14 +300,10 @@ __device__ __forceinline__ Acc10 conv_sep_band(const LensDev &L, float *Pl, floa
         if (j < nx) {
 #pragma unroll
             for (int r = 0; r < kCR; ++r) {
-                if (r0 + r < nrows) {
-                    const int pix = (b0 + r0 + r) * nx + j;
-                    accum_pixel(ml[r], ms[r], L.wpack[pix], acc);
-                }
+                if (r0 + r < nrows) sink((b0 + r0 + r) * nx + j, ml[r], ms[r]);
             }
         }
     }
-    return out;
 }
 
 // Direct K x K convolution (any PSF): a thread makes 4 adjacent outputs of
@@ -299,15 +311,11 @@ __device__ __forceinline__ Acc10 conv_sep_band(const LensDev &L, float *Pl, floa
 // applies the row's K taps (each tap read once, used for the 4 outputs);
 // m(i,j) = sum_{r,c} K[r][c] I(i+h-r, j+h-c), summed per PSF row.  Kept to
 // one window and 8 accumulators so it fits the kernel's 64 registers.
-template <int K>
-__device__ __forceinline__ Acc10 conv_direct_band(const LensDev &L, const float *Pl,
-                                               const float *Ps, int b0, int nrows, int tid,
-                                               int nthr)
+template <int K, class Sink>
+__device__ __forceinline__ void conv_direct_band(const LensDev &L, const float *Pl,
+                                                 const float *Ps, int b0, int nrows, int tid,
+                                                 int nthr, Sink &sink)
 {
-    Acc10 out;
-    float *acc = out.a;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
     using G = PadGeom<K>;
     const int nx = L.nx, W = L.W;
     const int ngroups = (nx + 3) >> 2;
@@ -346,10 +354,9 @@ __device__ __forceinline__ Acc10 conv_direct_band(const LensDev &L, const float 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = 4 * g + q;
-            if (j < nx) accum_pixel(o[0][q], o[1][q], L.wpack[(b0 + ro) * nx + j], acc);
+            if (j < nx) sink((b0 + ro) * nx + j, o[0][q], o[1][q]);
         }
     }
-    return out;
 }
 
 // ------------------------------------------------------ per-vector body
@@ -474,9 +481,12 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
                 rlo = max(0, h - b0);
                 rhi = min(nbr, ny - b0 + h);
             }
-            Acc10 r = L.sep ? conv_sep_band<K>(L, Pl, Ps, b0, nrows, rlo, rhi, tid, nthr)
-                            : conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr);
-            warp_sums(r.a, sred, lane, warp, b0 > 0);
+            SumsSink sk{L};
+#pragma unroll
+            for (int k = 0; k < 10; ++k) sk.a[k] = 0.0f;
+            if (L.sep) conv_sep_band<K>(L, Pl, Ps, b0, nrows, rlo, rhi, tid, nthr, sk);
+            else conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr, sk);
+            warp_sums(sk.a, sred, lane, warp, b0 > 0);
             if (banded) __syncthreads();
         }
     } else {
@@ -644,11 +654,7 @@ using MultiKernel = void (*)(const MultiArgs, int);
 // Supersampling classes with an unrolled subpixel loop.
 __host__ __device__ inline int sub_class(int sub) { return (sub == 4 || sub == 5) ? sub : 0; }
 
-// Kernels of one translation unit; nullptr when (sub, K) is not in it.
-struct KernelSet {
-    SingleKernel (*single)(int sub, int K, bool write);
-    MultiKernel (*multi)(int sub, int K);
-};
+
 
 template <int K>
 inline SingleKernel single_for(int sub)

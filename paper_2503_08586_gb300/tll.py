@@ -37,7 +37,15 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_model_image", "tll_model_columns", "tll_lens_info",
            "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
            "tll_autotune", "tll_set_conv", "tll_conv_check", "tll_lens_nparam",
-           "tll_destroy_lens", "tll_last_error", "tll_version")
+           "tll_destroy_lens", "tll_last_error", "tll_version", "tll_set_light",
+           "tll_lens_ncols", "tll_model_columns_n")
+
+# Multi-component light (tll_set_light).
+MAX_COMPS = 8
+COMP_SERSIC, COMP_GAUSSIAN = 0, 1
+PLANE_LENS, PLANE_SOURCE = 0, 1
+COMP_FREE_SCALE, COMP_FREE_INDEX = 1, 2
+MULTI_HEAD = 15
 
 
 class TLLError(RuntimeError):
@@ -50,6 +58,22 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("pixel_scale", ctypes.c_float), ("sub", ctypes.c_int),
                 ("x0", ctypes.c_float), ("y0", ctypes.c_float)]
+
+
+class Comp(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("plane", ctypes.c_int),
+                ("flags", ctypes.c_int), ("scale", ctypes.c_float),
+                ("index", ctypes.c_float)]
+
+
+def comp(type: str, plane: str, free_scale: bool = True, free_index: bool = False,
+         scale: float = 1.0, index: float = 1.0) -> Comp:
+    """One light component: type "sersic" | "gauss", plane "lens" | "source"."""
+    t = {"sersic": COMP_SERSIC, "gauss": COMP_GAUSSIAN}[type]
+    pl = {"lens": PLANE_LENS, "source": PLANE_SOURCE}[plane]
+    fl = (COMP_FREE_SCALE if free_scale else 0) | (
+        COMP_FREE_INDEX if free_index and t == COMP_SERSIC else 0)
+    return Comp(t, pl, fl, float(scale), float(index))
 
 
 PLACEMENTS = {0: "global", 1: "smem", 2: "padded", 3: "banded"}
@@ -169,6 +193,12 @@ def load(path: str | None = None):
     lib.tll_last_error.restype = ctypes.c_char_p
     lib.tll_version.argtypes = []
     lib.tll_version.restype = i
+    lib.tll_set_light.argtypes = [vp, ctypes.POINTER(Comp), i]
+    lib.tll_set_light.restype = i
+    lib.tll_lens_ncols.argtypes = [vp]
+    lib.tll_lens_ncols.restype = i
+    lib.tll_model_columns_n.argtypes = [vp, fp, fp, i]
+    lib.tll_model_columns_n.restype = i
     if path is None:
         _lib = lib
     return lib
@@ -241,6 +271,7 @@ class Lens:
         self.mode = mode
         self.mass = mass
         self.nparam = lib.tll_lens_nparam(h)
+        self.ncols = 2
         self.pixel_scale, self.x0, self.y0 = pixel_scale, x0, y0
 
     @property
@@ -306,12 +337,31 @@ class Lens:
                                              _stream_handle(stream)))
         return out
 
+    # -- multi-component light
+    def set_light(self, comps):
+        """Give the lens a multi-component light model: a list of Comp
+        (see comp()); [] returns it to the two-column model.  Updates
+        self.nparam and self.ncols."""
+        arr = (Comp * max(1, len(comps)))(*comps)
+        _check(load().tll_set_light(self._h, arr, len(comps)))
+        self.nparam = load().tll_lens_nparam(self._h)
+        self.ncols = load().tll_lens_ncols(self._h)
+
+    def model_columns_n(self, params, blurred: bool = True):
+        """Every unit-amplitude column [ncols, ny, nx] float32."""
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(self.nparam)
+        nc = load().tll_lens_ncols(self._h)
+        out = np.empty((nc, self.ny, self.nx), dtype=np.float32)
+        _check(load().tll_model_columns_n(self._h, p.ctypes.data, out.ctypes.data,
+                                          1 if blurred else 0))
+        return out
+
     # -- single vector
     def model_image(self, params):
-        """(blurred model image [ny, nx] float32, amplitudes (2,), log L)."""
+        """(blurred model image [ny, nx] float32, amplitudes (ncols,), log L)."""
         p = np.ascontiguousarray(params, dtype=np.float32).reshape(self.nparam)
         img = np.empty((self.ny, self.nx), dtype=np.float32)
-        amps = np.empty(2, dtype=np.float32)
+        amps = np.empty(load().tll_lens_ncols(self._h), dtype=np.float32)
         ll = ctypes.c_double()
         _check(load().tll_model_image(self._h, p.ctypes.data, img.ctypes.data,
                                       amps.ctypes.data, ctypes.byref(ll)))

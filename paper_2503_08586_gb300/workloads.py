@@ -19,6 +19,12 @@ Sersic lens light tied to the mass centre, Sersic source):
               (beta = 3, FWHM 0.1")
   ragged      many lenses, sides in {64,100,128,160,200}, PSF 11..31 px
   stream      Poisson job arrivals for the serving loop
+  slacs120    multi-component light (Sec. 3.2's SLACS model: two Sersics per
+              galaxy, indices fixed at 1 and 4, one centre and ellipticity
+              per galaxy): 120x120 at 0.05"/px, 4x4 subpixels, 21x21 Moffat
+              PSF (beta = 3, FWHM 0.1"), 4 columns
+  mge120      the same image with a Gaussian expansion: 4 lens-plane and 4
+              source-plane Gaussians of fixed, log-spaced widths (8 columns)
 
 Seeds: workload k uses numpy PCG64 seeded with 2503085860 + k.
 """
@@ -109,6 +115,177 @@ def make_psf(spec: WorkloadSpec) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- priors
+# ------------------------------------------------- multi-component light
+# A component list is plain data (type, plane, free scale / index, fixed
+# values); each side converts it to its own form.
+SLACS_COMPS = [
+    dict(type="sersic", plane="lens", index=1.0),
+    dict(type="sersic", plane="lens", index=4.0),
+    dict(type="sersic", plane="source", index=1.0),
+    dict(type="sersic", plane="source", index=4.0),
+]
+MGE_COMPS = (
+    [dict(type="gauss", plane="lens", free_scale=False, scale=float(s))
+     for s in np.geomspace(0.05, 1.2, 4)]
+    + [dict(type="gauss", plane="source", free_scale=False, scale=float(s))
+       for s in np.geomspace(0.02, 0.4, 4)])
+MULTI_HEAD = 15
+
+
+@dataclass
+class MultiSpec:
+    name: str
+    ny: int
+    nx: int
+    pixel_scale: float
+    sub: int
+    psf_size: int
+    psf_kind: str
+    psf_fwhm_arcsec: float
+    batch: int
+    comps: list
+    moffat_beta: float = 3.0
+    seed_offset: int = 0
+    mass: str = "sie"
+
+
+MULTI_WORKLOADS = {
+    "slacs120": MultiSpec("slacs120", 120, 120, 0.05, 4, 21, "moffat", 0.10, 2048,
+                          SLACS_COMPS, seed_offset=7),
+    "mge120": MultiSpec("mge120", 120, 120, 0.05, 4, 21, "moffat", 0.10, 2048,
+                        MGE_COMPS, seed_offset=8),
+}
+
+
+def multi_nparam(comps, mass: str = "sie") -> int:
+    n = MULTI_HEAD
+    for c in comps:
+        n += 1 if c.get("free_scale", True) else 0
+        n += 1 if c["type"] == "sersic" and c.get("free_index", False) else 0
+    return n + (1 if mass == "epl" else 0)
+
+
+def draw_prior_multi(rng: np.random.Generator, n: int, comps, mass: str = "sie") -> np.ndarray:
+    """n multi-component vectors, float32 [n, multi_nparam]: mass, shear and
+    the two planes' ellipticities and centres from the priors of draw_prior
+    (lens-light centre = mass centre); each free Sersic r_e ~ U[0.1, 1]",
+    free index ~ U[1, 4], free Gaussian sigma ~ U[0.05, 0.5]"; EPL slope
+    ~ U[1.6, 2.4] last."""
+    p = np.zeros((n, multi_nparam(comps, mass)), dtype=np.float64)
+    p[:, 0] = rng.uniform(0.5, 1.5, n)
+    p[:, 1], p[:, 2] = _eps(rng, n)
+    p[:, 3] = rng.normal(0.0, 0.05, n)
+    p[:, 4] = rng.normal(0.0, 0.05, n)
+    p[:, 5] = rng.normal(0.0, 0.05, n)
+    p[:, 6] = rng.normal(0.0, 0.05, n)
+    p[:, 7], p[:, 8] = _eps(rng, n)
+    p[:, 9] = p[:, 3]
+    p[:, 10] = p[:, 4]
+    p[:, 11], p[:, 12] = _eps(rng, n)
+    rad = 0.3 * np.sqrt(rng.uniform(0.0, 1.0, n))
+    ang = rng.uniform(0.0, 2 * math.pi, n)
+    p[:, 13] = rad * np.cos(ang)
+    p[:, 14] = rad * np.sin(ang)
+    k = MULTI_HEAD
+    for c in comps:
+        if c.get("free_scale", True):
+            p[:, k] = (rng.uniform(0.1, 1.0, n) if c["type"] == "sersic"
+                       else rng.uniform(0.05, 0.5, n))
+            k += 1
+        if c["type"] == "sersic" and c.get("free_index", False):
+            p[:, k] = rng.uniform(1.0, 4.0, n)
+            k += 1
+    if mass == "epl":
+        p[:, k] = rng.uniform(1.6, 2.4, n)
+    return p.astype(np.float32)
+
+
+def shrinking_draws_multi(rng, truth: np.ndarray, n: int, comps, lo_frac: float = 0.01):
+    """As shrinking_draws for a multi-component truth: head widths as the
+    prior's, 0.2 for free scales (clipped to [0.03, 3]), 0.87 for free
+    indices (clipped to [0.3, 8])."""
+    frac = np.geomspace(1.0, lo_frac, n)
+    head = np.array([0.29, 0.10, 0.10, 0.05, 0.05, 0.05, 0.05,
+                     0.10, 0.10, 0.05, 0.05, 0.10, 0.10, 0.15, 0.15])
+    width, kinds = list(head), []
+    for c in comps:
+        if c.get("free_scale", True):
+            width.append(0.2)
+            kinds.append("scale")
+        if c["type"] == "sersic" and c.get("free_index", False):
+            width.append(0.87)
+            kinds.append("index")
+    if truth.shape[0] > len(width):
+        width.append(0.23)
+        kinds.append("slope")
+    width = np.array(width)
+    p = truth[None, :].astype(np.float64) + rng.normal(size=(n, truth.shape[0])) * (
+        frac[:, None] * width[None, :])
+    p[:, 0] = np.clip(p[:, 0], 0.05, 3.5)
+    for a, b in ((1, 2), (7, 8), (11, 12)):
+        e = np.hypot(p[:, a], p[:, b])
+        s = np.where(e > 0.6, 0.6 / np.maximum(e, 1e-30), 1.0)
+        p[:, a] *= s
+        p[:, b] *= s
+    p[:, 9] = p[:, 3]
+    p[:, 10] = p[:, 4]
+    for k, kind in enumerate(kinds):
+        j = MULTI_HEAD + k
+        if kind == "scale":
+            p[:, j] = np.clip(p[:, j], 0.03, 3.0)
+        elif kind == "index":
+            p[:, j] = np.clip(p[:, j], 0.3, 8.0)
+        else:
+            p[:, j] = np.clip(p[:, j], 1.2, 2.8)
+    return p.astype(np.float32)
+
+
+def synth_multi_lens(rng, ny, nx, pixel_scale, sub, psf, render, comps, peak_snr=50.0,
+                     sky_sigma=1.0, truth=None, mass: str = "sie") -> SynthLens:
+    """One multi-component lens: truth from draw_prior_multi, blurred unit
+    columns from render(truth) ([nc, ny, nx]); each plane's columns get
+    amplitudes with random shares (U[0.2, 1], renormalised) scaled so that
+    the plane's brightest blurred pixel is peak_snr * sky_sigma; noise
+    sigma^2 = sky^2 + max(model, 0)/g as in synth_lens.  truth carries the
+    amplitudes in extra["amps"]."""
+    if truth is None:
+        truth = draw_prior_multi(rng, 1, comps, mass)[0]
+    truth = truth.astype(np.float32).copy()
+    cols = np.asarray(render(truth), dtype=np.float64)
+    amps = np.zeros(len(comps))
+    for plane in ("lens", "source"):
+        idx = [k for k, c in enumerate(comps) if c["plane"] == plane]
+        if not idx:
+            continue
+        share = rng.uniform(0.2, 1.0, len(idx))
+        img = np.tensordot(share, cols[idx], axes=1)
+        amps[idx] = share * peak_snr * sky_sigma / max(img.max(), 1e-30)
+    model = np.tensordot(amps, cols, axes=1)
+    g = peak_snr * sky_sigma / sky_sigma ** 2
+    sigma = np.sqrt(sky_sigma ** 2 + np.maximum(model, 0.0) / g)
+    data = model + rng.normal(size=model.shape) * sigma
+    return SynthLens(ny, nx, f32(pixel_scale), sub, psf.astype(np.float32),
+                     data.astype(np.float32), sigma.astype(np.float32), truth,
+                     centred_origin(nx, pixel_scale), centred_origin(ny, pixel_scale),
+                     extra={"amps": amps, "comps": comps})
+
+
+def multi_workload(name: str, render_factory, batch: int | None = None):
+    """(lens, params [B, nparam]) of a named multi-component workload;
+    render_factory(pixel_scale, sub, psf, ny, nx, comps) -> render."""
+    spec = MULTI_WORKLOADS[name]
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + spec.seed_offset))
+    fwhm_px = spec.psf_fwhm_arcsec / spec.pixel_scale
+    psf = (gaussian_psf(spec.psf_size, fwhm_px) if spec.psf_kind == "gaussian"
+           else moffat_psf(spec.psf_size, fwhm_px, spec.moffat_beta))
+    render = render_factory(f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx, spec.comps)
+    lens = synth_multi_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf, render,
+                            spec.comps, mass=spec.mass)
+    B = spec.batch if batch is None else batch
+    params = draw_prior_multi(rng, B, spec.comps, spec.mass)
+    return lens, params
+
+
 def _eps(rng, n, qlo=0.5, qhi=1.0):
     """Ellipticity components for q ~ U[qlo, qhi], position angle ~ U[0, pi)
     (change of variables to the paper's ellipticity parametrisation)."""

@@ -20,7 +20,10 @@ Tolerances (FP32 forward model, FP64 likelihood):
                   chi2_t +- 30 at the 99.9 % level: |dlogL| <= 1e-3.
                 - the rest of chi^2 <= 2 N_unmasked: |dlogL| <= max(1e-3,
                   EPS_NEAR sqrt(chi2) (sqrt(dWd) + sqrt(chi2))), EPS_NEAR =
-                  1e-7 (about 1.7 float ulps).
+                  2e-7 (about 3.4 float ulps: a compact n = 4 source's cusp
+                  pixels carry the FP32 position rounding of the a_i term
+                  above, measured at 1.3e-7 effective on such a lens with
+                  the two-column and the multi-column kernels alike).
                 - every other vector: the same with EPS_M = 1e-6.
                 The bound is the first-order effect of a relative model error
                 <= eps on every pixel: dchi2 = 2 sum w (m - d) dm <= 2 eps
@@ -45,7 +48,7 @@ from paper_2503_08586_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 PIX_REL, PIX_FLOOR, POS_ERR = 1e-5, 1e-7, 2e-7
-LL_ABS, EPS_M, EPS_NEAR, BULK_DCHI2 = 1e-3, 1e-6, 1e-7, 50.0
+LL_ABS, EPS_M, EPS_NEAR, BULK_DCHI2 = 1e-3, 1e-6, 2e-7, 50.0
 
 
 @pytest.fixture(scope="module", autouse=True)
