@@ -53,19 +53,40 @@ def flops_per_eval(ny, nx, sub, k, separable) -> float:
     return float(npix * per_pix)
 
 
+def flops_per_eval_multi(ny, nx, sub, k, separable, comps) -> float:
+    """Algorithmic FP32 work of one multi-component evaluation (same
+    counting): per subpixel grid 4, and when a source-plane component
+    exists the SIE 24 + sqrt, atan, atanh, shear 8, lens equation 2; per
+    plane with components its frame and R_p^2 (7); per Sersic component 10
+    + log, pow, exp; per Gaussian 3 + exp; one binning add per component.
+    Per pixel: the mean (1 per column), the PSF (2K separable | K^2 direct
+    taps x 2 per column) and 3 per weighted sum (nc(nc+1)/2 + nc sums)."""
+    nc = len(comps)
+    planes = {c["plane"] for c in comps}
+    per_sub = 4 + (24 + 3 + 8 + 2 if "source" in planes else 0) + 7 * len(planes)
+    for c in comps:
+        per_sub += (10 + 3 if c["type"] == "sersic" else 3 + 1) + 1
+    taps = 2 * k if separable else k * k
+    nsums = nc * (nc + 1) // 2 + nc
+    per_pix = sub * sub * per_sub + nc + nc * taps * 2 + 3 * nsums
+    return float(ny * nx * per_pix)
+
+
 def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
     return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
-def source_hash() -> str:
+def source_hash(kernel: str = "k_loglike") -> str:
     """Hash of the sources that define k_loglike (the per-subpixel model, the
-    kernel templates and their per-K instantiations)."""
+    kernel templates and their per-K instantiations); k_loglike_nc adds the
+    multi-column templates."""
     import glob
     import hashlib
     h = hashlib.sha256()
     c = os.path.join(ROOT, "paper_2503_08586_gb300", "csrc")
+    extra = ("tll_multi.cuh",) if kernel == "k_loglike_nc" else ()
     files = sorted([os.path.join(c, f) for f in ("tll_device.cuh", "tll_core.cuh",
-                                                 "tll_kernels.cuh", "tll_poly.cuh")]
+                                                 "tll_kernels.cuh", "tll_poly.cuh") + extra]
                    + glob.glob(os.path.join(c, "tll_kern_*.cu")))
     for f in files:
         h.update(os.path.basename(f).encode())
@@ -74,15 +95,15 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def captured_traffic(workload: str):
-    """DRAM bytes per launch of k_loglike from the committed ncu summary,
+def captured_traffic(workload: str, kernel: str = "k_loglike"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary,
     or None if there is none or the kernel sources changed since."""
     import re
-    path = os.path.join(ROOT, "profiles", f"k_loglike_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     m = re.search(r"traffic_bytes_per_launch: (\d+) source_hash: (\w+)", open(path).read())
-    if not m or m.group(2) != source_hash():
+    if not m or m.group(2) != source_hash(kernel):
         return None
     return float(m.group(1))
 
@@ -144,14 +165,16 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096):
+def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096, oracle_lens=None):
     """The FP64 oracle, as it stands, on all host cores over a bounded
-    sample of the same batch (about budget_cpu_s of CPU work)."""
+    sample of the same batch (about budget_cpu_s of CPU work).  oracle_lens:
+    the oracle's lens object to time (default: the two-column model)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    o = oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
-                    lens.x0, lens.y0, mass="epl" if params.shape[1] == 22 else "sie")
+    o = oracle_lens or oracle.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                                   lens.x0, lens.y0,
+                                   mass="epl" if params.shape[1] == 22 else "sie")
     P = params.astype(np.float64)
     n0 = min(2 * cores, len(P))
     t = time.perf_counter()
@@ -421,6 +444,155 @@ def run_ours(args):
     return line
 
 
+# ------------------------------------------------ multi-component light
+def run_multi(args):
+    """A multi-component workload (Sec. 2.3's N_l + N_s light profiles,
+    FNNLS amplitudes): one step = one tll_loglike_batch call over B vectors
+    with inputs resident in HBM (prologue + k_loglike_nc), L2 flushed
+    between steps; plus the host-buffer entry point end to end."""
+    import torch
+    from paper_2503_08586_gb300 import build, tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    tll.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = W.MULTI_WORKLOADS[args.workload]
+    comps = spec.comps
+    tcomps = [tll.comp(c["type"], c["plane"], c.get("free_scale", True),
+                       c.get("free_index", False), c.get("scale", 1.0), c.get("index", 1.0))
+              for c in comps]
+
+    def render_factory(pixel_scale, sub, psf, ny, nx, comps_):
+        g = tll.Lens(np.zeros((ny, nx), np.float32), np.ones((ny, nx), np.float32), psf,
+                     pixel_scale, sub, mass=spec.mass)
+        g.set_light(tcomps)
+        return lambda p: g.model_columns_n(p, blurred=True).astype(np.float64)
+
+    B = args.batch or spec.batch
+    lens, params = W.multi_workload(args.workload, render_factory, batch=B)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                 lens.x0, lens.y0, mass=spec.mass)
+    L.set_light(tcomps)
+    info = L.info()
+    p_dev = torch.from_numpy(params).to(dev)
+    out = torch.empty(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    L.profile(True)
+    for _ in range(args.warmup):
+        L.loglike_batch(p_dev, out)
+    barrier()
+    clocks = ClockSampler(local)
+    step_ms, main_ms, pro_ms = [], [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.loglike_batch(p_dev, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        a, b = L.profile_last()
+        pro_ms.append(a)
+        main_ms.append(b)
+    barrier()
+    clk = clocks.stop()
+    L.profile(False)
+    total = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / args.steps
+    value = B * ws / (ms_per_step / 1e3)
+    ll = out.cpu().numpy()
+    p_host = torch.from_numpy(params).pin_memory()
+    o_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        L.loglike_batch_host(p_host, o_host)
+    barrier()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.loglike_batch_host(p_host, o_host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = B * ws / (e2e_total / args.steps / 1e3)
+    assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return None
+    k = lens.psf.shape[0]
+    fpe = flops_per_eval_multi(lens.ny, lens.nx, lens.sub, k, info["separable"], comps)
+    main_avg = statistics.mean(main_ms)
+    achieved = fpe * B / (main_avg / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    kinds = ", ".join(f"{c['type']}@{c['plane']}" for c in comps)
+    line = {
+        "metric": f"log-likelihood evals/s ({args.workload}, {len(comps)} columns, FNNLS)",
+        "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": (f"{args.workload}: {lens.ny}x{lens.nx} px at {lens.pixel_scale}\"/px, "
+                         f"{lens.sub}x{lens.sub} subpixels, {k}x{k} {spec.psf_kind} PSF "
+                         f"({'separable' if info['separable'] else 'direct'} conv), SIE+shear, "
+                         f"components [{kinds}], FNNLS amplitudes"),
+            "batch_per_gpu": B, "global_batch": B * ws, "parallelism": f"replicas x{ws}",
+            "l2": "flushed between timed steps (256 MB write, outside the events)"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "kernel_ms": {"k_prologue_nc": statistics.mean(pro_ms), "k_loglike_nc": main_avg},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "traffic": captured_traffic(args.workload, "k_loglike_nc"),
+                     "kernel": "k_loglike_nc",
+                     "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                                   f"x {SM_MAX_MHZ:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "path": "tll_loglike_batch_host, pinned host buffers, B per step",
+                "h2d_bytes_per_step": B * L.nparam * 4, "d2h_bytes_per_step": B * 8},
+        "clocks": clk, "gpu_launches": 2 * args.steps, "impl": "ours",
+    }
+    if not args.skip_cpu_baseline:
+        import oracle
+        o = oracle.MultiLens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
+                             comps, lens.x0, lens.y0, mass=spec.mass)
+        line["cpu_baseline"] = cpu_baseline(lens, params, oracle_lens=o)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
 # ------------------------------------------------------------ ragged batch
 def run_ragged(args):
     """Many lenses of different sizes (sides {64..200}, PSF 11..31 px, 4x4
@@ -566,6 +738,8 @@ def main(argv=None):
         line = run_reference(args)
     elif args.workload == "ragged":
         line = run_ragged(args)
+    elif args.workload in ("slacs120", "mge120"):
+        line = run_multi(args)
     else:
         line = run_ours(args)
     if line is not None:
