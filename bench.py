@@ -39,18 +39,20 @@ SM_MAX_MHZ = 2070.0
 
 
 # ------------------------------------------------------------ work model
-def flops_per_eval(ny, nx, sub, k, separable) -> float:
+def flops_per_eval(ny, nx, sub, k, separable, ntrace=None) -> float:
     """Algorithmic FP32 work of one likelihood evaluation (add, sub, mul,
     div = 1 flop; FMA = 2; each transcendental evaluation = 1):
     per subpixel 72 flops + 9 transcendentals (grid 4, SIE 24 + sqrt, atan,
     atanh; shear 8; lens equation 2; two Sersics 2 x (16 + sqrt, pow, exp);
     binning 2); per pixel: mean 2, PSF 2 channels x (2K separable | K^2
-    direct) taps x 2, five weighted sums 15."""
+    direct) taps x 2, five weighted sums 15.  ntrace: pixels that need
+    tracing (a masked lens: those within the PSF's reach of an unmasked
+    pixel), default all."""
     npix = ny * nx
+    ntr = npix if ntrace is None else ntrace
     per_sub = 72 + 9
     taps = 2 * k if separable else k * k
-    per_pix = sub * sub * per_sub + 2 + 2 * taps * 2 + 15
-    return float(npix * per_pix)
+    return float(ntr * (sub * sub * per_sub + 2) + npix * (2 * taps * 2 + 15))
 
 
 def flops_per_eval_multi(ny, nx, sub, k, separable, comps) -> float:
@@ -386,7 +388,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return None
 
-    fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0], info["separable"])
+    fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0], info["separable"],
+                         L.ntrace())
     main_avg = statistics.mean(main_ms)
     achieved = fpe * B / (main_avg / 1e3) / 1e12
     peak = fp32_peak_tflops()
@@ -400,16 +403,20 @@ def run_ours(args):
                          f"{lens.sub}x{lens.sub} subpixels, {lens.psf.shape[0]}x"
                          f"{lens.psf.shape[0]} {spec.psf_kind} PSF "
                          f"({'separable' if info['separable'] else 'direct'} conv), "
-                         f"SIE+shear, Sersic lens+source, NNLS amplitudes"),
+                         f"SIE+shear, Sersic lens+source, NNLS amplitudes"
+                         + (f", {spec.mask[0]} mask {spec.mask[1]}-{spec.mask[2]}\" "
+                            f"({int(np.isfinite(lens.noise).sum())} pixels fitted)"
+                            if spec.mask else "")),
             "batch_per_gpu": B, "global_batch": B * ws, "path": "plain",
             "parallelism": f"replicas x{ws}",
             "l2": "flushed between timed steps (256 MB write, outside the events)",
             "launch_shape": L.shape(),
+            "traced_pixels": L.ntrace(),
             "conv": args.conv,
             "autotune": tune["tried"] if tune else "off"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
-        "subpixel_evals_per_s": value * lens.ny * lens.nx * lens.sub ** 2,
+        "subpixel_evals_per_s": value * L.ntrace() * lens.sub ** 2,
         "kernel_ms": {"k_prologue": statistics.mean(pro_ms), "k_loglike": main_avg},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,

@@ -39,7 +39,12 @@
  *     theta_E < 0, an EPL slope outside (1, 3), a non-finite entry) give
  *     log L = -INFINITY; the rest of the batch is unaffected.
  *   Masking: a pixel whose noise sigma is not finite and > 0, or whose datum
- *     is not finite, has weight 0 and no normalisation term.
+ *     is not finite, has weight 0 and no normalisation term.  (The paper fits
+ *     only a region of the image, Appendix A; give the other pixels an
+ *     infinite sigma.)  The batched kernels trace only the pixels within the
+ *     PSF's reach of an unmasked pixel (the unmasked set dilated by the
+ *     PSF box), since no other pixel can change an unmasked blurred pixel
+ *     (Eq. 3); the model-image calls trace every pixel.
  *   log L = -chi^2/2 - sum_{unmasked} log(2 pi sigma_i^2)/2, in FP64.
  *   Errors: every int-returning call returns TLL_OK (0) or a TLL_E* code and
  *     never aborts; tll_last_error() gives a message for the calling thread.
@@ -473,6 +478,10 @@ int tll_lens_ncols(const tll_lens *L);
  * TLL_EINVAL.
  */
 int tll_model_columns_n(tll_lens *L, const float *params, float *cols_out, int blurred);
+
+/* Pixels the batched kernels trace per vector: npix, or fewer for a lens
+ * with masked pixels (see Masking); -1 for NULL. */
+int tll_lens_ntrace(const tll_lens *L);
 
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,

@@ -184,6 +184,9 @@ struct tll_lens {
     bool prof_on = false, prof_recorded = false;
     // multi-component light (tll_set_light): nc > 0 columns, their list and
     // trace schedule, the multi-column kernel's shape and per-CTA slots
+    // pixels the batched kernels trace (masked lenses; null: all)
+    int *d_tlist = nullptr;
+    int ntrace = 0;
     int nc = 0;
     MultiDev md = {};
     Shape nc_shape;
@@ -255,6 +258,8 @@ LensDev lens_dev(const tll_lens *L)
     d.dWd = L->dWd; d.lognorm = L->lognorm;
     d.W = L->W; d.HL = L->HL; d.img = L->shape.img; d.band_rows = L->shape.band_rows;
     d.epl = L->epl;
+    d.tlist = L->d_tlist;
+    d.ntrace = L->d_tlist ? L->ntrace : L->npix;
     for (int k = 0; k < kMaxK * kMaxK; ++k)
         d.tk[k] = k < (int)L->psf_norm.size() && L->K <= kMaxK ? L->psf_norm[k] : 0.0f;
     grid_centre(L, &d.XC, &d.YC);
@@ -559,7 +564,8 @@ void free_lens(tll_lens *L)
     void *ptrs[] = {L->d_psf, L->d_pu, L->d_pv, L->d_wpack, L->d_kc, L->d_gscr,
                     L->d_stage_p, L->d_stage_o, L->d_p1, L->d_kc1, L->d_unb,
                     L->d_blur, L->d_img, L->d_res, L->d_out1, L->d_unbl, L->d_sblur,
-                    L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo, L->d_nscr, L->d_nres};
+                    L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo, L->d_nscr, L->d_nres,
+                    L->d_tlist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : L->prof_ev)
@@ -1425,11 +1431,13 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
     // weights (Eq. 5): w = 1/sigma^2 as a float pair, w*d likewise; masked
     // pixels get 0.  dWd = sum w d^2, lognorm = -sum log(2 pi sigma^2)/2.
     std::vector<float4> wp(npix);
+    std::vector<unsigned char> used(npix, 0);
     double dWd = 0.0, lognorm = 0.0;
     for (int t = 0; t < npix; ++t) {
         const double s = noise[t], d = image[t];
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
         if (isfinite(s) && s > 0.0 && isfinite(d)) {
+            used[t] = 1;
             const double w = 1.0 / (s * s), wd = w * d;
             q.x = (float)w; q.y = (float)(w - (double)q.x);
             q.z = (float)wd; q.w = (float)(wd - (double)q.z);
@@ -1440,6 +1448,36 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
     }
     L->dWd = dWd;
     L->lognorm = lognorm;
+    // Pixels within the PSF's reach of an unmasked pixel: the unmasked set
+    // dilated by the K x K box (rows, then columns).  Only they can change
+    // an unmasked blurred pixel (Eq. 3), so the batched kernels trace only
+    // them when that leaves any pixel out.
+    std::vector<int> tlist;
+    {
+        const int h = (K - 1) / 2, nx = g.nx, ny = g.ny;
+        std::vector<unsigned char> rowd(npix, 0);
+        for (int i = 0; i < ny; ++i) {
+            int last = -1000000;   // column of the last unmasked pixel at or left of j + h
+            for (int j = 0; j < nx + h; ++j) {
+                if (j < nx && used[i * nx + j]) last = j;
+                const int c = j - h;   // output column
+                if (c >= 0 && c < nx) {
+                    bool any = last >= c - h;
+                    rowd[i * nx + c] = any ? 1 : 0;
+                }
+            }
+        }
+        for (int j = 0; j < nx; ++j) {
+            int last = -1000000;
+            for (int i = 0; i < ny + h; ++i) {
+                if (i < ny && rowd[i * nx + j]) last = i;
+                const int r = i - h;
+                if (r >= 0 && r < ny && last >= r - h) tlist.push_back(r * nx + j);
+            }
+        }
+        std::sort(tlist.begin(), tlist.end());
+    }
+    const bool listed = (int)tlist.size() < npix;   // some pixel left out (or all)
 
     int rc = TLL_OK;
     auto alloc = [&](void **p, size_t bytes) -> int {
@@ -1464,7 +1502,15 @@ int tll_create_lens(const float *image, const float *noise, const float *psf,
         free_lens(L);
         return rc;
     }
+    L->ntrace = listed ? (int)tlist.size() : npix;
+    if (listed && (rc = alloc((void **)&L->d_tlist, std::max<size_t>(1, tlist.size()) * sizeof(int)))) {
+        free_lens(L);
+        return rc;
+    }
     cudaError_t e = cudaSuccess;
+    if (listed && !tlist.empty())
+        e = cudaMemcpy(L->d_tlist, tlist.data(), tlist.size() * sizeof(int),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->d_psf, pn.data(), K * K * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->d_pu, pu.data(), K * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->d_pv, pv.data(), K * sizeof(float), cudaMemcpyHostToDevice);
@@ -1507,6 +1553,12 @@ int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
     if (flags) *flags = L->flags;
     if (separable) *separable = L->sep;
     return TLL_OK;
+}
+
+int tll_lens_ntrace(const tll_lens *L)
+{
+    if (!L) return fail(TLL_EINVAL, "lens is NULL"), -1;
+    return L->d_tlist ? L->ntrace : L->npix;
 }
 
 int tll_lens_nparam(const tll_lens *L)

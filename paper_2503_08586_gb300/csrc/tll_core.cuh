@@ -31,6 +31,11 @@ struct LensDev {
     double dWd, lognorm;
     int band_rows;    // IMG_BANDED: output rows per shared-memory band
     int epl;          // elliptical power-law mass: 22 parameters per vector
+    // Pixels the batched kernels trace: tlist[0 .. ntrace) (row-major pixel
+    // indices) when masked pixels leave some pixels out of reach of every
+    // unmasked one through the PSF, else tlist = null (all npix pixels).
+    const int *tlist;
+    int ntrace;
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
     float tk[kMaxK * kMaxK];            // the full PSF (direct convolution)
 };

@@ -65,14 +65,20 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
 // offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
 // coordinate is an affine function of them (see decode_vector).
 // MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series coefficients ec).
+// skip: trace only the lens's listed pixels (L.tlist), those within the PSF's
+// reach of an unmasked pixel; the others keep whatever finite value they
+// hold, which only ever meets a zero weight.
 template <int SUB, int MODE>
 __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
                                             float *Il, float *Is, int stride, int off,
-                                            int tid, int nthr, const float *ec)
+                                            int tid, int nthr, const float *ec, bool skip)
 {
     const int sub = SUB > 0 ? SUB : L.sub;
     const int nx = L.nx;
-    for (int pix = tid; pix < L.npix; pix += nthr) {
+    const int *list = skip ? L.tlist : nullptr;
+    const int n = list ? L.ntrace : L.npix;
+    for (int t = tid; t < n; t += nthr) {
+        const int pix = list ? list[t] : t;
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
@@ -508,19 +514,33 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
 template <int SUB>
 __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, float *Il,
                                              float *Is, int stride, int off, float *sepl,
-                                             int tid, int nthr)
+                                             int tid, int nthr, bool skip)
 {
     const VecConst v = load_consts(kc);
     if (v.epl) {
         for (int t = tid; t <= v.en; t += nthr) sepl[t] = kc[K_EC0 + t];
         __syncthreads();
-        trace_image<SUB, 2>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+        trace_image<SUB, 2>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.fast) {
-        trace_image<SUB, 0>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+        trace_image<SUB, 0>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else {
-        trace_image<SUB, 1>(L, v, Il, Is, stride, off, tid, nthr, sepl);
+        trace_image<SUB, 1>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     }
     __syncthreads();
+}
+
+// Zero the two images of a lens whose traced pixels are listed (placements
+// that do not zero them in setup_lens): pixels never traced must start
+// finite.
+__device__ __forceinline__ void zero_untraced(const LensDev &L, const ImgPtrs &P, int tid,
+                                              int nthr)
+{
+    if (!L.tlist || L.img == IMG_PADDED) return;
+    for (int t = tid; t < L.npix; t += nthr) {
+        const int i = t / L.nx, j = t - i * L.nx;
+        P.Il[i * P.stride + P.off + j] = 0.0f;
+        P.Is[i * P.stride + P.off + j] = 0.0f;
+    }
 }
 
 template <int SUB, int K, bool WRITE>
@@ -531,7 +551,7 @@ __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
 {
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nx = L.nx, npix = L.npix;
-    trace_vector<SUB>(L, kc, P.Il, P.Is, P.stride, P.off, sepl, tid, nthr);
+    trace_vector<SUB>(L, kc, P.Il, P.Is, P.stride, P.off, sepl, tid, nthr, !WRITE);
     if (WRITE) {
         for (int t = tid; t < npix; t += nthr) {
             const int i = t / nx, j = t - i * nx;
@@ -581,6 +601,7 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
     const ImgPtrs P =
         img_ptrs(L, spsf, gslot ? R.gscr + (size_t)blockIdx.x * R.gslot : nullptr);
     setup_lens(L, spsf, tid, nthr);
+    if (!WRITE) zero_untraced(L, P, tid, nthr);
     __syncthreads();
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
@@ -631,6 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
             for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
             __syncthreads();
             setup_lens(sL, spsf, tid, nthr);
+            zero_untraced(sL, img_ptrs(sL, spsf, gslot), tid, nthr);
             __syncthreads();
             cur = sg.lens;
         }

@@ -127,20 +127,24 @@ __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, floa
 // subpixel, binned by the mean, written to U + chan[k] * npix.
 // MODE: 0 / 1 / 2 source plane with the SIE fast / general form or the EPL
 // series (ec); 3 lens plane (no deflection).
+// skip: trace only the lens's listed pixels (as trace_image).
 template <int SUB, int MODE>
 __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                                            const float *cq, int gmask, int ncp,
                                            const int *chan, float *U, int tid, int nthr,
-                                           const float *ec)
+                                           const float *ec, bool skip)
 {
     const int sub = SUB > 0 ? SUB : L.sub;
     const int nx = L.nx, npix = L.npix;
+    const int *list = skip ? L.tlist : nullptr;
+    const int n = list ? L.ntrace : npix;
     float q[kPassMax][6];
 #pragma unroll
     for (int k = 0; k < kPassMax; ++k)
 #pragma unroll
         for (int e = 0; e < 6; ++e) q[k][e] = k < ncp ? cq[6 * k + e] : 0.0f;
-    for (int pix = tid; pix < npix; pix += nthr) {
+    for (int t = tid; t < n; t += nthr) {
+        const int pix = list ? list[t] : t;
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
@@ -389,7 +393,11 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
     float *Mb = U + (size_t)nc * npix;
     float *H = Mb + (size_t)(nc + 1) * npix;
     setup_lens(L, spsf, tid, nthr);
+    // pixels never traced (masked lenses) must start finite
+    if (L.tlist)
+        for (int t = tid; t < nc * npix; t += nthr) U[t] = 0.0f;
     __syncthreads();
+    const bool skip = R.wr_res == nullptr;   // model columns: every pixel
     const int nch = max(1, min(kNcChunks, (2 * nwarp + nc - 1) / nc));
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
@@ -419,13 +427,13 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
             }
             const int *chan = M.pass_comp[ps];
             if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl);
+                trace_pass<SUB, 3>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
             else if (v.epl)
-                trace_pass<SUB, 2>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl);
+                trace_pass<SUB, 2>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
             else if (v.fast)
-                trace_pass<SUB, 0>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl);
+                trace_pass<SUB, 0>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
             else
-                trace_pass<SUB, 1>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl);
+                trace_pass<SUB, 1>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
         }
         __syncthreads();
         // 2. PSF, two columns at a time (an odd last column pairs with itself)

@@ -27,7 +27,7 @@ k_trace_split(const __grid_constant__ LensDev L, const float *__restrict__ kc, i
         const float *k = kc + (size_t)b * NCONST;
         if (k[K_VALID] == 0.0f) continue;
         float *Il = unbl + (size_t)b * 2 * L.npix, *Is = Il + L.npix;
-        trace_vector<SUB>(L, k, Il, Is, L.nx, 0, sepl, tid, nthr);
+        trace_vector<SUB>(L, k, Il, Is, L.nx, 0, sepl, tid, nthr, false);
     }
 }
 

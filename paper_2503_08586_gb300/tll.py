@@ -38,7 +38,7 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
            "tll_autotune", "tll_set_conv", "tll_conv_check", "tll_lens_nparam",
            "tll_destroy_lens", "tll_last_error", "tll_version", "tll_set_light",
-           "tll_lens_ncols", "tll_model_columns_n")
+           "tll_lens_ncols", "tll_model_columns_n", "tll_lens_ntrace")
 
 # Multi-component light (tll_set_light).
 MAX_COMPS = 8
@@ -197,6 +197,8 @@ def load(path: str | None = None):
     lib.tll_set_light.restype = i
     lib.tll_lens_ncols.argtypes = [vp]
     lib.tll_lens_ncols.restype = i
+    lib.tll_lens_ntrace.argtypes = [vp]
+    lib.tll_lens_ntrace.restype = i
     lib.tll_model_columns_n.argtypes = [vp, fp, fp, i]
     lib.tll_model_columns_n.restype = i
     if path is None:
@@ -277,6 +279,11 @@ class Lens:
     @property
     def handle(self):
         return self._h
+
+    def ntrace(self) -> int:
+        """Pixels the batched kernels trace per vector (fewer than ny * nx
+        when masked pixels leave some out of the PSF's reach)."""
+        return load().tll_lens_ntrace(self._h)
 
     def info(self) -> dict:
         v = [ctypes.c_int() for _ in range(6)]

@@ -69,6 +69,7 @@ class WorkloadSpec:
     moffat_beta: float = 3.0
     seed_offset: int = 0
     mass: str = "sie"      # "sie" | "epl"
+    mask: tuple | None = None   # ("annulus", r_in, r_out) arcsec about the image centre
 
 
 WORKLOADS = {
@@ -81,7 +82,32 @@ WORKLOADS = {
     # csst100 with the elliptical power-law mass of Eq. 12 (slope free)
     "csst100_epl": WorkloadSpec("csst100_epl", 100, 100, 0.074, 4, 21, "gaussian", 0.15,
                                 4096, "sky+poisson", seed_offset=6, mass="epl"),
+    # csst100 fitted only in an annulus around the Einstein ring (the paper's
+    # fitting regions, Appendix A): pixels outside 0.3" - 2.2" are masked
+    "csst100_mask": WorkloadSpec("csst100_mask", 100, 100, 0.074, 4, 21, "gaussian", 0.15,
+                                 4096, "sky+poisson", seed_offset=2,
+                                 mask=("annulus", 0.3, 2.2)),
 }
+
+
+def annulus_mask(ny, nx, pixel_scale, r_in, r_out, x0=None, y0=None) -> np.ndarray:
+    """Boolean [ny, nx]: True where the pixel centre lies at r_in <= r <=
+    r_out arcsec from the origin (the pixels fitted)."""
+    x0 = centred_origin(nx, pixel_scale) if x0 is None else x0
+    y0 = centred_origin(ny, pixel_scale) if y0 is None else y0
+    x = x0 + pixel_scale * np.arange(nx)
+    y = y0 + pixel_scale * np.arange(ny)
+    r = np.hypot(x[None, :], y[:, None])
+    return (r >= r_in) & (r <= r_out)
+
+
+def apply_mask(lens, keep: np.ndarray):
+    """Mask every pixel outside `keep` by an infinite noise sigma (the
+    library's and the oracle's masking rule)."""
+    noise = lens.noise.copy()
+    noise[~keep] = np.float32(np.inf)
+    lens.noise = noise
+    return lens
 
 
 # ------------------------------------------------------------------ PSFs
@@ -427,6 +453,10 @@ def workload(name: str, render_factory, batch: int | None = None):
     render = render_factory(f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx, **kw)
     lens = synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf,
                       render, spec.noise_kind, mass=spec.mass)
+    if spec.mask is not None:
+        kind, r_in, r_out = spec.mask
+        apply_mask(lens, annulus_mask(spec.ny, spec.nx, f32(spec.pixel_scale), r_in, r_out,
+                                      lens.x0, lens.y0))
     B = spec.batch if batch is None else batch
     params = draw_prior(rng, B, spec.mass)
     return lens, params
