@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
-    base = ["gcc", "-std=c11", "-D_GNU_SOURCE", "-O2", "-fPIC", "-shared",
+    base = ["gcc", "-std=c11", "-D_GNU_SOURCE", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
             "-o", _LIB + ".tmp", _SRC, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
@@ -71,6 +71,8 @@ def _load():
         return _lib
     lib = ctypes.CDLL(build())
     d, i, pd = ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    pf, pi = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)
+    pu32 = ctypes.POINTER(ctypes.c_uint32)
     sig = {
         "ora_ellipse": (i, [d, d, pd, pd]),
         "ora_gammainc_P": (d, [d, d]),
@@ -99,6 +101,11 @@ def _load():
                                     pd, pd]),
         "ora_loglike_multi_batch": (None, [ctypes.POINTER(_Lens), ctypes.POINTER(_Comp),
                                            i, pd, i, pd, i]),
+        "ora_philox4x32_10": (None, [pu32, pu32, pu32]),
+        "ora_stretch_propose": (None, [pf, i, i, i, ctypes.c_longlong, ctypes.c_uint64, d,
+                                       pf, pd, pi]),
+        "ora_stretch_accept": (i, [pf, pd, i, i, i, ctypes.c_longlong, ctypes.c_uint64, i,
+                                   pf, pd, pd, pf, pf, pi]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -358,6 +365,72 @@ def multi_columns_renderer(pixel_scale, sub, psf, ny, nx, comps, mass: str = "si
         return cols
 
     return render
+
+
+# ------------------------------------------------------- sampler loop
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon et al. 2011): four uint32 outputs."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    _load().ora_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def stretch_propose(x, h, step, seed, a=2.0):
+    """Half h's proposals of the stretch move: (Y [W/2, P] float32, z, j)."""
+    x = np.ascontiguousarray(x, np.float32)
+    W, P = x.shape
+    Y = np.zeros((W // 2, P), np.float32)
+    z = np.zeros(W // 2)
+    j = np.zeros(W // 2, np.int32)
+    _load().ora_stretch_propose(_fp(x), W, P, h, step, seed, a, _fp(Y), _p(z), _ip(j))
+    return Y, z, j
+
+
+def stretch_accept(x, lp, h, step, seed, ndim, Y, z, lpY, lo, hi):
+    """Accept / reject half h in place (x float32 [W, P], lp float64 [W]);
+    returns the accepted flags [W/2]."""
+    W, P = x.shape
+    assert x.dtype == np.float32 and x.flags.c_contiguous and lp.dtype == np.float64
+    Y = np.ascontiguousarray(Y, np.float32)
+    z, lpY = _f64(z), _f64(lpY)
+    lo = np.ascontiguousarray(lo, np.float32)
+    hi = np.ascontiguousarray(hi, np.float32)
+    acc = np.zeros(W // 2, np.int32)
+    _load().ora_stretch_accept(_fp(x), _p(lp), W, P, h, step, seed, ndim, _fp(Y), _p(z),
+                               _p(lpY), _fp(lo), _fp(hi), _ip(acc))
+    return acc
+
+
+def stretch_run(x0, logp, nsteps, seed, lo, hi, ndim=None, a=2.0, step0=0):
+    """The stretch-move loop with a Python log-density logp(Y [n, P]) -> [n]:
+    returns (chain [nsteps, W, P], lp chain [nsteps, W], acceptance rate)."""
+    x = np.ascontiguousarray(x0, np.float32).copy()
+    W, P = x.shape
+    lo = np.asarray(lo, np.float32)
+    hi = np.asarray(hi, np.float32)
+    ndim = int(np.sum(lo < hi)) if ndim is None else ndim
+    lp = np.asarray(logp(x), np.float64).copy()
+    chain = np.zeros((nsteps, W, P), np.float32)
+    lpc = np.zeros((nsteps, W))
+    nacc = 0
+    for s in range(nsteps):
+        for h in (0, 1):
+            Y, z, _ = stretch_propose(x, h, step0 + s, seed, a)
+            nacc += int(stretch_accept(x, lp, h, step0 + s, seed, ndim, Y, z, logp(Y), lo,
+                                       hi).sum())
+        chain[s] = x
+        lpc[s] = lp
+    return chain, lpc, nacc / (nsteps * W)
 
 
 def max_threads() -> int:

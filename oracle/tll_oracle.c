@@ -818,3 +818,120 @@ void ora_loglike_multi_batch(const ora_lens *L, const ora_comp_spec *c, int nc,
                         : ora_loglike_multi(L, c, nc, params + (size_t)b * np, NULL, NULL, NULL);
     (void)nthreads;
 }
+
+/* ================================================================
+ * A sampler loop: the affine-invariant ensemble "stretch move".
+ *
+ * The paper's sampler (nautilus) runs on the CPU and calls the GPU
+ * likelihood for batches of proposals; it names that host round trip as the
+ * bottleneck and proposes moving the sampler onto the GPU (Sec. 4.2).  The
+ * library's device-side loop runs the stretch move of Goodman & Weare
+ * (2010); this is that move written out plainly, for the tests.  Random
+ * numbers come from Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011), a
+ * counter-based generator, so both sides draw the same numbers from the
+ * same (key, counter).
+ *
+ * One step updates the two halves of the ensemble of W walkers in turn
+ * (half 0 = walkers [0, W/2), half 1 = [W/2, W)).  For walker k of half h,
+ * with Philox outputs r0..r3 at key (seed low, seed high) and counter
+ * (k, h, step low, step high):
+ *   partner  j = (other half's first walker) + floor(r0 (W/2) / 2^32)
+ *   stretch  u = (r1 + 1/2) 2^-32, z = ((a - 1) u + 1)^2 / a, which has the
+ *            density g(z) ~ 1/sqrt(z) on [1/a, a]
+ *   proposal Y = x_j + z (x_k - x_j), in FP64 from the float32 walkers,
+ *            rounded once to float32
+ *   accept   when log((r2 + 1/2) 2^-32) < (ndim - 1) log z + lp(Y) - lp(x_k)
+ *            and every free coordinate of Y lies in [lo, hi] (a uniform
+ *            box prior; coordinates with lo == hi are fixed).
+ * Every FP64 operation here is a single rounded operation (this file is
+ * compiled without contraction), so the proposals are reproducible bit for
+ * bit by another implementation that rounds the same way.
+ * ================================================================ */
+#include <stdint.h>
+
+/* Philox4x32-10: ten rounds of the Philox S-box on a 128-bit counter with a
+ * 64-bit key (Salmon et al. 2011, Sec. 5): each round multiplies counter
+ * words 0 and 2 by the two round multipliers, takes the high and low
+ * halves of the 64-bit products, and mixes them with the other two words
+ * and the key; the key advances by the two Weyl constants between rounds. */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The four Philox outputs of walker k, half h, at `step`. */
+static void ora_walker_rng(uint64_t seed, long long step, int h, int k, uint32_t r[4])
+{
+    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)h, (uint32_t)((uint64_t)step & 0xffffffffu),
+                       (uint32_t)((uint64_t)step >> 32)};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    ora_philox4x32_10(ctr, key, r);
+}
+
+/* Proposals of half h: Y[k - h W/2][P] (float32), the stretch factors z and
+ * the partners j of walkers k of that half. */
+void ora_stretch_propose(const float *x, int W, int P, int h, long long step, uint64_t seed,
+                         double a, float *Y, double *z_out, int *j_out)
+{
+    const int half = W / 2, first = h * half, other = (1 - h) * half;
+    for (int t = 0; t < half; ++t) {
+        const int k = first + t;
+        uint32_t r[4];
+        ora_walker_rng(seed, step, h, k, r);
+        const int j = other + (int)(((uint64_t)r[0] * (uint64_t)half) >> 32);
+        const double u = ((double)r[1] + 0.5) * 2.3283064365386963e-10;
+        const double w = (a - 1.0) * u + 1.0;
+        const double z = w * w / a;
+        for (int i = 0; i < P; ++i) {
+            const double xj = x[(size_t)j * P + i], xk = x[(size_t)k * P + i];
+            const double d = xk - xj;
+            const double t2 = z * d;
+            Y[(size_t)t * P + i] = (float)(xj + t2);
+        }
+        z_out[t] = z;
+        j_out[t] = j;
+    }
+}
+
+/* Accept / reject half h given the proposals' log posterior lpY (the caller
+ * evaluates them); updates x and lp in place and writes acc[t] = 1 for an
+ * accepted move.  Returns the number accepted. */
+int ora_stretch_accept(float *x, double *lp, int W, int P, int h, long long step,
+                       uint64_t seed, int ndim, const float *Y, const double *z,
+                       const double *lpY, const float *lo, const float *hi, int *acc)
+{
+    const int half = W / 2, first = h * half;
+    int n = 0;
+    for (int t = 0; t < half; ++t) {
+        const int k = first + t;
+        uint32_t r[4];
+        ora_walker_rng(seed, step, h, k, r);
+        int inside = 1;
+        for (int i = 0; i < P; ++i) {
+            const float v = Y[(size_t)t * P + i];
+            if (lo[i] < hi[i] && !(v >= lo[i] && v <= hi[i])) inside = 0;
+        }
+        const double lpy = inside ? lpY[t] : -INFINITY;
+        const double lu = log(((double)r[2] + 0.5) * 2.3283064365386963e-10);
+        const double rhs = (ndim - 1) * log(z[t]) + lpy - lp[k];
+        acc[t] = lu < rhs;
+        if (acc[t]) {
+            for (int i = 0; i < P; ++i) x[(size_t)k * P + i] = Y[(size_t)t * P + i];
+            lp[k] = lpy;
+            ++n;
+        }
+    }
+    return n;
+}
