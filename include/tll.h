@@ -483,6 +483,52 @@ int tll_model_columns_n(tll_lens *L, const float *params, float *cols_out, int b
  * with masked pixels (see Masking); -1 for NULL. */
 int tll_lens_ntrace(const tll_lens *L);
 
+/*
+ * Device-side sampler loop.  The paper's sampler runs on the CPU and calls
+ * the GPU likelihood for each batch of proposals; it names those host round
+ * trips as the bottleneck and proposes moving the sampler to the GPU
+ * (Sec. 4.2).  tll_sampler keeps an ensemble of W walkers on the device and
+ * advances it with the affine-invariant stretch move (Goodman & Weare 2010):
+ * proposals, the lens's batched likelihood, accept / reject and the chain all
+ * run in CUDA kernels, so tll_sampler_run enqueues any number of steps
+ * without waiting.  One step updates walkers [0, W/2) against partners from
+ * [W/2, W), then the reverse.  For walker k of half h, with r0..r3 the
+ * Philox4x32-10 outputs (Salmon et al. 2011) for key (seed mod 2^32,
+ * seed / 2^32) and counter (k, h, step mod 2^32, step / 2^32):
+ *   partner  j = first walker of the other half + floor(r0 (W/2) / 2^32)
+ *   stretch  z = ((a - 1) u + 1)^2 / a with u = (r1 + 1/2) / 2^32
+ *   proposal Y = x_j + z (x_k - x_j) in FP64 (one rounding per operation),
+ *            rounded to float32
+ *   accept   if log((r2 + 1/2) / 2^32) < (ndim - 1) log z + lp(Y) - lp(x_k)
+ * where lp = log L inside the box prior [lo, hi] and -inf outside (entries
+ * with lo == hi are fixed: give every walker that value).  Steps are numbered
+ * from 0 across runs, so a run continues the stream of random numbers.
+ */
+typedef struct tll_sampler tll_sampler;
+/* nwalkers even, >= 4; lo, hi host float32 [tll_lens_nparam(L)]; a > 1 (2 is
+ * the usual choice); ndim: dimension of the sampled space for the z^(ndim-1)
+ * factor, <= 0 for the number of entries with lo < hi.  Allocates the
+ * ensemble's buffers and the lens's one-lens image slots.  The sampler uses
+ * the lens: no other call on the lens may overlap a run. */
+int tll_sampler_create(tll_lens *L, int nwalkers, const float *lo, const float *hi,
+                       double a, int ndim, unsigned long long seed, tll_sampler **out);
+/* Copy the starting walkers (DEVICE float32 [W][nparam]) and evaluate their
+ * log posterior, on stream. */
+int tll_sampler_set_walkers(tll_sampler *S, const float *x0, void *stream);
+/* Enqueue nsteps steps on stream.  Optional DEVICE outputs (NULL to skip):
+ * chain float32 [nsteps][W][nparam] (the walkers after each step), lp_chain
+ * float64 [nsteps][W] (their log posterior), lp_prop_chain float64
+ * [nsteps][W] (each walker's proposal's log posterior at that step). */
+int tll_sampler_run(tll_sampler *S, int nsteps, float *chain, double *lp_chain,
+                    double *lp_prop_chain, void *stream);
+/* Copy the current walkers (DEVICE float32 [W][nparam]) and log posteriors
+ * (DEVICE float64 [W]) -- either may be NULL -- and report the steps taken
+ * and the moves accepted and proposed so far; waits for stream. */
+int tll_sampler_state(tll_sampler *S, float *x, double *lp, long long *step,
+                      long long *accepted, long long *proposed, void *stream);
+/* Wait for the device and release the sampler (NULL is a no-op). */
+void tll_sampler_destroy(tll_sampler *S);
+
 /* Image size and mode of a lens (any pointer may be NULL). */
 int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
                   int *flags, int *separable);

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "tll.h"
+#include "tll_internal.h"
 #include "tll_multi.cuh"
 #include "tll_split.cuh"
 
@@ -713,6 +714,37 @@ int reject_nc(const tll_lens *L, const char *what)
 }
 
 }  // namespace
+
+// ------------------------------------------- internal entry points
+namespace tll {
+
+int lens_prepare(tll_lens *L)
+{
+    DeviceGuard gd(L->dev);
+    return L->nc ? nc_ensure_scr(L) : ensure_gscr(L);
+}
+
+int lens_eval(tll_lens *L, const float *params, int B, double *out, cudaStream_t st, float *kc)
+{
+    if (B <= 0) return TLL_OK;
+    return L->nc ? run_batch_nc(L, params, B, out, st, kc, nullptr)
+                 : run_batch(L, params, B, out, st, false, kc);
+}
+
+int lens_nparam(const tll_lens *L) { return L->nparam; }
+int lens_device(const tll_lens *L) { return L->dev; }
+int const_block_floats() { return NCONST; }
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace tll
 
 // ------------------------------------------------------- batch context
 // Reusable buffers for multi-lens launches (and their CUDA graph).  The

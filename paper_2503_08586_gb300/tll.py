@@ -38,7 +38,9 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_profile_enable", "tll_profile_last", "tll_lens_shape", "tll_set_shape",
            "tll_autotune", "tll_set_conv", "tll_conv_check", "tll_lens_nparam",
            "tll_destroy_lens", "tll_last_error", "tll_version", "tll_set_light",
-           "tll_lens_ncols", "tll_model_columns_n", "tll_lens_ntrace")
+           "tll_lens_ncols", "tll_model_columns_n", "tll_lens_ntrace",
+           "tll_sampler_create", "tll_sampler_set_walkers", "tll_sampler_run",
+           "tll_sampler_state", "tll_sampler_destroy")
 
 # Multi-component light (tll_set_light).
 MAX_COMPS = 8
@@ -199,6 +201,18 @@ def load(path: str | None = None):
     lib.tll_lens_ncols.restype = i
     lib.tll_lens_ntrace.argtypes = [vp]
     lib.tll_lens_ntrace.restype = i
+    lib.tll_sampler_create.argtypes = [vp, i, fp, fp, ctypes.c_double, i, ctypes.c_ulonglong,
+                                       ctypes.POINTER(vp)]
+    lib.tll_sampler_create.restype = i
+    lib.tll_sampler_set_walkers.argtypes = [vp, fp, vp]
+    lib.tll_sampler_set_walkers.restype = i
+    lib.tll_sampler_run.argtypes = [vp, i, fp, dp, dp, vp]
+    lib.tll_sampler_run.restype = i
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    lib.tll_sampler_state.argtypes = [vp, fp, dp, ll, ll, ll, vp]
+    lib.tll_sampler_state.restype = i
+    lib.tll_sampler_destroy.argtypes = [vp]
+    lib.tll_sampler_destroy.restype = None
     lib.tll_model_columns_n.argtypes = [vp, fp, fp, i]
     lib.tll_model_columns_n.restype = i
     if path is None:
@@ -454,6 +468,74 @@ class Lens:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Sampler:
+    """Device-side ensemble sampler (stretch move, Philox4x32-10) over one
+    lens: proposals, likelihood, accept / reject and the chain stay on the
+    GPU (see tll_sampler_* in tll.h)."""
+
+    def __init__(self, lens: "Lens", nwalkers: int, lo, hi, a: float = 2.0, ndim: int = 0,
+                 seed: int = 0):
+        lo = np.ascontiguousarray(lo, np.float32)
+        hi = np.ascontiguousarray(hi, np.float32)
+        if lo.shape != (lens.nparam,) or hi.shape != (lens.nparam,):
+            raise ValueError(f"lo, hi must have {lens.nparam} entries")
+        h = ctypes.c_void_p()
+        _check(load().tll_sampler_create(lens.handle, int(nwalkers), lo.ctypes.data,
+                                         hi.ctypes.data, float(a), int(ndim), int(seed),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.lens, self.W, self.P = lens, int(nwalkers), lens.nparam
+
+    def set_walkers(self, x0, stream=None):
+        """x0: contiguous CUDA float32 [W, nparam]."""
+        import torch
+        if not (x0.is_cuda and x0.dtype == torch.float32 and x0.is_contiguous()
+                and tuple(x0.shape) == (self.W, self.P)):
+            raise ValueError(f"x0 must be a contiguous CUDA float32 [{self.W}, {self.P}]")
+        _check(load().tll_sampler_set_walkers(self._h, x0.data_ptr(), _stream_handle(stream)))
+
+    def run(self, nsteps: int, keep_chain: bool = True, keep_proposals: bool = False,
+            stream=None):
+        """Enqueue nsteps steps (asynchronous); returns (chain [n, W, P],
+        lp [n, W], proposals' lp [n, W] or None) CUDA tensors, or Nones when
+        keep_chain is False."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        chain = lpc = lpp = None
+        if keep_chain:
+            chain = torch.empty((nsteps, self.W, self.P), dtype=torch.float32, device=dev)
+            lpc = torch.empty((nsteps, self.W), dtype=torch.float64, device=dev)
+        if keep_proposals:
+            lpp = torch.empty((nsteps, self.W), dtype=torch.float64, device=dev)
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(load().tll_sampler_run(self._h, int(nsteps), ptr(chain), ptr(lpc), ptr(lpp),
+                                      _stream_handle(stream)))
+        return chain, lpc, lpp
+
+    def state(self, stream=None):
+        """(walkers [W, P], lp [W] CUDA tensors, steps, accepted, proposed)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        x = torch.empty((self.W, self.P), dtype=torch.float32, device=dev)
+        lp = torch.empty(self.W, dtype=torch.float64, device=dev)
+        st, acc, pro = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().tll_sampler_state(self._h, x.data_ptr(), lp.data_ptr(), ctypes.byref(st),
+                                        ctypes.byref(acc), ctypes.byref(pro),
+                                        _stream_handle(stream)))
+        return x, lp, st.value, acc.value, pro.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().tll_sampler_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batcher:
