@@ -600,6 +600,123 @@ def run_multi(args):
     return line
 
 
+# ------------------------------------------------------------ sampler loop
+def _host_stretch_half(x, h, rng, a, logp, lp, ndim, lo, hi):
+    """One half step of the stretch move on the host (numpy), the paper's
+    arrangement: proposals made on the CPU, their likelihood on the GPU
+    through host buffers, accept / reject on the CPU."""
+    W = x.shape[0]
+    half = W // 2
+    k = np.arange(half) + h * half
+    j = (1 - h) * half + rng.integers(0, half, half)
+    z = ((a - 1.0) * rng.random(half) + 1.0) ** 2 / a
+    Y = (x[j] + z[:, None] * (x[k] - x[j])).astype(np.float32)
+    inside = np.all(((Y >= lo) & (Y <= hi)) | (lo == hi), axis=1)
+    lpy = np.where(inside, logp(Y), -np.inf)
+    acc = np.log(rng.random(half)) < (ndim - 1) * np.log(z) + lpy - lp[k]
+    x[k[acc]] = Y[acc]
+    lp[k[acc]] = lpy[acc]
+    return int(acc.sum())
+
+
+def run_sampler(args):
+    """The stretch-move ensemble sampler on csst100: W walkers, K steps, each
+    step two half-batches of W/2 likelihood evaluations.  Device loop
+    (tll_sampler: proposals, likelihood, accept / reject, chain on the GPU,
+    one synchronisation per run) against the host loop of the paper's design
+    (numpy proposals and accept / reject, tll_loglike_batch_host per half
+    step: params copied in, log L copied out, a synchronisation each time)."""
+    import torch
+    from paper_2503_08586_gb300 import build, tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    tll.load()
+    nw = args.batch or 4096
+    nsteps = args.steps
+    lens, _ = W.workload("csst100", tll.columns_renderer, batch=8)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    truth = lens.truth.astype(np.float32)
+    lo, hi = truth - np.float32(0.5), truth + np.float32(0.5)
+    lo[[7, 14]] = hi[[7, 14]] = 1.0
+    lo[[9, 16]], hi[[9, 16]] = 0.5, 6.0
+    lo[[8, 15]], hi[[8, 15]] = 0.02, 3.0
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 30))
+    x0 = np.repeat(truth[None], nw, axis=0)
+    x0[:, [7, 14]] = 1.0
+    free = np.where(lo < hi)[0]
+    x0[:, free] += rng.normal(scale=0.05, size=(nw, free.size)).astype(np.float32)
+    x0[:, 12], x0[:, 13] = x0[:, 3], x0[:, 4]
+    x0 = np.clip(x0, lo, hi).astype(np.float32)
+    ndim = int(np.sum(lo < hi)) - 2
+    dev_x0 = torch.from_numpy(x0).cuda()
+    # device loop
+    S = tll.Sampler(L, nw, lo, hi, a=2.0, ndim=ndim, seed=W.SEED_BASE)
+    S.set_walkers(dev_x0)
+    S.run(args.warmup, keep_chain=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    chain, lpc, _ = S.run(nsteps, keep_chain=True)
+    e1.record()
+    e1.synchronize()
+    clk = clocks.stop()
+    dev_ms = e0.elapsed_time(e1)
+    _, _, steps, nacc, nprop = S.state()
+    S.close()
+    # host loop (the paper's arrangement)
+    p_host = torch.empty((nw // 2, L.nparam), dtype=torch.float32).pin_memory()
+    o_host = torch.empty(nw // 2, dtype=torch.float64).pin_memory()
+
+    def logp(Y):
+        p_host.numpy()[:] = Y
+        L.loglike_batch_host(p_host, o_host)
+        return o_host.numpy().copy()
+
+    x = x0.copy()
+    lp = np.full(nw, -np.inf)
+    for h in (0, 1):
+        sl_ = slice(h * nw // 2, (h + 1) * nw // 2)
+        lp[sl_] = logp(x[sl_])
+    hrng = np.random.Generator(np.random.PCG64(7))
+    for _ in range(args.warmup):
+        for h in (0, 1):
+            _host_stretch_half(x, h, hrng, 2.0, logp, lp, ndim, lo, hi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hacc = 0
+    for _ in range(nsteps):
+        for h in (0, 1):
+            hacc += _host_stretch_half(x, h, hrng, 2.0, logp, lp, ndim, lo, hi)
+    host_ms = (time.perf_counter() - t0) * 1e3
+    L.close()
+    evals = nsteps * nw
+    line = {
+        "metric": "log-likelihood evals/s inside a stretch-move sampler loop (csst100)",
+        "value": evals / (dev_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / nsteps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"csst100 lens, {nw} walkers (two half batches of {nw // 2} "
+                               f"per step), stretch move a = 2, box prior, ndim = {ndim}",
+                   "path": "device loop: tll_sampler_run, one synchronisation per run"},
+        "acceptance": nacc / max(nprop, 1),
+        "host_loop": {"evals_per_s": evals / (host_ms / 1e3), "ms_per_step": host_ms / nsteps,
+                      "acceptance": hacc / evals,
+                      "path": "numpy stretch move + tll_loglike_batch_host per half step "
+                              "(H2D params, D2H log L, synchronise)",
+                      "h2d_bytes_per_step": nw * L.nparam * 4, "d2h_bytes_per_step": nw * 8},
+        "e2e": {"value": evals / (host_ms / 1e3), "unit": UNIT,
+                "path": "host loop through tll_loglike_batch_host",
+                "h2d_bytes_per_step": nw * L.nparam * 4, "d2h_bytes_per_step": nw * 8},
+        "device_over_host": host_ms / dev_ms,
+        "clocks": clk, "gpu_launches": 8 * nsteps, "impl": "ours",
+    }
+    return line
+
+
 # ------------------------------------------------------------ ragged batch
 def run_ragged(args):
     """Many lenses of different sizes (sides {64..200}, PSF 11..31 px, 4x4
@@ -747,6 +864,8 @@ def main(argv=None):
         line = run_ragged(args)
     elif args.workload in ("slacs120", "mge120"):
         line = run_multi(args)
+    elif args.workload == "sampler":
+        line = run_sampler(args)
     else:
         line = run_ours(args)
     if line is not None:
