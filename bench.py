@@ -836,6 +836,11 @@ def run_reference(args):
     }
 
 
+def _multi_workloads():
+    from paper_2503_08586_gb300 import workloads as W
+    return W.MULTI_WORKLOADS
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -862,7 +867,7 @@ def main(argv=None):
         line = run_reference(args)
     elif args.workload == "ragged":
         line = run_ragged(args)
-    elif args.workload in ("slacs120", "mge120"):
+    elif args.workload in _multi_workloads():
         line = run_multi(args)
     elif args.workload == "sampler":
         line = run_sampler(args)

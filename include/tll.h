@@ -252,7 +252,7 @@ const char *tll_server_last_error(void);
  *   Same arguments, results and asynchrony as tll_loglike_batch.
  *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
  *     them into several calls).
- *   Scratch: a fixed 12 MiB array compiled into the library, held on every
+ *   Scratch: a fixed 20 MiB array compiled into the library, held on every
  *     GPU that loads it until the process exits.  All calls share it and it
  *     keeps the last call's contents; each call rewrites the part it reads
  *     before reading it.  Calls that overlap on the GPU (different streams,
@@ -438,7 +438,7 @@ int tll_lens_nparam(const tll_lens *L);
  * The amplitudes are the non-negative least-squares solution over all
  * columns (FNNLS, Bro & de Jong 1997, in FP64 per vector); log L as above.
  */
-#define TLL_MAX_COMPS 8
+#define TLL_MAX_COMPS 32
 enum { TLL_COMP_SERSIC = 0, TLL_COMP_GAUSSIAN = 1 };
 enum { TLL_PLANE_LENS = 0, TLL_PLANE_SOURCE = 1 };
 #define TLL_COMP_FREE_SCALE 1   /* scale read from the parameter vector */

@@ -516,7 +516,7 @@ int ora_max_threads(void)
 #define ORA_PLANE_SOURCE 1
 #define ORA_FREE_SCALE 1
 #define ORA_FREE_INDEX 2
-#define ORA_MAXC 16
+#define ORA_MAXC 64
 #define ORA_MHEAD 15
 
 typedef struct {

@@ -633,6 +633,17 @@ int nc_configure(tll_lens *L)
         const int psf_floats = L->sep ? 2 * L->K : L->K * L->K;
         S.smem = (size_t)((psf_floats + 3) & ~3) * sizeof(float);
     }
+    // the normal equations' pixel tiles reuse the dynamic shared memory:
+    // at least 256 pixels of every column per tile, and room for one FP64
+    // partial per thread after the last tile
+    {
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k));
+        const size_t tile = std::max((size_t)4 * ((L->nc * 257 + 3) & ~3) + 16 * 256 + 64,
+                                     (size_t)kThreads * sizeof(double));
+        const size_t cap = (size_t)(share - (long long)fa.sharedSizeBytes);
+        S.smem = std::max(S.smem, std::min(tile, cap));
+    }
     // the kernel is shared by every lens of its (s, K) class: allow the
     // most any of them can ask for, never less
     if (int rc = allow_dynamic_smem((const void *)k, D.optin)) return rc;
@@ -673,6 +684,7 @@ int run_batch_nc(tll_lens *L, const float *params, int B, double *out, cudaStrea
     LensDev d = lens_dev(L);
     d.img = L->nc_shape.img;
     d.band_rows = L->nc_shape.band_rows;
+    d.nc_smem = (int)L->nc_shape.smem;
     k_prologue_nc<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, d, L->md, L->bn_tab);
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
@@ -886,7 +898,7 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
 // array in the module instead, so the call itself allocates nothing; every
-// GPU that loads this library holds it (12 MiB) until the process exits.
+// GPU that loads this library holds it (20 MiB) until the process exits.
 constexpr int kNoAllocMaxB = 16384;
 static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
 
@@ -1792,19 +1804,27 @@ int tll_set_light(tll_lens *L, const tll_comp_t *comps, int ncomp)
         L->nparam = L->epl ? NPAR_EPL : NPAR;
         return TLL_OK;
     }
-    // trace schedule: lens-plane passes, then source-plane passes, each of
-    // up to kPassMax components in list order
+    // trace schedule: lens-plane passes, then source-plane passes; per plane
+    // the Gaussians in passes of up to kPassMax (lens plane) or kPassSrcG
+    // (source plane), then the Sersics in passes of up to kPassMix, each in
+    // list order
     for (int pl = 0; pl < 2; ++pl) {
         const int plane = pl == 0 ? PLANE_LENS : PLANE_SOURCE;
-        for (int c = 0; c < ncomp; ++c) {
-            if (md.plane[c] != plane) continue;
-            if (md.npass == 0 || md.pass_plane[md.npass - 1] != plane ||
-                md.pass_n[md.npass - 1] == kPassMax) {
-                md.pass_plane[md.npass] = plane;
-                md.pass_n[md.npass] = 0;
-                ++md.npass;
+        for (int kind = 0; kind < 2; ++kind) {   // 0: Gaussians, 1: Sersics
+            const int want = kind == 0 ? COMP_GAUSS : COMP_SERSIC;
+            const int cap = kind == 1 ? kPassMix : plane == PLANE_LENS ? kPassMax : kPassSrcG;
+            bool open = false;
+            for (int c = 0; c < ncomp; ++c) {
+                if (md.plane[c] != plane || md.type[c] != want) continue;
+                if (!open || md.pass_n[md.npass - 1] == cap) {
+                    md.pass_plane[md.npass] = plane;
+                    md.pass_gauss[md.npass] = kind == 0;
+                    md.pass_n[md.npass] = 0;
+                    ++md.npass;
+                    open = true;
+                }
+                md.pass_comp[md.npass - 1][md.pass_n[md.npass - 1]++] = c;
             }
-            md.pass_comp[md.npass - 1][md.pass_n[md.npass - 1]++] = c;
         }
     }
     md.nc = ncomp;

@@ -36,6 +36,7 @@ struct LensDev {
     // unmasked one through the PSF, else tlist = null (all npix pixels).
     const int *tlist;
     int ntrace;
+    int nc_smem;      // multi-column kernel: dynamic shared memory of the launch
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
     float tk[kMaxK * kMaxK];            // the full PSF (direct convolution)
 };

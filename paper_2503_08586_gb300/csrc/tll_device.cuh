@@ -44,7 +44,7 @@ enum : int {
     K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L, K_EC0,
     NCONST_USED = K_EC0 + kEplMaxN + 1
 };
-constexpr int NCONST = 192;
+constexpr int NCONST = 320;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
 
 // ------------------------------------------------------------------ b_n

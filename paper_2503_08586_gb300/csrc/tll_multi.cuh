@@ -13,26 +13,30 @@
 // 11).
 //
 // Per parameter vector (one persistent CTA at a time):
-//   1. trace passes: each pass evaluates up to kPassMax components of one
-//      plane on every subpixel (the deflection once per subpixel for a
-//      source pass), bins them, and writes the binned columns U[c] to the
-//      CTA's global slot (L2-resident);
+//   1. trace passes: each pass evaluates the components it lists (up to 4
+//      of any kind, or up to 8 Gaussians) of one plane on every subpixel (the
+//      deflection once per subpixel for a source pass), bins them, and
+//      writes the binned columns U[c] to the CTA's global slot (L2-resident);
 //   2. PSF: the columns two at a time through the compiled band convolution
 //      (or the generic one), blurred columns M[c] written to the slot;
-//   3. normal equations A = M^T W M, b = M^T W d: work items (row a, pixel
-//      chunk) over the warps, products exact as float pairs, double-float
-//      sums per lane, FP64 per item, FP64 over chunks;
-//   4. one thread: FNNLS on (A, b) in FP64, chi^2 = dWd - 2 s^T b + s^T A s,
-//      log L (Eq. 5).
+//   3. normal equations A = M^T W M, b = M^T W d: the blurred columns and
+//      the weights staged in shared memory a pixel tile at a time; thread
+//      (sum s, phase r) accumulates sum s over every R-th pixel of each tile
+//      in double-float (products exact as float pairs), then the R partials
+//      of each sum are added in FP64 in a fixed order;
+//   4. warp 0: FNNLS on (A, b) in FP64 with the passive-set Cholesky solves
+//      spread over the lanes, chi^2 = dWd - 2 s^T b + s^T A s, log L (Eq. 5).
 #pragma once
 
 #include "tll_kernels.cuh"
 
 namespace tll {
 
-constexpr int kMaxComps = 8;        // components (columns) per lens
-constexpr int kPassMax = 4;         // components traced per pass
-constexpr int kNcChunks = 8;        // pixel chunks per row of the normal equations
+constexpr int kMaxComps = 32;       // components (columns) per lens
+constexpr int kPassMax = 8;         // components of one trace pass (lens-plane Gaussians)
+constexpr int kPassSrcG = 6;        // ... source-plane Gaussians (the deflection's registers)
+constexpr int kPassMix = 4;         // ... a pass with Sersic components
+constexpr int kMaxPasses = 16;      // trace passes per vector
 constexpr int K_C0 = NCONST_USED;   // per-component constants, 6 floats each
 static_assert(K_C0 + 6 * kMaxComps <= NCONST, "constant block too small");
 
@@ -46,8 +50,10 @@ struct MultiDev {
     int nc, npar, npass;
     int type[kMaxComps], plane[kMaxComps], flags[kMaxComps];
     float scale[kMaxComps], index[kMaxComps];
-    int pass_plane[kMaxComps], pass_n[kMaxComps];
-    int pass_comp[kMaxComps][kPassMax];
+    // pass p: plane, component count, Gaussian-only (up to kPassMax
+    // components) or mixed (up to kPassMix), component indices
+    int pass_plane[kMaxPasses], pass_n[kMaxPasses], pass_gauss[kMaxPasses];
+    int pass_comp[kMaxPasses][kPassMax];
 };
 
 // Arguments of one multi-column launch.
@@ -122,27 +128,29 @@ __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, floa
     return sfu_ex2(fmaf(q4, omt, q5 * omt));
 }
 
-// One trace pass: the ncp (<= kPassMax) components listed in pc (their
-// constants cq[6 * k], Gaussian flags in gmask) of one plane on every
-// subpixel, binned by the mean, written to U + chan[k] * npix.
+// One trace pass: the ncp (<= NP) components listed in chan (their constants
+// cq[6 * k], Gaussian flags in gmask) of one plane on every subpixel, binned
+// by the mean, written to U + chan[k] * npix.  GAUSS: every component is a
+// Gaussian (only its first two constants are kept).
 // MODE: 0 / 1 / 2 source plane with the SIE fast / general form or the EPL
 // series (ec); 3 lens plane (no deflection).
 // skip: trace only the lens's listed pixels (as trace_image).
-template <int SUB, int MODE>
+template <int SUB, int MODE, int NP, bool GAUSS>
 __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                                            const float *cq, int gmask, int ncp,
                                            const int *chan, float *U, int tid, int nthr,
                                            const float *ec, bool skip)
 {
+    constexpr int NQ = GAUSS ? 2 : 6;
     const int sub = SUB > 0 ? SUB : L.sub;
     const int nx = L.nx, npix = L.npix;
     const int *list = skip ? L.tlist : nullptr;
     const int n = list ? L.ntrace : npix;
-    float q[kPassMax][6];
+    float q[NP][NQ];
 #pragma unroll
-    for (int k = 0; k < kPassMax; ++k)
+    for (int k = 0; k < NP; ++k)
 #pragma unroll
-        for (int e = 0; e < 6; ++e) q[k][e] = k < ncp ? cq[6 * k + e] : 0.0f;
+        for (int e = 0; e < NQ; ++e) q[k][e] = k < ncp ? cq[6 * k + e] : 0.0f;
     for (int t = tid; t < n; t += nthr) {
         const int pix = list ? list[t] : t;
         const int i = pix / nx, j = pix - i * nx;
@@ -153,9 +161,9 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
             nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
             nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
         }
-        float acc[kPassMax];
+        float acc[NP];
 #pragma unroll
-        for (int k = 0; k < kPassMax; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < NP; ++k) acc[k] = 0.0f;
 #pragma unroll 1
         for (int a = 0; a < sub; ++a) {
             const RowTerms r = row_terms(v, fi0 + (float)a);
@@ -184,205 +192,234 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                     }
                     const float R2 = fmaf(X, X, Y * Y);
 #pragma unroll
-                    for (int k = 0; k < kPassMax; ++k)
-                        if (k < ncp)
-                            acc[k] += comp_value((gmask >> k) & 1, R2, q[k][0], q[k][1],
-                                                 q[k][2], q[k][3], q[k][4], q[k][5]);
+                    for (int k = 0; k < NP; ++k) {
+                        if (k < ncp) {
+                            if constexpr (GAUSS)
+                                acc[k] += sfu_ex2(fmaf(q[k][0], R2, q[k][1] * R2));
+                            else
+                                acc[k] += comp_value((gmask >> k) & 1, R2, q[k][0], q[k][1],
+                                                     q[k][2], q[k][3], q[k][4], q[k][5]);
+                        }
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < kPassMax; ++k)
+        for (int k = 0; k < NP; ++k)
             if (k < ncp) U[(size_t)chan[k] * npix + pix] = acc[k] * L.inv_s2;
     }
 }
 
 // ----------------------------------------------------- normal equations
-// Row a of the normal equations over pixels [p0, p1): lane-strided, each
-// lane holds double-float sums of w m_a m_e (e = a .. nc-1) and w d m_a
-// (products exact as float pairs, as accum_pixel), reduced over the warp;
-// lane 0 returns them in FP64 to out[0 .. nc - a] (the last is b_a).
-__device__ __forceinline__ void nc_row_sums(const LensDev &L, const float *M, int nc, int a,
-                                            int p0, int p1, int lane, double *out)
+// Shared-memory tile of the sums: pixels [p0, p0 + T) of every blurred
+// column (row stride T + 1, odd, so the lanes of a warp -- consecutive
+// columns e at one pixel -- hit distinct banks) and their weights.
+__host__ __device__ inline int nc_tile_pixels(int nc, long long smem_bytes)
 {
-    const int npix = L.npix;
-    float acc[2 * (kMaxComps + 1)];
-#pragma unroll
-    for (int k = 0; k < 2 * (kMaxComps + 1); ++k) acc[k] = 0.0f;
-    const float *Ma = M + (size_t)a * npix;
-    for (int pix = p0 + lane; pix < p1; pix += 32) {
-        const float4 wp = L.wpack[pix];
-        const float ma = Ma[pix];
-        const float p1v = wp.x * ma;
-        float e1 = fmaf(wp.x, ma, -p1v);
-        e1 = fmaf(wp.y, ma, e1);
-#pragma unroll
-        for (int k = 0; k < kMaxComps; ++k) {
-            if (a + k < nc) {
-                const float me = M[(size_t)(a + k) * npix + pix];
-                const float p = p1v * me;
-                float e = fmaf(p1v, me, -p);
-                e = fmaf(e1, me, e);
-                df_acc(acc[2 * k], acc[2 * k + 1], p, e);
+    // 4 roundup4(nc (T + 1)) + 16 T <= smem_bytes, T a multiple of 32
+    const long long t = (smem_bytes - 4LL * nc - 16) / (4LL * nc + 16);
+    return (int)(t < 32 ? 32 : (t & ~31LL) > 4096 ? 4096 : (t & ~31LL));
+}
+
+// Sum s of the normal equations (s < nc(nc+1)/2: A[a][e], e >= a, row by
+// row; then b_a for a = s - nc(nc+1)/2) accumulated by this thread over the
+// pixels r, r + R, ... of every tile, in double-float (products exact as
+// float pairs); returns the thread's FP64 partial.  Every thread of the CTA
+// takes part in the tile loads (a < 0: no sum).
+__device__ __forceinline__ double nc_tile_sums(const LensDev &L, const float *M, int nc, int a,
+                                               int e, bool bsum, int r, int R, float *tile,
+                                               int T, int tid, int nthr)
+{
+    const int npix = L.npix, TS = T + 1;
+    float4 *wt = reinterpret_cast<float4 *>(tile + ((nc * TS + 3) & ~3));
+    float hi = 0.0f, lo = 0.0f;
+    for (int p0 = 0; p0 < npix; p0 += T) {
+        const int n = min(T, npix - p0);
+        for (int c = 0; c < nc; ++c)
+            for (int i = tid; i < n; i += nthr) tile[c * TS + i] = M[(size_t)c * npix + p0 + i];
+        for (int i = tid; i < n; i += nthr) wt[i] = L.wpack[p0 + i];
+        __syncthreads();
+        if (a >= 0) {
+            const float *ca = tile + a * TS, *ce = tile + (bsum ? a : e) * TS;
+            for (int i = r; i < n; i += R) {
+                const float4 w = wt[i];
+                const float ma = ca[i];
+                float p, er;
+                if (bsum) {
+                    p = w.z * ma;
+                    er = fmaf(w.z, ma, -p);
+                    er = fmaf(w.w, ma, er);
+                } else {
+                    const float me = ce[i];
+                    const float p1 = w.x * ma;
+                    float e1 = fmaf(w.x, ma, -p1);
+                    e1 = fmaf(w.y, ma, e1);
+                    p = p1 * me;
+                    er = fmaf(p1, me, -p);
+                    er = fmaf(e1, me, er);
+                }
+                df_acc(hi, lo, p, er);
             }
         }
-        const float p = wp.z * ma;
-        float e = fmaf(wp.z, ma, -p);
-        e = fmaf(wp.w, ma, e);
-        df_acc(acc[2 * kMaxComps], acc[2 * kMaxComps + 1], p, e);
+        __syncthreads();
     }
-#pragma unroll
-    for (int k = 0; k <= kMaxComps; ++k) {
-        if (k == kMaxComps || a + k < nc) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oh = __shfl_xor_sync(0xffffffffu, acc[2 * k], o);
-                const float ol = __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], o);
-                df_add(acc[2 * k], acc[2 * k + 1], oh, ol);
-            }
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kMaxComps; ++k)
-            if (a + k < nc) out[k] = (double)acc[2 * k] + (double)acc[2 * k + 1];
-        out[nc - a] = (double)acc[2 * kMaxComps] + (double)acc[2 * kMaxComps + 1];
-    }
+    return (double)hi + (double)lo;
 }
 
 // -------------------------------------------------------------- FNNLS
-// Solve G z = r for the passive columns listed in idx[0..k) of the n x n
-// matrix A (row-major): Cholesky G = R^T R, R upper triangular, stored
-// in place in F.  Returns false if a pivot is not positive.
-__device__ inline bool nc_passive_solve(const double *A, const double *b, int n,
-                                        const int *idx, int k, double *F, double *z)
+// Warp-cooperative least squares on the passive set (mask bit i set:
+// column i free) of the n x n system A x = b (row-major in shared memory,
+// n <= 32): lane p owns row p of the compacted k x k matrix G in F (stride
+// kMaxComps + 1); Cholesky G = L L^T column by column (the pivot lane takes
+// the square root, every lane below it its own entry), then the two
+// triangular solves with the solved entry broadcast by shuffle.  s (all
+// lanes, registers: lane i holds s_i) gets the solution on the passive
+// set and 0 elsewhere.  Returns false (all lanes) if a pivot is not
+// positive.
+__device__ inline bool nc_warp_solve(const double *A, const double *b, int n, unsigned P,
+                                     double *F, int lane, double &s)
 {
-    for (int i = 0; i < k; ++i) {
-        for (int j = i; j < k; ++j) {
-            double v = A[idx[i] * n + idx[j]];
-            for (int t = 0; t < i; ++t) v = fma(-F[t * kMaxComps + i], F[t * kMaxComps + j], v);
-            if (j == i) {
-                if (!(v > 0.0)) return false;
-                F[i * kMaxComps + i] = sqrt(v);
-            } else {
-                F[i * kMaxComps + j] = v / F[i * kMaxComps + i];
-            }
+    const bool mine = lane < n && (P >> lane & 1u);
+    const int k = __popc(P);
+    const int p = __popc(P & ((1u << lane) - 1u));   // my compacted position
+    // compacted rows: G[p][q] = A[lane][col of q]
+    if (mine) {
+        int q = 0;
+        for (int c = 0; c < n; ++c)
+            if (P >> c & 1u) F[p * (kMaxComps + 1) + q++] = A[lane * n + c];
+    }
+    __syncwarp();
+    const double bp = mine ? b[lane] : 0.0;
+    // Cholesky (lower): row p of L overwrites row p of G
+    bool ok = true;
+    for (int j = 0; j < k; ++j) {
+        double v = 0.0;
+        if (mine && p >= j) {
+            v = F[p * (kMaxComps + 1) + j];
+            for (int t = 0; t < j; ++t)
+                v = fma(-F[p * (kMaxComps + 1) + t], F[j * (kMaxComps + 1) + t], v);
         }
+        // the pivot first: from the lane holding compacted row j
+        const int src = __ffs(__ballot_sync(0xffffffffu, mine && p == j)) - 1;
+        const double piv2 = __shfl_sync(0xffffffffu, v, src);
+        if (!(piv2 > 0.0)) { ok = false; break; }
+        const double piv = sqrt(piv2);
+        if (mine && p > j) F[p * (kMaxComps + 1) + j] = v / piv;
+        if (mine && p == j) F[p * (kMaxComps + 1) + j] = piv;
+        __syncwarp();
     }
-    for (int i = 0; i < k; ++i) {
-        double v = b[idx[i]];
-        for (int t = 0; t < i; ++t) v = fma(-F[t * kMaxComps + i], z[t], v);
-        z[i] = v / F[i * kMaxComps + i];
+    if (!ok) return false;
+    // L y = b_P (forward), then L^T z = y (backward)
+    double y = bp;
+    for (int j = 0; j < k; ++j) {
+        const int src = __ffs(__ballot_sync(0xffffffffu, mine && p == j)) - 1;
+        double yj = 0.0;
+        if (mine && p == j) yj = y / F[p * (kMaxComps + 1) + p];
+        yj = __shfl_sync(0xffffffffu, yj, src);
+        if (mine && p == j) y = yj;
+        if (mine && p > j) y = fma(-F[p * (kMaxComps + 1) + j], yj, y);
     }
-    for (int i = k - 1; i >= 0; --i) {
-        double v = z[i];
-        for (int t = i + 1; t < k; ++t) v = fma(-F[i * kMaxComps + t], z[t], v);
-        z[i] = v / F[i * kMaxComps + i];
+    double z = y;
+    for (int j = k - 1; j >= 0; --j) {
+        const int src = __ffs(__ballot_sync(0xffffffffu, mine && p == j)) - 1;
+        double zj = 0.0;
+        if (mine && p == j) zj = z / F[p * (kMaxComps + 1) + p];
+        zj = __shfl_sync(0xffffffffu, zj, src);
+        if (mine && p == j) z = zj;
+        // row j of L^T is column j of L: L[q][j] for q > j sits in row q
+        const double lij = (mine && p < j) ? F[j * (kMaxComps + 1) + p] : 0.0;
+        if (mine && p < j) z = fma(-lij, zj, z);
     }
-    return true;
-}
-
-// Least squares on the passive set (mask bit i set: column i free):
-// s = A_PP^{-1} b_P there, 0 elsewhere.
-__device__ inline bool nc_solve_set(const double *A, const double *b, int n, unsigned mask,
-                                    double *s, double *F)
-{
-    int idx[kMaxComps];
-    double z[kMaxComps];
-    int k = 0;
-    for (int i = 0; i < n; ++i) {
-        s[i] = 0.0;
-        if (mask >> i & 1u) idx[k++] = i;
-    }
-    if (k == 0) return true;
-    if (!nc_passive_solve(A, b, n, idx, k, F, z)) return false;
-    for (int t = 0; t < k; ++t) s[idx[t]] = z[t];
+    s = mine ? z : 0.0;
+    __syncwarp();
     return true;
 }
 
 // FNNLS (Bro & de Jong 1997): the Lawson-Hanson active-set method on the
-// normal equations A x = b, x >= 0 (one thread, FP64, n <= kMaxComps).
-// All columns start at zero; while a zero column has gradient
-// g = b - A x above tol = 10 eps ||A||_1 n, the largest one is freed and
-// the free set's least-squares solution s is taken, stepping back to the
-// feasible boundary (freed columns that reach zero return to the zero set)
-// while some free s_i <= 0.  A column whose own least-squares value comes
-// out non-positive on entry is passed over until x next changes.  At most
-// 30 n steps.
-__device__ inline void nc_fnnls(const double *A, const double *b, int n, double *x)
+// normal equations A x = b, x >= 0, run by one warp (lane i holds x_i, the
+// gradient g_i and the solution s_i; n <= 32).  All columns start at zero;
+// while a zero column has gradient g = b - A x above tol = 10 eps ||A||_1 n,
+// the largest one is freed and the free set's least-squares solution s is
+// taken, stepping back to the feasible boundary (freed columns that reach
+// zero return to the zero set) while some free s_i <= 0.  A column whose own
+// least-squares value comes out non-positive on entry is passed over until x
+// next changes.  At most 30 n steps.  Lane i returns x_i.
+__device__ inline double nc_fnnls_warp(const double *A, const double *b, int n, double *F,
+                                       int lane)
 {
-    double F[kMaxComps * kMaxComps], s[kMaxComps], g[kMaxComps];
-    double norm1 = 0.0;
-    for (int j = 0; j < n; ++j) {
-        double cs = 0.0;
-        for (int i = 0; i < n; ++i) cs += fabs(A[i * n + j]);
-        norm1 = fmax(norm1, cs);
-    }
-    const double tol = 10.0 * 2.220446049250313e-16 * norm1 * n;
+    const bool in = lane < n;
+    double cs = 0.0;
+    if (in)
+        for (int i = 0; i < n; ++i) cs += fabs(A[i * n + lane]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+    const double tol = 10.0 * 2.220446049250313e-16 * cs * n;
     unsigned P = 0u, skip = 0u;
-    for (int i = 0; i < n; ++i) {
-        x[i] = 0.0;
-        g[i] = b[i];
-    }
+    double x = 0.0, g = in ? b[lane] : 0.0, s = 0.0;
     for (int step = 0; step < 30 * n; ++step) {
-        int j = -1;
-        double gmax = tol;
-        for (int i = 0; i < n; ++i)
-            if (!((P | skip) >> i & 1u) && g[i] > gmax) {
-                gmax = g[i];
-                j = i;
-            }
-        if (j < 0) return;
-        P |= 1u << j;
-        if (!nc_solve_set(A, b, n, P, s, F) || !(s[j] > 0.0)) {
-            P &= ~(1u << j);
-            skip |= 1u << j;
+        // the largest gradient among zero, not-skipped columns (ties: lowest index)
+        double gv = (in && !((P | skip) >> lane & 1u) && g > tol) ? g : -1.0;
+        int gi = gv > 0.0 ? lane : 64;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, gv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, gi, o);
+            if (ov > gv || (ov == gv && oi < gi)) { gv = ov; gi = oi; }
+        }
+        if (gi >= 64) break;
+        P |= 1u << gi;
+        bool ok = nc_warp_solve(A, b, n, P, F, lane, s);
+        const double sj = __shfl_sync(0xffffffffu, s, gi);
+        if (!ok || !(sj > 0.0)) {
+            P &= ~(1u << gi);
+            skip |= 1u << gi;
             continue;
         }
         for (int inner = 0; inner <= n; ++inner) {
-            double alpha = 2.0;
-            int kmin = -1;
-            for (int i = 0; i < n; ++i)
-                if ((P >> i & 1u) && s[i] <= 0.0) {
-                    const double t = x[i] / (x[i] - s[i]);
-                    if (t < alpha) {
-                        alpha = t;
-                        kmin = i;
-                    }
-                }
-            if (kmin < 0) break;
-            for (int i = 0; i < n; ++i) x[i] = fma(alpha, s[i] - x[i], x[i]);
-            x[kmin] = 0.0;
-            for (int i = 0; i < n; ++i)
-                if ((P >> i & 1u) && x[i] <= 0.0) {
-                    P &= ~(1u << i);
-                    x[i] = 0.0;
-                }
-            if (!nc_solve_set(A, b, n, P, s, F)) return;
+            const bool neg = in && (P >> lane & 1u) && s <= 0.0;
+            double al = neg ? x / (x - s) : 2.0;
+            int ai = neg ? lane : 64;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, al, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
+                if (ov < al || (ov == al && oi < ai)) { al = ov; ai = oi; }
+            }
+            if (ai >= 64) break;
+            if (in) x = fma(al, s - x, x);
+            if (lane == ai) x = 0.0;
+            const unsigned drop = __ballot_sync(0xffffffffu, in && (P >> lane & 1u) && x <= 0.0);
+            P &= ~drop;
+            if (drop >> lane & 1u) x = 0.0;
+            if (!nc_warp_solve(A, b, n, P, F, lane, s)) return x;
         }
         skip = 0u;
-        for (int i = 0; i < n; ++i) x[i] = s[i];
-        for (int i = 0; i < n; ++i) {
-            double v = b[i];
-            for (int k = 0; k < n; ++k) v = fma(-A[i * n + k], x[k], v);
-            g[i] = v;
+        x = s;
+        // g = b - A x: lane i needs row i of A and every x_k
+        double v = in ? b[lane] : 0.0;
+        for (int c = 0; c < n; ++c) {
+            const double xc = __shfl_sync(0xffffffffu, x, c);
+            if (in) v = fma(-A[lane * n + c], xc, v);
         }
+        g = v;
     }
+    return x;
 }
 
 // --------------------------------------------------------------- kernel
-// Shared memory: static -- partial sums, the normal equations, the
-// components' constants, the EPL series; dynamic -- K > 0: the padded band
-// buffer of the compiled convolution (2 channels x (band_rows + 2h + kCR)
-// rows x W); K == 0: the PSF taps of the generic convolution.
+// Shared memory: static -- partial sums, the normal equations, the Cholesky
+// work space, the components' constants, the EPL series; dynamic -- K > 0:
+// the padded band buffer of the compiled convolution (2 channels x
+// (band_rows + 2h + kCR) rows x W); K == 0: the PSF taps of the generic
+// convolution.
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads)
 k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev M,
              const __grid_constant__ NcArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double sPart[kMaxComps * kNcChunks * (kMaxComps + 1)];
     __shared__ double sA[kMaxComps * kMaxComps], sb[kMaxComps];
+    __shared__ double sF[kMaxComps * (kMaxComps + 1)];
     __shared__ float sq[kMaxComps * 6];
     __shared__ float sepl[kEplMaxN + 1];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -398,7 +435,7 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
         for (int t = tid; t < nc * npix; t += nthr) U[t] = 0.0f;
     __syncthreads();
     const bool skip = R.wr_res == nullptr;   // model columns: every pixel
-    const int nch = max(1, min(kNcChunks, (2 * nwarp + nc - 1) / nc));
+    const int T = nc_tile_pixels(nc, (long long)L.nc_smem);
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
         if (kc[K_VALID] == 0.0f) {
@@ -426,17 +463,32 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
                 if (k < ncp && M.type[c] == COMP_GAUSS) gmask |= 1 << k;
             }
             const int *chan = M.pass_comp[ps];
-            if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-            else if (v.epl)
-                trace_pass<SUB, 2>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-            else if (v.fast)
-                trace_pass<SUB, 0>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-            else
-                trace_pass<SUB, 1>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+            if (M.pass_gauss[ps]) {
+                if (M.pass_plane[ps] == PLANE_LENS)
+                    trace_pass<SUB, 3, kPassMax, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else if (v.epl)
+                    trace_pass<SUB, 2, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else if (v.fast)
+                    trace_pass<SUB, 0, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else
+                    trace_pass<SUB, 1, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+            } else {
+                if (M.pass_plane[ps] == PLANE_LENS)
+                    trace_pass<SUB, 3, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else if (v.epl)
+                    trace_pass<SUB, 2, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else if (v.fast)
+                    trace_pass<SUB, 0, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+                else
+                    trace_pass<SUB, 1, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
+            }
         }
         __syncthreads();
-        // 2. PSF, two columns at a time (an odd last column pairs with itself)
+        // 2. PSF, two columns at a time (an odd last column pairs with itself);
+        //    the sums of the previous vector used the dynamic shared memory,
+        //    so its zero halos (or the PSF taps) are set up again first
+        setup_lens(L, spsf, tid, nthr);
+        __syncthreads();
         for (int c = 0; c < nc; c += 2) {
             const int c2 = min(c + 1, nc - 1);
             const float *Il = U + (size_t)c * npix, *Is = U + (size_t)c2 * npix;
@@ -475,42 +527,67 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
             }
         }
         __syncthreads();
-        // 3. normal equations: items (row a, chunk) over the warps
-        const int per = (npix + nch - 1) / nch;
-        for (int item = warp; item < nc * nch; item += nwarp) {
-            const int a = item / nch, ch = item - a * nch;
-            const int p0 = ch * per, p1 = min(npix, p0 + per);
-            nc_row_sums(L, Mb, nc, a, p0, p1, lane,
-                        sPart + (size_t)(a * kNcChunks + ch) * (kMaxComps + 1));
-        }
-        __syncthreads();
-        if (tid < nc * (nc + 1)) {   // sum over chunks; A symmetric
-            const int a = tid / (nc + 1), k = tid - a * (nc + 1);
-            if (k >= a || k == nc) {
-                const int kk = k == nc ? nc - a : k - a;
-                double s = 0.0;
-                for (int ch = 0; ch < nch; ++ch)
-                    s += sPart[(size_t)(a * kNcChunks + ch) * (kMaxComps + 1) + kk];
-                if (k == nc) sb[a] = s;
-                else { sA[a * nc + k] = s; sA[k * nc + a] = s; }
+        // 3. normal equations through shared-memory tiles (the dynamic
+        //    shared memory is free again once the convolution is done): thread
+        //    (s, r) takes sum s (see nc_tile_sums) over pixel phase r of RP;
+        //    the FP64 partials go to the same space after the last tile
+        {
+            const int nA = nc * (nc + 1) / 2, S = nA + nc;
+            const int RP = max(1, nthr / S);
+            const int sr = tid / S, sidx = tid - sr * S;
+            int sa = -1, se = 0;
+            const bool sbsum = sidx >= nA;
+            if (tid < S * RP) {
+                if (sbsum) {
+                    sa = sidx - nA;
+                } else {   // row-major upper triangle
+                    int rem = sidx, a = 0;
+                    while (rem >= nc - a) {
+                        rem -= nc - a;
+                        ++a;
+                    }
+                    sa = a;
+                    se = a + rem;
+                }
+            }
+            const double part = nc_tile_sums(L, Mb, nc, sa, se, sbsum, sr, RP, spsf, T, tid, nthr);
+            double *parts = reinterpret_cast<double *>(spsf);   // [RP][S]
+            if (sa >= 0) parts[tid] = part;
+            __syncthreads();
+            for (int t = tid; t < S; t += nthr) {
+                double sum = 0.0;
+                for (int rr = 0; rr < RP; ++rr) sum += parts[rr * S + t];
+                if (t >= nA) {
+                    sb[t - nA] = sum;
+                } else {
+                    int rem = t, a = 0;
+                    while (rem >= nc - a) {
+                        rem -= nc - a;
+                        ++a;
+                    }
+                    const int e = a + rem;
+                    sA[a * nc + e] = sum;
+                    sA[e * nc + a] = sum;
+                }
             }
         }
         __syncthreads();
-        // 4. amplitudes and log L
-        if (tid == 0) {
-            double x[kMaxComps];
-            nc_fnnls(sA, sb, nc, x);
-            double chi2 = L.dWd;
-            for (int i = 0; i < nc; ++i) {
-                double Ax = 0.0;
-                for (int k = 0; k < nc; ++k) Ax = fma(sA[i * nc + k], x[k], Ax);
-                chi2 += x[i] * (Ax - 2.0 * sb[i]);
+        // 4. amplitudes (warp 0) and log L
+        if (warp == 0) {
+            const double x = nc_fnnls_warp(sA, sb, nc, sF, lane);
+            double Ax = 0.0;
+            for (int k = 0; k < nc; ++k) {
+                const double xk = __shfl_sync(0xffffffffu, x, k);
+                if (lane < nc) Ax = fma(sA[lane * nc + k], xk, Ax);
             }
-            const double ll = -0.5 * chi2 + L.lognorm;
-            R.out[b] = ll;
+            double term = lane < nc ? x * (Ax - 2.0 * sb[lane]) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+            const double ll = -0.5 * (L.dWd + term) + L.lognorm;
+            if (lane == 0) R.out[b] = ll;
             if (R.wr_res) {
-                for (int i = 0; i < nc; ++i) R.wr_res[i] = x[i];
-                R.wr_res[nc] = ll;
+                if (lane < nc) R.wr_res[lane] = x;
+                if (lane == 0) R.wr_res[nc] = ll;
             }
         }
         __syncthreads();

@@ -43,7 +43,7 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_sampler_state", "tll_sampler_destroy")
 
 # Multi-component light (tll_set_light).
-MAX_COMPS = 8
+MAX_COMPS = 32
 COMP_SERSIC, COMP_GAUSSIAN = 0, 1
 PLANE_LENS, PLANE_SOURCE = 0, 1
 COMP_FREE_SCALE, COMP_FREE_INDEX = 1, 2

@@ -25,6 +25,9 @@ Sersic lens light tied to the mass centre, Sersic source):
               PSF (beta = 3, FWHM 0.1"), 4 columns
   mge120      the same image with a Gaussian expansion: 4 lens-plane and 4
               source-plane Gaussians of fixed, log-spaced widths (8 columns)
+  mge32       a full Gaussian expansion on the csst100 image geometry: 20
+              lens-plane Gaussians (sigma 0.03" - 2.5") and 12 source-plane
+              Gaussians (0.01" - 0.6"), 32 columns
 
 Seeds: workload k uses numpy PCG64 seeded with 2503085860 + k.
 """
@@ -155,6 +158,11 @@ MGE_COMPS = (
      for s in np.geomspace(0.05, 1.2, 4)]
     + [dict(type="gauss", plane="source", free_scale=False, scale=float(s))
        for s in np.geomspace(0.02, 0.4, 4)])
+MGE32_COMPS = (
+    [dict(type="gauss", plane="lens", free_scale=False, scale=float(s))
+     for s in np.geomspace(0.03, 2.5, 20)]
+    + [dict(type="gauss", plane="source", free_scale=False, scale=float(s))
+       for s in np.geomspace(0.01, 0.6, 12)])
 MULTI_HEAD = 15
 
 
@@ -180,6 +188,8 @@ MULTI_WORKLOADS = {
                           SLACS_COMPS, seed_offset=7),
     "mge120": MultiSpec("mge120", 120, 120, 0.05, 4, 21, "moffat", 0.10, 2048,
                         MGE_COMPS, seed_offset=8),
+    "mge32": MultiSpec("mge32", 100, 100, 0.074, 4, 21, "gaussian", 0.15, 1024,
+                       MGE32_COMPS, seed_offset=9),
 }
 
 

@@ -27,6 +27,14 @@ MIXED = [dict(type="sersic", plane="lens", free_index=True),
          dict(type="sersic", plane="source", free_index=True),
          dict(type="gauss", plane="source")]     # 7 columns, two lens passes
 
+# 20 columns: 3 Sersic passes per plane mixed with Gaussian passes
+MANY = ([dict(type="sersic", plane="lens", index=float(n)) for n in (0.7, 1.0, 1.6, 2.5, 4.0, 6.0)]
+        + [dict(type="gauss", plane="lens", free_scale=False, scale=float(sg))
+           for sg in np.geomspace(0.05, 1.5, 5)]
+        + [dict(type="sersic", plane="source", index=float(n), free_index=(n == 1.0))
+           for n in (0.8, 1.0, 2.0, 3.0, 4.5)]
+        + [dict(type="gauss", plane="source") for _ in range(4)])
+
 # (name, ny, nx, pixel scale, s, PSF side, PSF kind, components, mass)
 CASES = [
     ("slacs_direct", 48, 40, 0.05, 4, 9, "moffat", W.SLACS_COMPS, "sie"),
@@ -34,6 +42,8 @@ CASES = [
     ("mixed_odd", 36, 36, 0.07, 3, 7, "moffat", MIXED, "sie"),
     ("mge_generic", 30, 34, 0.08, 4, 33, "moffat", W.MGE_COMPS, "sie"),
     ("slacs_epl", 40, 40, 0.06, 4, 13, "gaussian", W.SLACS_COMPS, "epl"),
+    ("mge32", 40, 36, 0.07, 3, 9, "gaussian", W.MGE32_COMPS, "sie"),
+    ("many20_generic", 34, 30, 0.08, 2, 33, "moffat", MANY, "sie"),
 ]
 
 
@@ -186,13 +196,13 @@ def test_multi_refused_by_batcher_and_variants(cases):
     assert lib.tll_set_light(g.handle, arr, 1) == tll.EINVAL
     arr = (tll.Comp * 1)(tll.Comp(0, 0, 0, 0.5, 12.0))   # fixed index out of range
     assert lib.tll_set_light(g.handle, arr, 1) == tll.EINVAL
-    arr = (tll.Comp * 9)(*[tll.comp("gauss", "lens")] * 9)
-    assert lib.tll_set_light(g.handle, arr, 9) == tll.EINVAL
+    arr = (tll.Comp * 33)(*[tll.comp("gauss", "lens")] * 33)
+    assert lib.tll_set_light(g.handle, arr, 33) == tll.EINVAL
     assert g.nparam == o.nparam          # the lens kept its model
     g.close()
 
 
-@pytest.mark.parametrize("name", ["slacs120", "mge120"])
+@pytest.mark.parametrize("name", ["slacs120", "mge120", "mge32"])
 def test_multi_full_size_sampled(name):
     """The bench workloads at full size, in the launch configuration the
     bench times (the whole batch in one call): 48 sampled vectors (the

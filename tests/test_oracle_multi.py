@@ -56,7 +56,7 @@ def test_fnnls_vs_brute_force(n):
         assert np.max(np.abs(x - xb)) <= 1e-7 * max(1.0, np.max(np.abs(xb)))
 
 
-@pytest.mark.parametrize("n", [2, 4, 8, 12, 16])
+@pytest.mark.parametrize("n", [2, 4, 8, 12, 16, 32, 48])
 def test_fnnls_vs_library_nnls_and_kkt(n):
     """scipy.optimize.nnls (Lawson-Hanson on Z itself) gives the same
     optimum; the KKT conditions hold: x >= 0, gradient b - A x <= 0 on the
