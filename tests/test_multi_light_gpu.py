@@ -14,8 +14,8 @@ import oracle
 from paper_2503_08586_gb300 import build, tll
 from paper_2503_08586_gb300 import workloads as W
 
-from test_parity_gpu import (PIX_FLOOR, PIX_REL, POS_ERR, _CHI2_TRUTH, _lens_consts,
-                             _ll_ok, _pix_ok)
+from test_parity_gpu import (PIX_FLOOR, PIX_REL, POS_ERR, POS_ERR_SRC, _CHI2_TRUTH,
+                             _lens_consts, _ll_ok, _pix_ok)
 
 pytestmark = pytest.mark.gpu
 
@@ -86,15 +86,17 @@ def _gpu(sl, comps, mass="sie", **kw):
 
 def _allowance(o, p, blurred):
     """Per-pixel allowance per column: the oracle column's change when both
-    planes' centres ([9], [10] and [13], [14]) move by +-POS_ERR."""
+    planes' centres ([9], [10] by +-POS_ERR and [13], [14] by +-POS_ERR_SRC)
+    move."""
     def cols(q):
         return o.model(q)[1] if blurred else o.unblurred(q)
     p0 = np.asarray(p, np.float64)
     base = cols(p0)
     allow = np.zeros_like(base)
-    for dx, dy in ((POS_ERR, 0), (-POS_ERR, 0), (0, POS_ERR), (0, -POS_ERR)):
+    for sx, sy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
         q = p0.copy()
-        q[9] += dx; q[10] += dy; q[13] += dx; q[14] += dy
+        q[9] += sx * POS_ERR; q[10] += sy * POS_ERR
+        q[13] += sx * POS_ERR_SRC; q[14] += sy * POS_ERR_SRC
         allow = np.maximum(allow, np.abs(cols(q) - base))
     return allow
 

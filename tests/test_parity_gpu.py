@@ -6,11 +6,16 @@ Tolerances (FP32 forward model, FP64 likelihood):
                 column.  The floor covers Sersic tails, where the FP32
                 exponent's rounding (|argument| * 2^-24) exceeds 1e-5
                 relative.  a_i is the pixel's change in the oracle when the
-                light centres move by POS_ERR = 2e-7 arcsec (1-2 float ulps
-                of an image-plane coordinate, the scale of FP32 position
-                rounding): negligible except at a Sersic cusp (n > 1, where
-                dI/dr ~ r^(1/n - 1) diverges), whose pixel no FP32
-                evaluation can bring within a relative gate.
+                image-plane light centre moves by POS_ERR = 2e-7 arcsec (1-2
+                float ulps of an image-plane coordinate, the scale of FP32
+                position rounding) and the source centre by POS_ERR_SRC =
+                4e-7 arcsec (the source-plane position beta = theta - alpha
+                is the difference of two ~1-2 arcsec quantities, so it
+                carries a couple of their ulps, ~2.5e-7, plus the
+                deflection's own rounding, ~1e-7): negligible except at a
+                Sersic cusp (n > 1, where dI/dr ~ r^(1/n - 1) diverges) or
+                on a source narrower than a pixel, where no FP32 evaluation
+                can bring the pixel within a relative gate.
   log L         three regions, by the oracle's chi^2 and the chi^2 of the
                 lens's true parameters (chi2_t):
                 - posterior bulk, chi^2 <= chi2_t + 50, where a converged
@@ -47,7 +52,7 @@ from paper_2503_08586_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-PIX_REL, PIX_FLOOR, POS_ERR = 1e-5, 1e-7, 2e-7
+PIX_REL, PIX_FLOOR, POS_ERR, POS_ERR_SRC = 1e-5, 1e-7, 2e-7, 4e-7
 LL_ABS, EPS_M, EPS_NEAR, BULK_DCHI2 = 1e-3, 1e-6, 2e-7, 50.0
 
 
@@ -60,8 +65,9 @@ def _lib():
 
 def _pix_allowance(o, params, blurred, mode=1):
     """Per-pixel allowance a_i for both columns (lens, source): the largest
-    change of the oracle's column when the lens-light centre ([12], [13]) and
-    the source centre ([19], [20]) move by +-POS_ERR in x and in y."""
+    change of the oracle's column when the lens-light centre ([12], [13])
+    moves by +-POS_ERR and the source centre ([19], [20]) by +-POS_ERR_SRC,
+    in x and in y."""
     p0 = np.asarray(params, np.float64)
 
     def cols(p):
@@ -72,9 +78,10 @@ def _pix_allowance(o, params, blurred, mode=1):
 
     base = cols(p0)
     allow = [np.zeros_like(base[0]), np.zeros_like(base[1])]
-    for dx, dy in ((POS_ERR, 0), (-POS_ERR, 0), (0, POS_ERR), (0, -POS_ERR)):
+    for sx, sy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
         p = p0.copy()
-        p[12] += dx; p[13] += dy; p[19] += dx; p[20] += dy
+        p[12] += sx * POS_ERR; p[13] += sy * POS_ERR
+        p[19] += sx * POS_ERR_SRC; p[20] += sy * POS_ERR_SRC
         for c, (a, b) in enumerate(zip(cols(p), base)):
             allow[c] = np.maximum(allow[c], np.abs(a - b))
     return allow
