@@ -444,6 +444,8 @@ def run_ours(args):
     }
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lens, params)
+    if not args.skip_rows and ws == 1 and args.workload == "csst100":
+        line["rows"] = measure_rows()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -717,6 +719,121 @@ def run_sampler(args):
     return line
 
 
+# ------------------------------------------------- the other rows, briefly
+def _time_lens(L, p_dev, out, steps, warmup, flush):
+    """Device-resident timing of tll_loglike_batch: (step ms, main-kernel
+    ms) lists, L2 flushed between steps, CUDA events on the stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    L.profile(True)
+    for _ in range(warmup):
+        L.loglike_batch(p_dev, out)
+    torch.cuda.synchronize()
+    step_ms, main_ms = [], []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.loglike_batch(p_dev, out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        main_ms.append(L.profile_last()[1])
+    L.profile(False)
+    return step_ms, main_ms
+
+
+def measure_rows(steps=8, warmup=3):
+    """Short device-resident measurements of the workloads beyond the
+    headline: the masked csst100, the multi-component SLACS and 32-Gaussian
+    models, and the device-side sampler loop.  Each: evals/s, ms per step,
+    the main kernel's ms and its fraction of the FP32 FMA peak by the
+    algorithmic flop count."""
+    import torch
+    from paper_2503_08586_gb300 import tll
+    from paper_2503_08586_gb300 import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peak = fp32_peak_tflops()
+    rows = {}
+    # masked csst100
+    lens, params = W.workload("csst100_mask", tll.columns_renderer)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    p_dev = torch.from_numpy(params).to(dev)
+    out = torch.empty(params.shape[0], dtype=torch.float64, device=dev)
+    st, mk = _time_lens(L, p_dev, out, steps, warmup, flush)
+    fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0], L.info()["separable"],
+                         L.ntrace())
+    rows["csst100_mask"] = {"value": params.shape[0] / (statistics.mean(st) / 1e3),
+                            "ms_per_step": statistics.mean(st), "kernel": "k_loglike",
+                            "kernel_ms": statistics.mean(mk), "traced_pixels": L.ntrace(),
+                            "roofline_frac": fpe * params.shape[0] / (statistics.mean(mk) / 1e3)
+                            / 1e12 / peak}
+    L.close()
+    # multi-component models
+    for name in ("slacs120", "mge32"):
+        spec = W.MULTI_WORKLOADS[name]
+        tcomps = [tll.comp(c["type"], c["plane"], c.get("free_scale", True),
+                           c.get("free_index", False), c.get("scale", 1.0), c.get("index", 1.0))
+                  for c in spec.comps]
+
+        def render_factory(pixel_scale, sub, psf, ny, nx, comps_):
+            g = tll.Lens(np.zeros((ny, nx), np.float32), np.ones((ny, nx), np.float32), psf,
+                         pixel_scale, sub)
+            g.set_light(tcomps)
+            return lambda p: g.model_columns_n(p, blurred=True).astype(np.float64)
+
+        lens, params = W.multi_workload(name, render_factory)
+        L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0,
+                     lens.y0)
+        L.set_light(tcomps)
+        p_dev = torch.from_numpy(params).to(dev)
+        out = torch.empty(params.shape[0], dtype=torch.float64, device=dev)
+        st, mk = _time_lens(L, p_dev, out, steps, warmup, flush)
+        fpe = flops_per_eval_multi(lens.ny, lens.nx, lens.sub, lens.psf.shape[0],
+                                   L.info()["separable"], spec.comps)
+        rows[name] = {"value": params.shape[0] / (statistics.mean(st) / 1e3),
+                      "ms_per_step": statistics.mean(st), "kernel": "k_loglike_nc",
+                      "kernel_ms": statistics.mean(mk), "columns": len(spec.comps),
+                      "roofline_frac": fpe * params.shape[0] / (statistics.mean(mk) / 1e3)
+                      / 1e12 / peak}
+        L.close()
+    # the device-side sampler loop on csst100 (4096 walkers)
+    lens, _ = W.workload("csst100", tll.columns_renderer, batch=8)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
+    truth = lens.truth.astype(np.float32)
+    lo, hi = truth - np.float32(0.5), truth + np.float32(0.5)
+    lo[[7, 14]] = hi[[7, 14]] = 1.0
+    lo[[9, 16]], hi[[9, 16]] = 0.5, 6.0
+    lo[[8, 15]], hi[[8, 15]] = 0.02, 3.0
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 30))
+    nw = 4096
+    x0 = np.repeat(truth[None], nw, axis=0)
+    free = np.where(lo < hi)[0]
+    x0[:, free] += rng.normal(scale=0.05, size=(nw, free.size)).astype(np.float32)
+    x0[:, 12], x0[:, 13] = x0[:, 3], x0[:, 4]
+    x0 = np.clip(x0, lo, hi).astype(np.float32)
+    S = tll.Sampler(L, nw, lo, hi, ndim=int(np.sum(lo < hi)) - 2, seed=W.SEED_BASE)
+    S.set_walkers(torch.from_numpy(x0).to(dev))
+    S.run(warmup, keep_chain=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S.run(2 * steps, keep_chain=True)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / (2 * steps)
+    _, _, _, nacc, nprop = S.state()
+    rows["sampler_4096"] = {"value": nw / (ms / 1e3), "ms_per_step": ms,
+                            "acceptance": nacc / max(nprop, 1),
+                            "path": "tll_sampler_run: stretch move, likelihood, accept on the "
+                                    "GPU; one step = 4096 evaluations"}
+    S.close()
+    L.close()
+    return rows
+
+
 # ------------------------------------------------------------ ragged batch
 def run_ragged(args):
     """Many lenses of different sizes (sides {64..200}, PSF 11..31 px, 4x4
@@ -852,6 +969,8 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-stream", action="store_true")
+    ap.add_argument("--skip-rows", action="store_true",
+                    help="omit the short measurements of the other workloads")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--conv", choices=["fused", "split-direct", "split-tc"], default="fused")
     ap.add_argument("--split-chunk", type=int, default=1024)
