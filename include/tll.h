@@ -459,13 +459,20 @@ typedef struct {
  * per-CTA image slots ((2 ncomp + 3) x 4 bytes per pixel per SM) and waits
  * for the device first.  Afterwards tll_loglike_batch, _host, _noalloc,
  * tll_model_image (amps_out receives ncomp amplitudes) and
- * tll_model_columns_n evaluate the new model; tll_model_columns, the
- * batcher, the server, tll_set_shape, tll_set_conv and tll_autotune refuse
- * the lens with TLL_EINVAL.
+ * tll_model_columns_n, the batcher (its multi-column lenses run in their
+ * own multi-lens launches) and the server (tll_server_set_light) evaluate
+ * the new model; tll_model_columns, tll_set_shape, tll_set_conv and
+ * tll_autotune refuse the lens with TLL_EINVAL.  A lens created with
+ * TLL_FLAG_BATCH_ONLY gets its one-lens image slots on first one-lens use.
  * Errors: TLL_EINVAL (bad list), TLL_ENOMEM, TLL_ECUDA (the lens keeps its
  * previous model).
  */
 int tll_set_light(tll_lens *L, const tll_comp_t *comps, int ncomp);
+
+/* Give a server job's lens a multi-component light model (as tll_set_light;
+ * its requests then take that model's parameter layout).  Only while the job
+ * has no request outstanding (else TLL_EBUSY).  Errors as tll_set_light. */
+int tll_server_set_light(tll_server *S, int job_id, const tll_comp_t *comps, int ncomp);
 
 /* Columns of the lens's model: 2 (lens, source) or its component count. */
 int tll_lens_ncols(const tll_lens *L);

@@ -90,8 +90,13 @@ __global__ void k_prologue_multi(const __grid_constant__ MultiArgs A)
     if (t >= A.all->total) return;
     const Segment &sg = A.segs[find_segment(A.segs, 0, A.all->nseg, t)];
     const LensDev &L = A.lenses[sg.lens];
-    decode_vector(sg.params + (size_t)(t - sg.first) * (L.epl ? NPAR_EPL : NPAR),
-                  A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0);
+    const MultiDev &M = A.mdevs[sg.lens];
+    if (M.nc > 0)
+        decode_multi(sg.params + (size_t)(t - sg.first) * M.npar, A.kc + (size_t)t * NCONST, L,
+                     M, A.bn_tab);
+    else
+        decode_vector(sg.params + (size_t)(t - sg.first) * (L.epl ? NPAR_EPL : NPAR),
+                      A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0);
 }
 
 // Multi-component prologue: one thread per vector.
@@ -259,6 +264,11 @@ LensDev lens_dev(const tll_lens *L)
     d.dWd = L->dWd; d.lognorm = L->lognorm;
     d.W = L->W; d.HL = L->HL; d.img = L->shape.img; d.band_rows = L->shape.band_rows;
     d.epl = L->epl;
+    if (L->nc) {   // the multi-column kernels' placement
+        d.img = L->nc_shape.img;
+        d.band_rows = L->nc_shape.band_rows;
+        d.nc_smem = (int)L->nc_shape.smem;
+    }
     d.tlist = L->d_tlist;
     d.ntrace = L->d_tlist ? L->ntrace : L->npix;
     for (int k = 0; k < kMaxK * kMaxK; ++k)
@@ -307,6 +317,13 @@ NcKernel find_nc(int sub, int Kc)
 {
     for (const KernelSet *ks : kSets)
         if (NcKernel f = ks->nc(sub, Kc)) return f;
+    return nullptr;
+}
+
+MultiKernel find_nc_multi(int sub, int Kc)
+{
+    for (const KernelSet *ks : kSets)
+        if (MultiKernel f = ks->nc_multi(sub, Kc)) return f;
     return nullptr;
 }
 
@@ -609,10 +626,15 @@ int nc_configure(tll_lens *L)
     NcKernel k = nullptr;
     if (L->K <= kMaxK && L->nx <= 256) {
         k = find_nc(L->sub, L->K);
-        if (!k) return fail(TLL_ECUDA, "no multi-column kernel for s=%d K=%d", L->sub, L->K);
-        cudaFuncAttributes fa;
+        const MultiKernel km = find_nc_multi(L->sub, L->K);
+        if (!k || !km) return fail(TLL_ECUDA, "no multi-column kernel for s=%d K=%d", L->sub, L->K);
+        // the band must fit both the one-lens kernel and the batcher's
+        // multi-lens one (which also holds a lens descriptor)
+        cudaFuncAttributes fa, fm;
         CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k));
-        const long long avail = share - (long long)fa.sharedSizeBytes;
+        CUDA_TRY(cudaFuncGetAttributes(&fm, (const void *)km));
+        const long long avail =
+            share - (long long)std::max(fa.sharedSizeBytes, fm.sharedSizeBytes);
         const size_t row_bytes = (size_t)2 * L->W * sizeof(float);
         const long long rows = avail / (long long)row_bytes - 2 * h - kCR;
         if (rows >= 8) {
@@ -783,6 +805,7 @@ struct tll_batcher {
     int cap_lenses = 0, cap_segs = 0, cap_items = 0, cap_ctas = 0;
     long long gslot_floats = 0;
     LensDev *d_lenses = nullptr, *h_lenses = nullptr;   // h_*: pinned staging
+    MultiDev *d_mdevs = nullptr, *h_mdevs = nullptr;   // per lens: component list
     Segment *d_segs = nullptr, *h_segs = nullptr;
     MultiHdr *d_groups = nullptr, *h_groups = nullptr; // [kMaxGroups] + the whole list
     float *d_kc = nullptr, *d_gscr = nullptr;
@@ -792,6 +815,7 @@ struct tll_batcher {
     bool staged_pending = false;
     std::vector<GroupLaunch> glaunch;  // this run's group launches
     std::vector<MultiKernel> kern_ready;  // kernels whose shared-memory limit is set
+    int dyn_smem_nc = 0;              // dynamic shared memory of the multi-column kernels
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;    // stream the graph was captured on
     std::vector<GroupLaunch> gcaptured;   // group launches baked into the graph
@@ -802,13 +826,15 @@ namespace {
 
 void batcher_free_buffers(tll_batcher *b)
 {
-    void *dev[] = {b->d_lenses, b->d_segs, b->d_groups, b->d_kc, b->d_gscr, b->d_counter};
+    void *dev[] = {b->d_lenses, b->d_segs, b->d_groups, b->d_kc, b->d_gscr, b->d_counter,
+                   b->d_mdevs};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *host[] = {b->h_lenses, b->h_segs, b->h_groups};
+    void *host[] = {b->h_lenses, b->h_segs, b->h_groups, b->h_mdevs};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     b->d_lenses = b->h_lenses = nullptr;
+    b->d_mdevs = b->h_mdevs = nullptr;
     b->d_segs = b->h_segs = nullptr;
     b->d_groups = b->h_groups = nullptr;
     b->d_kc = b->d_gscr = nullptr;
@@ -836,6 +862,8 @@ int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long g
     const int cc = std::max(ctas, b->cap_ctas);
     batcher_free_buffers(b);
     CUDA_TRY(cudaMalloc(&b->d_lenses, cl * sizeof(LensDev)));
+    CUDA_TRY(cudaMalloc(&b->d_mdevs, cl * sizeof(MultiDev)));
+    CUDA_TRY(cudaMallocHost(&b->h_mdevs, cl * sizeof(MultiDev)));
     CUDA_TRY(cudaMalloc(&b->d_segs, cs * sizeof(Segment)));
     CUDA_TRY(cudaMalloc(&b->d_groups, (kMaxGroups + 1) * sizeof(MultiHdr)));
     CUDA_TRY(cudaMalloc(&b->d_kc, (size_t)ci * NCONST * sizeof(float)));
@@ -856,6 +884,7 @@ MultiArgs batcher_args(const tll_batcher *b)
 {
     MultiArgs A;
     A.lenses = b->d_lenses;
+    A.mdevs = b->d_mdevs;
     A.segs = b->d_segs;
     A.groups = b->d_groups;
     A.all = b->d_groups + kMaxGroups;
@@ -875,6 +904,8 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
     const int cl = full ? b->cap_lenses : nl, cs = full ? b->cap_segs : ns;
     const int items = full ? b->cap_items : total;
     CUDA_TRY(cudaMemcpyAsync(b->d_lenses, b->h_lenses, cl * sizeof(LensDev),
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_mdevs, b->h_mdevs, cl * sizeof(MultiDev),
                              cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(b->d_segs, b->h_segs, cs * sizeof(Segment),
                              cudaMemcpyHostToDevice, st));
@@ -952,6 +983,10 @@ int tll_batcher_create(int use_graph, tll_batcher **out)
         if (!k0 || cudaFuncGetAttributes(&fa, k0) != cudaSuccess)
             return bad(fail(TLL_ECUDA, "k_loglike_multi attributes"));
         b->dyn_smem = b->optin - (int)fa.sharedSizeBytes;
+        const MultiKernel k1 = find_nc_multi(4, 0);
+        if (!k1 || cudaFuncGetAttributes(&fa, k1) != cudaSuccess)
+            return bad(fail(TLL_ECUDA, "k_loglike_nc_multi attributes"));
+        b->dyn_smem_nc = b->optin - (int)fa.sharedSizeBytes;
     }
     if ((rc = bn_table(b->dev, &b->bn_tab))) return bad(rc);
     if (cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess)
@@ -990,20 +1025,20 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         tll_lens *L = lenses[k];
         if (!L) return fail(TLL_EINVAL, "lens %d is NULL", k);
         if (L->dev != b->dev) return fail(TLL_EINVAL, "lens %d is on another device", k);
-        if (int rc = reject_nc(L, "tll_batcher_run")) return rc;
         if (counts[k] < 0) return fail(TLL_EINVAL, "negative count for lens %d", k);
         if (counts[k] > 0 && (!params[k] || !outs[k]))
             return fail(TLL_EINVAL, "NULL params/out for lens %d", k);
-        const Shape &S = L->shape;
-        if (S.smem > (size_t)b->dyn_smem)
+        const Shape &S = L->nc ? L->nc_shape : L->shape;
+        if (S.smem > (size_t)(L->nc ? b->dyn_smem_nc : b->dyn_smem))
             return fail(TLL_EINVAL, "lens %d needs more shared memory than the batch kernel has", k);
         int u = 0;
         while (u < (int)uniq.size() && uniq[u] != L) ++u;
         if (u == (int)uniq.size()) uniq.push_back(L);
         lid[k] = u;
-        // group key: supersampling class, convolution class, CTA size, CTAs per SM
-        key[k] = (((long long)sub_class(L->sub) * 1000 + conv_class(S.img, L->K)) * 2048 +
-                  S.threads) * 64 + std::min(S.per_sm, 63);
+        // group key: kind (two columns / multi-column), supersampling class,
+        // convolution class, CTA size, CTAs per SM
+        key[k] = ((((long long)(L->nc ? 1 : 0) * 8 + sub_class(L->sub)) * 1000 +
+                   conv_class(S.img, L->K)) * 2048 + S.threads) * 64 + std::min(S.per_sm, 63);
         if (counts[k] > 0) {
             order.push_back(k);
             if (S.gslot > 0) {
@@ -1024,21 +1059,27 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
     int rc = batcher_reserve(b, (int)uniq.size(), n, (int)total, gslot, ctas);
     if (rc) return rc;
     if (b->staged_pending) CUDA_TRY(cudaEventSynchronize(b->staged));
-    for (size_t u = 0; u < uniq.size(); ++u) b->h_lenses[u] = lens_dev(uniq[u]);
+    for (size_t u = 0; u < uniq.size(); ++u) {
+        b->h_lenses[u] = lens_dev(uniq[u]);
+        b->h_mdevs[u] = uniq[u]->md;
+        if (!uniq[u]->nc) b->h_mdevs[u].nc = 0;
+    }
     b->glaunch.clear();
     int first = 0, ns = 0, ng = 0;
     for (size_t q = 0; q < order.size(); ++q) {
         const int k = order[q];
-        const Shape &S = lenses[k]->shape;
+        const bool ncl = lenses[k]->nc > 0;
+        const Shape &S = ncl ? lenses[k]->nc_shape : lenses[k]->shape;
         if (q == 0 || key[k] != key[order[q - 1]]) {
             if (ng == kMaxGroups) return fail(TLL_EINVAL, "more than %d kernel groups", kMaxGroups);
             const int Kc = conv_class(S.img, lenses[k]->K);
-            const MultiKernel mk = find_multi(lenses[k]->sub, Kc);
+            const MultiKernel mk = ncl ? find_nc_multi(lenses[k]->sub, Kc)
+                                       : find_multi(lenses[k]->sub, Kc);
             if (!mk) return fail(TLL_ECUDA, "no multi-lens kernel for s=%d K=%d", lenses[k]->sub,
                                  Kc);
             if (std::find(b->kern_ready.begin(), b->kern_ready.end(), mk) == b->kern_ready.end()) {
                 CUDA_TRY(cudaFuncSetAttribute(mk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              b->dyn_smem));
+                                              ncl ? b->dyn_smem_nc : b->dyn_smem));
                 b->kern_ready.push_back(mk);
             }
             GroupLaunch gl;
@@ -1114,8 +1155,14 @@ int tll_loglike_batch_noalloc(tll_lens *L, const float *params, int B, double *o
     float *kc = nullptr;
     const int rc = noalloc_scratch(L->dev, &kc);
     if (rc) return rc;
-    // a multi-component lens's image slots were allocated by tll_set_light
-    if (L->nc) return run_batch_nc(L, params, B, out, (cudaStream_t)stream, kc, nullptr);
+    // a multi-component lens's image slots come from tll_set_light (or a
+    // first allocating one-lens call for a TLL_FLAG_BATCH_ONLY lens)
+    if (L->nc) {
+        if (L->nscr_floats < (long long)L->nc_shape.grid_cap * L->nc_shape.gslot)
+            return fail(TLL_EINVAL, "lens was created TLL_FLAG_BATCH_ONLY and has no one-lens "
+                                    "image slots; evaluate it with tll_loglike_batch once first");
+        return run_batch_nc(L, params, B, out, (cudaStream_t)stream, kc, nullptr);
+    }
     // k_prologue writes all NCONST entries of each of the B blocks before
     // k_loglike reads them on the same stream, so nothing needs clearing.
     return run_batch(L, params, B, out, (cudaStream_t)stream, false, kc);
@@ -1839,7 +1886,9 @@ int tll_set_light(tll_lens *L, const tll_comp_t *comps, int ncomp)
         if (e != cudaSuccess) rc = fail(TLL_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
         else L->dev_bytes += (kMaxComps + 1) * sizeof(double);
     }
-    if (!rc) rc = nc_ensure_scr(L);
+    // the one-lens image slots; a TLL_FLAG_BATCH_ONLY lens (evaluated through
+    // a batcher or the server) gets them on first one-lens use instead
+    if (!rc && !(L->flags & TLL_FLAG_BATCH_ONLY)) rc = nc_ensure_scr(L);
     if (rc) {
         L->nc = old_nc;
         L->md = old_md;

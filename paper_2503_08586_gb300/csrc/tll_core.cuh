@@ -121,8 +121,10 @@ struct Segment {
 struct MultiHdr {        // one group: items [first, first + total), segments [seg0, seg0 + nseg)
     int first, total, seg0, nseg;
 };
+struct MultiDev;   // the component list of a multi-column lens (tll_multi.cuh)
 struct MultiArgs {
     const LensDev *lenses;
+    const MultiDev *mdevs;     // per lens: its component list (nc = 0: two columns)
     const Segment *segs;
     const MultiHdr *groups;
     const MultiHdr *all;       // the whole work list (prologue)

@@ -26,8 +26,13 @@ NcKernel nc_k(int sub, int K)
     return K == 0 ? nc_for<0>(sub) : nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    return K == 0 ? nc_multi_for<0>(sub) : nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_generic = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_generic = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

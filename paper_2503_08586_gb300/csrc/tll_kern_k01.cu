@@ -33,8 +33,17 @@ NcKernel nc_k(int sub, int K)
     return nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    switch (K) {
+        case 1: return nc_multi_for<1>(sub);
+        case 3: return nc_multi_for<3>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k01 = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_k01 = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

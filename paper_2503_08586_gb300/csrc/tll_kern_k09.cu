@@ -33,8 +33,17 @@ NcKernel nc_k(int sub, int K)
     return nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    switch (K) {
+        case 9: return nc_multi_for<9>(sub);
+        case 11: return nc_multi_for<11>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k09 = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_k09 = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

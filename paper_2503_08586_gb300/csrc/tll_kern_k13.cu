@@ -33,8 +33,17 @@ NcKernel nc_k(int sub, int K)
     return nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    switch (K) {
+        case 13: return nc_multi_for<13>(sub);
+        case 15: return nc_multi_for<15>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k13 = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_k13 = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

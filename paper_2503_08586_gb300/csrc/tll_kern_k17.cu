@@ -33,8 +33,17 @@ NcKernel nc_k(int sub, int K)
     return nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    switch (K) {
+        case 17: return nc_multi_for<17>(sub);
+        case 19: return nc_multi_for<19>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k17 = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_k17 = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

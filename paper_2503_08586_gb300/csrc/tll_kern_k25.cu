@@ -33,8 +33,17 @@ NcKernel nc_k(int sub, int K)
     return nullptr;
 }
 
+MultiKernel nc_multi_k(int sub, int K)
+{
+    switch (K) {
+        case 25: return nc_multi_for<25>(sub);
+        case 27: return nc_multi_for<27>(sub);
+    }
+    return nullptr;
+}
+
 }  // namespace
 
-extern const KernelSet kernel_set_k25 = {single_k, multi_k, nc_k};
+extern const KernelSet kernel_set_k25 = {single_k, multi_k, nc_k, nc_multi_k};
 
 }  // namespace tll

@@ -406,29 +406,194 @@ __device__ inline double nc_fnnls_warp(const double *A, const double *b, int n, 
     return x;
 }
 
-// --------------------------------------------------------------- kernel
-// Shared memory: static -- partial sums, the normal equations, the Cholesky
-// work space, the components' constants, the EPL series; dynamic -- K > 0:
+// --------------------------------------------------------------- kernels
+// Static shared memory of the multi-column kernels: the normal equations,
+// the Cholesky work space, the components' constants, the EPL series.
+struct NcShared {
+    double A[kMaxComps * kMaxComps], b[kMaxComps];
+    double F[kMaxComps * (kMaxComps + 1)];
+    float q[kMaxComps * 6];
+    float epl[kEplMaxN + 1];
+};
+
+// One valid parameter vector of a multi-column lens (constant block kc):
+// trace passes, PSF, normal equations, FNNLS; log L to *outp (and, when
+// wres is given, the amplitudes and log L to wres).  U: the CTA's global
+// slot (U [nc], M [nc + 1], H [2] images); spsf: the dynamic shared memory
+// (band buffer or PSF taps, reused for the sums' tiles of T pixels).
+// Starts and ends with all threads in step (block barriers inside).
+template <int SUB, int K>
+__device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, const float *kc,
+                                          double *outp, double *wres, float *U, float *spsf,
+                                          NcShared &sh, bool skip, int T, int tid, int nthr)
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nc = M.nc, npix = L.npix;
+    float *Mb = U + (size_t)nc * npix;
+    float *H = Mb + (size_t)(nc + 1) * npix;
+    const VecConst v = load_consts(kc);
+    for (int t = tid; t < 6 * nc; t += nthr) sh.q[t] = kc[K_C0 + t];
+    if (v.epl)
+        for (int t = tid; t <= v.en; t += nthr) sh.epl[t] = kc[K_EC0 + t];
+    __syncthreads();
+    // 1. trace passes
+    for (int ps = 0; ps < M.npass; ++ps) {
+        const int ncp = M.pass_n[ps];
+        float cq[6 * kPassMax];
+        int gmask = 0;
+#pragma unroll
+        for (int k = 0; k < kPassMax; ++k) {
+            const int c = k < ncp ? M.pass_comp[ps][k] : 0;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) cq[6 * k + e] = sh.q[6 * c + e];
+            if (k < ncp && M.type[c] == COMP_GAUSS) gmask |= 1 << k;
+        }
+        const int *chan = M.pass_comp[ps];
+        if (M.pass_gauss[ps]) {
+            if (M.pass_plane[ps] == PLANE_LENS)
+                trace_pass<SUB, 3, kPassMax, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.epl)
+                trace_pass<SUB, 2, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.fast)
+                trace_pass<SUB, 0, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else
+                trace_pass<SUB, 1, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+        } else {
+            if (M.pass_plane[ps] == PLANE_LENS)
+                trace_pass<SUB, 3, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.epl)
+                trace_pass<SUB, 2, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.fast)
+                trace_pass<SUB, 0, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else
+                trace_pass<SUB, 1, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+        }
+    }
+    __syncthreads();
+    // 2. PSF, two columns at a time (an odd last column pairs with itself);
+    //    the sums of the previous vector used the dynamic shared memory,
+    //    so its zero halos (or the PSF taps) are set up again first
+    setup_lens(L, spsf, tid, nthr);
+    __syncthreads();
+    for (int c = 0; c < nc; c += 2) {
+        const int c2 = min(c + 1, nc - 1);
+        const float *Il = U + (size_t)c * npix, *Is = U + (size_t)c2 * npix;
+        if constexpr (K > 0) {
+            const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
+            const int step = L.band_rows;
+            float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
+            PairStore st{Mb + (size_t)c * npix, Mb + (size_t)c2 * npix};
+            for (int b0 = 0; b0 < ny; b0 += step) {
+                const int nrows = min(step, ny - b0);
+                const int nbr = nrows + 2 * h;
+                for (int t = tid; t < 2 * nbr * nx; t += nthr) {
+                    const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
+                    const int br = rem / nx, j = rem - br * nx;
+                    const int ir = b0 - h + br;
+                    const float val = (ir >= 0 && ir < ny) ? (ch ? Is : Il)[ir * nx + j] : 0.0f;
+                    (ch ? Ps : Pl)[br * W + HL + j] = val;
+                }
+                __syncthreads();
+                if (L.sep)
+                    conv_sep_band<K>(L, Pl, Ps, b0, nrows, max(0, h - b0),
+                                     min(nbr, ny - b0 + h), tid, nthr, st);
+                else
+                    conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr, st);
+                __syncthreads();
+            }
+        } else {
+            RunArgs ra = {};
+            ra.wr_blurred = Mb + (size_t)c * npix;
+            float dummy[10];
+            // writes M[c] and M[c + 1] (the spare column M[nc] for an odd
+            // last column); its five sums go unused
+            conv_generic<true>(L, ra, spsf, const_cast<float *>(Il), const_cast<float *>(Is),
+                               H, H + npix, dummy, tid, nthr, false);
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // 3. normal equations through shared-memory tiles (the dynamic
+    //    shared memory is free again once the convolution is done): thread
+    //    (s, r) takes sum s (see nc_tile_sums) over pixel phase r of RP;
+    //    the FP64 partials go to the same space after the last tile
+    {
+        const int nA = nc * (nc + 1) / 2, S = nA + nc;
+        const int RP = max(1, nthr / S);
+        const int sr = tid / S, sidx = tid - sr * S;
+        int sa = -1, se = 0;
+        const bool sbsum = sidx >= nA;
+        if (tid < S * RP) {
+            if (sbsum) {
+                sa = sidx - nA;
+            } else {   // row-major upper triangle
+                int rem = sidx, a = 0;
+                while (rem >= nc - a) {
+                    rem -= nc - a;
+                    ++a;
+                }
+                sa = a;
+                se = a + rem;
+            }
+        }
+        const double part = nc_tile_sums(L, Mb, nc, sa, se, sbsum, sr, RP, spsf, T, tid, nthr);
+        double *parts = reinterpret_cast<double *>(spsf);   // [RP][S]
+        if (sa >= 0) parts[tid] = part;
+        __syncthreads();
+        for (int t = tid; t < S; t += nthr) {
+            double sum = 0.0;
+            for (int rr = 0; rr < RP; ++rr) sum += parts[rr * S + t];
+            if (t >= nA) {
+                sh.b[t - nA] = sum;
+            } else {
+                int rem = t, a = 0;
+                while (rem >= nc - a) {
+                    rem -= nc - a;
+                    ++a;
+                }
+                const int e = a + rem;
+                sh.A[a * nc + e] = sum;
+                sh.A[e * nc + a] = sum;
+            }
+        }
+    }
+    __syncthreads();
+    // 4. amplitudes (warp 0) and log L
+    if (warp == 0) {
+        const double x = nc_fnnls_warp(sh.A, sh.b, nc, sh.F, lane);
+        double Ax = 0.0;
+        for (int k = 0; k < nc; ++k) {
+            const double xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane < nc) Ax = fma(sh.A[lane * nc + k], xk, Ax);
+        }
+        double term = lane < nc ? x * (Ax - 2.0 * sh.b[lane]) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+        const double ll = -0.5 * (L.dWd + term) + L.lognorm;
+        if (lane == 0) *outp = ll;
+        if (wres) {
+            if (lane < nc) wres[lane] = x;
+            if (lane == 0) wres[nc] = ll;
+        }
+    }
+    __syncthreads();
+}
+
+// One lens: persistent CTAs over the batch.  Dynamic shared memory: K > 0,
 // the padded band buffer of the compiled convolution (2 channels x
-// (band_rows + 2h + kCR) rows x W); K == 0: the PSF taps of the generic
-// convolution.
+// (band_rows + 2h + kCR) rows x W); K == 0, the PSF taps of the generic
+// convolution; at least the sums' smallest tile either way.
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads)
 k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev M,
              const __grid_constant__ NcArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double sA[kMaxComps * kMaxComps], sb[kMaxComps];
-    __shared__ double sF[kMaxComps * (kMaxComps + 1)];
-    __shared__ float sq[kMaxComps * 6];
-    __shared__ float sepl[kEplMaxN + 1];
+    __shared__ NcShared sh;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nc = M.nc, npix = L.npix;
     float *spsf = reinterpret_cast<float *>(smem);
     float *U = R.gscr + (size_t)blockIdx.x * R.gslot;
-    float *Mb = U + (size_t)nc * npix;
-    float *H = Mb + (size_t)(nc + 1) * npix;
     setup_lens(L, spsf, tid, nthr);
     // pixels never traced (masked lenses) must start finite
     if (L.tlist)
@@ -445,152 +610,61 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
             }
             continue;
         }
-        const VecConst v = load_consts(kc);
-        for (int t = tid; t < 6 * nc; t += nthr) sq[t] = kc[K_C0 + t];
-        if (v.epl)
-            for (int t = tid; t <= v.en; t += nthr) sepl[t] = kc[K_EC0 + t];
-        __syncthreads();
-        // 1. trace passes
-        for (int ps = 0; ps < M.npass; ++ps) {
-            const int ncp = M.pass_n[ps];
-            float cq[6 * kPassMax];
-            int gmask = 0;
-#pragma unroll
-            for (int k = 0; k < kPassMax; ++k) {
-                const int c = k < ncp ? M.pass_comp[ps][k] : 0;
-#pragma unroll
-                for (int e = 0; e < 6; ++e) cq[6 * k + e] = sq[6 * c + e];
-                if (k < ncp && M.type[c] == COMP_GAUSS) gmask |= 1 << k;
-            }
-            const int *chan = M.pass_comp[ps];
-            if (M.pass_gauss[ps]) {
-                if (M.pass_plane[ps] == PLANE_LENS)
-                    trace_pass<SUB, 3, kPassMax, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else if (v.epl)
-                    trace_pass<SUB, 2, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else if (v.fast)
-                    trace_pass<SUB, 0, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else
-                    trace_pass<SUB, 1, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-            } else {
-                if (M.pass_plane[ps] == PLANE_LENS)
-                    trace_pass<SUB, 3, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else if (v.epl)
-                    trace_pass<SUB, 2, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else if (v.fast)
-                    trace_pass<SUB, 0, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-                else
-                    trace_pass<SUB, 1, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sepl, skip);
-            }
+        nc_vector<SUB, K>(L, M, kc, R.out + b, R.wr_res, U, spsf, sh, skip, T, tid, nthr);
+    }
+}
+
+// Many lenses (the batcher's multi-column groups): CTAs take items from the
+// group's atomic counter and copy a lens's descriptor and component list
+// into shared memory when they switch lens (as k_loglike_multi).
+template <int SUB, int K>
+__global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_constant__ MultiArgs A,
+                                                               int group)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ NcShared sh;
+    __shared__ LensDev sL;
+    __shared__ MultiDev sM;
+    __shared__ int s_t, s_seg;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    float *spsf = reinterpret_cast<float *>(smem);
+    float *U = A.gscr + (size_t)blockIdx.x * A.gslot_floats;
+    const MultiHdr hd = A.groups[group];
+    int *counter = A.counter + group;
+    int cur = -1;
+    for (;;) {
+        if (tid == 0) {
+            const int t = hd.first + atomicAdd(counter, 1);
+            s_t = t;
+            s_seg = t < hd.first + hd.total ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
         }
         __syncthreads();
-        // 2. PSF, two columns at a time (an odd last column pairs with itself);
-        //    the sums of the previous vector used the dynamic shared memory,
-        //    so its zero halos (or the PSF taps) are set up again first
-        setup_lens(L, spsf, tid, nthr);
-        __syncthreads();
-        for (int c = 0; c < nc; c += 2) {
-            const int c2 = min(c + 1, nc - 1);
-            const float *Il = U + (size_t)c * npix, *Is = U + (size_t)c2 * npix;
-            if constexpr (K > 0) {
-                const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
-                const int step = L.band_rows;
-                float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
-                PairStore st{Mb + (size_t)c * npix, Mb + (size_t)c2 * npix};
-                for (int b0 = 0; b0 < ny; b0 += step) {
-                    const int nrows = min(step, ny - b0);
-                    const int nbr = nrows + 2 * h;
-                    for (int t = tid; t < 2 * nbr * nx; t += nthr) {
-                        const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
-                        const int br = rem / nx, j = rem - br * nx;
-                        const int ir = b0 - h + br;
-                        const float val = (ir >= 0 && ir < ny) ? (ch ? Is : Il)[ir * nx + j] : 0.0f;
-                        (ch ? Ps : Pl)[br * W + HL + j] = val;
-                    }
-                    __syncthreads();
-                    if (L.sep)
-                        conv_sep_band<K>(L, Pl, Ps, b0, nrows, max(0, h - b0),
-                                         min(nbr, ny - b0 + h), tid, nthr, st);
-                    else
-                        conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr, st);
-                    __syncthreads();
-                }
-            } else {
-                RunArgs ra = {};
-                ra.wr_blurred = Mb + (size_t)c * npix;
-                float dummy[10];
-                // writes M[c] and M[c + 1] (the spare column M[nc] for an odd
-                // last column); its five sums go unused
-                conv_generic<true>(L, ra, spsf, const_cast<float *>(Il), const_cast<float *>(Is),
-                                   H, H + npix, dummy, tid, nthr, false);
-                __syncthreads();
-            }
-        }
-        __syncthreads();
-        // 3. normal equations through shared-memory tiles (the dynamic
-        //    shared memory is free again once the convolution is done): thread
-        //    (s, r) takes sum s (see nc_tile_sums) over pixel phase r of RP;
-        //    the FP64 partials go to the same space after the last tile
-        {
-            const int nA = nc * (nc + 1) / 2, S = nA + nc;
-            const int RP = max(1, nthr / S);
-            const int sr = tid / S, sidx = tid - sr * S;
-            int sa = -1, se = 0;
-            const bool sbsum = sidx >= nA;
-            if (tid < S * RP) {
-                if (sbsum) {
-                    sa = sidx - nA;
-                } else {   // row-major upper triangle
-                    int rem = sidx, a = 0;
-                    while (rem >= nc - a) {
-                        rem -= nc - a;
-                        ++a;
-                    }
-                    sa = a;
-                    se = a + rem;
-                }
-            }
-            const double part = nc_tile_sums(L, Mb, nc, sa, se, sbsum, sr, RP, spsf, T, tid, nthr);
-            double *parts = reinterpret_cast<double *>(spsf);   // [RP][S]
-            if (sa >= 0) parts[tid] = part;
+        const int t = s_t;
+        if (t >= hd.first + hd.total) break;
+        const Segment sg = A.segs[s_seg];
+        if (sg.lens != cur) {
+            const unsigned *src = reinterpret_cast<const unsigned *>(A.lenses + sg.lens);
+            unsigned *dst = reinterpret_cast<unsigned *>(&sL);
+            for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
+            const unsigned *msrc = reinterpret_cast<const unsigned *>(A.mdevs + sg.lens);
+            unsigned *mdst = reinterpret_cast<unsigned *>(&sM);
+            for (int k = tid; k < (int)(sizeof(MultiDev) / 4); k += nthr) mdst[k] = msrc[k];
             __syncthreads();
-            for (int t = tid; t < S; t += nthr) {
-                double sum = 0.0;
-                for (int rr = 0; rr < RP; ++rr) sum += parts[rr * S + t];
-                if (t >= nA) {
-                    sb[t - nA] = sum;
-                } else {
-                    int rem = t, a = 0;
-                    while (rem >= nc - a) {
-                        rem -= nc - a;
-                        ++a;
-                    }
-                    const int e = a + rem;
-                    sA[a * nc + e] = sum;
-                    sA[e * nc + a] = sum;
-                }
-            }
+            setup_lens(sL, spsf, tid, nthr);
+            if (sL.tlist)
+                for (int k = tid; k < sM.nc * sL.npix; k += nthr) U[k] = 0.0f;
+            __syncthreads();
+            cur = sg.lens;
         }
-        __syncthreads();
-        // 4. amplitudes (warp 0) and log L
-        if (warp == 0) {
-            const double x = nc_fnnls_warp(sA, sb, nc, sF, lane);
-            double Ax = 0.0;
-            for (int k = 0; k < nc; ++k) {
-                const double xk = __shfl_sync(0xffffffffu, x, k);
-                if (lane < nc) Ax = fma(sA[lane * nc + k], xk, Ax);
-            }
-            double term = lane < nc ? x * (Ax - 2.0 * sb[lane]) : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
-            const double ll = -0.5 * (L.dWd + term) + L.lognorm;
-            if (lane == 0) R.out[b] = ll;
-            if (R.wr_res) {
-                if (lane < nc) R.wr_res[lane] = x;
-                if (lane == 0) R.wr_res[nc] = ll;
-            }
+        const float *kc = A.kc + (size_t)t * NCONST;
+        double *outp = sg.out + (t - sg.first);
+        if (kc[K_VALID] == 0.0f) {
+            if (tid == 0) *outp = -INFINITY;
+            __syncthreads();
+            continue;
         }
-        __syncthreads();
+        nc_vector<SUB, K>(sL, sM, kc, outp, nullptr, U, spsf, sh, true,
+                          nc_tile_pixels(sM.nc, (long long)sL.nc_smem), tid, nthr);
     }
 }
 
@@ -601,6 +675,7 @@ struct KernelSet {
     SingleKernel (*single)(int sub, int K, bool write);
     MultiKernel (*multi)(int sub, int K);
     NcKernel (*nc)(int sub, int K);
+    MultiKernel (*nc_multi)(int sub, int K);
 };
 
 template <int K>
@@ -610,6 +685,16 @@ inline NcKernel nc_for(int sub)
         case 4: return k_loglike_nc<4, K>;
         case 5: return k_loglike_nc<5, K>;
         default: return k_loglike_nc<0, K>;
+    }
+}
+
+template <int K>
+inline MultiKernel nc_multi_for(int sub)
+{
+    switch (sub_class(sub)) {
+        case 4: return k_loglike_nc_multi<4, K>;
+        case 5: return k_loglike_nc_multi<5, K>;
+        default: return k_loglike_nc_multi<0, K>;
     }
 }
 

@@ -411,6 +411,36 @@ int tll_server_open_job(tll_server *S, const float *image, const float *noise,
     return TLL_OK;
 }
 
+int tll_server_set_light(tll_server *S, int job_id, const tll_comp_t *comps, int ncomp)
+{
+    if (!S) return sfail(TLL_EINVAL, "NULL server");
+    tll_lens *L = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (job_id < 0 || job_id >= (int)S->jobs.size() || !S->jobs[job_id].L)
+            return sfail(TLL_EINVAL, "no open job %d", job_id);
+        Job &j = S->jobs[job_id];
+        if (j.outstanding > 0)
+            return sfail(TLL_EBUSY, "job %d has %d requests outstanding", job_id, j.outstanding);
+        L = j.L;
+        j.outstanding++;   // keeps the job from being closed or used meanwhile
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != S->dev) cudaSetDevice(S->dev);
+    int rc = tll_set_light(L, comps, ncomp);
+    size_t bytes = 0;
+    if (rc == TLL_OK) rc = tll_lens_footprint(L, &bytes);
+    if (prev >= 0 && prev != S->dev) cudaSetDevice(prev);
+    std::lock_guard<std::mutex> lk(S->mu);
+    Job &j = S->jobs[job_id];
+    j.outstanding--;
+    if (rc != TLL_OK) return sfail(rc, "set_light: %s", tll_last_error());
+    S->hbm_used = S->hbm_used - j.bytes + bytes;
+    j.bytes = bytes;
+    return TLL_OK;
+}
+
 int tll_server_close_job(tll_server *S, int job_id)
 {
     if (!S) return sfail(TLL_EINVAL, "NULL server");

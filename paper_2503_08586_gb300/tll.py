@@ -40,7 +40,7 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_destroy_lens", "tll_last_error", "tll_version", "tll_set_light",
            "tll_lens_ncols", "tll_model_columns_n", "tll_lens_ntrace",
            "tll_sampler_create", "tll_sampler_set_walkers", "tll_sampler_run",
-           "tll_sampler_state", "tll_sampler_destroy")
+           "tll_sampler_state", "tll_sampler_destroy", "tll_server_set_light")
 
 # Multi-component light (tll_set_light).
 MAX_COMPS = 32
@@ -213,6 +213,8 @@ def load(path: str | None = None):
     lib.tll_sampler_state.restype = i
     lib.tll_sampler_destroy.argtypes = [vp]
     lib.tll_sampler_destroy.restype = None
+    lib.tll_server_set_light.argtypes = [vp, i, ctypes.POINTER(Comp), i]
+    lib.tll_server_set_light.restype = i
     lib.tll_model_columns_n.argtypes = [vp, fp, fp, i]
     lib.tll_model_columns_n.restype = i
     if path is None:
@@ -605,6 +607,7 @@ class Server:
         self._h = h
         self._keep = {}
         self._nparam = {}
+        self._mass = {}
         self.max_vectors = max_vectors_per_launch
 
     def open_job(self, image, noise, psf, pixel_scale, sub, x0=None, y0=None,
@@ -627,7 +630,19 @@ class Server:
             return None
         _scheck(rc)
         self._nparam[jid.value] = NPARAM_EPL if mass == "epl" else NPARAM
+        self._mass[jid.value] = mass
         return jid.value
+
+    def set_light(self, job: int, comps):
+        """Give the job's lens a multi-component light model (a list of
+        Comp); its requests then take that model's parameter layout."""
+        arr = (Comp * max(1, len(comps)))(*comps)
+        _scheck(load().tll_server_set_light(self._h, int(job), arr, len(comps)))
+        n = MULTI_HEAD + sum((1 if c.flags & COMP_FREE_SCALE else 0)
+                             + (1 if c.flags & COMP_FREE_INDEX else 0) for c in comps)
+        epl = self._nparam.get(job) == NPARAM_EPL or self._mass.get(job) == "epl"
+        self._nparam[job] = n + (1 if epl else 0) if comps else (
+            NPARAM_EPL if epl else NPARAM)
 
     def close_job(self, job: int) -> bool:
         """True when closed; False while it still has requests in flight."""

@@ -2,7 +2,9 @@
 double Sersic; Gaussian components), through the C ABI, against the FP64
 oracle: unblurred and blurred columns per pixel, log L per vector (the
 parity gates of test_parity_gpu), model images, invalid vectors, the
-no-allocation entry point, and the calls that refuse such lenses."""
+no-allocation entry point, and the calls that refuse such lenses (launch
+shapes, the autotuner, the split convolutions; the batcher and the server
+take them, tests/test_multi_batch_gpu.py)."""
 import ctypes
 
 import numpy as np
@@ -178,7 +180,7 @@ def test_multi_noalloc_host_and_revert(cases):
     g.close()
 
 
-def test_multi_refused_by_batcher_and_variants(cases):
+def test_multi_refused_by_shape_and_conv_variants(cases):
     sl, P, o, ref = cases[0]
     g = _gpu(sl, CASES[0][7])
     for call in (lambda: g.set_conv(tll.CONV_SPLIT_DIRECT),
@@ -187,10 +189,6 @@ def test_multi_refused_by_batcher_and_variants(cases):
         with pytest.raises(tll.TLLError) as e:
             call()
         assert e.value.code == tll.EINVAL
-    bt = tll.Batcher(use_graph=False)
-    with pytest.raises(tll.TLLError):
-        bt.run([g], [torch.from_numpy(P).cuda()])
-    bt.close()
     # bad component lists
     lib = tll.load()
     bad = [tll.Comp(7, 0, 1, 1.0, 1.0)]
