@@ -408,6 +408,20 @@ int tll_autotune(tll_lens *L, const float *params, int B, void *stream,
                  tll_shape_t *chosen, tll_shape_t *tried, int max_tried,
                  int *n_tried);
 
+/*
+ * The autotuner's choices outlive the process in a cache file:
+ * tll_autotune_save writes every tuned signature of this process (GPU name,
+ * nx, ny, s, PSF side, separable PSF -> CTA size, CTAs per SM) as text;
+ * tll_autotune_load adds a file's entries for the GPUs present with the same
+ * name, so lenses created afterwards start with those shapes (a restarted
+ * server skips re-tuning); tll_autotune_clear forgets every tuned shape.
+ * Errors: TLL_EINVAL (NULL path, unreadable / unwritable or malformed
+ * file), TLL_ECUDA (load: no CUDA device).
+ */
+int tll_autotune_save(const char *path);
+int tll_autotune_load(const char *path);
+void tll_autotune_clear(void);
+
 /* Entries per parameter vector of this lens: TLL_NPARAM, or TLL_NPARAM_EPL
  * for a TLL_MASS_EPL lens, or the multi-component layout's count after
  * tll_set_light (-1 for NULL). */

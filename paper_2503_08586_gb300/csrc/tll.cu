@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <new>
 #include <vector>
@@ -1644,6 +1645,90 @@ int tll_lens_info(const tll_lens *L, int *nx, int *ny, int *sub, int *psf_size,
     if (flags) *flags = L->flags;
     if (separable) *separable = L->sep;
     return TLL_OK;
+}
+
+// ---------------------------------------------------- autotune cache
+// Text file: a header line "tll-autotune 1", then one line per tuned
+// signature: "<GPU name, spaces as _> nx ny sub K separable threads ctas_per_sm".
+namespace {
+std::string gpu_name(int dev)
+{
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return std::string();
+    std::string n(p.name);
+    for (char &c : n)
+        if (c == ' ' || c == '\t') c = '_';
+    return n;
+}
+}  // namespace
+
+int tll_autotune_save(const char *path)
+{
+    if (!path) return fail(TLL_EINVAL, "path is NULL");
+    std::vector<std::pair<TuneKey, std::pair<int, int>>> all;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        all.assign(g_tuned.begin(), g_tuned.end());
+    }
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(TLL_EINVAL, "cannot write %s", path);
+    fprintf(f, "tll-autotune 1\n");
+    for (const auto &e : all) {
+        const std::string n = gpu_name(e.first.dev);
+        fprintf(f, "%s %d %d %d %d %d %d %d\n", n.empty() ? "unknown" : n.c_str(), e.first.nx,
+                e.first.ny, e.first.sub, e.first.K, e.first.sep, e.second.first, e.second.second);
+    }
+    const bool ok = fflush(f) == 0;
+    fclose(f);
+    return ok ? TLL_OK : fail(TLL_EINVAL, "cannot write %s", path);
+}
+
+int tll_autotune_load(const char *path)
+{
+    if (!path) return fail(TLL_EINVAL, "path is NULL");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(TLL_EINVAL, "cannot read %s", path);
+    char line[512];
+    int version = 0;
+    if (!fgets(line, sizeof line, f) || sscanf(line, "tll-autotune %d", &version) != 1 ||
+        version != 1) {
+        fclose(f);
+        return fail(TLL_EINVAL, "%s is not a tll autotune file", path);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        fclose(f);
+        return fail(TLL_ECUDA, "no CUDA device");
+    }
+    std::vector<std::string> names(ndev);
+    for (int d = 0; d < ndev; ++d) names[d] = gpu_name(d);
+    std::vector<std::pair<TuneKey, std::pair<int, int>>> add;
+    int lineno = 1;
+    while (fgets(line, sizeof line, f)) {
+        ++lineno;
+        char name[256];
+        int nx, ny, sub, K, sep, threads, per_sm;
+        if (sscanf(line, "%255s %d %d %d %d %d %d %d", name, &nx, &ny, &sub, &K, &sep, &threads,
+                   &per_sm) != 8 ||
+            nx < 1 || ny < 1 || sub < 1 || K < 1 || (sep != 0 && sep != 1) || threads < 32 ||
+            threads > kThreads || threads % 32 || per_sm < 1) {
+            fclose(f);
+            return fail(TLL_EINVAL, "%s line %d is malformed", path, lineno);
+        }
+        for (int d = 0; d < ndev; ++d)
+            if (names[d] == name)
+                add.push_back({TuneKey{d, nx, ny, sub, K, sep}, {threads, per_sm}});
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &e : add) g_tuned[e.first] = e.second;
+    return TLL_OK;
+}
+
+void tll_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
 }
 
 int tll_lens_ntrace(const tll_lens *L)

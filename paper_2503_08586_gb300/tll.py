@@ -40,7 +40,8 @@ SYMBOLS = ("tll_create_lens", "tll_loglike_batch", "tll_loglike_batch_host",
            "tll_destroy_lens", "tll_last_error", "tll_version", "tll_set_light",
            "tll_lens_ncols", "tll_model_columns_n", "tll_lens_ntrace",
            "tll_sampler_create", "tll_sampler_set_walkers", "tll_sampler_run",
-           "tll_sampler_state", "tll_sampler_destroy", "tll_server_set_light")
+           "tll_sampler_state", "tll_sampler_destroy", "tll_server_set_light",
+           "tll_autotune_save", "tll_autotune_load", "tll_autotune_clear")
 
 # Multi-component light (tll_set_light).
 MAX_COMPS = 32
@@ -215,6 +216,12 @@ def load(path: str | None = None):
     lib.tll_sampler_destroy.restype = None
     lib.tll_server_set_light.argtypes = [vp, i, ctypes.POINTER(Comp), i]
     lib.tll_server_set_light.restype = i
+    lib.tll_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.tll_autotune_save.restype = i
+    lib.tll_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.tll_autotune_load.restype = i
+    lib.tll_autotune_clear.argtypes = []
+    lib.tll_autotune_clear.restype = None
     lib.tll_model_columns_n.argtypes = [vp, fp, fp, i]
     lib.tll_model_columns_n.restype = i
     if path is None:
@@ -470,6 +477,22 @@ class Lens:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune_save(path: str):
+    """Write this process's tuned launch shapes to a cache file."""
+    _check(load().tll_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path: str):
+    """Add a cache file's tuned shapes (for GPUs of the same name); lenses
+    created afterwards start with them."""
+    _check(load().tll_autotune_load(os.fsencode(path)))
+
+
+def autotune_clear():
+    """Forget every tuned launch shape of this process."""
+    load().tll_autotune_clear()
 
 
 class Sampler:

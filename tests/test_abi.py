@@ -91,3 +91,19 @@ def test_server_refuses_without_gpu(lib):
     cfg = tll.ServerConfig(0, 0, 16, 1, 1, 0)          # max_jobs = 0
     h = ctypes.c_void_p()
     assert lib.tll_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tll.EINVAL
+
+
+def test_autotune_cache_file_errors(lib, tmp_path):
+    """The cache file: a save of this process's (here empty) tuned shapes
+    writes the header; a missing, foreign or malformed file is refused."""
+    p = tmp_path / "tune.txt"
+    assert lib.tll_autotune_save(str(p).encode()) == tll.OK
+    assert p.read_text().splitlines()[0] == "tll-autotune 1"
+    assert lib.tll_autotune_save(None) == tll.EINVAL
+    assert lib.tll_autotune_load(str(tmp_path / "missing.txt").encode()) == tll.EINVAL
+    bad = tmp_path / "bad.txt"
+    bad.write_text("something else\n")
+    assert lib.tll_autotune_load(str(bad).encode()) == tll.EINVAL
+    bad.write_text("tll-autotune 1\nGB300 100 100 4 21 1 1000 1\n")   # CTA size not a warp multiple
+    assert lib.tll_autotune_load(str(bad).encode()) in (tll.EINVAL, tll.ECUDA)
+    lib.tll_autotune_clear()

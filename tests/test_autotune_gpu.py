@@ -124,3 +124,26 @@ def test_batcher_groups_by_shape(cases):
         b.close()
     for g in lenses:
         g.close()
+
+
+def test_autotune_cache_file_roundtrip(cases, tmp_path):
+    """A tuned shape saved to the cache file, forgotten, and loaded again:
+    a lens created after the load starts with it (marked tuned)."""
+    sl, P, ref = cases[0]
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+    chosen = g.autotune(torch.from_numpy(P).cuda())["chosen"]
+    g.close()
+    path = str(tmp_path / "tune.txt")
+    tll.autotune_save(path)
+    lines = open(path).read().splitlines()
+    assert lines[0] == "tll-autotune 1" and len(lines) >= 2
+    tll.autotune_clear()
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+    assert not g.shape()["tuned"]
+    g.close()
+    tll.autotune_load(path)
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+    sh = g.shape()
+    assert sh["tuned"] and sh["threads"] == chosen["threads"]
+    assert sh["ctas_per_sm"] == chosen["ctas_per_sm"]
+    g.close()

@@ -46,6 +46,8 @@ CASES = [
     ("slacs_epl", 40, 40, 0.06, 4, 13, "gaussian", W.SLACS_COMPS, "epl"),
     ("mge32", 40, 36, 0.07, 3, 9, "gaussian", W.MGE32_COMPS, "sie"),
     ("many20_generic", 34, 30, 0.08, 2, 33, "moffat", MANY, "sie"),
+    ("tiny_1x1", 1, 1, 0.1, 1, 1, "gaussian", W.SLACS_COMPS, "sie"),
+    ("tiny_3x2", 3, 2, 0.2, 4, 5, "moffat", MIXED, "sie"),
 ]
 
 
