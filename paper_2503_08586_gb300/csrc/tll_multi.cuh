@@ -221,49 +221,86 @@ __host__ __device__ inline int nc_tile_pixels(int nc, long long smem_bytes)
     return (int)(t < 32 ? 32 : (t & ~31LL) > 4096 ? 4096 : (t & ~31LL));
 }
 
-// Sum s of the normal equations (s < nc(nc+1)/2: A[a][e], e >= a, row by
-// row; then b_a for a = s - nc(nc+1)/2) accumulated by this thread over the
+// Sum s of the normal equations: s < nc(nc+1)/2 is A[a][e] (e >= a, row by
+// row), then b_a for a = s - nc(nc+1)/2.
+__device__ __forceinline__ void nc_sum_index(int nc, int s, int &a, int &e, bool &bsum)
+{
+    const int nA = nc * (nc + 1) / 2;
+    bsum = s >= nA;
+    if (bsum) {
+        a = s - nA;
+        e = a;
+        return;
+    }
+    int rem = s;
+    a = 0;
+    while (rem >= nc - a) {
+        rem -= nc - a;
+        ++a;
+    }
+    e = a + rem;
+}
+
+// The G sums st, st + NST, ..., st + (G-1) NST (those < S; the others are
+// computed on sum S - 1 and not stored) accumulated by this thread over the
 // pixels r, r + R, ... of every tile, in double-float (products exact as
-// float pairs); returns the thread's FP64 partial.  Every thread of the CTA
-// takes part in the tile loads (a < 0: no sum).
-__device__ __forceinline__ double nc_tile_sums(const LensDev &L, const float *M, int nc, int a,
-                                               int e, bool bsum, int r, int R, float *tile,
-                                               int T, int tid, int nthr)
+// float pairs); their FP64 partials go to part[0 .. G).  Lanes hold
+// consecutive st, so a warp reads consecutive columns at one pixel (the
+// tile's odd row stride puts them in distinct banks).  Every thread of the
+// CTA takes part in the tile loads (st < 0: no sums).
+template <int G>
+__device__ __forceinline__ void nc_tile_sums(const LensDev &L, const float *M, int nc, int S,
+                                             int st, int NST, int r, int R, float *tile, int T,
+                                             int tid, int nthr, double *part)
 {
     const int npix = L.npix, TS = T + 1;
     float4 *wt = reinterpret_cast<float4 *>(tile + ((nc * TS + 3) & ~3));
-    float hi = 0.0f, lo = 0.0f;
+    int ca[G], ce[G];
+    bool bs[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        int a, e;
+        nc_sum_index(nc, min(max(st, 0) + g * NST, S - 1), a, e, bs[g]);
+        ca[g] = a * TS;
+        ce[g] = e * TS;
+    }
+    float hi[G], lo[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) hi[g] = lo[g] = 0.0f;
     for (int p0 = 0; p0 < npix; p0 += T) {
         const int n = min(T, npix - p0);
         for (int c = 0; c < nc; ++c)
             for (int i = tid; i < n; i += nthr) tile[c * TS + i] = M[(size_t)c * npix + p0 + i];
         for (int i = tid; i < n; i += nthr) wt[i] = L.wpack[p0 + i];
         __syncthreads();
-        if (a >= 0) {
-            const float *ca = tile + a * TS, *ce = tile + (bsum ? a : e) * TS;
+        if (st >= 0) {
             for (int i = r; i < n; i += R) {
                 const float4 w = wt[i];
-                const float ma = ca[i];
-                float p, er;
-                if (bsum) {
-                    p = w.z * ma;
-                    er = fmaf(w.z, ma, -p);
-                    er = fmaf(w.w, ma, er);
-                } else {
-                    const float me = ce[i];
-                    const float p1 = w.x * ma;
-                    float e1 = fmaf(w.x, ma, -p1);
-                    e1 = fmaf(w.y, ma, e1);
-                    p = p1 * me;
-                    er = fmaf(p1, me, -p);
-                    er = fmaf(e1, me, er);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const float ma = tile[ca[g] + i];
+                    float p, er;
+                    if (bs[g]) {
+                        p = w.z * ma;
+                        er = fmaf(w.z, ma, -p);
+                        er = fmaf(w.w, ma, er);
+                    } else {
+                        const float me = tile[ce[g] + i];
+                        const float p1 = w.x * ma;
+                        float e1 = fmaf(w.x, ma, -p1);
+                        e1 = fmaf(w.y, ma, e1);
+                        p = p1 * me;
+                        er = fmaf(p1, me, -p);
+                        er = fmaf(e1, me, er);
+                    }
+                    df_acc(hi[g], lo[g], p, er);
                 }
-                df_acc(hi, lo, p, er);
             }
         }
         __syncthreads();
     }
-    return (double)hi + (double)lo;
+#pragma unroll
+    for (int g = 0; g < G; ++g) part[g] = (double)hi[g] + (double)lo[g];
 }
 
 // -------------------------------------------------------------- FNNLS
@@ -513,45 +550,45 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
         }
     }
     __syncthreads();
-    // 3. normal equations through shared-memory tiles (the dynamic
-    //    shared memory is free again once the convolution is done): thread
-    //    (s, r) takes sum s (see nc_tile_sums) over pixel phase r of RP;
-    //    the FP64 partials go to the same space after the last tile
+    // 3. normal equations through shared-memory tiles (the dynamic shared
+    //    memory is free again once the convolution is done): thread (st, r)
+    //    takes sums st, st + NST, ... (G of them) over pixel phase r of RP;
+    //    G is 1, or 5 when that spreads the S sums x T pixels of a tile over
+    //    more threads (many columns: S near or above the CTA size) and the
+    //    partials fit; the FP64 partials go to the same space after the last
+    //    tile, then are added in a fixed order
     {
-        const int nA = nc * (nc + 1) / 2, S = nA + nc;
-        const int RP = max(1, nthr / S);
-        const int sr = tid / S, sidx = tid - sr * S;
-        int sa = -1, se = 0;
-        const bool sbsum = sidx >= nA;
-        if (tid < S * RP) {
-            if (sbsum) {
-                sa = sidx - nA;
-            } else {   // row-major upper triangle
-                int rem = sidx, a = 0;
-                while (rem >= nc - a) {
-                    rem -= nc - a;
-                    ++a;
-                }
-                sa = a;
-                se = a + rem;
-            }
+        const int S = nc * (nc + 1) / 2 + nc;
+        const long long cap = (long long)L.nc_smem / (long long)sizeof(double);
+        int G = 1;
+        {   // G = 5 when it spreads the work better: 5 / floor(nthr / ceil(S / 5))
+            // below 1 / floor(nthr / S)
+            const int nst = (S + 4) / 5, den = nthr / nst, den1 = max(1, nthr / S);
+            if (den > 0 && (long long)den * 5 * nst <= cap && 5 * den1 < den) G = 5;
         }
-        const double part = nc_tile_sums(L, Mb, nc, sa, se, sbsum, sr, RP, spsf, T, tid, nthr);
-        double *parts = reinterpret_cast<double *>(spsf);   // [RP][S]
-        if (sa >= 0) parts[tid] = part;
+        const int NST = (S + G - 1) / G, RP = max(1, nthr / NST);
+        const int r = tid / NST;
+        const int st = tid < NST * RP ? tid - r * NST : -1;
+        double part[5];
+        if (G == 5)
+            nc_tile_sums<5>(L, Mb, nc, S, st, NST, r, RP, spsf, T, tid, nthr, part);
+        else
+            nc_tile_sums<1>(L, Mb, nc, S, st, NST, r, RP, spsf, T, tid, nthr, part);
+        double *parts = reinterpret_cast<double *>(spsf);   // [RP][G][NST]
+        if (st >= 0)
+            for (int g = 0; g < G; ++g)
+                if (st + g * NST < S) parts[((size_t)r * G + g) * NST + st] = part[g];
         __syncthreads();
         for (int t = tid; t < S; t += nthr) {
+            const int g = t / NST, stt = t - g * NST;
             double sum = 0.0;
-            for (int rr = 0; rr < RP; ++rr) sum += parts[rr * S + t];
-            if (t >= nA) {
-                sh.b[t - nA] = sum;
+            for (int rr = 0; rr < RP; ++rr) sum += parts[((size_t)rr * G + g) * NST + stt];
+            int a, e;
+            bool bsum;
+            nc_sum_index(nc, t, a, e, bsum);
+            if (bsum) {
+                sh.b[a] = sum;
             } else {
-                int rem = t, a = 0;
-                while (rem >= nc - a) {
-                    rem -= nc - a;
-                    ++a;
-                }
-                const int e = a + rem;
                 sh.A[a * nc + e] = sum;
                 sh.A[e * nc + a] = sum;
             }
