@@ -1442,7 +1442,7 @@ extern "C" int tll_autotune(tll_lens *L, const float *params, int B, void *strea
 
 const char *tll_last_error(void) { return g_err; }
 
-int tll_version(void) { return 100; }
+int tll_version(void) { return 200; }
 
 int tll_create_lens(const float *image, const float *noise, const float *psf,
                     int psf_size, const tll_grid_t *grid, int flags, tll_lens **out)

@@ -1,0 +1,87 @@
+"""Edge cases of the multi-column and sampler paths against the FP64 oracle:
+component lists confined to one plane (lens light only, lensed source
+only), the largest supersampling factor (s = 8, the generic subpixel loop),
+s = 1 with an odd column count, and the device sampler on a masked
+power-law multi-component lens."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2503_08586_gb300 import build, tll
+from paper_2503_08586_gb300 import workloads as W
+
+from test_multi_light_gpu import _case, _to_tll
+from test_parity_gpu import _CHI2_TRUTH, _lens_consts, _ll_ok
+
+pytestmark = pytest.mark.gpu
+
+LENS_ONLY = [dict(type="sersic", plane="lens", index=1.0),
+             dict(type="sersic", plane="lens", index=4.0),
+             dict(type="gauss", plane="lens", free_scale=False, scale=0.2)]
+SOURCE_ONLY = [dict(type="sersic", plane="source", free_index=True),
+               dict(type="gauss", plane="source")]
+
+EDGE = [
+    ("lens_only", 30, 28, 0.07, 4, 9, "moffat", LENS_ONLY, "sie"),
+    ("source_only", 32, 30, 0.07, 4, 11, "gaussian", SOURCE_ONLY, "epl"),
+    ("sub8", 20, 18, 0.1, 8, 7, "gaussian", W.SLACS_COMPS, "sie"),
+    ("sub1_odd", 40, 44, 0.06, 1, 13, "moffat", LENS_ONLY[:1] + SOURCE_ONLY, "sie"),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    tll.load()
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("spec", EDGE, ids=[e[0] for e in EDGE])
+def test_edge_multi_loglike(spec):
+    sl, P, o, ref = _case(90 + EDGE.index(spec), *spec)
+    comps, mass = spec[7], spec[8]
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0, mass=mass)
+    g.set_light(_to_tll(comps))
+    out = g.loglike_batch(torch.from_numpy(np.ascontiguousarray(P)).cuda())
+    torch.cuda.synchronize()
+    _ll_ok(out.cpu().numpy(), ref, sl)
+    # every column of the true vector within the pixel gate's plain part or
+    # a hundredth of the column's peak (the cusp allowance is not recomputed here)
+    gc = g.model_columns_n(P[0], blurred=True).astype(np.float64)
+    oc = o.model(P[0].astype(np.float64))[1]
+    for c in range(len(comps)):
+        tol = 1e-5 * np.abs(oc[c]) + 1e-7 * np.abs(oc[c]).max() + 1e-2 * np.abs(oc[c]).max()
+        assert np.all(np.abs(gc[c] - oc[c]) <= tol)
+    g.close()
+
+
+def test_sampler_on_masked_epl_multi_lens():
+    spec = ("slacs_epl_mask", 40, 40, 0.06, 4, 13, "gaussian", W.SLACS_COMPS, "epl")
+    sl, P, o, ref = _case(95, *spec)
+    W.apply_mask(sl, W.annulus_mask(sl.ny, sl.nx, sl.pixel_scale, 0.3, 1.1, sl.x0, sl.y0))
+    comps = W.SLACS_COMPS
+    om = oracle.MultiLens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, comps, sl.x0, sl.y0,
+                          mass="epl")
+    _, lognorm, _ = _lens_consts(sl)
+    _CHI2_TRUTH[id(sl)] = (sl, max(-2.0 * (om.loglike(sl.truth) - lognorm), 0.0))
+    g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0, mass="epl")
+    g.set_light(_to_tll(comps))
+    assert g.ntrace() < sl.ny * sl.nx
+    lo = np.asarray(sl.truth, np.float32) - 0.2
+    hi = np.asarray(sl.truth, np.float32) + 0.2
+    lo[15:19], hi[15:19] = 0.03, 3.0
+    lo[19], hi[19] = 1.5, 2.5
+    rng = np.random.Generator(np.random.PCG64(9600))
+    x0 = np.clip(sl.truth[None] + rng.normal(scale=0.005, size=(24, g.nparam)), lo, hi)
+    S = tll.Sampler(g, 24, lo, hi, seed=3)
+    S.set_walkers(torch.from_numpy(x0.astype(np.float32)).cuda())
+    chain, lpc, _ = S.run(5)
+    torch.cuda.synchronize()
+    last = chain[-1].cpu().numpy()
+    _ll_ok(lpc[-1].cpu().numpy(), om.loglike_batch(last.astype(np.float64)), sl)
+    _, _, steps, nacc, nprop = S.state()
+    assert steps == 5 and nprop == 5 * 24 and 0 < nacc <= nprop
+    S.close()
+    g.close()
