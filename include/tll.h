@@ -341,7 +341,9 @@ typedef struct {
                            lens of the same signature) */
 } tll_shape_t;
 
-/* The lens's current launch shape. Errors: TLL_EINVAL (NULL argument). */
+/* The lens's current launch shape (for a multi-component lens, the
+ * multi-column kernel's: 1024-thread CTAs, one per SM, its band rows and
+ * shared memory; never tuned). Errors: TLL_EINVAL (NULL argument). */
 int tll_lens_shape(const tll_lens *L, tll_shape_t *out);
 
 /*

@@ -1215,8 +1215,8 @@ void default_tuning_vectors(int B, int nparam, std::vector<float> &p)
 extern "C" int tll_lens_shape(const tll_lens *L, tll_shape_t *out)
 {
     if (!L || !out) return fail(TLL_EINVAL, "NULL argument");
-    shape_out(L->shape, out);
-    out->tuned = L->tuned ? 1 : 0;
+    shape_out(L->nc ? L->nc_shape : L->shape, out);
+    out->tuned = L->tuned && !L->nc ? 1 : 0;
     return TLL_OK;
 }
 

@@ -1,8 +1,9 @@
 """Edge cases of the multi-column and sampler paths against the FP64 oracle:
 component lists confined to one plane (lens light only, lensed source
 only), the largest supersampling factor (s = 8, the generic subpixel loop),
-s = 1 with an odd column count, and the device sampler on a masked
-power-law multi-component lens."""
+s = 1 with an odd column count, an image convolved band by band, an image
+wider than 256 pixels (generic convolution), and the device sampler on a
+masked power-law multi-component lens."""
 import numpy as np
 import pytest
 
@@ -28,6 +29,10 @@ EDGE = [
     ("source_only", 32, 30, 0.07, 4, 11, "gaussian", SOURCE_ONLY, "epl"),
     ("sub8", 20, 18, 0.1, 8, 7, "gaussian", W.SLACS_COMPS, "sie"),
     ("sub1_odd", 40, 44, 0.06, 1, 13, "moffat", LENS_ONLY[:1] + SOURCE_ONLY, "sie"),
+    # the compiled convolution band by band (the padded image exceeds shared memory)
+    ("banded_160x150", 160, 150, 0.05, 3, 31, "moffat", W.SLACS_COMPS, "sie"),
+    # nx > 256: the generic convolution on the global slots
+    ("wide_10x300", 10, 300, 0.03, 2, 5, "gaussian", W.SLACS_COMPS, "sie"),
 ]
 
 
@@ -44,6 +49,9 @@ def test_edge_multi_loglike(spec):
     comps, mass = spec[7], spec[8]
     g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0, mass=mass)
     g.set_light(_to_tll(comps))
+    if spec[0].startswith("banded"):
+        sh = g.shape()
+        assert sh["placement"] == "banded" and 0 < sh["band_rows"] < sl.ny
     out = g.loglike_batch(torch.from_numpy(np.ascontiguousarray(P)).cuda())
     torch.cuda.synchronize()
     _ll_ok(out.cpu().numpy(), ref, sl)
