@@ -110,6 +110,24 @@ def captured_traffic(workload: str, kernel: str = "k_loglike"):
     return float(m.group(1))
 
 
+def captured_pipes(workload: str, kernel: str = "k_loglike"):
+    """The FP32 FMA and XU (MUFU) pipe utilisation of the kernel from the
+    committed ncu summary (instruction rate and busy cycles as fractions of
+    the pipes' peaks, and issue-slot use), or None if there is none or the
+    kernel sources changed since."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"pipes: (.*?) source_hash: (\w+)", open(path).read())
+    if not m or m.group(2) != source_hash(kernel):
+        return None
+    f = m.group(1).split()
+    out = {k: float(v) for k, v in zip(f[0::2], f[1::2])}
+    out["source"] = f"profiles/{kernel}_{workload}.md (ncu --set full)"
+    return out
+
+
 # ------------------------------------------------------------ helpers
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
@@ -433,6 +451,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": captured_traffic(args.workload),
+                     "ncu_pipes": captured_pipes(args.workload),
                      "kernel": ("k_loglike" if args.conv == "fused" else
                                 "k_trace_split + conv + k_sums_split"),
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
@@ -595,6 +614,7 @@ def run_multi(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": captured_traffic(args.workload, "k_loglike_nc"),
+                     "ncu_pipes": captured_pipes(args.workload, "k_loglike_nc"),
                      "kernel": "k_loglike_nc",
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                                    f"x {SM_MAX_MHZ:.0f} MHz"},
