@@ -272,8 +272,12 @@ LensDev lens_dev(const tll_lens *L)
     }
     d.tlist = L->d_tlist;
     d.ntrace = L->d_tlist ? L->ntrace : L->npix;
-    for (int k = 0; k < kMaxK * kMaxK; ++k)
-        d.tk[k] = k < (int)L->psf_norm.size() && L->K <= kMaxK ? L->psf_norm[k] : 0.0f;
+    for (int k = 0; k < kMaxK * (kMaxK + 1); ++k) d.tk[k] = 0.0f;
+    if (L->K <= kMaxK) {
+        const int ts = tap_stride(L->K);
+        for (int r = 0; r < L->K; ++r)
+            for (int c = 0; c < L->K; ++c) d.tk[r * ts + c] = L->psf_norm[r * L->K + c];
+    }
     grid_centre(L, &d.XC, &d.YC);
     d.d = (double)L->dpix / L->sub;
     for (int k = 0; k < kMaxTaps; ++k) {

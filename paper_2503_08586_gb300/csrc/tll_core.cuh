@@ -17,6 +17,11 @@ constexpr int kRedBytes = 32 * 5 * 8;
 constexpr int kMaxTaps = 32;   // separable PSF factors carried in the parameter block
 constexpr int kMaxK = 31;      // largest PSF side of the compiled convolutions
 
+// Row stride of the full PSF in LensDev::tk: K + 1 for the odd sides K,
+// so that every row starts on an 8-byte boundary and its taps are read in
+// pairs; the extra entry of a row is zero.
+__host__ __device__ constexpr int tap_stride(int K) { return K + 1; }
+
 struct LensDev {
     int nx, ny, npix, sub, K, h, sep, mode;
     float JCX, JCY;   // subpixel index of the grid centre, (n*s - 1)/2
@@ -38,7 +43,8 @@ struct LensDev {
     int ntrace;
     int nc_smem;      // multi-column kernel: dynamic shared memory of the launch
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
-    float tk[kMaxK * kMaxK];            // the full PSF (direct convolution)
+    // the full PSF (direct convolution), row r at tk[r * tap_stride(K)]
+    alignas(8) float tk[kMaxK * (kMaxK + 1)];
 };
 
 // Image placement in k_loglike.

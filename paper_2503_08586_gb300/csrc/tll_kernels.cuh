@@ -210,8 +210,12 @@ __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
 // makes kCR rows of its column from one window) fused with the sums.
 // Output sinks of the compiled convolutions: SumsSink adds each output
 // pixel's pair to the five weighted sums (the fused reduction); PairStore
-// writes the pair to two images (the multi-column path).
+// writes the pair to two images (the multi-column path).  kRows: output
+// rows per item of the direct convolution -- two (each window read feeds
+// twice the outputs) where the registers allow it, one where the sink's
+// accumulators or the kernel's other live state would spill.
 struct SumsSink {
+    static constexpr int kRows = 1;
     const LensDev &L;
     float a[10];
     __device__ __forceinline__ void operator()(int pix, float ml, float ms)
@@ -219,7 +223,9 @@ struct SumsSink {
         accum_pixel(ml, ms, L.wpack[pix], a);
     }
 };
+template <int ROWS>
 struct PairStore {
+    static constexpr int kRows = ROWS;
     float *ol, *os;
     __device__ __forceinline__ void operator()(int pix, float ml, float ms)
     {
@@ -312,55 +318,109 @@ __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float
     }
 }
 
-// Direct K x K convolution (any PSF): a thread makes 4 adjacent outputs of
-// one row; for each channel and PSF row it reads one float4 window and
-// applies the row's K taps (each tap read once, used for the 4 outputs);
-// m(i,j) = sum_{r,c} K[r][c] I(i+h-r, j+h-c), summed per PSF row.  Kept to
-// one window and 8 accumulators so it fits the kernel's 64 registers.
+// Direct K x K convolution (any PSF), m(i,j) = sum_{r,c} K[r][c]
+// I(i+h-r, j+h-c), summed per PSF row.  A thread makes 4 adjacent outputs
+// of two adjacent rows: each buffer row's float4 window is read once and
+// meets PSF row r for the upper output row and row r + 1 for the lower one,
+// so a window feeds 8 outputs (half the shared-memory reads of one row at a
+// time); taps come from the parameter block in pairs.
+//
+// direct_window: one window (buffer row `row`, columns from 4g) applied
+// with the K taps of PSF row t0 to the upper outputs (R0) and of row t1 to
+// the lower ones (R1), each as a partial sum added to o0 / o1.
+template <int K, bool R0, bool R1>
+__device__ __forceinline__ void direct_window(const float *row, const float *t0,
+                                              const float *t1, float (&o0)[4], float (&o1)[4])
+{
+    using G = PadGeom<K>;
+    float win[4 * G::NW];
+    const float4 *src = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int k = 0; k < G::NW; ++k) {
+        const float4 v4 = src[k];
+        win[4 * k] = v4.x; win[4 * k + 1] = v4.y;
+        win[4 * k + 2] = v4.z; win[4 * k + 3] = v4.w;
+    }
+    const float2 *p0 = reinterpret_cast<const float2 *>(t0);
+    const float2 *p1 = reinterpret_cast<const float2 *>(t1);
+    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int c2 = 0; c2 < (K + 1) / 2; ++c2) {
+        // pairs of taps when the window meets two rows, else one at a time
+        // (fewer registers)
+        const float2 u = !R0 ? make_float2(0.0f, 0.0f)
+                         : R1 ? p0[c2] : make_float2(t0[2 * c2], 2 * c2 + 1 < K ? t0[2 * c2 + 1] : 0.0f);
+        const float2 w = !R1 ? make_float2(0.0f, 0.0f)
+                         : R0 ? p1[c2] : make_float2(t1[2 * c2], 2 * c2 + 1 < K ? t1[2 * c2 + 1] : 0.0f);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 2 * c2 + e;
+            if (c < K) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float x = win[G::D + K - 1 + q - c];
+                    if (R0) a[q] = fmaf(e ? u.y : u.x, x, a[q]);
+                    if (R1) b[q] = fmaf(e ? w.y : w.x, x, b[q]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (R0) o0[q] += a[q];
+        if (R1) o1[q] += b[q];
+    }
+}
+
 template <int K, class Sink>
 __device__ __forceinline__ void conv_direct_band(const LensDev &L, const float *Pl,
                                                  const float *Ps, int b0, int nrows, int tid,
                                                  int nthr, Sink &sink)
 {
-    using G = PadGeom<K>;
+    constexpr int TS = tap_stride(K), ROWS = Sink::kRows;
     const int nx = L.nx, W = L.W;
-    const int ngroups = (nx + 3) >> 2;
-    for (int item = tid; item < nrows * ngroups; item += nthr) {
-        const int ro = item / ngroups, g = item - ro * ngroups;
-        float o[2][4];
+    const int ngroups = (nx + 3) >> 2, nitems = (nrows + ROWS - 1) / ROWS;
+    for (int item = tid; item < nitems * ngroups; item += nthr) {
+        const int rb = item / ngroups, g = item - rb * ngroups, ro = ROWS * rb;
+        float m[2][ROWS][4];   // [channel][row][column]
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
-            const float *base = (ch == 0 ? Pl : Ps) + 4 * g;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) o[ch][q] = 0.0f;
+            // output row ro + k (image row b0 + ro + k) meets buffer row
+            // ro + t through PSF row K - 1 + k - t; the lower row of an odd
+            // last pair reads the buffer's spare rows and is not stored
+            const float *base = (ch == 0 ? Pl : Ps) + ro * W + 4 * g;
+            float o0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, o1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            // (both forms add the PSF rows' partials in the same order, last
+            // row first, so that one-lens and multi-lens kernels agree bit
+            // for bit)
+            if constexpr (ROWS == 1) {
 #pragma unroll 1
-            for (int r = 0; r < K; ++r) {
-                // PSF row r meets image row (b0 + ro) + h - r = buffer row ro + 2h - r
-                const float4 *src = reinterpret_cast<const float4 *>(base + (ro + 2 * G::h - r) * W);
-                float win[4 * G::NW];
+                for (int t = 0; t < K; ++t)
+                    direct_window<K, true, false>(base + t * W, L.tk + (K - 1 - t) * TS,
+                                                  nullptr, o0, o1);
+            } else {
+                direct_window<K, true, false>(base, L.tk + (K - 1) * TS, nullptr, o0, o1);
+#pragma unroll 1
+                for (int t = 1; t < K; ++t)
+                    direct_window<K, true, true>(base + t * W, L.tk + (K - 1 - t) * TS,
+                                                 L.tk + (K - t) * TS, o0, o1);
+                direct_window<K, false, true>(base + K * W, nullptr, L.tk, o0, o1);
+            }
 #pragma unroll
-                for (int k = 0; k < G::NW; ++k) {
-                    const float4 v4 = src[k];
-                    win[4 * k] = v4.x; win[4 * k + 1] = v4.y;
-                    win[4 * k + 2] = v4.z; win[4 * k + 3] = v4.w;
-                }
-                const float *tr = L.tk + r * K;
-                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    const float t = tr[c];
-                    a0 = fmaf(t, win[G::D + K - 1 - c], a0);
-                    a1 = fmaf(t, win[G::D + K - c], a1);
-                    a2 = fmaf(t, win[G::D + K + 1 - c], a2);
-                    a3 = fmaf(t, win[G::D + K + 2 - c], a3);
-                }
-                o[ch][0] += a0; o[ch][1] += a1; o[ch][2] += a2; o[ch][3] += a3;
+            for (int q = 0; q < 4; ++q) {
+                m[ch][0][q] = o0[q];
+                if constexpr (ROWS == 2) m[ch][ROWS - 1][q] = o1[q];
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = 4 * g + q;
-            if (j < nx) sink((b0 + ro) * nx + j, o[0][q], o[1][q]);
+        for (int k = 0; k < ROWS; ++k) {
+            if (ro + k < nrows) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * g + q;
+                    if (j < nx) sink((b0 + ro + k) * nx + j, m[0][k][q], m[1][k][q]);
+                }
+            }
         }
     }
 }

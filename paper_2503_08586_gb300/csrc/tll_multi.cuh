@@ -459,7 +459,7 @@ struct NcShared {
 // slot (U [nc], M [nc + 1], H [2] images); spsf: the dynamic shared memory
 // (band buffer or PSF taps, reused for the sums' tiles of T pixels).
 // Starts and ends with all threads in step (block barriers inside).
-template <int SUB, int K>
+template <int SUB, int K, int ROWS>
 __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, const float *kc,
                                           double *outp, double *wres, float *U, float *spsf,
                                           NcShared &sh, bool skip, int T, int tid, int nthr)
@@ -519,7 +519,7 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
             const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
             const int step = L.band_rows;
             float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
-            PairStore st{Mb + (size_t)c * npix, Mb + (size_t)c2 * npix};
+            PairStore<ROWS> st{Mb + (size_t)c * npix, Mb + (size_t)c2 * npix};
             for (int b0 = 0; b0 < ny; b0 += step) {
                 const int nrows = min(step, ny - b0);
                 const int nbr = nrows + 2 * h;
@@ -647,7 +647,10 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
             }
             continue;
         }
-        nc_vector<SUB, K>(L, M, kc, R.out + b, R.wr_res, U, spsf, sh, skip, T, tid, nthr);
+        // two output rows per direct-convolution item up to K = 21 (above,
+        // the longer windows would spill); one in the multi-lens kernel
+        nc_vector<SUB, K, (K <= 21 ? 2 : 1)>(L, M, kc, R.out + b, R.wr_res, U, spsf, sh, skip,
+                                             T, tid, nthr);
     }
 }
 
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
             __syncthreads();
             continue;
         }
-        nc_vector<SUB, K>(sL, sM, kc, outp, nullptr, U, spsf, sh, true,
+        nc_vector<SUB, K, 1>(sL, sM, kc, outp, nullptr, U, spsf, sh, true,
                           nc_tile_pixels(sM.nc, (long long)sL.nc_smem), tid, nthr);
     }
 }

@@ -75,7 +75,7 @@ k_conv_direct_split(const __grid_constant__ LensDev L, const float *__restrict__
                         win[4 * q] = v4.x; win[4 * q + 1] = v4.y;
                         win[4 * q + 2] = v4.z; win[4 * q + 3] = v4.w;
                     }
-                    const float *tr = L.tk + r * K;
+                    const float *tr = L.tk + r * tap_stride(K);
                     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
                     for (int c = 0; c < K; ++c) {
