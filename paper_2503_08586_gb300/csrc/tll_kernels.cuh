@@ -346,12 +346,8 @@ __device__ __forceinline__ void direct_window(const float *row, const float *t0,
     float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int c2 = 0; c2 < (K + 1) / 2; ++c2) {
-        // pairs of taps when the window meets two rows, else one at a time
-        // (fewer registers)
-        const float2 u = !R0 ? make_float2(0.0f, 0.0f)
-                         : R1 ? p0[c2] : make_float2(t0[2 * c2], 2 * c2 + 1 < K ? t0[2 * c2 + 1] : 0.0f);
-        const float2 w = !R1 ? make_float2(0.0f, 0.0f)
-                         : R0 ? p1[c2] : make_float2(t1[2 * c2], 2 * c2 + 1 < K ? t1[2 * c2 + 1] : 0.0f);
+        const float2 u = R0 ? p0[c2] : make_float2(0.0f, 0.0f);
+        const float2 w = R1 ? p1[c2] : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = 2 * c2 + e;
