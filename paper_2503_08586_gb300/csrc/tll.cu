@@ -666,7 +666,7 @@ int nc_configure(tll_lens *L)
     {
         cudaFuncAttributes fa;
         CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k));
-        const size_t tile = std::max((size_t)4 * ((L->nc * 257 + 3) & ~3) + 16 * 256 + 64,
+        const size_t tile = std::max((size_t)nc_tile_bytes(L->nc, 256) + 64,
                                      (size_t)kThreads * sizeof(double));
         const size_t cap = (size_t)(share - (long long)fa.sharedSizeBytes);
         S.smem = std::max(S.smem, std::min(tile, cap));

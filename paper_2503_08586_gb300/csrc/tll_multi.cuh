@@ -211,14 +211,23 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
 }
 
 // ----------------------------------------------------- normal equations
-// Shared-memory tile of the sums: pixels [p0, p0 + T) of every blurred
-// column (row stride T + 1, odd, so the lanes of a warp -- consecutive
-// columns e at one pixel -- hit distinct banks) and their weights.
+// Shared-memory tile of the sums, for pixels [p0, p0 + T): every blurred
+// column M_c (row stride T + 1, odd, so the lanes of a warp -- consecutive
+// columns at one pixel -- hit distinct banks), then every weighted column
+// w M_c as an exact float pair (same stride), then the pixels' w d pairs.
+__host__ __device__ inline long long nc_tile_bytes(int nc, int T)
+{
+    const long long ts = (long long)nc * (T + 1);
+    return 4 * ((ts + 1) & ~1LL) + 8 * ts + 8LL * T;
+}
+
+// The largest tile (pixels, a multiple of 32 in [32, 4096]) that fits.
 __host__ __device__ inline int nc_tile_pixels(int nc, long long smem_bytes)
 {
-    // 4 roundup4(nc (T + 1)) + 16 T <= smem_bytes, T a multiple of 32
-    const long long t = (smem_bytes - 4LL * nc - 16) / (4LL * nc + 16);
-    return (int)(t < 32 ? 32 : (t & ~31LL) > 4096 ? 4096 : (t & ~31LL));
+    long long t = (smem_bytes - 12LL * nc - 4) / (12LL * nc + 8);
+    t = t < 32 ? 32 : (t & ~31LL) > 4096 ? 4096 : (t & ~31LL);
+    while (t > 32 && nc_tile_bytes(nc, (int)t) > smem_bytes) t -= 32;
+    return (int)t;
 }
 
 // Sum s of the normal equations: s < nc(nc+1)/2 is A[a][e] (e >= a, row by
@@ -243,56 +252,63 @@ __device__ __forceinline__ void nc_sum_index(int nc, int s, int &a, int &e, bool
 
 // The G sums st, st + NST, ..., st + (G-1) NST (those < S; the others are
 // computed on sum S - 1 and not stored) accumulated by this thread over the
-// pixels r, r + R, ... of every tile, in double-float (products exact as
-// float pairs); their FP64 partials go to part[0 .. G).  Lanes hold
-// consecutive st, so a warp reads consecutive columns at one pixel (the
-// tile's odd row stride puts them in distinct banks).  Every thread of the
-// CTA takes part in the tile loads (st < 0: no sums).
+// pixels r, r + R, ... of every tile, in double-float; their FP64 partials
+// go to part[0 .. G).  Every term is a float pair times a float, the
+// product kept exact as a pair: A[a][e] takes (w M_a) M_e, b_a takes (w d)
+// M_a, where the pairs w M_a (w itself a pair) are formed once per tile
+// pixel at staging rather than once per sum.  Lanes hold consecutive st,
+// so a warp reads consecutive columns at one pixel (the tile's odd row
+// stride puts them in distinct banks).  Every thread of the CTA takes part
+// in the tile loads (st < 0: no sums).
 template <int G>
 __device__ __forceinline__ void nc_tile_sums(const LensDev &L, const float *M, int nc, int S,
                                              int st, int NST, int r, int R, float *tile, int T,
                                              int tid, int nthr, double *part)
 {
     const int npix = L.npix, TS = T + 1;
-    float4 *wt = reinterpret_cast<float4 *>(tile + ((nc * TS + 3) & ~3));
-    int ca[G], ce[G];
-    bool bs[G];
+    float2 *wm = reinterpret_cast<float2 *>(tile + ((nc * TS + 1) & ~1));
+    float2 *wd = wm + nc * TS;
+    // per sum: the pair operand at wm[po + i] (wd = wm + nc TS for b_a) and
+    // the float operand at tile[fo + i]
+    int po[G], fo[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         int a, e;
-        nc_sum_index(nc, min(max(st, 0) + g * NST, S - 1), a, e, bs[g]);
-        ca[g] = a * TS;
-        ce[g] = e * TS;
+        bool bs;
+        nc_sum_index(nc, min(max(st, 0) + g * NST, S - 1), a, e, bs);
+        po[g] = bs ? nc * TS : a * TS;
+        fo[g] = (bs ? a : e) * TS;
     }
     float hi[G], lo[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) hi[g] = lo[g] = 0.0f;
     for (int p0 = 0; p0 < npix; p0 += T) {
         const int n = min(T, npix - p0);
-        for (int c = 0; c < nc; ++c)
-            for (int i = tid; i < n; i += nthr) tile[c * TS + i] = M[(size_t)c * npix + p0 + i];
-        for (int i = tid; i < n; i += nthr) wt[i] = L.wpack[p0 + i];
+        for (int i = tid; i < n; i += nthr) {
+            const float4 w = L.wpack[p0 + i];
+            wd[i] = make_float2(w.z, w.w);
+        }
+        // every thread stages (column, pixel) entries k = c n + i
+        for (int k = tid; k < nc * n; k += nthr) {
+            const int c = k / n, i = k - c * n;
+            const float2 w = *reinterpret_cast<const float2 *>(&L.wpack[p0 + i]);
+            const float m = M[(size_t)c * npix + p0 + i];
+            const float p1 = w.x * m;
+            float e1 = fmaf(w.x, m, -p1);
+            e1 = fmaf(w.y, m, e1);
+            tile[c * TS + i] = m;
+            wm[c * TS + i] = make_float2(p1, e1);
+        }
         __syncthreads();
         if (st >= 0) {
             for (int i = r; i < n; i += R) {
-                const float4 w = wt[i];
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    const float ma = tile[ca[g] + i];
-                    float p, er;
-                    if (bs[g]) {
-                        p = w.z * ma;
-                        er = fmaf(w.z, ma, -p);
-                        er = fmaf(w.w, ma, er);
-                    } else {
-                        const float me = tile[ce[g] + i];
-                        const float p1 = w.x * ma;
-                        float e1 = fmaf(w.x, ma, -p1);
-                        e1 = fmaf(w.y, ma, e1);
-                        p = p1 * me;
-                        er = fmaf(p1, me, -p);
-                        er = fmaf(e1, me, er);
-                    }
+                    const float2 q = wm[po[g] + i];
+                    const float f = tile[fo[g] + i];
+                    const float p = q.x * f;
+                    float er = fmaf(q.x, f, -p);
+                    er = fmaf(q.y, f, er);
                     df_acc(hi[g], lo[g], p, er);
                 }
             }
