@@ -137,8 +137,14 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        """Starts nvidia-smi and waits (up to 5 s) for its first sample:
+        its start-up (NVML initialisation) can hold up the process's CUDA
+        calls for tens of milliseconds, so it must happen before the timed
+        region, not inside it.  Call mark() where the timed region starts;
+        stop() keeps the samples taken after it."""
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
+        self.skip = 0
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -146,6 +152,21 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self._lines() == 0 and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def _lines(self) -> int:
+        try:
+            with open(self.f.name) as fh:
+                return sum(1 for ln in fh if ln.strip())
+        except OSError:
+            return 0
+
+    def mark(self):
+        """The timed region starts: later samples are the ones reported."""
+        self.skip = self._lines()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -160,7 +181,11 @@ class ClockSampler:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for line in self.f.read().strip().splitlines():
+        lines = [ln for ln in self.f.read().strip().splitlines() if ln.strip()]
+        # the samples from the timed region on (all of them if it was
+        # shorter than one sampling interval)
+        lines = lines[self.skip:] if len(lines) > self.skip else lines
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -334,11 +359,12 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- device-resident timing
+    clocks = ClockSampler(local)
     L.profile(True)
     for _ in range(args.warmup):
         L.loglike_batch(p_dev, out)
     barrier()
-    clocks = ClockSampler(local)
+    clocks.mark()
     step_ms, main_ms, pro_ms = [], [], []
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -534,11 +560,12 @@ def run_multi(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    clocks = ClockSampler(local)
     L.profile(True)
     for _ in range(args.warmup):
         L.loglike_batch(p_dev, out)
     barrier()
-    clocks = ClockSampler(local)
+    clocks.mark()
     step_ms, main_ms, pro_ms = [], [], []
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -690,9 +717,10 @@ def run_sampler(args):
     # device loop
     S = tll.Sampler(L, nw, lo, hi, a=2.0, ndim=ndim, seed=W.SEED_BASE)
     S.set_walkers(dev_x0)
+    clocks = ClockSampler(local)
     S.run(args.warmup, keep_chain=False)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks.mark()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     chain, lpc, _ = S.run(nsteps, keep_chain=True)
@@ -907,11 +935,12 @@ def run_ragged(args):
     b = tll.Batcher(use_graph=True)
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(0)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             b.run(lenses, params, outs, stream=stream)
         stream.synchronize()
-        clocks = ClockSampler(0)
+        clocks.mark()
         ms = []
         for k in range(args.steps):
             flush.fill_(float(k))
