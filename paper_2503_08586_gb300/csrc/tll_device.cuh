@@ -387,18 +387,17 @@ __device__ __forceinline__ float poly_atanh_q(float s)
     return fmaf(q, s, 3.333328366e-01f);
 }
 
-// Unit-amplitude Sersic (Eq. 8) at scaled-frame coordinates (x1, x2), i.e.
-// (R_p/r_e)^2 = x1^2 + x2^2 (Eq. 10 folded into the coordinates):
-// t = (R_p/r_e)^{1/n} = 2^{log2((R_p/r_e)^2)/(2n)},
-// I = exp(-b (t - 1)) = 2^{b log2(e) (1 - t)}.  The pow's exponential is
-// range-reduced (its bias would scale with b t); the outer one is not (a
-// bias there is a near-uniform relative scale).
-__device__ __forceinline__ float sersic_scaled(float x1, float x2, float kh, float kl,
-                                               float bh, float bl)
+// Unit-amplitude Sersic (Eq. 8) from L = log2((R_p/r_e)^2) (Eq. 10 folded
+// into the scaled-frame coordinates x1, x2 with (R_p/r_e)^2 = x1^2 + x2^2):
+// t = (R_p/r_e)^{1/n} = 2^{L/(2n)}, I = exp(-b (t - 1)) = 2^{b log2(e) (1 - t)}.
+// 1/(2n) = kh + kl and b log2(e) = bh + bl are float pairs; the lo part of
+// the exponent, kl L, comes in as c (the pixel loop passes kl L of the
+// pixel's first subpixel: kl (L - L0) is far below an ulp of the exponent).
+// The pow's exponential is range-reduced (its bias would scale with b t);
+// the outer one is not (a bias there is a near-uniform relative scale).
+__device__ __forceinline__ float sersic_from_log(float L, float kh, float c, float bh, float bl)
 {
-    const float r2 = fmaf(x1, x1, x2 * x2);
-    const float L = sfu_lg2(r2);
-    const float t = exp2_rr(fmaf(kh, L, kl * L));
+    const float t = exp2_rr(fmaf(kh, L, c));
     const float omt = 1.0f - t;
     return sfu_ex2(fmaf(bh, omt, bl * omt));
 }
@@ -492,29 +491,67 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
                     fmaf(v.sx.ci, fi, v.sx.c0), fmaf(v.sy.ci, fi, v.sy.c0)};
 }
 
-// nlx, nly: minus the lo parts of the source coordinates at this pixel
-// (c0 + cj fj + ci fi of the lo constants, at the pixel's first subpixel;
-// they change by far less than a float ulp across a pixel).
-// MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series ec).
+// The mass deflection (the lens equation's alpha, Eq. 1) in its frame at
+// subpixel column fj of row r.  MODE: 0 SIE fast form, 1 SIE general form,
+// 2 EPL (series ec).
 template <int MODE>
-__device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
-                                         float nlx, float nly, const float *ec, float &il,
-                                         float &is)
+__device__ __forceinline__ void deflect(const VecConst &v, const RowTerms &r, float fj,
+                                        const float *ec, float &ux, float &uy)
 {
-    // mass deflection in its frame (the lens equation's alpha, Eq. 1)
-    float ux, uy;
     if constexpr (MODE == 2)
         epl_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, ux, uy);
     else
         sie_unit<MODE == 0>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
+}
+
+// Per-pixel parts of the float-pair constants.  nlx, nly: minus the source
+// position's lo terms at the pixel -- the source-plane affine map's lo
+// constants, and the lo parts of the deflection map Q times the deflection
+// of the pixel's first subpixel; cl, cs: the lo parts of 1/(2n) of the lens
+// and source Sersics times the log-radii of that subpixel.  Across a
+// pixel's subpixels these terms change by at most an ulp of the source
+// position (near the lens centre, where the deflection turns) and far less
+// than an ulp of the exponents, so the other subpixels reuse them.
+struct PixelLo {
+    float nlx, nly, cl, cs;
+};
+
+// The two unit columns at the pixel's first subpixel (fj, row r), in full;
+// fixes the pixel's lo terms (P.nlx, P.nly come in with the affine map's
+// part and leave with Q's added).
+template <int MODE>
+__device__ __forceinline__ void subpixel_first(const VecConst &v, const RowTerms &r, float fj,
+                                               const float *ec, PixelLo &P, float &il, float &is)
+{
+    float ux, uy;
+    deflect<MODE>(v, r, fj, ec, ux, uy);
+    P.nlx = fmaf(v.q11l, ux, fmaf(v.q12l, uy, P.nlx));
+    P.nly = fmaf(v.q21l, ux, fmaf(v.q22l, uy, P.nly));
     // lens light at theta (Eq. 2, first term)
-    il = sersic_scaled(fmaf(v.lx.cj, fj, r.lx), fmaf(v.ly.cj, fj, r.ly), v.khl, v.kll,
-                       v.bhl, v.bll);
+    const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
+    const float Ll = sfu_lg2(fmaf(x1, x1, x2 * x2));
+    P.cl = v.kll * Ll;
+    il = sersic_from_log(Ll, v.khl, P.cl, v.bhl, v.bll);
     // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
-    const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux, fmaf(v.q12h, uy, fmaf(v.q12l, uy, nlx))));
-    const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux, fmaf(v.q22h, uy, fmaf(v.q22l, uy, nly))));
-    is = sersic_scaled(fmaf(v.sx.cj, fj, r.sx) - t1, fmaf(v.sy.cj, fj, r.sy) - t2, v.khs,
-                       v.kls, v.bhs, v.bls);
+    const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
+    const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
+    const float Ls = sfu_lg2(fmaf(y1, y1, y2 * y2));
+    P.cs = v.kls * Ls;
+    is = sersic_from_log(Ls, v.khs, P.cs, v.bhs, v.bls);
+}
+
+// The two unit columns at any other subpixel of the pixel.
+template <int MODE>
+__device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
+                                         const float *ec, const PixelLo &P, float &il, float &is)
+{
+    float ux, uy;
+    deflect<MODE>(v, r, fj, ec, ux, uy);
+    const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
+    il = sersic_from_log(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl, v.bhl, v.bll);
+    const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
+    const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
+    is = sersic_from_log(sfu_lg2(fmaf(y1, y1, y2 * y2)), v.khs, P.cs, v.bhs, v.bls);
 }
 
 // ------------------------------------------------------ double-float

@@ -82,17 +82,20 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
-        const float nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
-        const float nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
-        float accl = 0.0f, accs = 0.0f;
+        PixelLo lo;
+        lo.nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
+        lo.nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
+        float accl, accs;
+        subpixel_first<MODE>(v, row_terms(v, fi0), fj0, ec, lo, accl, accs);
 #pragma unroll 1
         for (int a = 0; a < sub; ++a) {
             const RowTerms r = row_terms(v, fi0 + (float)a);
 #pragma unroll
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
+                    if (a == 0 && c == 0 && cr == 0) continue;   // the first, done above
                     float il, is;
-                    subpixel<MODE>(v, r, fj0 + (float)(SUB > 0 ? c : cr), nlx, nly, ec, il, is);
+                    subpixel<MODE>(v, r, fj0 + (float)(SUB > 0 ? c : cr), ec, lo, il, is);
                     accl += il;
                     accs += is;
                 }
