@@ -412,6 +412,20 @@ __device__ __forceinline__ float rsqrt_nr(float a)
     return fmaf(y, fmaf(-hy, y, 0.5f), y);
 }
 
+// Per-pixel parts of the float-pair constants, taken at the pixel's first
+// subpixel and reused by the others.  nlx, nly: minus the source position's
+// lo terms -- the source-plane affine map's lo constants, and the lo parts
+// of the deflection map Q times the deflection; cl, cs: the lo parts of
+// 1/(2n) of the lens and source Sersics times the log-radii; dq, dfx, dfy:
+// the lo parts of q and f times the mass-frame x' and the SIE's x'/psi,
+// y'/psi (EPL: de, the magnitude exponent's lo part e1l log2 psi^2 + e0l).
+// Across a pixel these terms change by at most an ulp of what they enter
+// near the lens centre, where the deflection turns, and by far less
+// elsewhere.
+struct PixelLo {
+    float nlx, nly, cl, cs, dq, dfx, dfy;
+};
+
 // SIE deflection (Eq. 12 at gamma = 2, elliptical radius of Eq. 10) in the
 // mass frame at (xp, yp), as alpha' = A (ux, uy) up to the column scales the
 // prologue folds into Q: with psi = sqrt(q^2 xp^2 + yp^2), zx = f xp/psi,
@@ -424,16 +438,22 @@ __device__ __forceinline__ float rsqrt_nr(float a)
 //  general (f > 1/2 here, so 1/f is bounded): ux = atan(zx), reduced to
 //   sign(z) pi/2 - atan(1/z) where |z| > 1; uy = log2(1 + zy) - log2(1 - zy)
 //   = 2 atanh(zy)/ln 2 (|zy| <= f < 1), accurate in absolute terms.
-template <bool FAST>
-__device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
+template <bool FAST, bool FIRST>
+__device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, PixelLo &P,
                                          float &ux, float &uy)
 {
     // q and f enter as double-float constants (their rounding would change
-    // the profile coherently); the products are rounded once
-    const float qx = fmaf(v.ql, xp, v.q * xp);
+    // the profile coherently); the products are rounded once, their lo
+    // parts taken at the pixel's first subpixel
+    if (FIRST) P.dq = v.ql * xp;
+    const float qx = fmaf(v.q, xp, P.dq);
     const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
     const float xr = xp * rpsi, yr = yp * rpsi;
-    const float zx = fmaf(v.fl, xr, v.f * xr), zy = fmaf(v.fl, yr, v.f * yr);
+    if (FIRST) {
+        P.dfx = v.fl * xr;
+        P.dfy = v.fl * yr;
+    }
+    const float zx = fmaf(v.f, xr, P.dfx), zy = fmaf(v.f, yr, P.dfy);
     if (FAST) {
         const float sx = zx * zx, sy = zy * zy;
         ux = fmaf(xr * sx, poly_atan_q(sx), xr);
@@ -457,10 +477,12 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp,
 // the sum by Horner in complex arithmetic over the coefficients ec[0..N]
 // (staged in shared memory per vector), the magnitude as
 // 2^(e0 + e1 log2 psi^2) with a range-reduced exp2.
+template <bool FIRST>
 __device__ __forceinline__ void epl_unit(const VecConst &v, float xp, float yp,
-                                         const float *ec, float &ux, float &uy)
+                                         const float *ec, PixelLo &P, float &ux, float &uy)
 {
-    const float qx = fmaf(v.ql, xp, v.q * xp);
+    if (FIRST) P.dq = v.ql * xp;
+    const float qx = fmaf(v.q, xp, P.dq);
     const float a = fmaxf(fmaf(qx, qx, yp * yp), 1e-24f);
     const float rpsi = rsqrt_nr(a);
     const float c = qx * rpsi, s = yp * rpsi;            // e^{i vphi}
@@ -473,7 +495,8 @@ __device__ __forceinline__ void epl_unit(const VecConst &v, float xp, float yp,
         ar = nr;
     }
     const float L = sfu_lg2(a);
-    const float m = exp2_rr(fmaf(v.e1h, L, fmaf(v.e1l, L, v.e0l)) + v.e0h);
+    if (FIRST) P.dfx = fmaf(v.e1l, L, v.e0l);   // de
+    const float m = exp2_rr(fmaf(v.e1h, L, P.dfx) + v.e0h);
     ux = m * fmaf(c, ar, -s * ai);
     uy = m * fmaf(c, ai, s * ar);
 }
@@ -494,27 +517,16 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
 // The mass deflection (the lens equation's alpha, Eq. 1) in its frame at
 // subpixel column fj of row r.  MODE: 0 SIE fast form, 1 SIE general form,
 // 2 EPL (series ec).
-template <int MODE>
+template <int MODE, bool FIRST>
 __device__ __forceinline__ void deflect(const VecConst &v, const RowTerms &r, float fj,
-                                        const float *ec, float &ux, float &uy)
+                                        const float *ec, PixelLo &P, float &ux, float &uy)
 {
     if constexpr (MODE == 2)
-        epl_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, ux, uy);
+        epl_unit<FIRST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, P, ux, uy);
     else
-        sie_unit<MODE == 0>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ux, uy);
+        sie_unit<MODE == 0, FIRST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), P, ux,
+                                   uy);
 }
-
-// Per-pixel parts of the float-pair constants.  nlx, nly: minus the source
-// position's lo terms at the pixel -- the source-plane affine map's lo
-// constants, and the lo parts of the deflection map Q times the deflection
-// of the pixel's first subpixel; cl, cs: the lo parts of 1/(2n) of the lens
-// and source Sersics times the log-radii of that subpixel.  Across a
-// pixel's subpixels these terms change by at most an ulp of the source
-// position (near the lens centre, where the deflection turns) and far less
-// than an ulp of the exponents, so the other subpixels reuse them.
-struct PixelLo {
-    float nlx, nly, cl, cs;
-};
 
 // The two unit columns at the pixel's first subpixel (fj, row r), in full;
 // fixes the pixel's lo terms (P.nlx, P.nly come in with the affine map's
@@ -524,7 +536,7 @@ __device__ __forceinline__ void subpixel_first(const VecConst &v, const RowTerms
                                                const float *ec, PixelLo &P, float &il, float &is)
 {
     float ux, uy;
-    deflect<MODE>(v, r, fj, ec, ux, uy);
+    deflect<MODE, true>(v, r, fj, ec, P, ux, uy);
     P.nlx = fmaf(v.q11l, ux, fmaf(v.q12l, uy, P.nlx));
     P.nly = fmaf(v.q21l, ux, fmaf(v.q22l, uy, P.nly));
     // lens light at theta (Eq. 2, first term)
@@ -543,10 +555,10 @@ __device__ __forceinline__ void subpixel_first(const VecConst &v, const RowTerms
 // The two unit columns at any other subpixel of the pixel.
 template <int MODE>
 __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, float fj,
-                                         const float *ec, const PixelLo &P, float &il, float &is)
+                                         const float *ec, PixelLo &P, float &il, float &is)
 {
     float ux, uy;
-    deflect<MODE>(v, r, fj, ec, ux, uy);
+    deflect<MODE, false>(v, r, fj, ec, P, ux, uy);
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
     il = sersic_from_log(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl, v.bhl, v.bll);
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));

@@ -176,13 +176,15 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                         X = fmaf(v.lx.cj, fj, r.lx);
                         Y = fmaf(v.ly.cj, fj, r.ly);
                     } else {
+                        // the lo parts of q and f taken at every subpixel here
                         float ux, uy;
+                        PixelLo pl;
                         if constexpr (MODE == 2)
-                            epl_unit(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec,
-                                     ux, uy);
+                            epl_unit<true>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py),
+                                           ec, pl, ux, uy);
                         else
-                            sie_unit<MODE == 0>(v, fmaf(v.px.cj, fj, r.px),
-                                                fmaf(v.py.cj, fj, r.py), ux, uy);
+                            sie_unit<MODE == 0, true>(v, fmaf(v.px.cj, fj, r.px),
+                                                      fmaf(v.py.cj, fj, r.py), pl, ux, uy);
                         const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux,
                                          fmaf(v.q12h, uy, fmaf(v.q12l, uy, nlx))));
                         const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux,
