@@ -390,16 +390,18 @@ __device__ __forceinline__ float poly_atanh_q(float s)
 // Unit-amplitude Sersic (Eq. 8) from L = log2((R_p/r_e)^2) (Eq. 10 folded
 // into the scaled-frame coordinates x1, x2 with (R_p/r_e)^2 = x1^2 + x2^2):
 // t = (R_p/r_e)^{1/n} = 2^{L/(2n)}, I = exp(-b (t - 1)) = 2^{b log2(e) (1 - t)}.
-// 1/(2n) = kh + kl and b log2(e) = bh + bl are float pairs; the lo part of
-// the exponent, kl L, comes in as c (the pixel loop passes kl L of the
-// pixel's first subpixel: kl (L - L0) is far below an ulp of the exponent).
-// The pow's exponential is range-reduced (its bias would scale with b t);
-// the outer one is not (a bias there is a near-uniform relative scale).
-__device__ __forceinline__ float sersic_from_log(float L, float kh, float c, float bh, float bl)
+// 1/(2n) = kh + kl and b log2(e) = bh + bl are float pairs; the lo parts
+// of the two exponents, kl L and bl (1 - t), come in as c and d (the pixel
+// loop passes those of the pixel's first subpixel).  The pow's exponential
+// is range-reduced (its bias would scale with b t); the outer one is not (a
+// bias there is a near-uniform relative scale).
+__device__ __forceinline__ float sersic_omt(float L, float kh, float c)
 {
-    const float t = exp2_rr(fmaf(kh, L, c));
-    const float omt = 1.0f - t;
-    return sfu_ex2(fmaf(bh, omt, bl * omt));
+    return 1.0f - exp2_rr(fmaf(kh, L, c));
+}
+__device__ __forceinline__ float sersic_outer(float omt, float bh, float d)
+{
+    return sfu_ex2(fmaf(bh, omt, d));
 }
 
 // 1/sqrt(a) to about 1 ulp for normal a: the hardware estimate
@@ -416,14 +418,15 @@ __device__ __forceinline__ float rsqrt_nr(float a)
 // subpixel and reused by the others.  nlx, nly: minus the source position's
 // lo terms -- the source-plane affine map's lo constants, and the lo parts
 // of the deflection map Q times the deflection; cl, cs: the lo parts of
-// 1/(2n) of the lens and source Sersics times the log-radii; dq, dfx, dfy:
+// 1/(2n) of the lens and source Sersics times the log-radii, dl, ds: the
+// lo parts of b log2(e) times 1 - t; dq, dfx, dfy:
 // the lo parts of q and f times the mass-frame x' and the SIE's x'/psi,
 // y'/psi (EPL: de, the magnitude exponent's lo part e1l log2 psi^2 + e0l).
 // Across a pixel these terms change by at most an ulp of what they enter
-// near the lens centre, where the deflection turns, and by far less
-// elsewhere.
+// near the lens and light centres, where the deflection turns and t moves
+// fastest, and by far less elsewhere.
 struct PixelLo {
-    float nlx, nly, cl, cs, dq, dfx, dfy;
+    float nlx, nly, cl, cs, dl, ds, dq, dfx, dfy;
 };
 
 // SIE deflection (Eq. 12 at gamma = 2, elliptical radius of Eq. 10) in the
@@ -543,13 +546,17 @@ __device__ __forceinline__ void subpixel_first(const VecConst &v, const RowTerms
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
     const float Ll = sfu_lg2(fmaf(x1, x1, x2 * x2));
     P.cl = v.kll * Ll;
-    il = sersic_from_log(Ll, v.khl, P.cl, v.bhl, v.bll);
+    const float ol = sersic_omt(Ll, v.khl, P.cl);
+    P.dl = v.bll * ol;
+    il = sersic_outer(ol, v.bhl, P.dl);
     // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
     const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
     const float Ls = sfu_lg2(fmaf(y1, y1, y2 * y2));
     P.cs = v.kls * Ls;
-    is = sersic_from_log(Ls, v.khs, P.cs, v.bhs, v.bls);
+    const float os = sersic_omt(Ls, v.khs, P.cs);
+    P.ds = v.bls * os;
+    is = sersic_outer(os, v.bhs, P.ds);
 }
 
 // The two unit columns at any other subpixel of the pixel.
@@ -560,10 +567,10 @@ __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, f
     float ux, uy;
     deflect<MODE, false>(v, r, fj, ec, P, ux, uy);
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
-    il = sersic_from_log(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl, v.bhl, v.bll);
+    il = sersic_outer(sersic_omt(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl), v.bhl, P.dl);
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
     const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
-    is = sersic_from_log(sfu_lg2(fmaf(y1, y1, y2 * y2)), v.khs, P.cs, v.bhs, v.bls);
+    is = sersic_outer(sersic_omt(sfu_lg2(fmaf(y1, y1, y2 * y2)), v.khs, P.cs), v.bhs, P.ds);
 }
 
 // ------------------------------------------------------ double-float

@@ -116,7 +116,7 @@ __device__ inline void decode_multi(const float *__restrict__ p, float *__restri
 // ---------------------------------------------------------------- trace
 // One component at R2 = R_p^2 (its plane's shared frame), constants q[0..5].
 // Sersic (Eq. 8): (R_p/r_e)^2 = R2 / r_e^2, then the same steps as
-// sersic_from_log.  Gaussian: 2^(-log2(e) R2 / (2 sigma^2)).
+// sersic_omt and sersic_outer.  Gaussian: 2^(-log2(e) R2 / (2 sigma^2)).
 __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, float q1, float q2,
                                             float q3, float q4, float q5)
 {
