@@ -210,6 +210,63 @@ def dist_env():
     return ws, rank, local
 
 
+class Ranks:
+    """The ranks of a one-node launch: one process per GPU under torchrun
+    (WORLD_SIZE, RANK, LOCAL_RANK, MASTER_* from the environment), a single
+    rank without it.  The replicas share no data, so the only collectives
+    are the timing ones: a barrier, the maximum of the ranks' times and the
+    sum of their throughputs.  backend "nccl" binds the process to GPU
+    LOCAL_RANK and reduces on it; "gloo" reduces on the host (the CPU tests
+    of this logic)."""
+
+    def __init__(self, backend: str = "nccl"):
+        import torch
+        self.ws, self.rank, self.local = dist_env()
+        self.dist = None
+        self.device = torch.device("cpu")
+        if backend == "nccl":
+            torch.cuda.set_device(self.local if self.ws > 1 else 0)
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        """The largest x over the ranks (a job's time is its slowest rank's)."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, xs) -> list:
+        """The element-wise sum of xs over the ranks (whole-job throughputs)."""
+        if self.dist is None:
+            return [float(x) for x in xs]
+        import torch
+        t = torch.tensor([float(x) for x in xs], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return [float(v) for v in t.tolist()]
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_per_rank_step: float, ws: int, total_ms: float, steps: int) -> float:
+    """Units every rank processed per second: each did units_per_rank_step
+    per step, and the job took the slowest rank's total_ms over steps."""
+    return units_per_rank_step * ws / (total_ms / steps / 1e3)
+
+
 def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096, oracle_lens=None):
     """The FP64 oracle, as it stands, on all host cores over a bounded
     sample of the same batch (about budget_cpu_s of CPU work).  oracle_lens:
@@ -323,16 +380,11 @@ def run_ours(args):
     from paper_2503_08586_gb300 import build, tll
     from paper_2503_08586_gb300 import workloads as W
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    R = Ranks("nccl")
+    ws, rank, local = R.ws, R.rank, R.local
     build.build()
     tll.load()
-    dev = torch.device("cuda", torch.cuda.current_device())
+    dev = R.device
     spec = W.WORKLOADS[args.workload]
     B = args.batch or spec.batch
     lens, params = W.workload(args.workload, tll.columns_renderer, batch=B)
@@ -353,9 +405,7 @@ def run_ours(args):
         L.set_conv(conv_variant, chunk=args.split_chunk)
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        R.barrier()
         torch.cuda.synchronize()
 
     # ---- device-resident timing
@@ -383,14 +433,9 @@ def run_ours(args):
     L.profile(False)
     per_step = 2 if args.conv == "fused" else 1 + 3 * -(-B // args.split_chunk)
     launches = per_step * args.steps
-    total = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = R.max(sum(step_ms))
     ms_per_step = total / args.steps
-    value = B * ws / (ms_per_step / 1e3)
+    value = whole_job_rate(B, ws, total, args.steps)
     ll = out.cpu().numpy()
 
     # ---- end to end through the host-buffer entry point (pinned memory)
@@ -406,13 +451,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         L.loglike_batch_host(p_host, o_host)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = B * ws / (e2e_total / args.steps / 1e3)
+    e2e_total = R.max(sum(e2e_ms))
+    e2e_value = whole_job_rate(B, ws, e2e_total, args.steps)
     assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
 
     # ---- request stream: served (merged launches) vs plain (one per launch)
@@ -422,14 +462,10 @@ def run_ours(args):
                             args.workload)
         plain = run_stream(False, args.stream_jobs, args.stream_iters, args.stream_rate,
                            args.workload)
-        vals = torch.tensor([served["evals_per_s"], plain["evals_per_s"]],
-                            dtype=torch.float64, device=dev)
-        if ws > 1:
-            import torch.distributed as dist
-            # replicas: whole-job throughput is the sum over ranks
-            dist.all_reduce(vals, op=dist.ReduceOp.SUM)
-        served["evals_per_s_all_ranks"] = float(vals[0])
-        plain["evals_per_s_all_ranks"] = float(vals[1])
+        # replicas: whole-job throughput is the sum over ranks
+        vals = R.sum([served["evals_per_s"], plain["evals_per_s"]])
+        served["evals_per_s_all_ranks"] = vals[0]
+        plain["evals_per_s_all_ranks"] = vals[1]
         # the same stream at about 80 % of the measured device throughput
         # (the default rate offers several times what the GPU can serve)
         demand = args.stream_iters * 2750.0   # mean vectors per job
@@ -438,10 +474,7 @@ def run_ours(args):
         served_80["offered_fraction_of_device_rate"] = 0.8
 
     if rank != 0:
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-            dist.destroy_process_group()
+        R.close()
         return None
 
     fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0], info["separable"],
@@ -504,10 +537,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(lens, params)
     if not args.skip_rows and ws == 1 and args.workload == "csst100":
         line["rows"] = measure_rows()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    R.close()
     return line
 
 
@@ -521,16 +551,11 @@ def run_multi(args):
     from paper_2503_08586_gb300 import build, tll
     from paper_2503_08586_gb300 import workloads as W
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    R = Ranks("nccl")
+    ws, rank, local = R.ws, R.rank, R.local
     build.build()
     tll.load()
-    dev = torch.device("cuda", torch.cuda.current_device())
+    dev = R.device
     spec = W.MULTI_WORKLOADS[args.workload]
     comps = spec.comps
     tcomps = [tll.comp(c["type"], c["plane"], c.get("free_scale", True),
@@ -555,9 +580,7 @@ def run_multi(args):
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        R.barrier()
         torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -582,14 +605,9 @@ def run_multi(args):
     barrier()
     clk = clocks.stop()
     L.profile(False)
-    total = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = R.max(sum(step_ms))
     ms_per_step = total / args.steps
-    value = B * ws / (ms_per_step / 1e3)
+    value = whole_job_rate(B, ws, total, args.steps)
     ll = out.cpu().numpy()
     p_host = torch.from_numpy(params).pin_memory()
     o_host = torch.empty(B, dtype=torch.float64).pin_memory()
@@ -603,19 +621,11 @@ def run_multi(args):
         t0 = time.perf_counter()
         L.loglike_batch_host(p_host, o_host)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = B * ws / (e2e_total / args.steps / 1e3)
+    e2e_total = R.max(sum(e2e_ms))
+    e2e_value = whole_job_rate(B, ws, e2e_total, args.steps)
     assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
     if rank != 0:
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-            dist.destroy_process_group()
+        R.close()
         return None
     k = lens.psf.shape[0]
     fpe = flops_per_eval_multi(lens.ny, lens.nx, lens.sub, k, info["separable"], comps)
@@ -655,10 +665,7 @@ def run_multi(args):
         o = oracle.MultiLens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub,
                              comps, lens.x0, lens.y0, mass=spec.mass)
         line["cpu_baseline"] = cpu_baseline(lens, params, oracle_lens=o)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    R.close()
     return line
 
 
@@ -692,8 +699,8 @@ def run_sampler(args):
     from paper_2503_08586_gb300 import build, tll
     from paper_2503_08586_gb300 import workloads as W
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
+    R = Ranks("nccl")
+    ws, rank, local = R.ws, R.rank, R.local
     build.build()
     tll.load()
     nw = args.batch or 4096
@@ -727,7 +734,7 @@ def run_sampler(args):
     e1.record()
     e1.synchronize()
     clk = clocks.stop()
-    dev_ms = e0.elapsed_time(e1)
+    dev_ms = R.max(e0.elapsed_time(e1))
     _, _, steps, nacc, nprop = S.state()
     S.close()
     # host loop (the paper's arrangement)
@@ -754,12 +761,15 @@ def run_sampler(args):
     for _ in range(nsteps):
         for h in (0, 1):
             hacc += _host_stretch_half(x, h, hrng, 2.0, logp, lp, ndim, lo, hi)
-    host_ms = (time.perf_counter() - t0) * 1e3
+    host_ms = R.max((time.perf_counter() - t0) * 1e3)
     L.close()
-    evals = nsteps * nw
+    if rank != 0:
+        R.close()
+        return None
+    evals = nsteps * nw * ws   # every rank runs its own sampler (replicas)
     line = {
         "metric": "log-likelihood evals/s inside a stretch-move sampler loop (csst100)",
-        "value": evals / (dev_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+        "value": evals / (dev_ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": nsteps,
         "warmup": args.warmup, "ms_per_step": dev_ms / nsteps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"csst100 lens, {nw} walkers (two half batches of {nw // 2} "
@@ -777,6 +787,7 @@ def run_sampler(args):
         "device_over_host": host_ms / dev_ms,
         "clocks": clk, "gpu_launches": 8 * nsteps, "impl": "ours",
     }
+    R.close()
     return line
 
 
@@ -905,7 +916,7 @@ def run_ragged(args):
     from paper_2503_08586_gb300 import build, tll
     from paper_2503_08586_gb300 import workloads as W
 
-    torch.cuda.set_device(0)
+    R = Ranks("nccl")
     build.build()
     tll.load()
     t0 = time.perf_counter()
@@ -935,11 +946,12 @@ def run_ragged(args):
     b = tll.Batcher(use_graph=True)
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(R.local)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             b.run(lenses, params, outs, stream=stream)
         stream.synchronize()
+        R.barrier()
         clocks.mark()
         ms = []
         for k in range(args.steps):
@@ -955,20 +967,25 @@ def run_ragged(args):
     nvec = sum(p.shape[0] for p in params)
     nsub = sum(p.shape[0] * L.nx * L.ny * L.sub ** 2 for p, L in zip(params, lenses))
     allfin = all(bool(torch.isfinite(o).all()) for o in outs)
-    step = sum(ms) / len(ms)
+    step = R.max(sum(ms)) / len(ms)
+    if R.rank != 0:
+        R.close()
+        return None
+    R.close()
     return {
         "metric": "log-likelihood evals/s (ragged multi-lens batch, one launch)",
-        "value": nvec / (step / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "value": whole_job_rate(nvec, R.ws, step, 1), "unit": UNIT, "n_gpus": R.ws,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"ragged: {len(lenses)} lenses, sides {{64..200}}, PSF 11..31, "
                                f"4x4 subpixels, {args.ragged_vectors} vectors each, one "
                                "multi-lens launch under a CUDA graph",
-                   "global_batch": nvec, "setup_s": setup_s,
+                   "global_batch": nvec * R.ws, "setup_s": setup_s,
                    "launch_shapes": sorted({(t["threads"], t["ctas_per_sm"], t["placement"])
                                             for t in tuned.values()}) or "default",
                    "l2": "flushed between timed steps"},
-        "subpixel_evals_per_s": nsub / (step / 1e3), "all_finite": allfin,
+        "subpixel_evals_per_s": whole_job_rate(nsub, R.ws, step, 1), "all_finite": allfin,
         "clocks": clk, "gpu_launches": 2 * args.steps, "impl": "ours"}
 
 
