@@ -287,10 +287,16 @@ def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096, oracle_lens=None):
     t = time.perf_counter()
     o.loglike_batch(P[:n], nthreads=cores)
     wall = time.perf_counter() - t
+    # one core, on about a second of work
+    n1 = int(min(len(P), max(1, 1.0 / max(per_cpu, 1e-9))))
+    t = time.perf_counter()
+    o.loglike_batch(P[:n1], nthreads=1)
+    wall1 = time.perf_counter() - t
     return {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {n} of the {len(P)} vectors of one step, FP64 C oracle, "
                       f"OpenMP over vectors on {cores} threads",
-            "wall_s": wall}
+            "wall_s": wall,
+            "one_core": {"value": n1 / wall1, "unit": UNIT, "sample": f"first {n1} vectors"}}
 
 
 # ------------------------------------------------------------ request stream
@@ -818,8 +824,9 @@ def _time_lens(L, p_dev, out, steps, warmup, flush):
 
 def measure_rows(steps=8, warmup=3):
     """Short device-resident measurements of the workloads beyond the
-    headline: the masked csst100, the multi-component SLACS and 32-Gaussian
-    models, and the device-side sampler loop.  Each: evals/s, ms per step,
+    headline: the masked csst100, csst100 with fixed amplitudes
+    (TLL_AMP_FIXED), the multi-component SLACS and 32-Gaussian models, and
+    the device-side sampler loop.  Each: evals/s, ms per step,
     the main kernel's ms and its fraction of the FP32 FMA peak by the
     algorithmic flop count."""
     import torch
@@ -842,6 +849,18 @@ def measure_rows(steps=8, warmup=3):
                             "kernel_ms": statistics.mean(mk), "traced_pixels": L.ntrace(),
                             "roofline_frac": fpe * params.shape[0] / (statistics.mean(mk) / 1e3)
                             / 1e12 / peak}
+    L.close()
+    # csst100 with fixed amplitudes (TLL_AMP_FIXED: the I_e slots, no solve)
+    lens, params = W.workload("csst100", tll.columns_renderer)
+    L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0,
+                 mode=tll.AMP_FIXED)
+    p_dev = torch.from_numpy(params).to(dev)
+    out = torch.empty(params.shape[0], dtype=torch.float64, device=dev)
+    st, mk = _time_lens(L, p_dev, out, steps, warmup, flush)
+    rows["csst100_fixed_amp"] = {"value": params.shape[0] / (statistics.mean(st) / 1e3),
+                                 "ms_per_step": statistics.mean(st), "kernel": "k_loglike",
+                                 "kernel_ms": statistics.mean(mk),
+                                 "path": "TLL_AMP_FIXED: amplitudes from the I_e slots"}
     L.close()
     # multi-component models
     for name in ("slacs120", "mge32"):
