@@ -78,6 +78,23 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
     return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def hbm_check(traffic_bytes, kernel_ms):
+    """The dominant kernel's DRAM traffic per launch (from the committed ncu
+    summary) over its measured launch time, against the measured HBM copy
+    bandwidth of MEASURED_PEAKS.json: how far the ALU-bound kernel is from
+    the memory roof.  None without either number."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if traffic_bytes is None or not os.path.exists(path):
+        return None
+    try:
+        peak = float(json.load(open(path))["hbm_gbs"])
+    except (KeyError, ValueError, OSError):
+        return None
+    gbs = traffic_bytes / (kernel_ms / 1e3) / 1e9
+    return {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
 def source_hash(kernel: str = "k_loglike") -> str:
     """Hash of the sources that define k_loglike (the per-subpixel model, the
     kernel templates and their per-K instantiations); k_loglike_nc adds the
@@ -517,6 +534,7 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": captured_traffic(args.workload),
                      "ncu_pipes": captured_pipes(args.workload),
+                     "hbm": hbm_check(captured_traffic(args.workload), main_avg),
                      "kernel": ("k_loglike" if args.conv == "fused" else
                                 "k_trace_split + conv + k_sums_split"),
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
@@ -658,6 +676,8 @@ def run_multi(args):
                      "frac": achieved / peak,
                      "traffic": captured_traffic(args.workload, "k_loglike_nc"),
                      "ncu_pipes": captured_pipes(args.workload, "k_loglike_nc"),
+                     "hbm": hbm_check(captured_traffic(args.workload, "k_loglike_nc"),
+                                      main_avg),
                      "kernel": "k_loglike_nc",
                      "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                                    f"x {SM_MAX_MHZ:.0f} MHz"},
