@@ -1,0 +1,59 @@
+"""bench.py's host-side pieces that need no GPU: the algorithmic flop
+counts behind the roofline, the machine-readable lines of the committed ncu
+summaries (traffic per launch, pipe fractions, source hash) and the HBM
+check against the measured peaks."""
+import json
+import os
+import re
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+SUMMARIES = [("csst100", "k_loglike"), ("slacs120", "k_loglike_nc"), ("mge32", "k_loglike_nc")]
+
+
+def test_flop_counts_scale_with_the_work():
+    sep = bench.flops_per_eval(100, 100, 4, 21, True, 10000)
+    direct = bench.flops_per_eval(100, 100, 4, 21, False, 10000)
+    assert direct > sep > 0
+    # csst100 by hand: 10^4 pixels x (16 subpixels x (72 + 9) + 2) + 10^4 x
+    # (2 channels x 2 x 42 separable taps + 15 sums)
+    assert sep == 10000 * (16 * 81 + 2) + 10000 * (2 * 2 * 42 + 15)
+    # half the pixels traced: the per-subpixel part halves, the per-pixel part stays
+    half = bench.flops_per_eval(100, 100, 4, 21, True, 5000)
+    assert sep / 2 < half < sep
+    # supersampling 5 x 5 against 4 x 4: the per-subpixel part grows by 25/16
+    assert bench.flops_per_eval(100, 100, 5, 21, True, 10000) > sep
+
+
+@pytest.mark.parametrize("workload,kernel", SUMMARIES)
+def test_summary_machine_lines_parse(workload, kernel):
+    text = open(os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")).read()
+    m = re.search(r"traffic_bytes_per_launch: (\d+) source_hash: ([0-9a-f]{16})", text)
+    assert m and int(m.group(1)) > 0
+    p = re.search(r"pipes: (.*?) source_hash: ([0-9a-f]{16})", text)
+    assert p and p.group(2) == m.group(2)
+    f = p.group(1).split()
+    vals = dict(zip(f[0::2], map(float, f[1::2])))
+    assert set(vals) == {"fma_inst", "xu_inst", "xu_cycles", "alu_cycles", "issue"}
+    assert all(0.0 < v <= 1.0 for v in vals.values())
+    # the reading functions agree with the text when the sources match it
+    if m.group(2) == bench.source_hash(kernel):
+        assert bench.captured_traffic(workload, kernel) == float(m.group(1))
+        assert bench.captured_pipes(workload, kernel)["issue"] == vals["issue"]
+
+
+def test_hbm_check_against_measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):
+        pytest.skip("no measured peaks in this checkout")
+    peak = float(json.load(open(path))["hbm_gbs"])
+    h = bench.hbm_check(2.0e9, 1000.0)      # 2 GB in one second
+    assert h["peak_gbs"] == peak
+    assert h["achieved_gbs"] == pytest.approx(2.0)
+    assert h["frac"] == pytest.approx(2.0 / peak)
+    assert bench.hbm_check(None, 1.0) is None
