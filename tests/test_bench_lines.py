@@ -30,6 +30,18 @@ def test_flop_counts_scale_with_the_work():
     assert bench.flops_per_eval(100, 100, 5, 21, True, 10000) > sep
 
 
+def test_multi_flop_count_by_hand():
+    from paper_2503_08586_gb300 import workloads as W
+    s = W.MULTI_WORKLOADS["slacs120"]
+    got = bench.flops_per_eval_multi(s.ny, s.nx, s.sub, s.psf_size, s.psf_kind == "gaussian",
+                                     s.comps)
+    # per subpixel: grid 4, SIE + shear + lens equation 37, two planes' frames 14,
+    # four Sersics 4 x (13 + 1); per pixel: 4 means, 4 columns x 441 taps x 2,
+    # 14 weighted sums x 3
+    per_sub = 4 + 37 + 14 + 4 * 14
+    assert got == 120 * 120 * (16 * per_sub + 4 + 4 * 441 * 2 + 3 * 14)
+
+
 @pytest.mark.parametrize("workload,kernel", SUMMARIES)
 def test_summary_machine_lines_parse(workload, kernel):
     text = open(os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")).read()
