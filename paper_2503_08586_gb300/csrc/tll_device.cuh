@@ -24,7 +24,7 @@ constexpr int kEplMaxN = 63;     // highest power of the EPL deflection series
 enum : int {
     K_VALID = 0,
     // mass frame: x' = PX0 + PXJ fj + PXI fi, y' = PY0 + PYJ fj + PYI fi;
-    // q, f = sqrt(1 - q^2) (hi, lo), fast-path flag
+    // q, f = sqrt(1 - q^2) (hi, lo), SIE form (1 fast, 2 mid, 0 general)
     K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_QML, K_F, K_FL, K_FAST,
     // lens light, scaled frame (x1 sqrt(q)/r_e, x2/(sqrt(q) r_e)):
     // affine coefficients, 1/(2n) (hi, lo), b log2(e) (hi, lo)
@@ -184,7 +184,7 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     const double qm = (1.0 - e_m) / (1.0 + e_m);
     const double f = 2.0 * sqrt(e_m) / (1.0 + e_m);
     const double A = v[0] * sqrt(qm);
-    bool fast;
+    bool fast, mid;
     double cm, sm;
     half_angle(v[1], v[2], e_m, &cm, &sm);
     {
@@ -197,10 +197,13 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         o[K_PYI] = (float)(d * cm);
         split2(qm, &o[K_QM], &o[K_QML]);
         split2(f, &o[K_F], &o[K_FL]);
-        // fast path when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
-        // for every point: no atan range reduction, no atanh logarithm
-        o[K_FAST] = (f <= qm && f <= 0.5) ? 1.0f : 0.0f;
+        // fast form when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
+        // for every point: no atan range reduction, no atanh logarithm;
+        // mid form when f/q <= 1 but f > 1/2: no atan range reduction, the
+        // atanh by logarithms (1/f < 2 keeps them accurate)
         fast = f <= qm && f <= 0.5;
+        mid = f <= qm && !fast;
+        o[K_FAST] = fast ? 1.0f : mid ? 2.0f : 0.0f;
     }
     const double g1 = v[5], g2 = v[6];
 
@@ -247,10 +250,11 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
         const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
         const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
-        // The fast path's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
-        // path's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
-        // so its columns carry 1/f and ln 2/(2f).
-        double c1 = fast ? 1.0 : 1.0 / f;
+        // The fast form's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
+        // form's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
+        // so its columns carry 1/f and ln 2/(2f); the mid form has the fast
+        // ux and the general uy.
+        double c1 = (fast || mid) ? 1.0 : 1.0 / f;
         double c2 = fast ? 1.0 : 0.34657359027997264 / f;
         double Am = A;
         if (epl) {
@@ -296,7 +300,7 @@ struct VecConst {
     Affine px, py, lx, ly, sx, sy;
     Affine sxl, syl;      // lo parts of sx, sy
     float q, ql, f, fl;   // q, f (hi, lo)
-    bool fast;
+    bool fast, mid;       // SIE form (general when neither)
     float khl, kll, bhl, bll, khs, kls, bhs, bls;
     float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
     bool epl;                       // elliptical power-law mass
@@ -317,7 +321,8 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.sx = load_affine(kc, K_SX0); v.sy = load_affine(kc, K_SY0);
     v.sxl = load_affine(kc, K_SX0L); v.syl = load_affine(kc, K_SY0L);
     v.q = kc[K_QM]; v.ql = kc[K_QML]; v.f = kc[K_F]; v.fl = kc[K_FL];
-    v.fast = kc[K_FAST] != 0.0f;
+    v.fast = kc[K_FAST] == 1.0f;
+    v.mid = kc[K_FAST] == 2.0f;
     v.khl = kc[K_KHL]; v.kll = kc[K_KLL]; v.bhl = kc[K_BHL]; v.bll = kc[K_BLL];
     v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
     v.q11h = kc[K_Q11H]; v.q11l = kc[K_Q11L]; v.q12h = kc[K_Q12H]; v.q12l = kc[K_Q12L];
@@ -441,7 +446,7 @@ struct PixelLo {
 //  general (f > 1/2 here, so 1/f is bounded): ux = atan(zx), reduced to
 //   sign(z) pi/2 - atan(1/z) where |z| > 1; uy = log2(1 + zy) - log2(1 - zy)
 //   = 2 atanh(zy)/ln 2 (|zy| <= f < 1), accurate in absolute terms.
-template <bool FAST, bool FIRST>
+template <int FORM, bool FIRST>
 __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, PixelLo &P,
                                          float &ux, float &uy)
 {
@@ -457,10 +462,14 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, 
         P.dfy = v.fl * yr;
     }
     const float zx = fmaf(v.f, xr, P.dfx), zy = fmaf(v.f, yr, P.dfy);
-    if (FAST) {
+    if (FORM == 0) {
         const float sx = zx * zx, sy = zy * zy;
         ux = fmaf(xr * sx, poly_atan_q(sx), xr);
         uy = fmaf(yr * sy, poly_atanh_q(sy), yr);
+    } else if (FORM == 2) {
+        const float sx = zx * zx;
+        ux = fmaf(xr * sx, poly_atan_q(sx), xr);
+        uy = sfu_lg2(1.0f + zy) - sfu_lg2(1.0f - zy);
     } else {
         const float ax = fabsf(zx);
         const bool big = ax > 1.0f;
@@ -519,7 +528,7 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
 
 // The mass deflection (the lens equation's alpha, Eq. 1) in its frame at
 // subpixel column fj of row r.  MODE: 0 SIE fast form, 1 SIE general form,
-// 2 EPL (series ec).
+// 2 EPL (series ec), 4 SIE mid form.
 template <int MODE, bool FIRST>
 __device__ __forceinline__ void deflect(const VecConst &v, const RowTerms &r, float fj,
                                         const float *ec, PixelLo &P, float &ux, float &uy)
@@ -527,8 +536,8 @@ __device__ __forceinline__ void deflect(const VecConst &v, const RowTerms &r, fl
     if constexpr (MODE == 2)
         epl_unit<FIRST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, P, ux, uy);
     else
-        sie_unit<MODE == 0, FIRST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), P, ux,
-                                   uy);
+        sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, FIRST>(v, fmaf(v.px.cj, fj, r.px),
+                                                           fmaf(v.py.cj, fj, r.py), P, ux, uy);
 }
 
 // The two unit columns at the pixel's first subpixel (fj, row r), in full;

@@ -64,7 +64,8 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
 // Subpixel (J, I) of the supersampled grid has exact integer-or-half
 // offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
 // coordinate is an affine function of them (see decode_vector).
-// MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series coefficients ec).
+// MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series coefficients ec),
+// 4 SIE mid form.
 // skip: trace only the lens's listed pixels (L.tlist), those within the PSF's
 // reach of an unmasked pixel; the others keep whatever finite value they
 // hold, which only ever meets a zero weight.
@@ -582,6 +583,8 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
         trace_image<SUB, 2>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.fast) {
         trace_image<SUB, 0>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
+    } else if (v.mid) {
+        trace_image<SUB, 4>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else {
         trace_image<SUB, 1>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
     }

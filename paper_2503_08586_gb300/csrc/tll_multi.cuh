@@ -132,8 +132,8 @@ __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, floa
 // cq[6 * k], Gaussian flags in gmask) of one plane on every subpixel, binned
 // by the mean, written to U + chan[k] * npix.  GAUSS: every component is a
 // Gaussian (only its first two constants are kept).
-// MODE: 0 / 1 / 2 source plane with the SIE fast / general form or the EPL
-// series (ec); 3 lens plane (no deflection).
+// MODE: 0 / 1 / 4 / 2 source plane with the SIE fast / general / mid form or
+// the EPL series (ec); 3 lens plane (no deflection).
 // skip: trace only the lens's listed pixels (as trace_image).
 template <int SUB, int MODE, int NP, bool GAUSS>
 __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
@@ -183,8 +183,8 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                             epl_unit<true>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py),
                                            ec, pl, ux, uy);
                         else
-                            sie_unit<MODE == 0, true>(v, fmaf(v.px.cj, fj, r.px),
-                                                      fmaf(v.py.cj, fj, r.py), pl, ux, uy);
+                            sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, true>(
+                                v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), pl, ux, uy);
                         const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux,
                                          fmaf(v.q12h, uy, fmaf(v.q12l, uy, nlx))));
                         const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux,
@@ -511,6 +511,8 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
                 trace_pass<SUB, 2, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.fast)
                 trace_pass<SUB, 0, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.mid)
+                trace_pass<SUB, 4, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else
                 trace_pass<SUB, 1, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
         } else {
@@ -520,6 +522,8 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
                 trace_pass<SUB, 2, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.fast)
                 trace_pass<SUB, 0, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+            else if (v.mid)
+                trace_pass<SUB, 4, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else
                 trace_pass<SUB, 1, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
         }
