@@ -203,6 +203,32 @@ def test_columns_parity_plain64():
             assert ok, f"blurred {nm}: worst error / tol = {worst:.3f}"
 
 
+def test_sie_form_boundaries():
+    """The SIE's three forms (fast for q >= sqrt(3)/2, mid for 1/sqrt(2) <= q
+    < sqrt(3)/2, general below) on both sides of each switch and at two
+    position angles: unblurred columns within the pixel gate and log L
+    within the gates."""
+    lens, _ = _workload("plain64", batch=8)
+    g, o = _pair(lens)
+    vecs = []
+    for q in (0.99, 0.8662, 0.8659, 0.7072, 0.7070, 0.55):
+        for phi in (0.3, 1.9):
+            p = np.array(lens.truth, np.float64)
+            e = (1.0 - q) / (1.0 + q)
+            p[1], p[2] = e * np.cos(2 * phi), e * np.sin(2 * phi)
+            vecs.append(p.astype(np.float32))
+    P = np.stack(vecs)
+    for p in P:
+        il, is_ = o.unblurred(p.astype(np.float64))
+        gl, gs = g.model_columns(p, blurred=False)
+        au = _pix_allowance(o, p, blurred=False)
+        for gg, oo, aa, nm in ((gl, il, au[0], "lens"), (gs, is_, au[1], "src")):
+            ok, worst = _pix_ok(gg, oo, aa)
+            assert ok, f"q-form case {nm}: worst error / tol = {worst:.3f}"
+    _ll_ok(_gpu_ll(g, P), o.loglike_batch(P.astype(np.float64)), lens)
+    g.close()
+
+
 def test_model_image_and_amplitudes():
     lens, params = _workload("plain64", batch=4)
     g, o = _pair(lens)
