@@ -95,22 +95,31 @@ def hbm_check(traffic_bytes, kernel_ms):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
 
-def source_hash(kernel: str = "k_loglike") -> str:
-    """Hash of the sources that define k_loglike (the per-subpixel model, the
-    kernel templates and their per-K instantiations); k_loglike_nc adds the
-    multi-column templates."""
+def _code_only(text: str) -> str:
+    """A C/CUDA source without its comments and with its white space
+    collapsed: what the compiler sees, not the prose around it."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return " ".join(text.split())
+
+
+def source_hash(kernel: str = "k_loglike", root: str = None) -> str:
+    """Hash of the code (comments left out) of the sources that define
+    k_loglike (the per-subpixel model, the kernel templates and their per-K
+    instantiations); k_loglike_nc adds the multi-column templates."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    c = os.path.join(ROOT, "paper_2503_08586_gb300", "csrc")
+    c = os.path.join(root or ROOT, "paper_2503_08586_gb300", "csrc")
     extra = ("tll_multi.cuh",) if kernel == "k_loglike_nc" else ()
     files = sorted([os.path.join(c, f) for f in ("tll_device.cuh", "tll_core.cuh",
                                                  "tll_kernels.cuh", "tll_poly.cuh") + extra]
                    + glob.glob(os.path.join(c, "tll_kern_*.cu")))
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -446,6 +446,9 @@ struct PixelLo {
 //  general (f > 1/2 here, so 1/f is bounded): ux = atan(zx), reduced to
 //   sign(z) pi/2 - atan(1/z) where |z| > 1; uy = log2(1 + zy) - log2(1 - zy)
 //   = 2 atanh(zy)/ln 2 (|zy| <= f < 1), accurate in absolute terms.
+//  mid (f/q <= 1 but f > 1/2): the fast ux (|zx| <= 1, no reduction) and
+//   the general uy.
+// FORM: 0 fast, 1 general, 2 mid (decided once per vector by the prologue).
 template <int FORM, bool FIRST>
 __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, PixelLo &P,
                                          float &ux, float &uy)
