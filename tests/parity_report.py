@@ -10,7 +10,9 @@ chi^2 <= 2N, and prior draws -- plus the error of log L differences between
 bulk vectors (what a sampler compares).  hst200 is reported again with the
 split pipeline's two convolutions (direct FP32, and the banded-Toeplitz GEMM
 on the tensor cores); csst100_mask is csst100 fitted in an annulus; the
-multi-component workloads report every column.  Inputs are the seeded synthetic workloads; nothing is
+multi-component workloads report every column; the ragged and served rows
+are a few lenses of those recipes through the batcher and the server (log L
+only: their columns are the one-lens kernels').  Inputs are the seeded synthetic workloads; nothing is
 stored.
 """
 import os
@@ -138,6 +140,100 @@ def report_multi(name, n_prior=16, n_conv=48):
             f"{mx(far)} |")
 
 
+def _regions(got, ref, which, lenses, chi2_truths):
+    """max |dlogL| (count) per region over several lenses: got and ref are
+    concatenated, which[i] is the index of entry i's lens in lenses, and
+    chi2_truths[k] is lens k's chi^2 at its true parameters."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    fin = np.isfinite(ref)
+    bulk = np.zeros(len(ref), bool)
+    near = np.zeros(len(ref), bool)
+    pair = 0.0
+    for k, lens in enumerate(lenses):
+        m = which == k
+        _, lognorm, nun = _lens_consts(lens)
+        chi2 = -2.0 * (ref[m] - lognorm)
+        b = fin[m] & (chi2 <= chi2_truths[k] + BULK_DCHI2)
+        bulk[m] = b
+        near[m] = fin[m] & ~b & (chi2 <= 2 * nun)
+        if b.sum() >= 2:
+            gb, rb = got[m][b], ref[m][b]
+            pair = max(pair, float(np.abs((gb[:, None] - gb[None])
+                                          - (rb[:, None] - rb[None])).max()))
+    far = fin & ~bulk & ~near
+    d = np.abs(got - ref)
+
+    def mx(m):
+        return f"{d[m].max():.2e} ({int(m.sum())})" if m.any() else "-"
+    return mx(bulk), f"{pair:.2e}", mx(near), mx(far)
+
+
+def _against_oracle(items, outs):
+    """Concatenated GPU and oracle log L of (lens, params) items, the lens
+    index of each entry and each lens's chi^2 at its truth."""
+    got, ref, which, chi2_t = [], [], [], []
+    for k, ((sl, P), out) in enumerate(zip(items, outs)):
+        o = oracle.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+        got.append(np.asarray(out))
+        ref.append(o.loglike_batch(np.asarray(P, np.float64)))
+        which.append(np.full(len(P), k))
+        _, lognorm, _ = _lens_consts(sl)
+        chi2_t.append(-2.0 * (o.loglike(sl.truth) - lognorm))
+    return np.concatenate(got), np.concatenate(ref), np.concatenate(which), chi2_t
+
+
+def report_ragged(n_lenses=6, per_lens=48):
+    """A few lenses of the ragged recipe (sides 64..200, PSF 11..31, 4 x 4
+    subpixels, vectors shrinking around each truth) in one multi-lens
+    launch replayed as a CUDA graph (tll_batcher), against the oracle."""
+    items = W.ragged_workload(n_lenses, per_lens, oracle.columns_renderer, seed_offset=40)
+    lenses = [tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0,
+                       batch_only=True) for sl, _ in items]
+    params = [torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda() for _, P in items]
+    b = tll.Batcher(use_graph=True)
+    b.run(lenses, params)            # the capture; the second run replays it
+    outs = b.run(lenses, params)
+    torch.cuda.synchronize()
+    outs = [o.cpu().numpy() for o in outs]
+    b.close()
+    for L in lenses:
+        L.close()
+    got, ref, which, chi2_t = _against_oracle(items, outs)
+    cols = _regions(got, ref, which, [sl for sl, _ in items], chi2_t)
+    sides = sorted({sl.ny for sl, _ in items})
+    ks = sorted({sl.psf.shape[0] for sl, _ in items})
+    return (f"| ragged ({n_lenses} lenses, one graph-replayed multi-lens launch) | sides "
+            f"{sides}, s=4, K {ks} | - | " + " | ".join(cols) + " |")
+
+
+def report_served(n_jobs=4, per_job=48):
+    """Jobs of the request-stream recipe (sides 64..200, PSF 11..31) through
+    the server (tll_server: host buffers, their requests coalesced per
+    launch), against the oracle."""
+    jobs = W.request_stream(n_jobs, iters=1, seed_offset=50)
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 51))
+    items = []
+    for jd in jobs:
+        psf = W.gaussian_psf(jd["psf"], jd["psf"] / 7.0)
+        render = oracle.columns_renderer(W.f32(0.074), 4, psf, jd["side"], jd["side"])
+        sl = W.synth_lens(rng, jd["side"], jd["side"], 0.074, 4, psf, render, "sky+poisson")
+        items.append((sl, W.shrinking_draws(rng, sl.truth, per_job).astype(np.float32)))
+    S = tll.Server(max_jobs=2 * n_jobs)
+    ids = [S.open_job(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+           for sl, _ in items]
+    reqs = [S.submit(j, P) for j, (_, P) in zip(ids, items)]
+    outs = [S.wait(r)[0] for r in reqs]
+    for j in ids:
+        S.close_job(j)
+    S.close()
+    got, ref, which, chi2_t = _against_oracle(items, outs)
+    cols = _regions(got, ref, which, [sl for sl, _ in items], chi2_t)
+    sides = sorted({sl.ny for sl, _ in items})
+    ks = sorted({sl.psf.shape[0] for sl, _ in items})
+    return (f"| served ({n_jobs} jobs through tll_server, host buffers) | sides {sides}, "
+            f"s=4, K {ks} | - | " + " | ".join(cols) + " |")
+
+
 def main():
     build.build()
     tll.load()
@@ -148,6 +244,8 @@ def main():
         print(report(name), flush=True)
     for name in ("slacs120", "mge120", "mge32"):
         print(report_multi(name), flush=True)
+    print(report_ragged(), flush=True)
+    print(report_served(), flush=True)
     # the hst200 convolution (Eq. 3) run three ways
     for conv in (("split, direct FP32", tll.CONV_SPLIT_DIRECT),
                  ("split, Toeplitz 3xTF32 tensor cores", tll.CONV_SPLIT_TOEPLITZ_TC)):
