@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-SUMMARIES = [("csst100", "k_loglike"), ("slacs120", "k_loglike_nc"), ("mge32", "k_loglike_nc")]
+SUMMARIES = [("csst100", "k_loglike"), ("csst100_epl", "k_loglike"), ("slacs120", "k_loglike_nc"),
+             ("mge32", "k_loglike_nc")]
 
 
 def test_flop_counts_scale_with_the_work():
