@@ -70,3 +70,11 @@ def test_hbm_check_against_measured_peak():
     assert h["achieved_gbs"] == pytest.approx(2.0)
     assert h["frac"] == pytest.approx(2.0 / peak)
     assert bench.hbm_check(None, 1.0) is None
+
+
+def test_source_hash_follows_code_not_comments():
+    a = "int f(int x) { return x + 1; }  // one more\n/* block\n comment */"
+    b = "int f(int x)\n{\n    return x + 1;   // a different comment\n}\n"
+    c = "int f(int x) { return x + 2; }"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
