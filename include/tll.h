@@ -252,8 +252,11 @@ const char *tll_server_last_error(void);
  *   Same arguments, results and asynchrony as tll_loglike_batch.
  *   B must be <= TLL_NOALLOC_MAX_B; larger batches give TLL_EINVAL (split
  *     them into several calls).
- *   Scratch: a fixed 20 MiB array compiled into the library, held on every
- *     GPU that loads it until the process exits.  All calls share it and it
+ *   Scratch: a fixed array (TLL_NOALLOC_MAX_B constant blocks, 22 MB)
+ *     compiled into the library.  A device holds it from the first use of
+ *     the library's kernels there (module loading is lazy by default; the
+ *     lens's tll_create_lens already loaded it) until the process exits.
+ *     All calls share it and it
  *     keeps the last call's contents; each call rewrites the part it reads
  *     before reading it.  Calls that overlap on the GPU (different streams,
  *     different lenses) race on it: order them on one stream or synchronise.

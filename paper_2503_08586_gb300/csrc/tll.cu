@@ -933,9 +933,13 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
 // ------------------------------------------- no-allocation entry point
 // Scratch for tll_loglike_batch_noalloc: the per-vector constant blocks
 // that tll_loglike_batch keeps in a lens-owned buffer it may grow.  A fixed
-// array in the module instead, so the call itself allocates nothing; every
-// GPU that loads this library holds it (20 MiB) until the process exits.
-constexpr int kNoAllocMaxB = 16384;
+// array in this module instead, so the call itself allocates nothing.  The
+// module's globals are placed on a device when the module is loaded there
+// (lazily, at the first use of one of its kernels or symbols, by default
+// since CUDA 12.2); tll_create_lens launches k_bn_table from this module,
+// so every device with a lens holds the array (22 MB) from then until the
+// process exits.
+constexpr int kNoAllocMaxB = TLL_NOALLOC_MAX_B;
 static __device__ __align__(256) float g_noalloc_kc[kNoAllocMaxB * NCONST];
 
 namespace {

@@ -19,33 +19,49 @@ constexpr int kEplMaxN = 63;     // highest power of the EPL deflection series
 
 // Per-vector constants written by the prologue, NCONST floats per vector.
 // Every coordinate a subpixel needs is an affine function of its integer
-// offsets (fj, fi) from the grid centre: C0 + CJ fj + CI fi.  *H / *L pairs
-// are the high and low float parts of a constant (double-float).
+// offsets (fj, fi) from the grid centre: C0 + CJ fj + CI fi.  Constants
+// whose rounding to float would move the model coherently are float pairs
+// (hi + lo): the hi parts sit in the slots below, every lo part in the
+// aligned block at K_LO (layout LO_*), which the trace reads once per
+// pixel (load_pixlo) instead of holding it in registers.
 enum : int {
     K_VALID = 0,
     // mass frame: x' = PX0 + PXJ fj + PXI fi, y' = PY0 + PYJ fj + PYI fi;
-    // q, f = sqrt(1 - q^2) (hi, lo), SIE form (1 fast, 2 mid, 0 general)
-    K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_QML, K_F, K_FL, K_FAST,
+    // q, f = sqrt(1 - q^2); SIE form (1 fast, 2 mid, 0 general)
+    K_PX0, K_PXJ, K_PXI, K_PY0, K_PYJ, K_PYI, K_QM, K_F, K_FAST,
     // lens light, scaled frame (x1 sqrt(q)/r_e, x2/(sqrt(q) r_e)):
-    // affine coefficients, 1/(2n) (hi, lo), b log2(e) (hi, lo)
-    K_LX0, K_LXJ, K_LXI, K_LY0, K_LYJ, K_LYI, K_KHL, K_KLL, K_BHL, K_BLL,
-    // source, scaled frame at theta minus shear (linear part; hi parts,
-    // then lo parts) ...
-    K_SX0, K_SXJ, K_SXI, K_SY0, K_SYJ, K_SYI, K_KHS, K_KLS, K_BHS, K_BLS,
-    K_SX0L, K_SXJL, K_SXIL, K_SY0L, K_SYJL, K_SYIL,
+    // affine coefficients, 1/(2n), b log2(e)
+    K_LX0, K_LXJ, K_LXI, K_LY0, K_LYJ, K_LYI, K_KHL, K_BHL,
+    // source, scaled frame at theta minus shear (linear part), 1/(2n),
+    // b log2(e) ...
+    K_SX0, K_SXJ, K_SXI, K_SY0, K_SYJ, K_SYI, K_KHS, K_BHS,
     // ... minus the SIE deflection A (ux, uy) mapped from the mass frame:
-    // [Q11 Q12; Q21 Q22] (hi, lo)
-    K_Q11H, K_Q11L, K_Q12H, K_Q12L, K_Q21H, K_Q21L, K_Q22H, K_Q22L,
+    // [Q11 Q12; Q21 Q22]
+    K_Q11H, K_Q12H, K_Q21H, K_Q22H,
     // fixed amplitudes
     K_IEL, K_IES,
     // elliptical power law (Eq. 12 at any slope): flag, highest power N of
     // the deflection series, the magnitude's exponent e0 + e1 log2(psi^2)
-    // (hi, lo each), the series coefficients c_0 .. c_N
-    K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L, K_EC0,
+    // (hi, lo each)
+    K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L,
+    // the lo parts (float4-aligned), then the EPL series coefficients c_0 .. c_N
+    K_LO = (K_E1L + 4) & ~3,
+    K_EC0 = K_LO + 28,
     NCONST_USED = K_EC0 + kEplMaxN + 1
 };
-constexpr int NCONST = 320;
+// Layout of the lo block: the affine maps' (c0, cj, ci) of the mass frame
+// (PX, PY), the lens-light frame (LX, LY) and the source frame (SX, SY);
+// q and f of the mass; 1/(2n) and b log2(e) of the lens light (KL, BL)
+// and of the source (KS, BS); the deflection map Q.
+enum : int {
+    LO_PX = 0, LO_PY = 3, LO_LX = 6, LO_LY = 9, LO_SX = 12, LO_SY = 15,
+    LO_Q = 18, LO_F = 19, LO_KL = 20, LO_BL = 21, LO_KS = 22, LO_BS = 23,
+    LO_Q11 = 24, LO_Q12 = 25, LO_Q21 = 26, LO_Q22 = 27, LO_N = 28
+};
+constexpr int NCONST = 336;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
+static_assert(K_LO % 4 == 0 && LO_N % 4 == 0 && NCONST % 4 == 0 && K_EC0 == K_LO + LO_N,
+              "float4 reads of the lo block");
 
 // ------------------------------------------------------------------ b_n
 // Root of P(2n, b) = 1/2 (Eq. 9: Gamma(2n) = 2 gamma(2n, b_n)) by a
@@ -189,14 +205,15 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     half_angle(v[1], v[2], e_m, &cm, &sm);
     {
         const double dx = XC - v[3], dy = YC - v[4];
-        o[K_PX0] = (float)(dx * cm + dy * sm);
-        o[K_PXJ] = (float)(d * cm);
-        o[K_PXI] = (float)(d * sm);
-        o[K_PY0] = (float)(-dx * sm + dy * cm);
-        o[K_PYJ] = (float)(-d * sm);
-        o[K_PYI] = (float)(d * cm);
-        split2(qm, &o[K_QM], &o[K_QML]);
-        split2(f, &o[K_F], &o[K_FL]);
+        float *lo = o + K_LO;
+        split2(dx * cm + dy * sm, &o[K_PX0], &lo[LO_PX]);
+        split2(d * cm, &o[K_PXJ], &lo[LO_PX + 1]);
+        split2(d * sm, &o[K_PXI], &lo[LO_PX + 2]);
+        split2(-dx * sm + dy * cm, &o[K_PY0], &lo[LO_PY]);
+        split2(-d * sm, &o[K_PYJ], &lo[LO_PY + 1]);
+        split2(d * cm, &o[K_PYI], &lo[LO_PY + 2]);
+        split2(qm, &o[K_QM], &lo[LO_Q]);
+        split2(f, &o[K_F], &lo[LO_F]);
         // fast form when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
         // for every point: no atan range reduction, no atanh logarithm;
         // mid form when f/q <= 1 but f > 1/2: no atan range reduction, the
@@ -215,14 +232,15 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         half_angle(v[10], v[11], e_l, &c, &s);
         const double s1 = sqrt(q) / re, s2 = 1.0 / (sqrt(q) * re);
         const double dx = XC - v[12], dy = YC - v[13];
-        o[K_LX0] = (float)(s1 * (dx * c + dy * s));
-        o[K_LXJ] = (float)(s1 * d * c);
-        o[K_LXI] = (float)(s1 * d * s);
-        o[K_LY0] = (float)(s2 * (-dx * s + dy * c));
-        o[K_LYJ] = (float)(-s2 * d * s);
-        o[K_LYI] = (float)(s2 * d * c);
-        split2(0.5 / n, &o[K_KHL], &o[K_KLL]);
-        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHL], &o[K_BLL]);
+        float *lo = o + K_LO;
+        split2(s1 * (dx * c + dy * s), &o[K_LX0], &lo[LO_LX]);
+        split2(s1 * d * c, &o[K_LXJ], &lo[LO_LX + 1]);
+        split2(s1 * d * s, &o[K_LXI], &lo[LO_LX + 2]);
+        split2(s2 * (-dx * s + dy * c), &o[K_LY0], &lo[LO_LY]);
+        split2(-s2 * d * s, &o[K_LYJ], &lo[LO_LY + 1]);
+        split2(s2 * d * c, &o[K_LYI], &lo[LO_LY + 2]);
+        split2(0.5 / n, &o[K_KHL], &lo[LO_KL]);
+        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHL], &lo[LO_BL]);
     }
     // source
     {
@@ -239,14 +257,15 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         // double-float: rounding these to float alone would move the whole
         // source plane coherently (a shift and scale near 1e-7), which the
         // likelihood near its optimum resolves
-        split2(s1 * (c * bx0 + s * by0), &o[K_SX0], &o[K_SX0L]);
-        split2(s1 * (c * bxj + s * byj), &o[K_SXJ], &o[K_SXJL]);
-        split2(s1 * (c * bxi + s * byi), &o[K_SXI], &o[K_SXIL]);
-        split2(s2 * (-s * bx0 + c * by0), &o[K_SY0], &o[K_SY0L]);
-        split2(s2 * (-s * bxj + c * byj), &o[K_SYJ], &o[K_SYJL]);
-        split2(s2 * (-s * bxi + c * byi), &o[K_SYI], &o[K_SYIL]);
-        split2(0.5 / n, &o[K_KHS], &o[K_KLS]);
-        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &o[K_BLS]);
+        float *lo = o + K_LO;
+        split2(s1 * (c * bx0 + s * by0), &o[K_SX0], &lo[LO_SX]);
+        split2(s1 * (c * bxj + s * byj), &o[K_SXJ], &lo[LO_SX + 1]);
+        split2(s1 * (c * bxi + s * byi), &o[K_SXI], &lo[LO_SX + 2]);
+        split2(s2 * (-s * bx0 + c * by0), &o[K_SY0], &lo[LO_SY]);
+        split2(s2 * (-s * bxj + c * byj), &o[K_SYJ], &lo[LO_SY + 1]);
+        split2(s2 * (-s * bxi + c * byi), &o[K_SYI], &lo[LO_SY + 2]);
+        split2(0.5 / n, &o[K_KHS], &lo[LO_KS]);
+        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &lo[LO_BS]);
         // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
         const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
         const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
@@ -282,10 +301,10 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
             c1 = c2 = 1.0;
             Am = 2.0 * A / (1.0 + qm);
         }
-        split2(s1 * Am * cd * c1, &o[K_Q11H], &o[K_Q11L]);
-        split2(-s1 * Am * sd * c2, &o[K_Q12H], &o[K_Q12L]);
-        split2(s2 * Am * sd * c1, &o[K_Q21H], &o[K_Q21L]);
-        split2(s2 * Am * cd * c2, &o[K_Q22H], &o[K_Q22L]);
+        split2(s1 * Am * cd * c1, &o[K_Q11H], &lo[LO_Q11]);
+        split2(-s1 * Am * sd * c2, &o[K_Q12H], &lo[LO_Q12]);
+        split2(s2 * Am * sd * c1, &o[K_Q21H], &lo[LO_Q21]);
+        split2(s2 * Am * cd * c2, &o[K_Q22H], &lo[LO_Q22]);
     }
     o[K_IEL] = (float)v[7];
     o[K_IES] = (float)v[14];
@@ -298,11 +317,10 @@ struct Affine {    // v = c0 + cj fj + ci fi
 };
 struct VecConst {
     Affine px, py, lx, ly, sx, sy;
-    Affine sxl, syl;      // lo parts of sx, sy
-    float q, ql, f, fl;   // q, f (hi, lo)
+    float q, f;           // q, f of the mass (hi parts)
     bool fast, mid;       // SIE form (general when neither)
-    float khl, kll, bhl, bll, khs, kls, bhs, bls;
-    float q11h, q11l, q12h, q12l, q21h, q21l, q22h, q22l;
+    float khl, bhl, khs, bhs;
+    float q11h, q12h, q21h, q22h;
     bool epl;                       // elliptical power-law mass
     int en;                         // highest power of its series
     float e0h, e0l, e1h, e1l;       // its magnitude's exponent
@@ -319,18 +337,37 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.px = load_affine(kc, K_PX0); v.py = load_affine(kc, K_PY0);
     v.lx = load_affine(kc, K_LX0); v.ly = load_affine(kc, K_LY0);
     v.sx = load_affine(kc, K_SX0); v.sy = load_affine(kc, K_SY0);
-    v.sxl = load_affine(kc, K_SX0L); v.syl = load_affine(kc, K_SY0L);
-    v.q = kc[K_QM]; v.ql = kc[K_QML]; v.f = kc[K_F]; v.fl = kc[K_FL];
+    v.q = kc[K_QM]; v.f = kc[K_F];
     v.fast = kc[K_FAST] == 1.0f;
     v.mid = kc[K_FAST] == 2.0f;
-    v.khl = kc[K_KHL]; v.kll = kc[K_KLL]; v.bhl = kc[K_BHL]; v.bll = kc[K_BLL];
-    v.khs = kc[K_KHS]; v.kls = kc[K_KLS]; v.bhs = kc[K_BHS]; v.bls = kc[K_BLS];
-    v.q11h = kc[K_Q11H]; v.q11l = kc[K_Q11L]; v.q12h = kc[K_Q12H]; v.q12l = kc[K_Q12L];
-    v.q21h = kc[K_Q21H]; v.q21l = kc[K_Q21L]; v.q22h = kc[K_Q22H]; v.q22l = kc[K_Q22L];
+    v.khl = kc[K_KHL]; v.bhl = kc[K_BHL]; v.khs = kc[K_KHS]; v.bhs = kc[K_BHS];
+    v.q11h = kc[K_Q11H]; v.q12h = kc[K_Q12H]; v.q21h = kc[K_Q21H]; v.q22h = kc[K_Q22H];
     v.epl = kc[K_EPL] != 0.0f;
     v.en = (int)kc[K_EN];
     v.e0h = kc[K_E0H]; v.e0l = kc[K_E0L]; v.e1h = kc[K_E1H]; v.e1l = kc[K_E1L];
     return v;
+}
+
+// The lo block of a vector's constants (LO_* layout), read at a pixel's
+// first subpixel: seven float4 loads (L1-resident: every thread of the CTA
+// reads the same block), live only until the pixel's lo terms are formed.
+// The loads are volatile so that the compiler keeps them in the pixel loop
+// rather than hoisting them out of it and holding 28 registers throughout.
+struct PixLo {
+    float w[LO_N];
+};
+
+__device__ __forceinline__ PixLo load_pixlo(const float *__restrict__ kc)
+{
+    PixLo p;
+    const float *s = kc + K_LO;
+#pragma unroll
+    for (int k = 0; k < LO_N / 4; ++k)
+        asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(p.w[4 * k]), "=f"(p.w[4 * k + 1]), "=f"(p.w[4 * k + 2]),
+                       "=f"(p.w[4 * k + 3])
+                     : "l"(s + 4 * k));
+    return p;
 }
 
 // SFU instructions (PTX ISA: ex2.approx, lg2.approx, rcp.approx).
@@ -449,20 +486,21 @@ struct PixelLo {
 //  mid (f/q <= 1 but f > 1/2): the fast ux (|zx| <= 1, no reduction) and
 //   the general uy.
 // FORM: 0 fast, 1 general, 2 mid (decided once per vector by the prologue).
+// ql, fl: the lo parts of q and f (read when FIRST).
 template <int FORM, bool FIRST>
-__device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, PixelLo &P,
-                                         float &ux, float &uy)
+__device__ __forceinline__ void sie_unit(const VecConst &v, float ql, float fl, float xp,
+                                         float yp, PixelLo &P, float &ux, float &uy)
 {
     // q and f enter as double-float constants (their rounding would change
     // the profile coherently); the products are rounded once, their lo
     // parts taken at the pixel's first subpixel
-    if (FIRST) P.dq = v.ql * xp;
+    if (FIRST) P.dq = ql * xp;
     const float qx = fmaf(v.q, xp, P.dq);
     const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
     const float xr = xp * rpsi, yr = yp * rpsi;
     if (FIRST) {
-        P.dfx = v.fl * xr;
-        P.dfy = v.fl * yr;
+        P.dfx = fl * xr;
+        P.dfy = fl * yr;
     }
     const float zx = fmaf(v.f, xr, P.dfx), zy = fmaf(v.f, yr, P.dfy);
     if (FORM == 0) {
@@ -491,12 +529,13 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float xp, float yp, 
 //   psi e^{i vphi} = q xp + i yp, w = e^{2 i vphi},
 // the sum by Horner in complex arithmetic over the coefficients ec[0..N]
 // (staged in shared memory per vector), the magnitude as
-// 2^(e0 + e1 log2 psi^2) with a range-reduced exp2.
+// 2^(e0 + e1 log2 psi^2) with a range-reduced exp2.  ql: the lo part of q
+// (read when FIRST).
 template <bool FIRST>
-__device__ __forceinline__ void epl_unit(const VecConst &v, float xp, float yp,
+__device__ __forceinline__ void epl_unit(const VecConst &v, float ql, float xp, float yp,
                                          const float *ec, PixelLo &P, float &ux, float &uy)
 {
-    if (FIRST) P.dq = v.ql * xp;
+    if (FIRST) P.dq = ql * xp;
     const float qx = fmaf(v.q, xp, P.dq);
     const float a = fmaxf(fmaf(qx, qx, yp * yp), 1e-24f);
     const float rpsi = rsqrt_nr(a);
@@ -522,52 +561,90 @@ struct RowTerms {
     float px, py, lx, ly, sx, sy;
 };
 
-__device__ __forceinline__ RowTerms row_terms(const VecConst &v, float fi)
+// A pixel's constant terms of the four image-plane coordinates (mass frame
+// x', y'; lens-light frame x1, x2): c0 plus the lo parts of the whole map
+// at the pixel's first subpixel (fj0, fi0), c0_lo + cj_lo fj0 + ci_lo fi0.
+// Rounded to float, the steps cj, ci alone would stretch these frames
+// coherently over the field -- by up to half an ulp of the step per
+// subpixel of offset, about a third of an ulp of the coordinate at the edge
+// of an 11 arcsec field -- a shift and scale of the whole model that the
+// likelihood near its optimum resolves.  Across a pixel the lo sum changes
+// by (s - 1) ulps of the step's lo part, far below a coordinate's rounding,
+// so it is formed once per pixel and enters every subpixel through the row
+// terms.
+struct PixOrigin {
+    float px, py, lx, ly;
+};
+
+__device__ __forceinline__ PixOrigin pixel_origin(const VecConst &v, const PixLo &lc, float fj0,
+                                                  float fi0)
 {
-    return RowTerms{fmaf(v.px.ci, fi, v.px.c0), fmaf(v.py.ci, fi, v.py.c0),
-                    fmaf(v.lx.ci, fi, v.lx.c0), fmaf(v.ly.ci, fi, v.ly.c0),
+    const float *w = lc.w;
+    return PixOrigin{v.px.c0 + fmaf(w[LO_PX + 1], fj0, fmaf(w[LO_PX + 2], fi0, w[LO_PX])),
+                     v.py.c0 + fmaf(w[LO_PY + 1], fj0, fmaf(w[LO_PY + 2], fi0, w[LO_PY])),
+                     v.lx.c0 + fmaf(w[LO_LX + 1], fj0, fmaf(w[LO_LX + 2], fi0, w[LO_LX])),
+                     v.ly.c0 + fmaf(w[LO_LY + 1], fj0, fmaf(w[LO_LY + 2], fi0, w[LO_LY]))};
+}
+
+// Minus the source-plane affine map's lo part at the pixel's first subpixel
+// (the source position's lo terms start from it; P.nlx, P.nly).
+__device__ __forceinline__ void source_lo(const PixLo &lc, float fj0, float fi0, float &nlx,
+                                          float &nly)
+{
+    const float *w = lc.w;
+    nlx = -fmaf(w[LO_SX + 1], fj0, fmaf(w[LO_SX + 2], fi0, w[LO_SX]));
+    nly = -fmaf(w[LO_SY + 1], fj0, fmaf(w[LO_SY + 2], fi0, w[LO_SY]));
+}
+
+__device__ __forceinline__ RowTerms row_terms(const VecConst &v, const PixOrigin &o, float fi)
+{
+    return RowTerms{fmaf(v.px.ci, fi, o.px), fmaf(v.py.ci, fi, o.py),
+                    fmaf(v.lx.ci, fi, o.lx), fmaf(v.ly.ci, fi, o.ly),
                     fmaf(v.sx.ci, fi, v.sx.c0), fmaf(v.sy.ci, fi, v.sy.c0)};
 }
 
 // The mass deflection (the lens equation's alpha, Eq. 1) in its frame at
 // subpixel column fj of row r.  MODE: 0 SIE fast form, 1 SIE general form,
-// 2 EPL (series ec), 4 SIE mid form.
+// 2 EPL (series ec), 4 SIE mid form.  ql, fl: lo parts of q and f (FIRST).
 template <int MODE, bool FIRST>
-__device__ __forceinline__ void deflect(const VecConst &v, const RowTerms &r, float fj,
-                                        const float *ec, PixelLo &P, float &ux, float &uy)
+__device__ __forceinline__ void deflect(const VecConst &v, float ql, float fl, const RowTerms &r,
+                                        float fj, const float *ec, PixelLo &P, float &ux,
+                                        float &uy)
 {
     if constexpr (MODE == 2)
-        epl_unit<FIRST>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, P, ux, uy);
+        epl_unit<FIRST>(v, ql, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, P, ux, uy);
     else
-        sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, FIRST>(v, fmaf(v.px.cj, fj, r.px),
-                                                           fmaf(v.py.cj, fj, r.py), P, ux, uy);
+        sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, FIRST>(
+            v, ql, fl, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), P, ux, uy);
 }
 
 // The two unit columns at the pixel's first subpixel (fj, row r), in full;
-// fixes the pixel's lo terms (P.nlx, P.nly come in with the affine map's
-// part and leave with Q's added).
+// fixes the pixel's lo terms from the lo block lc (P.nlx, P.nly come in
+// with the affine map's part and leave with Q's added).
 template <int MODE>
-__device__ __forceinline__ void subpixel_first(const VecConst &v, const RowTerms &r, float fj,
-                                               const float *ec, PixelLo &P, float &il, float &is)
+__device__ __forceinline__ void subpixel_first(const VecConst &v, const PixLo &lc,
+                                               const RowTerms &r, float fj, const float *ec,
+                                               PixelLo &P, float &il, float &is)
 {
+    const float *w = lc.w;
     float ux, uy;
-    deflect<MODE, true>(v, r, fj, ec, P, ux, uy);
-    P.nlx = fmaf(v.q11l, ux, fmaf(v.q12l, uy, P.nlx));
-    P.nly = fmaf(v.q21l, ux, fmaf(v.q22l, uy, P.nly));
+    deflect<MODE, true>(v, w[LO_Q], w[LO_F], r, fj, ec, P, ux, uy);
+    P.nlx = fmaf(w[LO_Q11], ux, fmaf(w[LO_Q12], uy, P.nlx));
+    P.nly = fmaf(w[LO_Q21], ux, fmaf(w[LO_Q22], uy, P.nly));
     // lens light at theta (Eq. 2, first term)
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
     const float Ll = sfu_lg2(fmaf(x1, x1, x2 * x2));
-    P.cl = v.kll * Ll;
+    P.cl = w[LO_KL] * Ll;
     const float ol = sersic_omt(Ll, v.khl, P.cl);
-    P.dl = v.bll * ol;
+    P.dl = w[LO_BL] * ol;
     il = sersic_outer(ol, v.bhl, P.dl);
     // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
     const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
     const float Ls = sfu_lg2(fmaf(y1, y1, y2 * y2));
-    P.cs = v.kls * Ls;
+    P.cs = w[LO_KS] * Ls;
     const float os = sersic_omt(Ls, v.khs, P.cs);
-    P.ds = v.bls * os;
+    P.ds = w[LO_BS] * os;
     is = sersic_outer(os, v.bhs, P.ds);
 }
 
@@ -577,7 +654,7 @@ __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, f
                                          const float *ec, PixelLo &P, float &il, float &is)
 {
     float ux, uy;
-    deflect<MODE, false>(v, r, fj, ec, P, ux, uy);
+    deflect<MODE, false>(v, 0.0f, 0.0f, r, fj, ec, P, ux, uy);
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
     il = sersic_outer(sersic_omt(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl), v.bhl, P.dl);
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));

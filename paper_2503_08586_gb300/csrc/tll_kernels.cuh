@@ -70,7 +70,7 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
 // reach of an unmasked pixel; the others keep whatever finite value they
 // hold, which only ever meets a zero weight.
 template <int SUB, int MODE>
-__device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
+__device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v, const float *kc,
                                             float *Il, float *Is, int stride, int off,
                                             int tid, int nthr, const float *ec, bool skip)
 {
@@ -83,14 +83,15 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
+        const PixLo lc = load_pixlo(kc);
         PixelLo lo;
-        lo.nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
-        lo.nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
+        source_lo(lc, fj0, fi0, lo.nlx, lo.nly);
+        const PixOrigin po = pixel_origin(v, lc, fj0, fi0);
         float accl, accs;
-        subpixel_first<MODE>(v, row_terms(v, fi0), fj0, ec, lo, accl, accs);
+        subpixel_first<MODE>(v, lc, row_terms(v, po, fi0), fj0, ec, lo, accl, accs);
 #pragma unroll 1
         for (int a = 0; a < sub; ++a) {
-            const RowTerms r = row_terms(v, fi0 + (float)a);
+            const RowTerms r = row_terms(v, po, fi0 + (float)a);
 #pragma unroll
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
@@ -580,13 +581,13 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
     if (v.epl) {
         for (int t = tid; t <= v.en; t += nthr) sepl[t] = kc[K_EC0 + t];
         __syncthreads();
-        trace_image<SUB, 2>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
+        trace_image<SUB, 2>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.fast) {
-        trace_image<SUB, 0>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
+        trace_image<SUB, 0>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.mid) {
-        trace_image<SUB, 4>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
+        trace_image<SUB, 4>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else {
-        trace_image<SUB, 1>(L, v, Il, Is, stride, off, tid, nthr, sepl, skip);
+        trace_image<SUB, 1>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     }
     __syncthreads();
 }

@@ -137,7 +137,7 @@ __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, floa
 // skip: trace only the lens's listed pixels (as trace_image).
 template <int SUB, int MODE, int NP, bool GAUSS>
 __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
-                                           const float *cq, int gmask, int ncp,
+                                           const float *kc, const float *cq, int gmask, int ncp,
                                            const int *chan, float *U, int tid, int nthr,
                                            const float *ec, bool skip)
 {
@@ -156,17 +156,16 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
         const int i = pix / nx, j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
+        const PixLo lc = load_pixlo(kc);
         float nlx = 0.0f, nly = 0.0f;
-        if (MODE != 3) {
-            nlx = -fmaf(v.sxl.cj, fj0, fmaf(v.sxl.ci, fi0, v.sxl.c0));
-            nly = -fmaf(v.syl.cj, fj0, fmaf(v.syl.ci, fi0, v.syl.c0));
-        }
+        if (MODE != 3) source_lo(lc, fj0, fi0, nlx, nly);
+        const PixOrigin po = pixel_origin(v, lc, fj0, fi0);
         float acc[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) acc[k] = 0.0f;
 #pragma unroll 1
         for (int a = 0; a < sub; ++a) {
-            const RowTerms r = row_terms(v, fi0 + (float)a);
+            const RowTerms r = row_terms(v, po, fi0 + (float)a);
 #pragma unroll
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
@@ -179,16 +178,18 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                         // the lo parts of q and f taken at every subpixel here
                         float ux, uy;
                         PixelLo pl;
+                        const float *w = lc.w;
                         if constexpr (MODE == 2)
-                            epl_unit<true>(v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py),
-                                           ec, pl, ux, uy);
+                            epl_unit<true>(v, w[LO_Q], fmaf(v.px.cj, fj, r.px),
+                                           fmaf(v.py.cj, fj, r.py), ec, pl, ux, uy);
                         else
                             sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, true>(
-                                v, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), pl, ux, uy);
-                        const float t1 = fmaf(v.q11h, ux, fmaf(v.q11l, ux,
-                                         fmaf(v.q12h, uy, fmaf(v.q12l, uy, nlx))));
-                        const float t2 = fmaf(v.q21h, ux, fmaf(v.q21l, ux,
-                                         fmaf(v.q22h, uy, fmaf(v.q22l, uy, nly))));
+                                v, w[LO_Q], w[LO_F], fmaf(v.px.cj, fj, r.px),
+                                fmaf(v.py.cj, fj, r.py), pl, ux, uy);
+                        const float t1 = fmaf(v.q11h, ux, fmaf(w[LO_Q11], ux,
+                                         fmaf(v.q12h, uy, fmaf(w[LO_Q12], uy, nlx))));
+                        const float t2 = fmaf(v.q21h, ux, fmaf(w[LO_Q21], ux,
+                                         fmaf(v.q22h, uy, fmaf(w[LO_Q22], uy, nly))));
                         X = fmaf(v.sx.cj, fj, r.sx) - t1;
                         Y = fmaf(v.sy.cj, fj, r.sy) - t2;
                     }
@@ -506,26 +507,26 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
         const int *chan = M.pass_comp[ps];
         if (M.pass_gauss[ps]) {
             if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3, kPassMax, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 3, kPassMax, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.epl)
-                trace_pass<SUB, 2, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 2, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.fast)
-                trace_pass<SUB, 0, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 0, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.mid)
-                trace_pass<SUB, 4, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 4, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else
-                trace_pass<SUB, 1, kPassSrcG, true>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 1, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
         } else {
             if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 3, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.epl)
-                trace_pass<SUB, 2, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 2, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.fast)
-                trace_pass<SUB, 0, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 0, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else if (v.mid)
-                trace_pass<SUB, 4, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 4, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
             else
-                trace_pass<SUB, 1, kPassMix, false>(L, v, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
+                trace_pass<SUB, 1, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
         }
     }
     __syncthreads();

@@ -107,3 +107,14 @@ def test_autotune_cache_file_errors(lib, tmp_path):
     bad.write_text("tll-autotune 1\nGB300 100 100 4 21 1 1000 1\n")   # CTA size not a warp multiple
     assert lib.tll_autotune_load(str(bad).encode()) in (tll.EINVAL, tll.ECUDA)
     lib.tll_autotune_clear()
+
+
+def test_noalloc_limit_matches_header():
+    """The binding's copy of the no-allocation batch limit is the header's
+    (the library takes it from the header's #define)."""
+    txt = open(os.path.join(ROOT, "include", "tll.h")).read()
+    m = re.search(r"#define\s+TLL_NOALLOC_MAX_B\s+(\d+)", txt)
+    assert m, "TLL_NOALLOC_MAX_B not defined in include/tll.h"
+    assert int(m.group(1)) == tll.NOALLOC_MAX_B
+    src = open(os.path.join(ROOT, "paper_2503_08586_gb300", "csrc", "tll.cu")).read()
+    assert re.search(r"kNoAllocMaxB\s*=\s*TLL_NOALLOC_MAX_B\s*;", src)

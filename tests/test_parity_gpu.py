@@ -33,10 +33,16 @@ Tolerances (FP32 forward model, FP64 likelihood):
                 Where a test passes `allow` -- the oracle's own |dlogL| when
                 the image grid moves by POS_ERR in x or in y, the FP32
                 position rounding of the pixel gates' a_i carried to log L
-                -- no region's tolerance is below it: a sharp source on a
-                wide field (0.03 arcsec pixels, |x| up to 4.5 arcsec) moves
-                log L by up to 2e-2 under such a shift, away from the bulk,
-                which no FP32 evaluation of its coordinates can avoid.
+                -- no region outside the posterior bulk has a tolerance
+                below it: a sharp source on a wide field (0.03 arcsec
+                pixels, |x| up to 4.5 arcsec) moves log L by up to 2e-2
+                under such a shift away from the bulk, which no FP32
+                evaluation of its coordinates can avoid.  The bulk keeps
+                the literal 1e-3 on images up to 200 x 200, the scope of
+                that tolerance; on the one wider test image (10 x 300 at
+                0.03 arcsec, s = 2, a sharp source) the oracle's own log L
+                moves by 1.4e-3 at the truth under that shift, and the
+                allowance applies in its bulk as well.
                 The bound is the first-order effect of a relative model error
                 <= eps on every pixel: dchi2 = 2 sum w (m - d) dm <= 2 eps
                 sqrt(chi2) sqrt(sum w m^2) (Cauchy-Schwarz) and
@@ -135,7 +141,9 @@ def _ll_ok(gpu, ora, lens, mode=0, allow=None):
     """Check log L against the gates above; returns the |dlogL| array.
     mode 1 (fixed amplitudes) has no posterior bulk at the truth's
     amplitudes, so only the error-model regions apply there.  allow: the
-    per-vector position allowance described above (or None)."""
+    per-vector position allowance described above (or None).  The bulk's
+    literal 1e-3 holds for images up to 200 x 200 (the stated scope of that
+    tolerance); a wider image keeps the allowance in its bulk too."""
     gpu, ora = np.asarray(gpu), np.asarray(ora)
     assert np.array_equal(np.isneginf(gpu), np.isneginf(ora)), "validity differs"
     fin = ~np.isneginf(ora)
@@ -147,11 +155,15 @@ def _ll_ok(gpu, ora, lens, mode=0, allow=None):
     eps = np.where(near, EPS_NEAR, EPS_M)
     tol = np.maximum(LL_ABS, eps * np.sqrt(chi2) * (np.sqrt(dWd) + np.sqrt(chi2)))
     bulk = np.zeros_like(near)
-    if mode == 0 and getattr(lens, "truth", None) is not None:
-        bulk = chi2 <= _chi2_truth(lens) + BULK_DCHI2
-        tol = np.where(bulk, LL_ABS, tol)
     if allow is not None:
         tol = np.maximum(tol, np.asarray(allow)[fin])
+    if mode == 0 and getattr(lens, "truth", None) is not None:
+        # the posterior bulk takes the literal 1e-3 whatever the allowance
+        bulk = chi2 <= _chi2_truth(lens) + BULK_DCHI2
+        if allow is None or max(lens.ny, lens.nx) <= 200:
+            tol = np.where(bulk, LL_ABS, tol)
+        else:
+            tol = np.where(bulk, np.maximum(LL_ABS, np.asarray(allow)[fin]), tol)
     k = int(np.argmax(d / tol))
     assert np.all(d <= tol), (
         f"|dlogL| {d[k]:.3e} > tol {tol[k]:.3e} (chi2 {chi2[k]:.4g}, near {near[k]}, "

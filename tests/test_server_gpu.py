@@ -158,3 +158,46 @@ def test_autotune_at_admission(lenses):
         assert np.allclose(out[fin], ref[fin], rtol=1e-10, atol=1e-8)
         assert S.close_job(j)
     S.close()
+
+
+# Jobs at the wide end of the request-stream recipe (0.074 arcsec pixels,
+# sides up to 200: 11-15 arcsec fields, where a coherent FP32 stretch of the
+# image-plane grid would move log L by more than 1e-3): side, PSF side.
+WIDE = [(200, 31), (176, 25), (148, 17), (154, 27)]
+
+
+def test_served_wide_fields_against_oracle():
+    """Jobs of 148-200 px at 0.074 arcsec through the server (host buffers,
+    requests coalesced into shared launches) against the FP64 oracle: every
+    vector within the parity gates, and |dlogL| <= 1e-3 on each job's
+    posterior bulk (chi^2 within 50 of the truth's)."""
+    from test_parity_gpu import BULK_DCHI2, LL_ABS, _chi2_truth, _lens_consts, _ll_ok
+    build.build()
+    tll.load()
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 77))
+    items = []
+    for side, k in WIDE:
+        psf = W.gaussian_psf(k, k / 7.0)
+        render = oracle.columns_renderer(W.f32(0.074), 4, psf, side, side)
+        sl = W.synth_lens(rng, side, side, 0.074, 4, psf, render, "sky+poisson")
+        # vectors converging on the truth (the second half sits in the bulk)
+        P = W.shrinking_draws(rng, sl.truth, 48, lo_frac=1e-6)[16:]
+        items.append((sl, np.ascontiguousarray(P, np.float32)))
+    S = tll.Server(max_jobs=8)
+    ids = [_open(S, sl) for sl, _ in items]
+    assert all(j is not None for j in ids)
+    reqs = [S.submit(j, P) for j, (_, P) in zip(ids, items)]
+    outs = [S.wait(r)[0].copy() for r in reqs]
+    for j in ids:
+        assert S.close_job(j)
+    S.close()
+    worst = 0.0
+    for (sl, P), got in zip(items, outs):
+        o = oracle.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+        ref = o.loglike_batch(P.astype(np.float64))
+        _ll_ok(got, ref, sl)
+        _, lognorm, _ = _lens_consts(sl)
+        bulk = np.isfinite(ref) & (-2.0 * (ref - lognorm) <= _chi2_truth(sl) + BULK_DCHI2)
+        assert bulk.sum() >= 8, f"{sl.ny} px: only {bulk.sum()} vectors in the bulk"
+        worst = max(worst, float(np.abs(got - ref)[bulk].max()))
+    assert worst <= LL_ABS, f"bulk |dlogL| {worst:.3e}"
