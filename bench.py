@@ -33,9 +33,9 @@ if ROOT not in sys.path:
 METRIC = ("log-likelihood evals/s (100×100, 4×4 subpix) served vs plain; "
           "p50/p99 latency")
 UNIT = "evals/s"
-N_SM = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (sm_10x: 4 sub-partitions x 32)
+MUFU_LANES_PER_SM = 16    # transcendental (XU / MUFU) lanes per SM (4 per sub-partition)
+SM_MAX_MHZ = 2070.0       # only when neither a clock sample nor nvidia-smi's maximum exists
 
 
 # ------------------------------------------------------------ work model
@@ -74,8 +74,65 @@ def flops_per_eval_multi(ny, nx, sub, k, separable, comps) -> float:
     return float(ny * nx * per_pix)
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ) -> float:
-    return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def transcendentals_per_eval(sub, ntrace) -> float:
+    """Transcendental evaluations of one two-column evaluation: per
+    subpixel sqrt, atan, atanh of the SIE and sqrt, pow, exp of each Sersic
+    (the 9 of flops_per_eval)."""
+    return float(ntrace * sub * sub * 9)
+
+
+def transcendentals_per_eval_multi(ny, nx, sub, comps) -> float:
+    """The same for a multi-component model: the SIE's 3 when a
+    source-plane component exists, 3 per Sersic, 1 per Gaussian."""
+    per_sub = 3 if any(c["plane"] == "source" for c in comps) else 0
+    per_sub += sum(3 if c["type"] == "sersic" else 1 for c in comps)
+    return float(ny * nx * sub * sub * per_sub)
+
+
+def device_sms():
+    """The current CUDA device's SM count (device properties), or None."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(
+                torch.cuda.current_device()).multi_processor_count)
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def pipe_peaks(clocks=None, n_sm=None) -> dict:
+    """Peaks of the FP32 FMA and MUFU pipes at run time: the SM count from
+    the device properties, times the SM clock sampled under load in the
+    timed region (median; else nvidia-smi's maximum SM clock, else
+    SM_MAX_MHZ), times the lanes per SM."""
+    n = n_sm or device_sms()
+    n_src = "device properties"
+    if not n:
+        n, n_src = 152, "GB300's count (no device)"
+    mhz, src = None, None
+    if clocks:
+        if clocks.get("sm_mhz"):
+            mhz, src = float(clocks["sm_mhz"]), "median SM clock sampled in the timed region"
+        elif clocks.get("sm_max_mhz"):
+            mhz, src = float(clocks["sm_max_mhz"]), "maximum SM clock (nvidia-smi)"
+    if mhz is None:
+        mhz, src = SM_MAX_MHZ, "GB300's maximum SM clock (no sample)"
+    return {"n_sm": n, "mhz": mhz,
+            "fp32_tflops": n * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            "mufu_gops": n * MUFU_LANES_PER_SM * mhz * 1e6 / 1e9,
+            "basis": f"FP32 FMA: {n} SMs ({n_src}) x {FP32_LANES_PER_SM} lanes x 2 x "
+                     f"{mhz:.0f} MHz ({src})",
+            "mufu_basis": f"MUFU: {n} SMs x {MUFU_LANES_PER_SM} lanes x {mhz:.0f} MHz ({src})"}
+
+
+def mufu_roof(trans_per_launch, kernel_ms, peaks) -> dict:
+    """The kernel's algorithmic transcendental rate against the MUFU
+    pipe's peak (each evaluation counted as one MUFU operation, whatever
+    the kernel computes it with)."""
+    g = trans_per_launch / (kernel_ms / 1e3) / 1e9
+    return {"achieved": g, "peak": peaks["mufu_gops"], "unit": "Gop/s",
+            "frac": g / peaks["mufu_gops"], "peak_basis": peaks["mufu_basis"]}
 
 
 def hbm_check(traffic_bytes, kernel_ms):
@@ -326,26 +383,59 @@ def cpu_baseline(lens, params, budget_cpu_s=15.0, max_n=4096, oracle_lens=None):
 
 
 # ------------------------------------------------------------ request stream
+def stream_lenses(n_jobs: int, workload: str, seed_offset: int = 20):
+    """The lenses of a request stream: n_jobs lenses of the named workload's
+    geometry, or (workload "config5") the served-stream recipe's mixed sizes
+    -- image side ~U[64, 200] at 0.074"/px, 4x4 subpixels, Gaussian PSF of
+    side ~U{11, 13, ..., 31} with FWHM = side/7 px (workloads.request_stream).
+    Returns (lenses, rng for the stream's arrivals)."""
+    from paper_2503_08586_gb300 import tll
+    from paper_2503_08586_gb300 import workloads as W
+
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + seed_offset))
+    lenses = []
+    if workload == "config5":
+        cache = {}
+        for jd in W.request_stream(n_jobs, iters=1, seed_offset=seed_offset + 1):
+            key = (jd["side"], jd["psf"])
+            if key not in cache:
+                psf = W.gaussian_psf(jd["psf"], jd["psf"] / 7.0)
+                cache[key] = (psf, tll.columns_renderer(W.f32(0.074), 4, psf, jd["side"],
+                                                         jd["side"]))
+            psf, render = cache[key]
+            lenses.append(W.synth_lens(rng, jd["side"], jd["side"], 0.074, 4, psf, render,
+                                       "sky+poisson"))
+        for _, r in cache.values():
+            r.lens.close()
+        return lenses, rng
+    spec = W.WORKLOADS[workload]
+    psf = W.make_psf(spec)
+    render = tll.columns_renderer(W.f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx)
+    lenses = [W.synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf, render,
+                           spec.noise_kind) for _ in range(n_jobs)]
+    render.lens.close()
+    return lenses, rng
+
+
 def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload: str,
-               seed_offset: int = 20):
+               seed_offset: int = 20, lenses=None):
     """A Poisson stream of lens-modelling jobs through the server, each a
     closed-loop synthetic sampler: `iters` batches of U{500..5000} vectors
     drawn from a Gaussian shrinking around its lens's truth, each submitted
     from host memory after the previous result came back.  coalesce=True is
     the served path (requests of all jobs merged per launch, 2 launches in
     flight, graph replay); False is the plain path (one request per launch,
-    one at a time).  Returns throughput and request latencies."""
+    one at a time).  lenses: the jobs' lenses (stream_lenses), made here
+    when not given.  Returns throughput and request latencies."""
     import threading
     from paper_2503_08586_gb300 import tll
     from paper_2503_08586_gb300 import workloads as W
 
-    spec = W.WORKLOADS[workload]
-    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + seed_offset))
-    psf = W.make_psf(spec)
-    render = tll.columns_renderer(W.f32(spec.pixel_scale), spec.sub, psf, spec.ny, spec.nx)
-    lenses = [W.synth_lens(rng, spec.ny, spec.nx, spec.pixel_scale, spec.sub, psf, render,
-                           spec.noise_kind) for _ in range(n_jobs)]
-    render.lens.close()
+    if lenses is None:
+        lenses, rng = stream_lenses(n_jobs, workload, seed_offset)
+    else:
+        rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + seed_offset + 2))
+    n_jobs = len(lenses)
     arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
     seeds = rng.integers(0, 2 ** 31, n_jobs)
     S = tll.Server(max_jobs=max(64, n_jobs), max_vectors_per_launch=16384,
@@ -396,6 +486,8 @@ def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload
         raise RuntimeError(errors[0])
     mean_b = vecs[0] / max(1, len(lat))
     return {"evals_per_s": vecs[0] / wall, "wall_s": wall, "requests": len(lat),
+            "path": "served: requests coalesced per launch" if coalesce else
+                    "plain: one request per launch, one at a time",
             "vectors": vecs[0], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "launches": st["launches"],
             "vectors_per_launch": vecs[0] / max(1, st["launches"]),
@@ -404,6 +496,28 @@ def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload
             "admission_wait_ms": {"p50": float(np.percentile(admit, 50)),
                                   "p99": float(np.percentile(admit, 99)),
                                   "max": float(np.max(admit))}}
+
+
+def run_config5(n_jobs: int, iters: int, rate_hz: float):
+    """The served request stream as configured: Poisson arrivals (rate_hz),
+    image sides ~U[64, 200] at 0.074\"/px with 4x4 subpixels and Gaussian
+    PSFs of side 11..31, each job a closed-loop sampler of `iters` batches of
+    U{500..5000} vectors.  Served and plain paths at that rate (which offers
+    more than the GPU serves) and both again at 80 % of the served path's
+    measured throughput; lens state stays on the device per job."""
+    lenses, _ = stream_lenses(n_jobs, "config5", seed_offset=60)
+    out = {"jobs": n_jobs, "iters_per_job": iters,
+           "sides": [int(sl.ny) for sl in lenses],
+           "psf_sides": [int(sl.psf.shape[0]) for sl in lenses],
+           "mean_pixels": float(np.mean([sl.ny * sl.nx for sl in lenses]))}
+    out["served"] = run_stream(True, n_jobs, iters, rate_hz, "config5", 60, lenses)
+    out["plain"] = run_stream(False, n_jobs, iters, rate_hz, "config5", 60, lenses)
+    rate80 = 0.8 * out["served"]["evals_per_s"] / (iters * 2750.0)
+    out["served_80pct"] = run_stream(True, n_jobs, iters, rate80, "config5", 60, lenses)
+    out["plain_80pct"] = run_stream(False, n_jobs, iters, rate80, "config5", 60, lenses)
+    for k in ("served_80pct", "plain_80pct"):
+        out[k]["offered_fraction_of_served_rate"] = 0.8
+    return out
 
 
 # ------------------------------------------------------------ our arm
@@ -488,22 +602,32 @@ def run_ours(args):
     assert np.array_equal(o_host.numpy(), ll), "host and device entry points differ"
 
     # ---- request stream: served (merged launches) vs plain (one per launch)
-    served = plain = served_80 = None
+    served = plain = served_80 = plain_80 = None
     if not args.skip_stream:
+        slenses, _ = stream_lenses(args.stream_jobs, args.workload)
         served = run_stream(True, args.stream_jobs, args.stream_iters, args.stream_rate,
-                            args.workload)
+                            args.workload, lenses=slenses)
         plain = run_stream(False, args.stream_jobs, args.stream_iters, args.stream_rate,
-                           args.workload)
+                           args.workload, lenses=slenses)
         # replicas: whole-job throughput is the sum over ranks
         vals = R.sum([served["evals_per_s"], plain["evals_per_s"]])
         served["evals_per_s_all_ranks"] = vals[0]
         plain["evals_per_s_all_ranks"] = vals[1]
-        # the same stream at about 80 % of the measured device throughput
-        # (the default rate offers several times what the GPU can serve)
+        # the same stream offered at about 80 % of the measured device
+        # throughput (the default rate offers several times what the GPU can
+        # serve), through both paths
         demand = args.stream_iters * 2750.0   # mean vectors per job
-        served_80 = run_stream(True, args.stream_jobs, args.stream_iters,
-                               0.8 * value / ws / demand, args.workload)
-        served_80["offered_fraction_of_device_rate"] = 0.8
+        rate80 = 0.8 * value / ws / demand
+        served_80 = run_stream(True, args.stream_jobs, args.stream_iters, rate80,
+                               args.workload, lenses=slenses)
+        plain_80 = run_stream(False, args.stream_jobs, args.stream_iters, rate80,
+                              args.workload, lenses=slenses)
+        for r in (served_80, plain_80):
+            r["offered_fraction_of_device_rate"] = 0.8
+    # ---- the served request stream as configured: mixed image sides
+    stream5 = None
+    if not args.skip_stream and not args.skip_config5 and ws == 1:
+        stream5 = run_config5(args.c5_jobs, args.c5_iters, args.stream_rate)
 
     if rank != 0:
         R.close()
@@ -513,7 +637,8 @@ def run_ours(args):
                          L.ntrace())
     main_avg = statistics.mean(main_ms)
     achieved = fpe * B / (main_avg / 1e3) / 1e12
-    peak = fp32_peak_tflops()
+    peaks = pipe_peaks(clk)
+    peak = peaks["fp32_tflops"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -546,8 +671,9 @@ def run_ours(args):
                      "hbm": hbm_check(captured_traffic(args.workload), main_avg),
                      "kernel": ("k_loglike" if args.conv == "fused" else
                                 "k_trace_split + conv + k_sums_split"),
-                     "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
-                                   f"x {SM_MAX_MHZ:.0f} MHz"},
+                     "peak_basis": peaks["basis"],
+                     "mufu": mufu_roof(transcendentals_per_eval(lens.sub, L.ntrace()) * B,
+                                       main_avg, peaks)},
         "e2e": ({"value": served["evals_per_s_all_ranks"], "unit": UNIT,
                  "path": "served request stream through tll_server (host buffers)",
                  "h2d_bytes_per_step": int(served["mean_batch"] * 21 * 4),
@@ -562,6 +688,8 @@ def run_ours(args):
         "served": served,
         "plain": plain,
         "served_80pct": served_80 if served else None,
+        "plain_80pct": plain_80 if served else None,
+        "stream_config5": stream5,
         "clocks": clk,
         "gpu_launches": launches,
         "impl": "ours",
@@ -569,7 +697,7 @@ def run_ours(args):
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lens, params)
     if not args.skip_rows and ws == 1 and args.workload == "csst100":
-        line["rows"] = measure_rows()
+        line["rows"] = measure_rows(clocks=clk)
     R.close()
     return line
 
@@ -664,7 +792,8 @@ def run_multi(args):
     fpe = flops_per_eval_multi(lens.ny, lens.nx, lens.sub, k, info["separable"], comps)
     main_avg = statistics.mean(main_ms)
     achieved = fpe * B / (main_avg / 1e3) / 1e12
-    peak = fp32_peak_tflops()
+    peaks = pipe_peaks(clk)
+    peak = peaks["fp32_tflops"]
     kinds = ", ".join(f"{c['type']}@{c['plane']}" for c in comps)
     line = {
         "metric": f"log-likelihood evals/s ({args.workload}, {len(comps)} columns, FNNLS)",
@@ -688,8 +817,9 @@ def run_multi(args):
                      "hbm": hbm_check(captured_traffic(args.workload, "k_loglike_nc"),
                                       main_avg),
                      "kernel": "k_loglike_nc",
-                     "peak_basis": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 "
-                                   f"x {SM_MAX_MHZ:.0f} MHz"},
+                     "peak_basis": peaks["basis"],
+                     "mufu": mufu_roof(transcendentals_per_eval_multi(
+                         lens.ny, lens.nx, lens.sub, comps) * B, main_avg, peaks)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "path": "tll_loglike_batch_host, pinned host buffers, B per step",
                 "h2d_bytes_per_step": B * L.nparam * 4, "d2h_bytes_per_step": B * 8},
@@ -851,20 +981,52 @@ def _time_lens(L, p_dev, out, steps, warmup, flush):
     return step_ms, main_ms
 
 
-def measure_rows(steps=8, warmup=3):
+def measure_rows(steps=8, warmup=3, clocks=None):
     """Short device-resident measurements of the workloads beyond the
-    headline: the masked csst100, csst100 with fixed amplitudes
-    (TLL_AMP_FIXED), the multi-component SLACS and 32-Gaussian models, and
-    the device-side sampler loop.  Each: evals/s, ms per step,
-    the main kernel's ms and its fraction of the FP32 FMA peak by the
-    algorithmic flop count."""
+    headline: configs 1 and 3 (plain64 at B = 256, hst200 at B = 2048), the
+    ragged multi-lens batch (config 4: 1000 lenses x 2048 vectors in one
+    graph-replayed launch), the masked csst100, csst100 with fixed
+    amplitudes (TLL_AMP_FIXED), the multi-component SLACS and 32-Gaussian
+    models, and the device-side sampler loop.  Each: evals/s, ms per step,
+    the main kernel's ms and its fraction of the FP32 FMA and MUFU peaks by
+    the algorithmic counts (at the SM clock sampled in the headline's timed
+    region)."""
     import torch
     from paper_2503_08586_gb300 import tll
     from paper_2503_08586_gb300 import workloads as W
     dev = torch.device("cuda", torch.cuda.current_device())
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    peak = fp32_peak_tflops()
-    rows = {}
+    peaks = pipe_peaks(clocks)
+    peak = peaks["fp32_tflops"]
+    rows = {"_peak_basis": peaks["basis"]}
+    # configs 1 and 3: the plain 64x64 lens (B = 256) and the HST-like 200x200
+    for name in ("plain64", "hst200"):
+        lens, params = W.workload(name, tll.columns_renderer)
+        L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0,
+                     lens.y0)
+        p_dev = torch.from_numpy(params).to(dev)
+        out = torch.empty(params.shape[0], dtype=torch.float64, device=dev)
+        st, mk = _time_lens(L, p_dev, out, steps, warmup, flush)
+        B = params.shape[0]
+        fpe = flops_per_eval(lens.ny, lens.nx, lens.sub, lens.psf.shape[0],
+                             L.info()["separable"], L.ntrace())
+        kms = statistics.mean(mk)
+        rows[name] = {"value": B / (statistics.mean(st) / 1e3),
+                      "ms_per_step": statistics.mean(st), "batch": B, "kernel": "k_loglike",
+                      "kernel_ms": kms, "launch_shape": L.shape(),
+                      "roofline_frac": fpe * B / (kms / 1e3) / 1e12 / peak,
+                      "mufu_frac": mufu_roof(transcendentals_per_eval(lens.sub, L.ntrace()) * B,
+                                             kms, peaks)["frac"]}
+        L.close()
+    # config 4: the ragged multi-lens batch in one graph-replayed launch
+    m = ragged_measure(1000, 2048, 2, max(3, warmup // 2))
+    rms = statistics.mean(m["ms"])
+    rows["ragged_1000x2048"] = {
+        "value": m["nvec"] / (rms / 1e3), "ms_per_step": rms, "vectors": m["nvec"],
+        "kernel": "k_prologue_multi + k_loglike_multi (whole step)",
+        "roofline_frac": m["flops"] / (rms / 1e3) / 1e12 / peak,
+        "launch_shapes": m["launch_shapes"], "all_finite": m["all_finite"],
+        "setup_s": m["setup_s"]}
     # masked csst100
     lens, params = W.workload("csst100_mask", tll.columns_renderer)
     L = tll.Lens(lens.data, lens.noise, lens.psf, lens.pixel_scale, lens.sub, lens.x0, lens.y0)
@@ -877,7 +1039,10 @@ def measure_rows(steps=8, warmup=3):
                             "ms_per_step": statistics.mean(st), "kernel": "k_loglike",
                             "kernel_ms": statistics.mean(mk), "traced_pixels": L.ntrace(),
                             "roofline_frac": fpe * params.shape[0] / (statistics.mean(mk) / 1e3)
-                            / 1e12 / peak}
+                            / 1e12 / peak,
+                            "mufu_frac": mufu_roof(transcendentals_per_eval(
+                                lens.sub, L.ntrace()) * params.shape[0],
+                                statistics.mean(mk), peaks)["frac"]}
     L.close()
     # csst100 with fixed amplitudes (TLL_AMP_FIXED: the I_e slots, no solve)
     lens, params = W.workload("csst100", tll.columns_renderer)
@@ -917,7 +1082,10 @@ def measure_rows(steps=8, warmup=3):
                       "ms_per_step": statistics.mean(st), "kernel": "k_loglike_nc",
                       "kernel_ms": statistics.mean(mk), "columns": len(spec.comps),
                       "roofline_frac": fpe * params.shape[0] / (statistics.mean(mk) / 1e3)
-                      / 1e12 / peak}
+                      / 1e12 / peak,
+                      "mufu_frac": mufu_roof(transcendentals_per_eval_multi(
+                          lens.ny, lens.nx, lens.sub, spec.comps) * params.shape[0],
+                          statistics.mean(mk), peaks)["frac"]}
         L.close()
     # the device-side sampler loop on csst100 (4096 walkers)
     lens, _ = W.workload("csst100", tll.columns_renderer, batch=8)
@@ -955,20 +1123,17 @@ def measure_rows(steps=8, warmup=3):
 
 
 # ------------------------------------------------------------ ragged batch
-def run_ragged(args):
+def ragged_measure(n_lenses, n_vec, steps, warmup, autotune=True, ranks=None):
     """Many lenses of different sizes (sides {64..200}, PSF 11..31 px, 4x4
-    subpixels), each with its own batch of vectors shrinking around its
+    subpixels), each with its own batch of n_vec vectors shrinking around its
     truth, evaluated in ONE persistent multi-lens launch replayed as a CUDA
-    graph; one step = that launch."""
+    graph; one step = that launch.  Returns timings and counts."""
     import torch
-    from paper_2503_08586_gb300 import build, tll
+    from paper_2503_08586_gb300 import tll
     from paper_2503_08586_gb300 import workloads as W
 
-    R = Ranks("nccl")
-    build.build()
-    tll.load()
     t0 = time.perf_counter()
-    rng, specs = W.ragged_specs(args.ragged_lenses)
+    rng, specs = W.ragged_specs(n_lenses)
     lenses, params = [], []
     cache, tuned = {}, {}
     for side, k in specs:
@@ -980,9 +1145,8 @@ def run_ragged(args):
         sl = W.synth_lens(rng, side, side, 0.074, 4, psf, render, "sky+poisson")
         lenses.append(tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0,
                                sl.y0, batch_only=True))
-        params.append(torch.from_numpy(W.shrinking_draws(rng, sl.truth,
-                                                         args.ragged_vectors)).cuda())
-        if not args.no_autotune and key not in tuned:
+        params.append(torch.from_numpy(W.shrinking_draws(rng, sl.truth, n_vec)).cuda())
+        if autotune and key not in tuned:
             # first lens of a signature: tune it; later ones start tuned
             tuned[key] = lenses[-1].autotune(params[-1])["chosen"]
         elif key in tuned:
@@ -994,15 +1158,16 @@ def run_ragged(args):
     b = tll.Batcher(use_graph=True)
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(R.local)
+    clocks = ClockSampler(torch.cuda.current_device())
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             b.run(lenses, params, outs, stream=stream)
         stream.synchronize()
-        R.barrier()
+        if ranks is not None:
+            ranks.barrier()
         clocks.mark()
         ms = []
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(float(k))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -1014,27 +1179,54 @@ def run_ragged(args):
         clk = clocks.stop()
     nvec = sum(p.shape[0] for p in params)
     nsub = sum(p.shape[0] * L.nx * L.ny * L.sub ** 2 for p, L in zip(params, lenses))
+    flops = sum(p.shape[0] * flops_per_eval(L.ny, L.nx, L.sub, sp[1], True)
+                for p, L, sp in zip(params, lenses, specs))
     allfin = all(bool(torch.isfinite(o).all()) for o in outs)
-    step = R.max(sum(ms)) / len(ms)
+    b.close()
+    for L in lenses:
+        L.close()
+    return {"ms": ms, "nvec": nvec, "nsub": nsub, "flops": flops, "all_finite": allfin,
+            "setup_s": setup_s, "clocks": clk,
+            "launch_shapes": sorted({(t["threads"], t["ctas_per_sm"], t["placement"])
+                                     for t in tuned.values()}) or "default"}
+
+
+def run_ragged(args):
+    """The ragged multi-lens batch as the bench's workload (one JSON line)."""
+    from paper_2503_08586_gb300 import build, tll
+
+    R = Ranks("nccl")
+    build.build()
+    tll.load()
+    m = ragged_measure(args.ragged_lenses, args.ragged_vectors, args.steps, args.warmup,
+                       not args.no_autotune, R)
+    step = R.max(sum(m["ms"])) / len(m["ms"])
     if R.rank != 0:
         R.close()
         return None
     R.close()
+    peak = pipe_peaks(m["clocks"])
+    peak["tflops"] = peak["fp32_tflops"]
     return {
         "metric": "log-likelihood evals/s (ragged multi-lens batch, one launch)",
-        "value": whole_job_rate(nvec, R.ws, step, 1), "unit": UNIT, "n_gpus": R.ws,
+        "value": whole_job_rate(m["nvec"], R.ws, step, 1), "unit": UNIT, "n_gpus": R.ws,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ragged: {len(lenses)} lenses, sides {{64..200}}, PSF 11..31, "
-                               f"4x4 subpixels, {args.ragged_vectors} vectors each, one "
-                               "multi-lens launch under a CUDA graph",
-                   "global_batch": nvec * R.ws, "setup_s": setup_s,
-                   "launch_shapes": sorted({(t["threads"], t["ctas_per_sm"], t["placement"])
-                                            for t in tuned.values()}) or "default",
+        "config": {"workload": f"ragged: {args.ragged_lenses} lenses, sides {{64..200}}, "
+                               f"PSF 11..31, 4x4 subpixels, {args.ragged_vectors} vectors "
+                               "each, one multi-lens launch under a CUDA graph",
+                   "global_batch": m["nvec"] * R.ws, "setup_s": m["setup_s"],
+                   "launch_shapes": m["launch_shapes"],
                    "l2": "flushed between timed steps"},
-        "subpixel_evals_per_s": whole_job_rate(nsub, R.ws, step, 1), "all_finite": allfin,
-        "clocks": clk, "gpu_launches": 2 * args.steps, "impl": "ours"}
+        "subpixel_evals_per_s": whole_job_rate(m["nsub"], R.ws, step, 1),
+        "all_finite": m["all_finite"],
+        "roofline": {"bound": "alu", "achieved": m["flops"] / (step / 1e3) / 1e12,
+                     "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": m["flops"] / (step / 1e3) / 1e12 / peak["tflops"],
+                     "kernel": "k_prologue_multi + k_loglike_multi (whole step)",
+                     "peak_basis": peak["basis"]},
+        "clocks": m["clocks"], "gpu_launches": 2 * args.steps, "impl": "ours"}
 
 
 # ------------------------------------------------------------ reference arm
@@ -1104,6 +1296,10 @@ def main(argv=None):
     ap.add_argument("--stream-jobs", type=int, default=32)
     ap.add_argument("--stream-iters", type=int, default=100)
     ap.add_argument("--stream-rate", type=float, default=20.0)
+    ap.add_argument("--skip-config5", action="store_true",
+                    help="omit the mixed-size served request stream")
+    ap.add_argument("--c5-jobs", type=int, default=16)
+    ap.add_argument("--c5-iters", type=int, default=300)
     ap.add_argument("--ragged-lenses", type=int, default=1000)
     ap.add_argument("--ragged-vectors", type=int, default=2048)
     args = ap.parse_args(argv)

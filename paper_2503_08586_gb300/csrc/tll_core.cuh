@@ -92,10 +92,12 @@ __device__ __forceinline__ void accum_pixel(float ml, float ms, float4 wp, float
 // [HL, HL + nx) hold zeros, so no tap needs a bounds check.
 //  Row pass (in place, one warp per row): a lane computes 4 adjacent
 //  outputs from one window of K + 3 values read as float4s.
-//  Column pass: a warp takes 32 adjacent columns x CR rows; a lane reads
-//  CR + K - 1 values of its column and computes CR outputs per channel.
-// Taps come from the parameter block (compile-time indices).
-constexpr int kCR = 4;
+//  Column pass: a thread takes one column x CR rows (CR = 4 or 5, whichever
+//  needs fewer rounds of the CTA's threads), reads CR + K - 1 values of its
+//  column and computes CR outputs per channel.
+// Taps come from the parameter block (compile-time indices).  kCR: the
+// largest CR, the zero rows kept below the image for the last row block.
+constexpr int kCR = 5;
 
 template <int K>
 struct PadGeom {

@@ -16,25 +16,25 @@ namespace tll {
 // face {none, lens only, source only, both} that is feasible; chi^2 of a
 // face's minimiser s is dWd - s^T b.  Fixed mode: s = (I_e^L, I_e^S) and
 // chi^2 = dWd - 2 s^T b + s^T A s.
-__device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
-                                              float IeL, float IeS, double *sl_o,
-                                              double *ss_o, double *ll_o)
+__device__ __forceinline__ void finish_core(int mode, double dWd, double lognorm,
+                                            const double *S, float IeL, float IeS,
+                                            double *sl_o, double *ss_o, double *ll_o)
 {
     const double All = S[0], Als = S[1], Ass = S[2], bl = S[3], bs = S[4];
     double sl, ss, chi2;
-    if (L.mode == TLL_AMP_FIXED) {
+    if (mode == TLL_AMP_FIXED) {
         sl = IeL;
         ss = IeS;
-        chi2 = L.dWd - 2.0 * (sl * bl + ss * bs) + sl * sl * All +
+        chi2 = dWd - 2.0 * (sl * bl + ss * bs) + sl * sl * All +
                2.0 * sl * ss * Als + ss * ss * Ass;
     } else {
-        sl = 0.0; ss = 0.0; chi2 = L.dWd;
+        sl = 0.0; ss = 0.0; chi2 = dWd;
         if (All > 0.0 && bl > 0.0) {
-            const double c = L.dWd - bl * (bl / All);
+            const double c = dWd - bl * (bl / All);
             if (c < chi2) { chi2 = c; sl = bl / All; ss = 0.0; }
         }
         if (Ass > 0.0 && bs > 0.0) {
-            const double c = L.dWd - bs * (bs / Ass);
+            const double c = dWd - bs * (bs / Ass);
             if (c < chi2) { chi2 = c; sl = 0.0; ss = bs / Ass; }
         }
         // Both columns free only when they are not collinear to rounding:
@@ -47,7 +47,7 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
             const double tl = (Ass * bl - Als * bs) / det;
             const double ts = (All * bs - Als * bl) / det;
             if (tl > 0.0 && ts > 0.0) {
-                const double c = L.dWd - 2.0 * (tl * bl + ts * bs) + tl * tl * All +
+                const double c = dWd - 2.0 * (tl * bl + ts * bs) + tl * tl * All +
                                  2.0 * tl * ts * Als + ts * ts * Ass;
                 if (c < chi2) { chi2 = c; sl = tl; ss = ts; }
             }
@@ -55,7 +55,57 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
     }
     *sl_o = sl;
     *ss_o = ss;
-    *ll_o = -0.5 * chi2 + L.lognorm;
+    *ll_o = -0.5 * chi2 + lognorm;
+}
+
+__device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
+                                              float IeL, float IeS, double *sl_o,
+                                              double *ss_o, double *ll_o)
+{
+    finish_core(L.mode, L.dWd, L.lognorm, S, IeL, IeS, sl_o, ss_o, ll_o);
+}
+
+// The five sums of a vector from the warps' FP64 partials sred[w*5 + k]
+// (w < nwarp): one warp adds them as a butterfly over its lanes (every lane
+// ends with the same bits); called by all 32 lanes of that warp.
+__device__ __forceinline__ void block_sums(const double *sred, int nwarp, int lane, double *S)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) S[k] = lane < nwarp ? sred[lane * 5 + k] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o);
+    }
+}
+
+// The amplitude solve and log L of a vector whose five sums wait in sred
+// (the warps' partials of the last convolution): deferred to the CTA's last
+// warp, which takes it at the start of the next vector's trace (its sums
+// stay in sred until that vector's convolution, after the trace barrier) or
+// after the CTA's last vector.  The last warp traces the fewest pixels when
+// the threads do not divide them evenly, so the other warps never wait for
+// the FP64 solve.  Record written and read by that warp only.
+struct PendingFinish {
+    double dWd, lognorm;
+    double *outp;
+    float IeL, IeS;
+    int mode, valid;
+};
+
+__device__ __forceinline__ void finish_pending(PendingFinish &pf, const double *sred,
+                                               int lane, int nwarp)
+{
+    if (!pf.valid) return;
+    double S[5];
+    block_sums(sred, nwarp, lane, S);
+    if (lane == 0) {
+        double sl, ss, ll;
+        finish_core(pf.mode, pf.dWd, pf.lognorm, S, pf.IeL, pf.IeS, &sl, &ss, &ll);
+        *pf.outp = ll;
+        pf.valid = 0;
+    }
+    __syncwarp();
 }
 
 // --------------------------------------------------------- trace phase
@@ -239,6 +289,42 @@ struct PairStore {
     }
 };
 
+// Column pass of the separable convolution: thread unit u = (column j,
+// row block rb) makes output rows [CR rb, CR rb + CR) of column j in both
+// channels from one window of CR + K - 1 buffer rows (lanes of a warp hold
+// consecutive columns: conflict-free shared-memory reads).
+template <int K, int CR, class Sink>
+__device__ __forceinline__ void conv_sep_cols(const LensDev &L, const float *Pl,
+                                              const float *Ps, int b0, int nrows, int tid,
+                                              int nthr, Sink &sink)
+{
+    using G = PadGeom<K>;
+    static_assert(CR <= kCR, "the padded layout keeps kCR rows below the image");
+    const int nx = L.nx, W = L.W;
+    const int nrb = (nrows + CR - 1) / CR;
+    for (int u = tid; u < nx * nrb; u += nthr) {
+        const int rb = u / nx, j = u - rb * nx, r0 = rb * CR;
+        float ml[CR], ms[CR];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const float *col = (ch == 0 ? Pl : Ps) + r0 * W + G::HL + j;
+            float win[CR + K - 1];
+#pragma unroll
+            for (int t = 0; t < CR + K - 1; ++t) win[t] = col[t * W];
+#pragma unroll
+            for (int r = 0; r < CR; ++r) {
+                float a = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) a = fmaf(L.tu[c], win[r + K - 1 - c], a);
+                if (ch == 0) ml[r] = a; else ms[r] = a;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < CR; ++r)
+            if (r0 + r < nrows) sink((b0 + r0 + r) * nx + j, ml[r], ms[r]);
+    }
+}
+
 template <int K, class Sink>
 __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float *Ps,
                                               int b0, int nrows, int rlo, int rhi, int tid,
@@ -293,34 +379,13 @@ __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float
     }
     __syncthreads();
     // column pass with the fused weighted sums: output row ro (image row
-    // b0 + ro) reads buffer rows ro .. ro + K - 1
-    const int ncg = (nx + 31) >> 5, nrb = (nrows + kCR - 1) / kCR;
-    for (int item = warp; item < ncg * nrb; item += nwarp) {
-        const int cg = item % ncg, rb = item / ncg;
-        const int j = 32 * cg + lane, r0 = rb * kCR;
-        const int jc = min(j, nx - 1);
-        float ml[kCR], ms[kCR];
-#pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-            const float *col = (ch == 0 ? Pl : Ps) + r0 * W + G::HL + jc;
-            float win[kCR + K - 1];
-#pragma unroll
-            for (int t = 0; t < kCR + K - 1; ++t) win[t] = col[t * W];
-#pragma unroll
-            for (int r = 0; r < kCR; ++r) {
-                float a = 0.0f;
-#pragma unroll
-                for (int c = 0; c < K; ++c) a = fmaf(L.tu[c], win[r + K - 1 - c], a);
-                if (ch == 0) ml[r] = a; else ms[r] = a;
-            }
-        }
-        if (j < nx) {
-#pragma unroll
-            for (int r = 0; r < kCR; ++r) {
-                if (r0 + r < nrows) sink((b0 + r0 + r) * nx + j, ml[r], ms[r]);
-            }
-        }
-    }
+    // b0 + ro) reads buffer rows ro .. ro + K - 1; (column, row block)
+    // units spread over every thread of the CTA, CR rows per unit
+    const int nu4 = nx * ((nrows + 3) / 4), nu5 = nx * ((nrows + 4) / 5);
+    if (((nu5 + nthr - 1) / nthr) * 5 < ((nu4 + nthr - 1) / nthr) * 4)
+        conv_sep_cols<K, 5>(L, Pl, Ps, b0, nrows, tid, nthr, sink);
+    else
+        conv_sep_cols<K, 4>(L, Pl, Ps, b0, nrows, tid, nthr, sink);
 }
 
 // Direct K x K convolution (any PSF), m(i,j) = sum_{r,c} K[r][c]
@@ -575,7 +640,9 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
 template <int SUB>
 __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, float *Il,
                                              float *Is, int stride, int off, float *sepl,
-                                             int tid, int nthr, bool skip)
+                                             int tid, int nthr, bool skip,
+                                             PendingFinish *pf = nullptr,
+                                             const double *sred = nullptr)
 {
     const VecConst v = load_consts(kc);
     if (v.epl) {
@@ -589,6 +656,8 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
     } else {
         trace_image<SUB, 1>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     }
+    // the previous vector's solve, by the last warp once its pixels are done
+    if (pf && (tid >> 5) == (nthr >> 5) - 1) finish_pending(*pf, sred, tid & 31, nthr >> 5);
     __syncthreads();
 }
 
@@ -609,12 +678,13 @@ __device__ __forceinline__ void zero_untraced(const LensDev &L, const ImgPtrs &P
 template <int SUB, int K, bool WRITE>
 __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
                                             const float *kc, double *outp, const ImgPtrs &P,
-                                            float *spsf, double *sred, float *sepl, int tid,
-                                            int nthr)
+                                            float *spsf, double *sred, float *sepl,
+                                            PendingFinish &pf, int tid, int nthr)
 {
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nx = L.nx, npix = L.npix;
-    trace_vector<SUB>(L, kc, P.Il, P.Is, P.stride, P.off, sepl, tid, nthr, !WRITE);
+    trace_vector<SUB>(L, kc, P.Il, P.Is, P.stride, P.off, sepl, tid, nthr, !WRITE,
+                      WRITE ? nullptr : &pf, sred);
     if (WRITE) {
         for (int t = tid; t < npix; t += nthr) {
             const int i = t / nx, j = t - i * nx;
@@ -626,24 +696,25 @@ __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
     // warp sums in double-float, then per warp in FP64, block sum in FP64
     convolve<K, WRITE>(L, R, P, spsf, sred, tid, nthr);
     __syncthreads();
-    if (warp == 0) {
-        double sacc = 0.0;
-        if (lane < 5)
-            for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
-        double S[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) S[k] = __shfl_sync(0xffffffffu, sacc, k);
-        if (lane == 0) {
-            double sl, ss, ll;
-            finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
-            *outp = ll;
-            if (WRITE) {
+    if (WRITE) {
+        if (warp == 0) {
+            double S[5];
+            block_sums(sred, nwarp, lane, S);
+            if (lane == 0) {
+                double sl, ss, ll;
+                finish_vector(L, S, kc[K_IEL], kc[K_IES], &sl, &ss, &ll);
+                *outp = ll;
                 for (int k = 0; k < 5; ++k) R.wr_res[k] = S[k];
                 R.wr_res[5] = sl;
                 R.wr_res[6] = ss;
                 R.wr_res[7] = ll;
             }
         }
+        __syncthreads();
+    } else if (warp == nwarp - 1) {
+        if (lane == 0)
+            pf = PendingFinish{L.dWd, L.lognorm, outp, kc[K_IEL], kc[K_IES], L.mode, 1};
+        __syncwarp();
     }
     __syncthreads();
 }
@@ -657,9 +728,11 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float sepl[kEplMaxN + 1];
+    __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
+    if (tid == 0) spf.valid = 0;
     const bool gslot = L.img == IMG_GLOBAL || L.img == IMG_BANDED;
     const ImgPtrs P =
         img_ptrs(L, spsf, gslot ? R.gscr + (size_t)blockIdx.x * R.gslot : nullptr);
@@ -675,8 +748,9 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
             }
             continue;
         }
-        vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, sepl, tid, nthr);
+        vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, sepl, spf, tid, nthr);
     }
+    if (!WRITE && (tid >> 5) == (nthr >> 5) - 1) finish_pending(spf, sred, tid & 31, nthr >> 5);
 }
 
 // ----------------------------------------------------- multi-lens kernel
@@ -692,7 +766,9 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     __shared__ LensDev sL;
     __shared__ int s_t, s_seg;
     __shared__ float sepl[kEplMaxN + 1];
+    __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) spf.valid = 0;
     double *sred = reinterpret_cast<double *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
     float *gslot = A.gscr ? A.gscr + (size_t)blockIdx.x * A.gslot_floats : nullptr;
@@ -728,8 +804,9 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
         }
         RunArgs R = {};
         const ImgPtrs P = img_ptrs(sL, spsf, gslot);
-        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, sepl, tid, nthr);
+        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, sepl, spf, tid, nthr);
     }
+    if ((tid >> 5) == (nthr >> 5) - 1) finish_pending(spf, sred, tid & 31, nthr >> 5);
 }
 
 // --------------------------------------------------------------- registry

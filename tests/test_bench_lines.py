@@ -78,3 +78,30 @@ def test_source_hash_follows_code_not_comments():
     c = "int f(int x) { return x + 2; }"
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(c)
+
+
+def test_pipe_peaks_from_device_count_and_sampled_clock():
+    p = bench.pipe_peaks({"sm_mhz": 1800.0, "sm_max_mhz": 2070.0}, n_sm=152)
+    assert p["mhz"] == 1800.0 and p["n_sm"] == 152
+    assert p["fp32_tflops"] == pytest.approx(152 * 128 * 2 * 1800e6 / 1e12)
+    assert p["mufu_gops"] == pytest.approx(152 * 16 * 1800e6 / 1e9)
+    assert "sampled" in p["basis"]
+    # no sample under load: nvidia-smi's maximum clock, then the fallback
+    assert bench.pipe_peaks({"sm_mhz": None, "sm_max_mhz": 2070.0}, n_sm=100)["mhz"] == 2070.0
+    q = bench.pipe_peaks(None, n_sm=100)
+    assert q["mhz"] == bench.SM_MAX_MHZ and "no sample" in q["basis"]
+
+
+def test_transcendental_counts_and_mufu_roof():
+    # csst100: 10^4 pixels x 16 subpixels x 9 (SIE sqrt, atan, atanh; two
+    # Sersics' sqrt, pow, exp)
+    assert bench.transcendentals_per_eval(4, 10000) == 10000 * 16 * 9
+    from paper_2503_08586_gb300 import workloads as W
+    s = W.MULTI_WORKLOADS["slacs120"]
+    # SLACS: the SIE's 3 plus 4 Sersics x 3 per subpixel
+    assert bench.transcendentals_per_eval_multi(s.ny, s.nx, s.sub, s.comps) == \
+        s.ny * s.nx * s.sub ** 2 * (3 + 4 * 3)
+    peaks = bench.pipe_peaks({"sm_mhz": 2000.0}, n_sm=100)
+    r = bench.mufu_roof(3.2e9, 1.0, peaks)           # 3.2e9 evaluations in 1 ms
+    assert r["achieved"] == pytest.approx(3.2e3)      # Gop/s
+    assert r["frac"] == pytest.approx(3.2e3 / (100 * 16 * 2000e6 / 1e9))
