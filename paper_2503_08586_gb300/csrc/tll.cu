@@ -65,14 +65,21 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 // -------------------------------------------------------------- kernels
-__global__ void k_prologue(const float *__restrict__ params, int B,
-                           float *__restrict__ kc, double XC, double YC, double d,
-                           const double *__restrict__ bn_tab, int epl)
+// Block (32, 4): warp y decodes part y (decode_vector) of vectors
+// 32 blockIdx.x + [0, 32).  The FP64 work of a vector is split four ways
+// over four warps (four sub-partitions) rather than run by one thread:
+// GB300's FP64 pipe takes a warp instruction every 64 cycles or so, so a
+// vector's decode time is set by its longest serial FP64 chain.
+constexpr int kPrologueVectors = 32;
+__global__ void __launch_bounds__(128) k_prologue(const float *__restrict__ params, int B,
+                                                  float *__restrict__ kc, double XC, double YC,
+                                                  double d, const double *__restrict__ bn_tab,
+                                                  int epl)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x * kPrologueVectors + threadIdx.x;
     if (b < B)
         decode_vector(params + (size_t)b * (epl ? NPAR_EPL : NPAR), kc + (size_t)b * NCONST,
-                      XC, YC, d, bn_tab, epl != 0);
+                      XC, YC, d, bn_tab, epl != 0, threadIdx.y);
 }
 
 // One thread per node of the b_n table (run once per device).
@@ -85,19 +92,24 @@ __global__ void k_bn_table(double *__restrict__ tab)
 }
 
 // ------------------------------------------------- multi-lens prologue
-__global__ void k_prologue_multi(const __grid_constant__ MultiArgs A)
+// Block (32, 4) as k_prologue: a two-column vector's four parts on four
+// warps; a multi-component vector decoded whole by warp 0.
+__global__ void __launch_bounds__(128) k_prologue_multi(const __grid_constant__ MultiArgs A)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * kPrologueVectors + threadIdx.x;
     if (t >= A.all->total) return;
     const Segment &sg = A.segs[find_segment(A.segs, 0, A.all->nseg, t)];
     const LensDev &L = A.lenses[sg.lens];
     const MultiDev &M = A.mdevs[sg.lens];
-    if (M.nc > 0)
-        decode_multi(sg.params + (size_t)(t - sg.first) * M.npar, A.kc + (size_t)t * NCONST, L,
-                     M, A.bn_tab);
-    else
+    if (M.nc > 0) {
+        if (threadIdx.y == 0)
+            decode_multi(sg.params + (size_t)(t - sg.first) * M.npar, A.kc + (size_t)t * NCONST,
+                         L, M, A.bn_tab);
+    } else {
         decode_vector(sg.params + (size_t)(t - sg.first) * (L.epl ? NPAR_EPL : NPAR),
-                      A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0);
+                      A.kc + (size_t)t * NCONST, L.XC, L.YC, L.d, A.bn_tab, L.epl != 0,
+                      threadIdx.y);
+    }
 }
 
 // Multi-component prologue: one thread per vector.
@@ -375,8 +387,8 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
     double xc, yc;
     grid_centre(L, &xc, &yc);
-    k_prologue<<<(B + 127) / 128, 128, 0, st>>>(params, B, kc, xc, yc,
-                                                (double)L->dpix / L->sub, L->bn_tab, L->epl);
+    k_prologue<<<(B + kPrologueVectors - 1) / kPrologueVectors, dim3(kPrologueVectors, 4), 0,
+                 st>>>(params, B, kc, xc, yc, (double)L->dpix / L->sub, L->bn_tab, L->epl);
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
     RunArgs R;
@@ -918,7 +930,8 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
                              cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, kMaxGroups * sizeof(int), st));
     const MultiArgs A = batcher_args(b);
-    k_prologue_multi<<<(items + 127) / 128, 128, 0, st>>>(A);
+    k_prologue_multi<<<(items + kPrologueVectors - 1) / kPrologueVectors,
+                       dim3(kPrologueVectors, 4), 0, st>>>(A);
     CUDA_TRY(cudaGetLastError());
     for (int g = 0; g < (int)b->glaunch.size(); ++g) {
         const GroupLaunch &gl = b->glaunch[g];

@@ -170,10 +170,27 @@ __device__ __forceinline__ void split2(double v, float *o_hi, float *o_lo)
 //                     x1^2 + x2^2                                    (Eq. 10)
 // so the scaled source coordinates are an affine map of theta minus
 // S R(phi_m - phi_s) A (ux, uy), S = diag of the scales.
+//
+// part: which slots to write -- all of them (part < 0), or one of four
+// disjoint sets, so that four threads (one per warp of a (32, 4) block)
+// decode one vector together: 0 validity, mass frame, q, f, SIE form,
+// fixed amplitudes; 1 lens light; 2 source frame and Sersic; 3 the
+// deflection map Q and the EPL series.  A part recomputes the few shared
+// quantities it needs (the mass angle and q for part 3, ...).  Every part
+// finds the same validity; an invalid vector's part 0 writes K_VALID = 0
+// and nothing else is read.  |eps| < 1 is tested as eps1^2 + eps2^2 < 1,
+// the same decision as sqrt(.) < 1 under correctly rounded sqrt.
+__device__ __forceinline__ void zero_range(float *o, int a, int b)
+{
+    for (int k = a; k < b; ++k) o[k] = 0.0f;
+}
+
 __device__ inline void decode_vector(const float *__restrict__ p, float *__restrict__ o,
                                      double XC, double YC, double d,
-                                     const double *__restrict__ bn_tab, bool epl = false)
+                                     const double *__restrict__ bn_tab, bool epl = false,
+                                     int part = -1)
 {
+    const bool all = part < 0;
     bool ok = true;
     double v[NPAR_EPL];
 #pragma unroll
@@ -186,26 +203,54 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
     ok = ok && v[0] >= 0.0;
     ok = ok && v[8] > 0.0 && v[15] > 0.0;
     ok = ok && v[9] >= 0.2 && v[9] <= 10.0 && v[16] >= 0.2 && v[16] <= 10.0;
-    const double e_m = sqrt(v[1] * v[1] + v[2] * v[2]);
-    const double e_l = sqrt(v[10] * v[10] + v[11] * v[11]);
-    const double e_s = sqrt(v[17] * v[17] + v[18] * v[18]);
-    ok = ok && e_m < 1.0 && e_l < 1.0 && e_s < 1.0;
-#pragma unroll
-    for (int k = 0; k < NCONST_USED; ++k) o[k] = 0.0f;
+    const double e2_m = v[1] * v[1] + v[2] * v[2];
+    const double e2_l = v[10] * v[10] + v[11] * v[11];
+    const double e2_s = v[17] * v[17] + v[18] * v[18];
+    ok = ok && e2_m < 1.0 && e2_l < 1.0 && e2_s < 1.0;
+    float *lo = o + K_LO;
+    if (all) {
+        zero_range(o, 0, NCONST_USED);
+    } else if (part == 0) {
+        zero_range(o, K_VALID, K_FAST + 1);
+        zero_range(o, K_IEL, K_IES + 1);
+        zero_range(lo, LO_PX, LO_PY + 3);
+        zero_range(lo, LO_Q, LO_F + 1);
+    } else if (part == 1) {
+        zero_range(o, K_LX0, K_BHL + 1);
+        zero_range(lo, LO_LX, LO_LY + 3);
+        zero_range(lo, LO_KL, LO_BL + 1);
+    } else if (part == 2) {
+        zero_range(o, K_SX0, K_BHS + 1);
+        zero_range(lo, LO_SX, LO_SY + 3);
+        zero_range(lo, LO_KS, LO_BS + 1);
+    } else {
+        zero_range(o, K_Q11H, K_Q22H + 1);
+        zero_range(o, K_EPL, K_LO);
+        zero_range(lo, LO_Q11, LO_Q22 + 1);
+        zero_range(o, K_EC0, NCONST_USED);
+    }
     if (!ok) return;
-    o[K_VALID] = 1.0f;
+    if (all || part == 0) o[K_VALID] = 1.0f;
     const double LOG2E = 1.4426950408889634;
 
     // mass: q = (1-e)/(1+e), f = sqrt(1 - q^2) = 2 sqrt(e)/(1+e)
-    const double qm = (1.0 - e_m) / (1.0 + e_m);
-    const double f = 2.0 * sqrt(e_m) / (1.0 + e_m);
-    const double A = v[0] * sqrt(qm);
-    bool fast, mid;
-    double cm, sm;
-    half_angle(v[1], v[2], e_m, &cm, &sm);
-    {
+    double qm = 0.0, f = 0.0, A = 0.0, cm = 1.0, sm = 0.0;
+    bool fast = false, mid = false;
+    if (all || part == 0 || part == 3) {
+        const double e_m = sqrt(e2_m);
+        qm = (1.0 - e_m) / (1.0 + e_m);
+        f = 2.0 * sqrt(e_m) / (1.0 + e_m);
+        A = v[0] * sqrt(qm);
+        half_angle(v[1], v[2], e_m, &cm, &sm);
+        // fast form when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
+        // for every point: no atan range reduction, no atanh logarithm;
+        // mid form when f/q <= 1 but f > 1/2: no atan range reduction, the
+        // atanh by logarithms (1/f < 2 keeps them accurate)
+        fast = f <= qm && f <= 0.5;
+        mid = f <= qm && !fast;
+    }
+    if (all || part == 0) {
         const double dx = XC - v[3], dy = YC - v[4];
-        float *lo = o + K_LO;
         split2(dx * cm + dy * sm, &o[K_PX0], &lo[LO_PX]);
         split2(d * cm, &o[K_PXJ], &lo[LO_PX + 1]);
         split2(d * sm, &o[K_PXI], &lo[LO_PX + 2]);
@@ -214,25 +259,21 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         split2(d * cm, &o[K_PYI], &lo[LO_PY + 2]);
         split2(qm, &o[K_QM], &lo[LO_Q]);
         split2(f, &o[K_F], &lo[LO_F]);
-        // fast form when |f x'/psi| <= f/q <= 1 and |f y'/psi| <= f <= 1/2
-        // for every point: no atan range reduction, no atanh logarithm;
-        // mid form when f/q <= 1 but f > 1/2: no atan range reduction, the
-        // atanh by logarithms (1/f < 2 keeps them accurate)
-        fast = f <= qm && f <= 0.5;
-        mid = f <= qm && !fast;
         o[K_FAST] = fast ? 1.0f : mid ? 2.0f : 0.0f;
+        o[K_IEL] = (float)v[7];
+        o[K_IES] = (float)v[14];
     }
     const double g1 = v[5], g2 = v[6];
 
     // lens light (centre in slots 12, 13)
-    {
+    if (all || part == 1) {
         const double re = v[8], n = v[9];
+        const double e_l = sqrt(e2_l);
         const double q = (1.0 - e_l) / (1.0 + e_l);
         double c, s;
         half_angle(v[10], v[11], e_l, &c, &s);
         const double s1 = sqrt(q) / re, s2 = 1.0 / (sqrt(q) * re);
         const double dx = XC - v[12], dy = YC - v[13];
-        float *lo = o + K_LO;
         split2(s1 * (dx * c + dy * s), &o[K_LX0], &lo[LO_LX]);
         split2(s1 * d * c, &o[K_LXJ], &lo[LO_LX + 1]);
         split2(s1 * d * s, &o[K_LXI], &lo[LO_LX + 2]);
@@ -243,71 +284,73 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
         split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHL], &lo[LO_BL]);
     }
     // source
-    {
+    if (all || part == 2 || part == 3) {
         const double re = v[15], n = v[16];
+        const double e_s = sqrt(e2_s);
         const double q = (1.0 - e_s) / (1.0 + e_s);
         double c, s;
         half_angle(v[17], v[18], e_s, &c, &s);
         const double s1 = sqrt(q) / re, s2 = 1.0 / (sqrt(q) * re);
-        // linear part: beta_lin = (I - G) theta - c_s, theta = (XC + fj d, YC + fi d)
-        const double bx0 = (1.0 - g1) * XC - g2 * YC - v[19];
-        const double by0 = -g2 * XC + (1.0 + g1) * YC - v[20];
-        const double bxj = (1.0 - g1) * d, bxi = -g2 * d;
-        const double byj = -g2 * d, byi = (1.0 + g1) * d;
-        // double-float: rounding these to float alone would move the whole
-        // source plane coherently (a shift and scale near 1e-7), which the
-        // likelihood near its optimum resolves
-        float *lo = o + K_LO;
-        split2(s1 * (c * bx0 + s * by0), &o[K_SX0], &lo[LO_SX]);
-        split2(s1 * (c * bxj + s * byj), &o[K_SXJ], &lo[LO_SX + 1]);
-        split2(s1 * (c * bxi + s * byi), &o[K_SXI], &lo[LO_SX + 2]);
-        split2(s2 * (-s * bx0 + c * by0), &o[K_SY0], &lo[LO_SY]);
-        split2(s2 * (-s * bxj + c * byj), &o[K_SYJ], &lo[LO_SY + 1]);
-        split2(s2 * (-s * bxi + c * byi), &o[K_SYI], &lo[LO_SY + 2]);
-        split2(0.5 / n, &o[K_KHS], &lo[LO_KS]);
-        split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &lo[LO_BS]);
-        // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
-        const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
-        const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
-        // The fast form's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
-        // form's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
-        // so its columns carry 1/f and ln 2/(2f); the mid form has the fast
-        // ux and the general uy.
-        double c1 = (fast || mid) ? 1.0 : 1.0 / f;
-        double c2 = fast ? 1.0 : 0.34657359027997264 / f;
-        double Am = A;
-        if (epl) {
-            // EPL (Tessore & Metcalf 2015 in this normalisation): with
-            // t = gamma - 1, b = theta_E sqrt(q), psi^2 = q^2 x'^2 + y'^2 and
-            // psi e^{i vphi} = q x' + i y', the deflection in the mass frame
-            // is 2b/(1+q) (b/psi)^(t-1) e^{i vphi} sum_n c_n e^{2 i n vphi},
-            // c_n = prod_{k<=n} (2k - 2 + t)/(2k + 2 - t) (-(1-q)/(1+q))^n
-            // (the series of 2F1(1, t/2; 2 - t/2; .)).  (ux, uy) is that sum
-            // times (b/psi)^(t-1) = 2^(e0 + e1 log2 psi^2); Q carries 2b/(1+q).
-            const double t = v[21] - 1.0, fr = -(1.0 - qm) / (1.0 + qm);
-            o[K_EPL] = 1.0f;
-            split2((t - 1.0) * log2(A), &o[K_E0H], &o[K_E0L]);
-            split2(0.5 * (1.0 - t), &o[K_E1H], &o[K_E1L]);
-            double cn = 1.0;
-            int N = 0;
-            o[K_EC0] = 1.0f;
-            for (int n = 1; n <= kEplMaxN; ++n) {
-                cn *= fr * (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
-                o[K_EC0 + n] = (float)cn;
-                N = n;
-                if (fabs(cn) < 1e-9) break;   // the rest of the series is below float rounding
-            }
-            o[K_EN] = (float)N;
-            c1 = c2 = 1.0;
-            Am = 2.0 * A / (1.0 + qm);
+        if (all || part == 2) {
+            // linear part: beta_lin = (I - G) theta - c_s, theta = (XC + fj d, YC + fi d)
+            const double bx0 = (1.0 - g1) * XC - g2 * YC - v[19];
+            const double by0 = -g2 * XC + (1.0 + g1) * YC - v[20];
+            const double bxj = (1.0 - g1) * d, bxi = -g2 * d;
+            const double byj = -g2 * d, byi = (1.0 + g1) * d;
+            // double-float: rounding these to float alone would move the whole
+            // source plane coherently (a shift and scale near 1e-7), which the
+            // likelihood near its optimum resolves
+            split2(s1 * (c * bx0 + s * by0), &o[K_SX0], &lo[LO_SX]);
+            split2(s1 * (c * bxj + s * byj), &o[K_SXJ], &lo[LO_SX + 1]);
+            split2(s1 * (c * bxi + s * byi), &o[K_SXI], &lo[LO_SX + 2]);
+            split2(s2 * (-s * bx0 + c * by0), &o[K_SY0], &lo[LO_SY]);
+            split2(s2 * (-s * bxj + c * byj), &o[K_SYJ], &lo[LO_SY + 1]);
+            split2(s2 * (-s * bxi + c * byi), &o[K_SYI], &lo[LO_SY + 2]);
+            split2(0.5 / n, &o[K_KHS], &lo[LO_KS]);
+            split2(sersic_bn_lookup(bn_tab, n) * LOG2E, &o[K_BHS], &lo[LO_BS]);
         }
-        split2(s1 * Am * cd * c1, &o[K_Q11H], &lo[LO_Q11]);
-        split2(-s1 * Am * sd * c2, &o[K_Q12H], &lo[LO_Q12]);
-        split2(s2 * Am * sd * c1, &o[K_Q21H], &lo[LO_Q21]);
-        split2(s2 * Am * cd * c2, &o[K_Q22H], &lo[LO_Q22]);
+        if (all || part == 3) {
+            // deflection term: S R(-phi_s) R(phi_m) A = S R(phi_m - phi_s) A
+            const double cd = cm * c + sm * s;    // cos(phi_m - phi_s)
+            const double sd = sm * c - cm * s;    // sin(phi_m - phi_s)
+            // The fast form's (ux, uy) are atan(zx)/f, atanh(zy)/f; the general
+            // form's are atan(zx) and log2((1 + zy)/(1 - zy)) = 2 atanh(zy)/ln 2,
+            // so its columns carry 1/f and ln 2/(2f); the mid form has the fast
+            // ux and the general uy.
+            double c1 = (fast || mid) ? 1.0 : 1.0 / f;
+            double c2 = fast ? 1.0 : 0.34657359027997264 / f;
+            double Am = A;
+            if (epl) {
+                // EPL (Tessore & Metcalf 2015 in this normalisation): with
+                // t = gamma - 1, b = theta_E sqrt(q), psi^2 = q^2 x'^2 + y'^2 and
+                // psi e^{i vphi} = q x' + i y', the deflection in the mass frame
+                // is 2b/(1+q) (b/psi)^(t-1) e^{i vphi} sum_n c_n e^{2 i n vphi},
+                // c_n = prod_{k<=n} (2k - 2 + t)/(2k + 2 - t) (-(1-q)/(1+q))^n
+                // (the series of 2F1(1, t/2; 2 - t/2; .)).  (ux, uy) is that sum
+                // times (b/psi)^(t-1) = 2^(e0 + e1 log2 psi^2); Q carries 2b/(1+q).
+                const double t = v[21] - 1.0, fr = -(1.0 - qm) / (1.0 + qm);
+                o[K_EPL] = 1.0f;
+                split2((t - 1.0) * log2(A), &o[K_E0H], &o[K_E0L]);
+                split2(0.5 * (1.0 - t), &o[K_E1H], &o[K_E1L]);
+                double cn = 1.0;
+                int N = 0;
+                o[K_EC0] = 1.0f;
+                for (int nn = 1; nn <= kEplMaxN; ++nn) {
+                    cn *= fr * (2.0 * nn - 2.0 + t) / (2.0 * nn + 2.0 - t);
+                    o[K_EC0 + nn] = (float)cn;
+                    N = nn;
+                    if (fabs(cn) < 1e-9) break;   // the rest of the series is below float rounding
+                }
+                o[K_EN] = (float)N;
+                c1 = c2 = 1.0;
+                Am = 2.0 * A / (1.0 + qm);
+            }
+            split2(s1 * Am * cd * c1, &o[K_Q11H], &lo[LO_Q11]);
+            split2(-s1 * Am * sd * c2, &o[K_Q12H], &lo[LO_Q12]);
+            split2(s2 * Am * sd * c1, &o[K_Q21H], &lo[LO_Q21]);
+            split2(s2 * Am * cd * c2, &o[K_Q22H], &lo[LO_Q22]);
+        }
     }
-    o[K_IEL] = (float)v[7];
-    o[K_IES] = (float)v[14];
 }
 
 // ------------------------------------------------------------ subpixel
@@ -394,12 +437,14 @@ __device__ __forceinline__ float sfu_rcp(float x)
 // ex2.approx on f (unbiased on that interval, unlike on wide arguments),
 // times 2^k added into the exponent field.  rint: adding 1.5 * 2^23 leaves
 // k in the low mantissa bits of kf, and kf's bits << 23 are k << 23.
-// x is clamped below at -125 so the result stays a normal float (smaller
-// values only enter pixel sums far below the model's rounding); a NaN x
-// (only from 0 * inf at r = 0, where 2^x -> 0 is wanted) also becomes -125.
+// CLAMP: x is first clamped below at -125 so the result stays a normal
+// float (smaller values only enter pixel sums far below the model's
+// rounding); a NaN x (only from 0 * inf at r = 0, where 2^x -> 0 is wanted)
+// also becomes -125.  Without CLAMP the caller guarantees x >= -125.
+template <bool CLAMP = true>
 __device__ __forceinline__ float exp2_rr(float x)
 {
-    x = fmaxf(x, -125.0f);
+    if (CLAMP) x = fmaxf(x, -125.0f);
     const float kf = x + 12582912.0f;
     const float f = x - (kf - 12582912.0f);
     const float y = sfu_ex2(f);
@@ -439,7 +484,17 @@ __device__ __forceinline__ float poly_atanh_q(float s)
 // bias there is a near-uniform relative scale).
 __device__ __forceinline__ float sersic_omt(float L, float kh, float c)
 {
-    return 1.0f - exp2_rr(fmaf(kh, L, c));
+    return 1.0f - exp2_rr<false>(fmaf(kh, L, c));
+}
+
+// (R_p/r_e)^2 = x1^2 + x2^2 with a floor of 2^-50 added inside the FMA:
+// log2 of it is >= -50, so kh L >= -125 for every valid index (n >= 0.2,
+// kh = 1/(2n) <= 2.5) and the pow's exp2 needs no clamp.  The floor changes
+// (R_p/r_e)^2 by less than an ulp wherever R_p/r_e > 3e-4.
+constexpr float kR2Floor = 8.8817842e-16f;   // 2^-50
+__device__ __forceinline__ float radius2(float x1, float x2)
+{
+    return fmaf(x1, x1, fmaf(x2, x2, kR2Floor));
 }
 __device__ __forceinline__ float sersic_outer(float omt, float bh, float d)
 {
@@ -496,7 +551,8 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float ql, float fl, 
     // parts taken at the pixel's first subpixel
     if (FIRST) P.dq = ql * xp;
     const float qx = fmaf(v.q, xp, P.dq);
-    const float rpsi = rsqrt_nr(fmaxf(fmaf(qx, qx, yp * yp), 1e-24f));
+    // psi^2 >= 1e-24 (the singular centre, reading R4), added inside the FMA
+    const float rpsi = rsqrt_nr(fmaf(qx, qx, fmaf(yp, yp, 1e-24f)));
     const float xr = xp * rpsi, yr = yp * rpsi;
     if (FIRST) {
         P.dfx = fl * xr;
@@ -537,7 +593,7 @@ __device__ __forceinline__ void epl_unit(const VecConst &v, float ql, float xp, 
 {
     if (FIRST) P.dq = ql * xp;
     const float qx = fmaf(v.q, xp, P.dq);
-    const float a = fmaxf(fmaf(qx, qx, yp * yp), 1e-24f);
+    const float a = fmaf(qx, qx, fmaf(yp, yp, 1e-24f));
     const float rpsi = rsqrt_nr(a);
     const float c = qx * rpsi, s = yp * rpsi;            // e^{i vphi}
     const float wr = fmaf(c, c, -s * s), wi = 2.0f * c * s;
@@ -633,7 +689,7 @@ __device__ __forceinline__ void subpixel_first(const VecConst &v, const PixLo &l
     P.nly = fmaf(w[LO_Q21], ux, fmaf(w[LO_Q22], uy, P.nly));
     // lens light at theta (Eq. 2, first term)
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
-    const float Ll = sfu_lg2(fmaf(x1, x1, x2 * x2));
+    const float Ll = sfu_lg2(radius2(x1, x2));
     P.cl = w[LO_KL] * Ll;
     const float ol = sersic_omt(Ll, v.khl, P.cl);
     P.dl = w[LO_BL] * ol;
@@ -641,7 +697,7 @@ __device__ __forceinline__ void subpixel_first(const VecConst &v, const PixLo &l
     // source at beta = theta - alpha_SIE - alpha_shear (Eq. 2, second term)
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
     const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
-    const float Ls = sfu_lg2(fmaf(y1, y1, y2 * y2));
+    const float Ls = sfu_lg2(radius2(y1, y2));
     P.cs = w[LO_KS] * Ls;
     const float os = sersic_omt(Ls, v.khs, P.cs);
     P.ds = w[LO_BS] * os;
@@ -656,10 +712,10 @@ __device__ __forceinline__ void subpixel(const VecConst &v, const RowTerms &r, f
     float ux, uy;
     deflect<MODE, false>(v, 0.0f, 0.0f, r, fj, ec, P, ux, uy);
     const float x1 = fmaf(v.lx.cj, fj, r.lx), x2 = fmaf(v.ly.cj, fj, r.ly);
-    il = sersic_outer(sersic_omt(sfu_lg2(fmaf(x1, x1, x2 * x2)), v.khl, P.cl), v.bhl, P.dl);
+    il = sersic_outer(sersic_omt(sfu_lg2(radius2(x1, x2)), v.khl, P.cl), v.bhl, P.dl);
     const float y1 = fmaf(v.sx.cj, fj, r.sx) - fmaf(v.q11h, ux, fmaf(v.q12h, uy, P.nlx));
     const float y2 = fmaf(v.sy.cj, fj, r.sy) - fmaf(v.q21h, ux, fmaf(v.q22h, uy, P.nly));
-    is = sersic_outer(sersic_omt(sfu_lg2(fmaf(y1, y1, y2 * y2)), v.khs, P.cs), v.bhs, P.ds);
+    is = sersic_outer(sersic_omt(sfu_lg2(radius2(y1, y2)), v.khs, P.cs), v.bhs, P.ds);
 }
 
 // ------------------------------------------------------ double-float
