@@ -42,10 +42,21 @@ struct LensDev {
     const int *tlist;
     int ntrace;
     int nc_smem;      // multi-column kernel: dynamic shared memory of the launch
+    // n / nx as __umulhi(n, nx_mul), nx_mul = ceil(2^32 / nx): exact for
+    // n < 2^32 / nx, which nx_fast records for every index a kernel divides
+    // (pixel indices and column-pass units, n < nx (ny + 8))
+    unsigned nx_mul;
+    int nx_fast;
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
     // the full PSF (direct convolution), row r at tk[r * tap_stride(K)]
     alignas(8) float tk[kMaxK * (kMaxK + 1)];
 };
+
+// Row of index n in a row-major image of L.nx columns.
+__device__ __forceinline__ int div_nx(const LensDev &L, int n)
+{
+    return L.nx_fast ? (int)__umulhi((unsigned)n, L.nx_mul) : n / L.nx;
+}
 
 // Image placement in k_loglike.
 enum : int {

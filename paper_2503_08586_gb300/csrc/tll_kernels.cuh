@@ -130,7 +130,7 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
     const int n = list ? L.ntrace : L.npix;
     for (int t = tid; t < n; t += nthr) {
         const int pix = list ? list[t] : t;
-        const int i = pix / nx, j = pix - i * nx;
+        const int i = div_nx(L, pix), j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
         const PixLo lc = load_pixlo(kc);
@@ -139,9 +139,10 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
         const PixOrigin po = pixel_origin(v, lc, fj0, fi0);
         float accl, accs;
         subpixel_first<MODE>(v, lc, row_terms(v, po, fi0), fj0, ec, lo, accl, accs);
-#pragma unroll 1
-        for (int a = 0; a < sub; ++a) {
-            const RowTerms r = row_terms(v, po, fi0 + (float)a);
+        float fi = fi0;
+#pragma unroll
+        for (int a = 0; a < (SUB > 0 ? SUB : sub); ++a, fi += 1.0f) {
+            const RowTerms r = row_terms(v, po, fi);
 #pragma unroll
             for (int c = 0; c < (SUB > 0 ? SUB : 1); ++c) {
                 for (int cr = 0; cr < (SUB > 0 ? 1 : sub); ++cr) {
@@ -303,7 +304,7 @@ __device__ __forceinline__ void conv_sep_cols(const LensDev &L, const float *Pl,
     const int nx = L.nx, W = L.W;
     const int nrb = (nrows + CR - 1) / CR;
     for (int u = tid; u < nx * nrb; u += nthr) {
-        const int rb = u / nx, j = u - rb * nx, r0 = rb * CR;
+        const int rb = div_nx(L, u), j = u - rb * nx, r0 = rb * CR;
         float ml[CR], ms[CR];
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) {

@@ -153,7 +153,7 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
         for (int e = 0; e < NQ; ++e) q[k][e] = k < ncp ? cq[6 * k + e] : 0.0f;
     for (int t = tid; t < n; t += nthr) {
         const int pix = list ? list[t] : t;
-        const int i = pix / nx, j = pix - i * nx;
+        const int i = div_nx(L, pix), j = pix - i * nx;
         const float fj0 = (float)(j * sub) - L.JCX;
         const float fi0 = (float)(i * sub) - L.JCY;
         const PixLo lc = load_pixlo(kc);
