@@ -647,7 +647,7 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
 {
     const VecConst v = load_consts(kc);
     if (v.epl) {
-        for (int t = tid; t <= v.en; t += nthr) sepl[t] = kc[K_EC0 + t];
+        for (int t = tid; t <= kEplMaxN; t += nthr) sepl[t] = kc[K_EC0 + t];
         __syncthreads();
         trace_image<SUB, 2>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.fast) {
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kThreads)
 k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float sepl[kEplMaxN + 1];
+    __shared__ __align__(16) float sepl[kEplMaxN + 1];
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *sred = reinterpret_cast<double *>(smem);
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LensDev sL;
     __shared__ int s_t, s_seg;
-    __shared__ float sepl[kEplMaxN + 1];
+    __shared__ __align__(16) float sepl[kEplMaxN + 1];
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) spf.valid = 0;

@@ -469,7 +469,7 @@ struct NcShared {
     double A[kMaxComps * kMaxComps], b[kMaxComps];
     double F[kMaxComps * (kMaxComps + 1)];
     float q[kMaxComps * 6];
-    float epl[kEplMaxN + 1];
+    alignas(16) float epl[kEplMaxN + 1];
 };
 
 // One valid parameter vector of a multi-column lens (constant block kc):
@@ -490,7 +490,7 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
     const VecConst v = load_consts(kc);
     for (int t = tid; t < 6 * nc; t += nthr) sh.q[t] = kc[K_C0 + t];
     if (v.epl)
-        for (int t = tid; t <= v.en; t += nthr) sh.epl[t] = kc[K_EC0 + t];
+        for (int t = tid; t <= kEplMaxN; t += nthr) sh.epl[t] = kc[K_EC0 + t];
     __syncthreads();
     // 1. trace passes
     for (int ps = 0; ps < M.npass; ++ps) {
