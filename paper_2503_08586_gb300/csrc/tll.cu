@@ -393,7 +393,7 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
                  st>>>(params, B, kc, xc, yc, (double)L->dpix / L->sub, L->bn_tab, L->epl);
     CUDA_TRY(cudaGetLastError());
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
-    RunArgs R;
+    RunArgs R = {};
     R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr; R.gslot = L->shape.gslot;
     R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
     const int grid = std::min(B, L->shape.grid_cap);

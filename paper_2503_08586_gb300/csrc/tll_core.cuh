@@ -52,6 +52,18 @@ struct LensDev {
     alignas(8) float tk[kMaxK * (kMaxK + 1)];
 };
 
+// Barrier over the threads taking part in a phase: BAR 0 is the whole CTA
+// (__syncthreads); BAR > 0 is named barrier BAR over the first nthr threads
+// (a multiple of 32), which leaves the other warps free for other work.
+template <int BAR>
+__device__ __forceinline__ void phase_sync(int nthr)
+{
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "r"(nthr) : "memory");
+}
+
 // Row of index n in a row-major image of L.nx columns.
 __device__ __forceinline__ int div_nx(const LensDev &L, int n)
 {
@@ -75,6 +87,7 @@ struct RunArgs {
     long long gslot;
     float *wr_unblurred; // WRITE: [2][npix]
     float *wr_blurred;   // WRITE: [2][npix]
+    float *wr_blurred_s; // WRITE: the second column there instead, when not null
     double *wr_res;      // WRITE: [8] All Als Ass bl bs sl ss logL
 };
 

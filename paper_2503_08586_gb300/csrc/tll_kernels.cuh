@@ -166,7 +166,7 @@ __device__ __forceinline__ void trace_image(const LensDev &L, const VecConst &v,
 // m(i,j) = sum_r u[r] H(i+h-r, j); direct: m = sum_{r,c} K[r][c] I(i+h-r, j+h-c);
 // zero outside the image (Eq. 3).  Each output pixel's (m_l, m_s) goes to
 // accum_pixel.
-template <bool WRITE>
+template <bool WRITE, int BAR = 0>
 __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
                                              const float *spsf, float *Il, float *Is,
                                              float *Hl, float *Hs, float *acc, int tid,
@@ -207,7 +207,7 @@ __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
                 }
             }
         }
-        __syncthreads();
+        phase_sync<BAR>(nthr);
         const int nb = max(1, nthr / nx);
         const int rb = (ny + nb - 1) / nb;
         for (int it = tid; it < nx * nb; it += nthr) {
@@ -224,7 +224,7 @@ __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
                 const int pix = i * nx + j;
                 if (WRITE) {
                     R.wr_blurred[pix] = ml;
-                    R.wr_blurred[npix + pix] = ms;
+                    (R.wr_blurred_s ? R.wr_blurred_s : R.wr_blurred + npix)[pix] = ms;
                 }
                 accum_pixel(ml, ms, L.wpack[pix], acc);
             }
@@ -248,7 +248,7 @@ __device__ __forceinline__ void conv_generic(const LensDev &L, const RunArgs &R,
             }
             if (WRITE) {
                 R.wr_blurred[pix] = ml;
-                R.wr_blurred[npix + pix] = ms;
+                (R.wr_blurred_s ? R.wr_blurred_s : R.wr_blurred + npix)[pix] = ms;
             }
             accum_pixel(ml, ms, L.wpack[pix], acc);
         }
@@ -326,7 +326,7 @@ __device__ __forceinline__ void conv_sep_cols(const LensDev &L, const float *Pl,
     }
 }
 
-template <int K, class Sink>
+template <int K, class Sink, int BAR = 0>
 __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float *Ps,
                                               int b0, int nrows, int rlo, int rhi, int tid,
                                               int nthr, Sink &sink)
@@ -378,7 +378,7 @@ __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float
         }
         __syncwarp();
     }
-    __syncthreads();
+    phase_sync<BAR>(nthr);
     // column pass with the fused weighted sums: output row ro (image row
     // b0 + ro) reads buffer rows ro .. ro + K - 1; (column, row block)
     // units spread over every thread of the CTA, CR rows per unit

@@ -128,17 +128,19 @@ __device__ __forceinline__ float comp_value(bool gauss, float R2, float q0, floa
     return sfu_ex2(fmaf(q4, omt, q5 * omt));
 }
 
-// One trace pass: the ncp (<= NP) components listed in chan (their constants
-// cq[6 * k], Gaussian flags in gmask) of one plane on every subpixel, binned
-// by the mean, written to U + chan[k] * npix.  GAUSS: every component is a
-// Gaussian (only its first two constants are kept).
+// One trace pass: ncp (<= NP) components (their constants cq[6 * k],
+// Gaussian flags in gmask) of one plane on every subpixel, binned by the
+// mean, component k written to U + k * npix, or to U + chan[k] * npix when
+// full.  GAUSS: every component is a Gaussian (only its first two constants
+// are kept).
 // MODE: 0 / 1 / 4 / 2 source plane with the SIE fast / general / mid form or
 // the EPL series (ec); 3 lens plane (no deflection).
 // skip: trace only the lens's listed pixels (as trace_image).
 template <int SUB, int MODE, int NP, bool GAUSS>
 __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
                                            const float *kc, const float *cq, int gmask, int ncp,
-                                           const int *chan, float *U, int tid, int nthr,
+                                           const int *chan, bool full, float *U, int tid,
+                                           int nthr,
                                            const float *ec, bool skip)
 {
     constexpr int NQ = GAUSS ? 2 : 6;
@@ -209,7 +211,7 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k)
-            if (k < ncp) U[(size_t)chan[k] * npix + pix] = acc[k] * L.inv_s2;
+            if (k < ncp) U[(size_t)(full ? chan[k] : k) * npix + pix] = acc[k] * L.inv_s2;
     }
 }
 
@@ -472,104 +474,181 @@ struct NcShared {
     alignas(16) float epl[kEplMaxN + 1];
 };
 
+// FNNLS on the normal equations in sh (nc columns), chi^2 = dWd - 2 x^T b
+// + x^T A x and log L (Eq. 5) to *outp; the amplitudes and log L also to
+// wres when given.  One warp (all 32 lanes).
+__device__ inline void nc_solve(NcShared &sh, int nc, double dWd, double lognorm, double *outp,
+                                double *wres, int lane)
+{
+    const double x = nc_fnnls_warp(sh.A, sh.b, nc, sh.F, lane);
+    double Ax = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        const double xk = __shfl_sync(0xffffffffu, x, k);
+        if (lane < nc) Ax = fma(sh.A[lane * nc + k], xk, Ax);
+    }
+    double term = lane < nc ? x * (Ax - 2.0 * sh.b[lane]) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+    const double ll = -0.5 * (dWd + term) + lognorm;
+    if (lane == 0) *outp = ll;
+    if (wres) {
+        if (lane < nc) wres[lane] = x;
+        if (lane == 0) wres[nc] = ll;
+    }
+    __syncwarp();
+}
+
+// A vector whose normal equations wait in sh.A, sh.b for their solve: the
+// CTA's last warp (the solver) takes it while the other warps trace and
+// convolve the next vector (sh.A, sh.b are rewritten only by that vector's
+// sums, after a full barrier), or after the CTA's last vector.  Written and
+// read by the solver warp only.
+constexpr int kDeferCols = 8;
+struct NcPending {
+    double dWd, lognorm;
+    double *outp;
+    int nc, valid;
+};
+
+__device__ __forceinline__ void nc_solve_pending(NcShared &sh, NcPending &pf, int lane)
+{
+    if (!pf.valid) return;
+    nc_solve(sh, pf.nc, pf.dWd, pf.lognorm, pf.outp, nullptr, lane);
+    if (lane == 0) pf.valid = 0;
+    __syncwarp();
+}
+
 // One valid parameter vector of a multi-column lens (constant block kc):
-// trace passes, PSF, normal equations, FNNLS; log L to *outp (and, when
-// wres is given, the amplitudes and log L to wres).  U: the CTA's global
-// slot (U [nc], M [nc + 1], H [2] images); spsf: the dynamic shared memory
-// (band buffer or PSF taps, reused for the sums' tiles of T pixels).
-// Starts and ends with all threads in step (block barriers inside).
+// trace passes each followed by the PSF of its columns, normal equations,
+// FNNLS; log L to *outp (and, when wres is given, the amplitudes and log L
+// to wres).  U: the CTA's global slot (U [nc] binned columns, of which a
+// pass uses the first ncp; M [nc + 1] blurred columns; H [2] images); spsf:
+// the dynamic shared memory (band buffer or PSF taps, reused for the sums'
+// tiles of T pixels).  Warps 0 .. nwarp-2 (the workers, named barrier 1)
+// trace and convolve; meanwhile the last warp (the solver) runs the
+// previous vector's FNNLS (pf); all warps form the sums.  With wres the
+// solve is this vector's own, at the end.  Starts and ends with all threads
+// in step.
 template <int SUB, int K, int ROWS>
 __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, const float *kc,
                                           double *outp, double *wres, float *U, float *spsf,
-                                          NcShared &sh, bool skip, int T, int tid, int nthr)
+                                          NcShared &sh, NcPending &pf, bool skip, int T, int tid,
+                                          int nthr)
 {
-    const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31;
     const int nc = M.nc, npix = L.npix;
+    // the solve is deferred to the solver warp from kDeferCols columns on
+    // (below, FNNLS is cheap next to the warp's share of the trace)
+    const bool defer = wres == nullptr && nc >= kDeferCols;
+    const int nwk = defer ? nthr - 32 : nthr;   // worker threads
     float *Mb = U + (size_t)nc * npix;
     float *H = Mb + (size_t)(nc + 1) * npix;
-    const VecConst v = load_consts(kc);
     for (int t = tid; t < 6 * nc; t += nthr) sh.q[t] = kc[K_C0 + t];
-    if (v.epl)
+    if (kc[K_EPL] != 0.0f)
         for (int t = tid; t <= kEplMaxN; t += nthr) sh.epl[t] = kc[K_EC0 + t];
     __syncthreads();
-    // 1. trace passes
-    for (int ps = 0; ps < M.npass; ++ps) {
-        const int ncp = M.pass_n[ps];
-        float cq[6 * kPassMax];
-        int gmask = 0;
+    // the previous vector's amplitudes and log L, when deferred (the last
+    // warp; it then joins the workers unless this vector defers too)
+    if (tid >= nthr - 32) nc_solve_pending(sh, pf, lane);
+    if (tid < nwk) {
+        // the workers: the sums of the previous vector used the dynamic
+        // shared memory, so its zero halos (or the PSF taps) are set first
+        setup_lens(L, spsf, tid, nwk);
+        phase_sync<1>(nwk);
+        // stage 2 ps: trace pass ps; stage 2 ps + 1: its convolutions (the
+        // vector's constants live within a trace stage only, not through
+        // the convolutions)
+#pragma unroll 1
+        for (int stage = 0; stage < 2 * M.npass; ++stage) {
+          const int ps = stage >> 1;
+          const int ncp = M.pass_n[ps];
+          const int *chan = M.pass_comp[ps];
+          const bool full = wres != nullptr;
+          if (!(stage & 1)) {
+            // 1. one trace pass: its ncp columns to U[0 .. ncp)
+            const VecConst v = load_consts(kc);
+            float cq[6 * kPassMax];
+            int gmask = 0;
 #pragma unroll
-        for (int k = 0; k < kPassMax; ++k) {
-            const int c = k < ncp ? M.pass_comp[ps][k] : 0;
+            for (int k = 0; k < kPassMax; ++k) {
+                const int c = k < ncp ? M.pass_comp[ps][k] : 0;
 #pragma unroll
-            for (int e = 0; e < 6; ++e) cq[6 * k + e] = sh.q[6 * c + e];
-            if (k < ncp && M.type[c] == COMP_GAUSS) gmask |= 1 << k;
-        }
-        const int *chan = M.pass_comp[ps];
-        if (M.pass_gauss[ps]) {
-            if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3, kPassMax, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.epl)
-                trace_pass<SUB, 2, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.fast)
-                trace_pass<SUB, 0, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.mid)
-                trace_pass<SUB, 4, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else
-                trace_pass<SUB, 1, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-        } else {
-            if (M.pass_plane[ps] == PLANE_LENS)
-                trace_pass<SUB, 3, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.epl)
-                trace_pass<SUB, 2, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.fast)
-                trace_pass<SUB, 0, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else if (v.mid)
-                trace_pass<SUB, 4, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-            else
-                trace_pass<SUB, 1, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, U, tid, nthr, sh.epl, skip);
-        }
-    }
-    __syncthreads();
-    // 2. PSF, two columns at a time (an odd last column pairs with itself);
-    //    the sums of the previous vector used the dynamic shared memory,
-    //    so its zero halos (or the PSF taps) are set up again first
-    setup_lens(L, spsf, tid, nthr);
-    __syncthreads();
-    for (int c = 0; c < nc; c += 2) {
-        const int c2 = min(c + 1, nc - 1);
-        const float *Il = U + (size_t)c * npix, *Is = U + (size_t)c2 * npix;
-        if constexpr (K > 0) {
-            const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
-            const int step = L.band_rows;
-            float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
-            PairStore<ROWS> st{Mb + (size_t)c * npix, Mb + (size_t)c2 * npix};
-            for (int b0 = 0; b0 < ny; b0 += step) {
-                const int nrows = min(step, ny - b0);
-                const int nbr = nrows + 2 * h;
-                for (int t = tid; t < 2 * nbr * nx; t += nthr) {
-                    const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
-                    const int br = rem / nx, j = rem - br * nx;
-                    const int ir = b0 - h + br;
-                    const float val = (ir >= 0 && ir < ny) ? (ch ? Is : Il)[ir * nx + j] : 0.0f;
-                    (ch ? Ps : Pl)[br * W + HL + j] = val;
-                }
-                __syncthreads();
-                if (L.sep)
-                    conv_sep_band<K>(L, Pl, Ps, b0, nrows, max(0, h - b0),
-                                     min(nbr, ny - b0 + h), tid, nthr, st);
-                else
-                    conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nthr, st);
-                __syncthreads();
+                for (int e = 0; e < 6; ++e) cq[6 * k + e] = sh.q[6 * c + e];
+                if (k < ncp && M.type[c] == COMP_GAUSS) gmask |= 1 << k;
             }
-        } else {
-            RunArgs ra = {};
-            ra.wr_blurred = Mb + (size_t)c * npix;
-            float dummy[10];
-            // writes M[c] and M[c + 1] (the spare column M[nc] for an odd
-            // last column); its five sums go unused
-            conv_generic<true>(L, ra, spsf, const_cast<float *>(Il), const_cast<float *>(Is),
-                               H, H + npix, dummy, tid, nthr, false);
-            __syncthreads();
+            // binned columns: the pass's own slots 0 .. ncp-1, or each
+            // component's slot when the binned columns are written out
+            if (M.pass_gauss[ps]) {
+                if (M.pass_plane[ps] == PLANE_LENS)
+                    trace_pass<SUB, 3, kPassMax, true>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.epl)
+                    trace_pass<SUB, 2, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.fast)
+                    trace_pass<SUB, 0, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.mid)
+                    trace_pass<SUB, 4, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else
+                    trace_pass<SUB, 1, kPassSrcG, true>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+            } else {
+                if (M.pass_plane[ps] == PLANE_LENS)
+                    trace_pass<SUB, 3, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.epl)
+                    trace_pass<SUB, 2, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.fast)
+                    trace_pass<SUB, 0, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else if (v.mid)
+                    trace_pass<SUB, 4, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+                else
+                    trace_pass<SUB, 1, kPassMix, false>(L, v, kc, cq, gmask, ncp, chan, full, U, tid, nwk, sh.epl, skip);
+            }
+            phase_sync<1>(nwk);
+            continue;
+          }
+            // 2. the pass's columns through the PSF two at a time (an odd
+            //    last one pairs with itself), blurred to M[chan[k]]: the
+            //    binned columns are read back while they are still in L2
+            for (int k = 0; k < ncp; k += 2) {
+                const int k2 = min(k + 1, ncp - 1);
+                const float *Il = U + (size_t)(full ? chan[k] : k) * npix;
+                const float *Is = U + (size_t)(full ? chan[k2] : k2) * npix;
+                float *Ml = Mb + (size_t)chan[k] * npix, *Ms = Mb + (size_t)chan[k2] * npix;
+                if constexpr (K > 0) {
+                    const int h = L.h, W = L.W, HL = L.HL, ny = L.ny, nx = L.nx;
+                    const int step = L.band_rows;
+                    float *Pl = spsf, *Ps = spsf + (step + 2 * h + kCR) * W;
+                    PairStore<ROWS> st{Ml, Ms};
+                    for (int b0 = 0; b0 < ny; b0 += step) {
+                        const int nrows = min(step, ny - b0);
+                        const int nbr = nrows + 2 * h;
+                        for (int t = tid; t < 2 * nbr * nx; t += nwk) {
+                            const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
+                            const int br = rem / nx, j = rem - br * nx;
+                            const int ir = b0 - h + br;
+                            const float val = (ir >= 0 && ir < ny) ? (ch ? Is : Il)[ir * nx + j] : 0.0f;
+                            (ch ? Ps : Pl)[br * W + HL + j] = val;
+                        }
+                        phase_sync<1>(nwk);
+                        if (L.sep)
+                            conv_sep_band<K, PairStore<ROWS>, 1>(L, Pl, Ps, b0, nrows,
+                                                                max(0, h - b0),
+                                                                min(nbr, ny - b0 + h), tid, nwk,
+                                                                st);
+                        else
+                            conv_direct_band<K>(L, Pl, Ps, b0, nrows, tid, nwk, st);
+                        phase_sync<1>(nwk);
+                    }
+                } else {
+                    RunArgs ra = {};
+                    ra.wr_blurred = Ml;
+                    ra.wr_blurred_s = Ms;
+                    float dummy[10];
+                    // (its five sums go unused)
+                    conv_generic<true, 1>(L, ra, spsf, const_cast<float *>(Il),
+                                          const_cast<float *>(Is), H, H + npix, dummy, tid, nwk,
+                                          false);
+                    phase_sync<1>(nwk);
+                }
+            }
         }
     }
     __syncthreads();
@@ -618,22 +697,14 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
         }
     }
     __syncthreads();
-    // 4. amplitudes (warp 0) and log L
-    if (warp == 0) {
-        const double x = nc_fnnls_warp(sh.A, sh.b, nc, sh.F, lane);
-        double Ax = 0.0;
-        for (int k = 0; k < nc; ++k) {
-            const double xk = __shfl_sync(0xffffffffu, x, k);
-            if (lane < nc) Ax = fma(sh.A[lane * nc + k], xk, Ax);
-        }
-        double term = lane < nc ? x * (Ax - 2.0 * sh.b[lane]) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
-        const double ll = -0.5 * (L.dWd + term) + L.lognorm;
-        if (lane == 0) *outp = ll;
-        if (wres) {
-            if (lane < nc) wres[lane] = x;
-            if (lane == 0) wres[nc] = ll;
+    // 4. amplitudes and log L: deferred to the solver during the next
+    //    vector, or now (the last warp)
+    if (tid >= nthr - 32) {
+        if (defer) {
+            if (lane == 0) pf = NcPending{L.dWd, L.lognorm, outp, nc, 1};
+            __syncwarp();
+        } else {
+            nc_solve(sh, nc, L.dWd, L.lognorm, outp, wres, lane);
         }
     }
     __syncthreads();
@@ -650,10 +721,12 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ NcShared sh;
+    __shared__ NcPending spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int nc = M.nc, npix = L.npix;
     float *spsf = reinterpret_cast<float *>(smem);
     float *U = R.gscr + (size_t)blockIdx.x * R.gslot;
+    if (tid == 0) spf.valid = 0;
     setup_lens(L, spsf, tid, nthr);
     // pixels never traced (masked lenses) must start finite
     if (L.tlist)
@@ -672,9 +745,10 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
         }
         // two output rows per direct-convolution item up to K = 21 (above,
         // the longer windows would spill); one in the multi-lens kernel
-        nc_vector<SUB, K, (K <= 21 ? 2 : 1)>(L, M, kc, R.out + b, R.wr_res, U, spsf, sh, skip,
-                                             T, tid, nthr);
+        nc_vector<SUB, K, (K <= 21 ? 2 : 1)>(L, M, kc, R.out + b, R.wr_res, U, spsf, sh, spf,
+                                             skip, T, tid, nthr);
     }
+    if (tid >= nthr - 32) nc_solve_pending(sh, spf, tid & 31);
 }
 
 // Many lenses (the batcher's multi-column groups): CTAs take items from the
@@ -689,7 +763,9 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
     __shared__ LensDev sL;
     __shared__ MultiDev sM;
     __shared__ int s_t, s_seg;
+    __shared__ NcPending spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) spf.valid = 0;
     float *spsf = reinterpret_cast<float *>(smem);
     float *U = A.gscr + (size_t)blockIdx.x * A.gslot_floats;
     const MultiHdr hd = A.groups[group];
@@ -726,9 +802,10 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
             __syncthreads();
             continue;
         }
-        nc_vector<SUB, K, 1>(sL, sM, kc, outp, nullptr, U, spsf, sh, true,
+        nc_vector<SUB, K, 1>(sL, sM, kc, outp, nullptr, U, spsf, sh, spf, true,
                           nc_tile_pixels(sM.nc, (long long)sL.nc_smem), tid, nthr);
     }
+    if (tid >= nthr - 32) nc_solve_pending(sh, spf, tid & 31);
 }
 
 using NcKernel = void (*)(const LensDev, const MultiDev, const NcArgs);
