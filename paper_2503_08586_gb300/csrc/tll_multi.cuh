@@ -255,38 +255,72 @@ __device__ __forceinline__ void nc_sum_index(int nc, int s, int &a, int &e, bool
     e = a + rem;
 }
 
-// The G sums st, st + NST, ..., st + (G-1) NST (those < S; the others are
-// computed on sum S - 1 and not stored) accumulated by this thread over the
-// pixels r, r + R, ... of every tile, in double-float; their FP64 partials
-// go to part[0 .. G).  Every term is a float pair times a float, the
-// product kept exact as a pair: A[a][e] takes (w M_a) M_e, b_a takes (w d)
-// M_a, where the pairs w M_a (w itself a pair) are formed once per tile
-// pixel at staging rather than once per sum.  Lanes hold consecutive st,
-// so a warp reads consecutive columns at one pixel (the tile's odd row
-// stride puts them in distinct banks).  Every thread of the CTA takes part
-// in the tile loads (st < 0: no sums).
-template <int G>
-__device__ __forceinline__ void nc_tile_sums(const LensDev &L, const float *M, int nc, int S,
-                                             int st, int NST, int r, int R, float *tile, int T,
-                                             int tid, int nthr, double *part)
+// The normal equations as 2 x 2 blocks of an extended matrix: rows are the
+// pair operands w M_0 .. w M_{nc-1} and w d (row nc), columns the blurred
+// columns M_0 .. M_{nc-1}; A[a][e] (a <= e) is (row a, column e) and b_e is
+// (row nc, column e).  Unit u is row block i (rows 2i, 2i + 1) by column
+// block j (columns 2j, 2j + 1), for j >= i up to the row block holding row
+// nc (i = nc/2), which takes every j.  Rows past nc and columns past nc - 1
+// (odd counts) are read as the last valid one and their sums dropped, as is
+// the block-diagonal entry below the diagonal.
+__device__ __forceinline__ int nc_units(int nc)
+{
+    const int rb = nc >> 1, cb = (nc + 1) >> 1;
+    return rb * cb - rb * (rb - 1) / 2 + cb;
+}
+
+// Unit u's rows r[0..1], columns c[0..1] (clamped to valid operands) and the
+// sum index of each of its four entries (row k, column l) at s[2k + l], or
+// -1 when dropped: A[a][e] is sum a nc - a (a - 1)/2 + e - a, b_e is sum
+// nc (nc + 1)/2 + e.
+__device__ __forceinline__ void nc_unit(int nc, int u, int *r, int *c, int *sx)
+{
+    const int rb = nc >> 1, cb = (nc + 1) >> 1;
+    int i = 0, j = 0;
+    for (i = 0; i < rb; ++i) {
+        if (u < cb - i) { j = i + u; break; }
+        u -= cb - i;
+    }
+    if (i == rb) j = u;
+    const int nA = nc * (nc + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        r[k] = min(2 * i + k, nc);
+        c[k] = min(2 * j + k, nc - 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int rk = 2 * i + k, cl = 2 * j + l;
+            int idx = -1;
+            if (rk <= nc && cl < nc) {
+                if (rk == nc) idx = nA + cl;
+                else if (rk <= cl) idx = rk * nc - rk * (rk - 1) / 2 + cl - rk;
+            }
+            sx[2 * k + l] = idx;
+        }
+}
+
+// Unit unit's four sums (those with sx >= 0) accumulated over the pixels
+// r, r + R, ... of every tile in double-float; FP64 partials to part[0..3].
+// Every term is a float pair times a float, the product kept exact as a
+// pair: A[a][e] takes (w M_a) M_e, b_e takes (w d) M_e, where the pairs
+// w M_a are formed once per tile pixel at staging.  Each pixel reads two
+// pairs and two floats for four terms through running pointers.  Every
+// thread of the CTA takes part in the tile loads (unit < 0: no sums).
+__device__ __forceinline__ void nc_tile_sums22(const LensDev &L, const float *M, int nc, int unit,
+                                               int r, int R, float *tile, int T, int tid,
+                                               int nthr, double *part)
 {
     const int npix = L.npix, TS = T + 1;
     float2 *wm = reinterpret_cast<float2 *>(tile + ((nc * TS + 1) & ~1));
-    float2 *wd = wm + nc * TS;
-    // per sum: the pair operand at wm[po + i] (wd = wm + nc TS for b_a) and
-    // the float operand at tile[fo + i]
-    int po[G], fo[G];
+    float2 *wd = wm + nc * TS;          // = row nc of the pair operands
+    int rr[2], cc[2], sx[4];
+    nc_unit(nc, max(unit, 0), rr, cc, sx);
+    float hi[4], lo[4];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        int a, e;
-        bool bs;
-        nc_sum_index(nc, min(max(st, 0) + g * NST, S - 1), a, e, bs);
-        po[g] = bs ? nc * TS : a * TS;
-        fo[g] = (bs ? a : e) * TS;
-    }
-    float hi[G], lo[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) hi[g] = lo[g] = 0.0f;
+    for (int g = 0; g < 4; ++g) hi[g] = lo[g] = 0.0f;
     for (int p0 = 0; p0 < npix; p0 += T) {
         const int n = min(T, npix - p0);
         for (int i = tid; i < n; i += nthr) {
@@ -305,23 +339,24 @@ __device__ __forceinline__ void nc_tile_sums(const LensDev &L, const float *M, i
             wm[c * TS + i] = make_float2(p1, e1);
         }
         __syncthreads();
-        if (st >= 0) {
-            for (int i = r; i < n; i += R) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const float2 q = wm[po[g] + i];
-                    const float f = tile[fo[g] + i];
-                    const float p = q.x * f;
-                    float er = fmaf(q.x, f, -p);
-                    er = fmaf(q.y, f, er);
-                    df_acc(hi[g], lo[g], p, er);
-                }
+        if (unit >= 0) {
+            const float2 *q0 = wm + rr[0] * TS + r, *q1 = wm + rr[1] * TS + r;
+            const float *f0 = tile + cc[0] * TS + r, *f1 = tile + cc[1] * TS + r;
+#pragma unroll 2
+            for (int i = r; i < n; i += R, q0 += R, q1 += R, f0 += R, f1 += R) {
+                const float2 a = *q0, b = *q1;
+                const float x = *f0, y = *f1;
+                float p, er;
+                p = a.x * x; er = fmaf(a.x, x, -p); er = fmaf(a.y, x, er); df_acc(hi[0], lo[0], p, er);
+                p = a.x * y; er = fmaf(a.x, y, -p); er = fmaf(a.y, y, er); df_acc(hi[1], lo[1], p, er);
+                p = b.x * x; er = fmaf(b.x, x, -p); er = fmaf(b.y, x, er); df_acc(hi[2], lo[2], p, er);
+                p = b.x * y; er = fmaf(b.x, y, -p); er = fmaf(b.y, y, er); df_acc(hi[3], lo[3], p, er);
             }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int g = 0; g < G; ++g) part[g] = (double)hi[g] + (double)lo[g];
+    for (int g = 0; g < 4; ++g) part[g] = (double)hi[g] + (double)lo[g];
 }
 
 // -------------------------------------------------------------- FNNLS
@@ -653,38 +688,32 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
     }
     __syncthreads();
     // 3. normal equations through shared-memory tiles (the dynamic shared
-    //    memory is free again once the convolution is done): thread (st, r)
-    //    takes sums st, st + NST, ... (G of them) over pixel phase r of RP;
-    //    G is 1, or 5 when that spreads the S sums x T pixels of a tile over
-    //    more threads (many columns: S near or above the CTA size) and the
-    //    partials fit; the FP64 partials go to the same space after the last
-    //    tile, then are added in a fixed order
+    //    memory is free again once the convolution is done): thread
+    //    (unit, r) takes a 2 x 2 block of sums (nc_unit) over pixel phase r
+    //    of RP; the FP64 partials go to the same space after the last tile
+    //    ([RP][S]), then are added in a fixed order
     {
         const int S = nc * (nc + 1) / 2 + nc;
         const long long cap = (long long)L.nc_smem / (long long)sizeof(double);
-        int G = 1;
-        {   // G = 5 when it spreads the work better: 5 / floor(nthr / ceil(S / 5))
-            // below 1 / floor(nthr / S)
-            const int nst = (S + 4) / 5, den = nthr / nst, den1 = max(1, nthr / S);
-            if (den > 0 && (long long)den * 5 * nst <= cap && 5 * den1 < den) G = 5;
+        const int NU = nc_units(nc);
+        int RP = max(1, nthr / NU);
+        while (RP > 1 && (long long)RP * S > cap) --RP;
+        const int r = tid / NU;
+        const int unit = r < RP ? tid - r * NU : -1;
+        double part[4];
+        nc_tile_sums22(L, Mb, nc, unit, r, RP, spsf, T, tid, nthr, part);
+        double *parts = reinterpret_cast<double *>(spsf);
+        if (unit >= 0) {
+            int rr[2], cc[2], sx[4];
+            nc_unit(nc, unit, rr, cc, sx);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (sx[g] >= 0) parts[(size_t)r * S + sx[g]] = part[g];
         }
-        const int NST = (S + G - 1) / G, RP = max(1, nthr / NST);
-        const int r = tid / NST;
-        const int st = tid < NST * RP ? tid - r * NST : -1;
-        double part[5];
-        if (G == 5)
-            nc_tile_sums<5>(L, Mb, nc, S, st, NST, r, RP, spsf, T, tid, nthr, part);
-        else
-            nc_tile_sums<1>(L, Mb, nc, S, st, NST, r, RP, spsf, T, tid, nthr, part);
-        double *parts = reinterpret_cast<double *>(spsf);   // [RP][G][NST]
-        if (st >= 0)
-            for (int g = 0; g < G; ++g)
-                if (st + g * NST < S) parts[((size_t)r * G + g) * NST + st] = part[g];
         __syncthreads();
         for (int t = tid; t < S; t += nthr) {
-            const int g = t / NST, stt = t - g * NST;
             double sum = 0.0;
-            for (int rr = 0; rr < RP; ++rr) sum += parts[((size_t)rr * G + g) * NST + stt];
+            for (int q = 0; q < RP; ++q) sum += parts[(size_t)q * S + t];
             int a, e;
             bool bsum;
             nc_sum_index(nc, t, a, e, bsum);
