@@ -577,7 +577,11 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     L.profile(False)
-    per_step = 2 if args.conv == "fused" else 1 + 3 * -(-B // args.split_chunk)
+    # fused: prologue + likelihood kernel, or the likelihood kernel alone
+    # when the batch fits the grid (it then decodes its own vectors)
+    grid_cap = (device_sms() or 152) * L.shape()["ctas_per_sm"]
+    per_step = ((1 if B <= grid_cap else 2) if args.conv == "fused"
+                else 1 + 3 * -(-B // args.split_chunk))
     launches = per_step * args.steps
     total = R.max(sum(step_ms))
     ms_per_step = total / args.steps

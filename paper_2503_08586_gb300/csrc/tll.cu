@@ -389,13 +389,26 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
     double xc, yc;
     grid_centre(L, &xc, &yc);
-    k_prologue<<<(B + kPrologueVectors - 1) / kPrologueVectors, dim3(kPrologueVectors, 4), 0,
-                 st>>>(params, B, kc, xc, yc, (double)L->dpix / L->sub, L->bn_tab, L->epl);
-    CUDA_TRY(cudaGetLastError());
+    const double d = (double)L->dpix / L->sub;
+    // a batch no larger than the grid (each CTA one vector) is decoded by the
+    // likelihood kernel itself: one launch instead of two, which is most of
+    // the gain for small batches (a sampler's few hundred walkers)
+    const bool fused = !write && B <= L->shape.grid_cap && L->conv_variant == TLL_CONV_FUSED;
+    if (!fused) {
+        k_prologue<<<(B + kPrologueVectors - 1) / kPrologueVectors, dim3(kPrologueVectors, 4),
+                     0, st>>>(params, B, kc, xc, yc, d, L->bn_tab, L->epl);
+        CUDA_TRY(cudaGetLastError());
+    }
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[1], st));
     RunArgs R = {};
     R.kc = kc; R.B = B; R.out = out; R.gscr = L->d_gscr; R.gslot = L->shape.gslot;
     R.wr_unblurred = L->d_unb; R.wr_blurred = L->d_blur; R.wr_res = L->d_res;
+    R.fused = fused ? 1 : 0;
+    R.epl = L->epl;
+    R.np = L->epl ? NPAR_EPL : NPAR;
+    R.params = params;
+    R.XC = xc; R.YC = yc; R.d = d;
+    R.bn_tab = L->bn_tab;
     const int grid = std::min(B, L->shape.grid_cap);
     if (write) return launch_main(L, R, 1, true, st);
     const int rc = L->conv_variant == TLL_CONV_FUSED ? launch_main(L, R, grid, false, st)

@@ -81,6 +81,13 @@ enum : int {
 
 struct RunArgs {
     const float *kc;     // [B][NCONST]
+    // fused: the kernel decodes its own vectors into kc (each CTA at most
+    // one vector: batches no larger than the grid) from params [B][np]
+    // (grid centre XC, YC, subpixel step d, b_n table), no separate prologue
+    int fused, epl, np;
+    const float *params;
+    double XC, YC, d;
+    const double *bn_tab;
     int B;
     double *out;         // [B]
     float *gscr;         // global image scratch, gslot floats per CTA

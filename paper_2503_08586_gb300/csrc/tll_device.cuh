@@ -401,7 +401,9 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
 // first subpixel: seven float4 loads (L1-resident: every thread of the CTA
 // reads the same block), live only until the pixel's lo terms are formed.
 // The loads are volatile so that the compiler keeps them in the pixel loop
-// rather than hoisting them out of it and holding 28 registers throughout.
+// rather than hoisting them out of it and holding 28 registers throughout;
+// plain (coherent) global loads, since a kernel may have written the block
+// itself before a barrier (the fused prologue of small batches).
 struct PixLo {
     float w[LO_N];
 };
@@ -412,7 +414,7 @@ __device__ __forceinline__ PixLo load_pixlo(const float *__restrict__ kc)
     const float *s = kc + K_LO;
 #pragma unroll
     for (int k = 0; k < LO_N / 4; ++k)
-        asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(p.w[4 * k]), "=f"(p.w[4 * k + 1]), "=f"(p.w[4 * k + 2]),
                        "=f"(p.w[4 * k + 3])
                      : "l"(s + 4 * k));

@@ -720,6 +720,14 @@ __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
     __syncthreads();
 }
 
+// One part of a vector's decode (decode_vector), kept out of line so that
+// its FP64 working set does not weigh on the likelihood kernel's registers.
+static __device__ __noinline__ void decode_part(const float *p, float *o, double XC, double YC,
+                                         double d, const double *bn_tab, bool epl, int part)
+{
+    decode_vector(p, o, XC, YC, d, bn_tab, epl, part);
+}
+
 // ------------------------------------------------------- one-lens kernel
 // K > 0: compiled convolution of side K (placements IMG_PADDED, IMG_BANDED);
 // K == 0: generic convolution (IMG_SMEM, IMG_GLOBAL).
@@ -742,6 +750,14 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
     __syncthreads();
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
+        if (!WRITE && R.fused) {
+            // the vector's four decode parts on lane 0 of warps 0-3 (four
+            // sub-partitions), visible to the CTA after the barrier
+            if ((tid & 31) == 0 && tid < 128)
+                decode_part(R.params + (size_t)b * R.np, const_cast<float *>(kc), R.XC, R.YC,
+                            R.d, R.bn_tab, R.epl != 0, tid >> 5);
+            __syncthreads();
+        }
         if (kc[K_VALID] == 0.0f) {
             if (tid == 0) {
                 R.out[b] = -INFINITY;
