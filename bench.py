@@ -546,7 +546,8 @@ def run_ours(args):
     # in this process (the request stream's) start with the chosen shape
     tune = None if args.no_autotune else L.autotune(p_dev)
     conv_variant = {"fused": tll.CONV_FUSED, "split-direct": tll.CONV_SPLIT_DIRECT,
-                    "split-tc": tll.CONV_SPLIT_TOEPLITZ_TC}[args.conv]
+                    "split-tc": tll.CONV_SPLIT_TOEPLITZ_TC,
+                    "split-bf16": tll.CONV_SPLIT_TOEPLITZ_BF16}[args.conv]
     if conv_variant != tll.CONV_FUSED:
         L.set_conv(conv_variant, chunk=args.split_chunk)
 
@@ -1099,29 +1100,30 @@ def measure_rows(steps=8, warmup=3, clocks=None):
     lo[[7, 14]] = hi[[7, 14]] = 1.0
     lo[[9, 16]], hi[[9, 16]] = 0.5, 6.0
     lo[[8, 15]], hi[[8, 15]] = 0.02, 3.0
-    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 30))
-    nw = 4096
-    x0 = np.repeat(truth[None], nw, axis=0)
     free = np.where(lo < hi)[0]
-    x0[:, free] += rng.normal(scale=0.05, size=(nw, free.size)).astype(np.float32)
-    x0[:, 12], x0[:, 13] = x0[:, 3], x0[:, 4]
-    x0 = np.clip(x0, lo, hi).astype(np.float32)
-    S = tll.Sampler(L, nw, lo, hi, ndim=int(np.sum(lo < hi)) - 2, seed=W.SEED_BASE)
-    S.set_walkers(torch.from_numpy(x0).to(dev))
-    S.run(warmup, keep_chain=False)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    S.run(2 * steps, keep_chain=True)
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / (2 * steps)
-    _, _, _, nacc, nprop = S.state()
-    rows["sampler_4096"] = {"value": nw / (ms / 1e3), "ms_per_step": ms,
-                            "acceptance": nacc / max(nprop, 1),
-                            "path": "tll_sampler_run: stretch move, likelihood, accept on the "
-                                    "GPU; one step = 4096 evaluations"}
-    S.close()
+    for nw in (4096, 256):
+        rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 30))
+        x0 = np.repeat(truth[None], nw, axis=0)
+        x0[:, free] += rng.normal(scale=0.05, size=(nw, free.size)).astype(np.float32)
+        x0[:, 12], x0[:, 13] = x0[:, 3], x0[:, 4]
+        x0 = np.clip(x0, lo, hi).astype(np.float32)
+        S = tll.Sampler(L, nw, lo, hi, ndim=int(np.sum(lo < hi)) - 2, seed=W.SEED_BASE)
+        S.set_walkers(torch.from_numpy(x0).to(dev))
+        S.run(warmup, keep_chain=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nstep = 2 * steps if nw >= 1024 else 16 * steps
+        e0.record()
+        S.run(nstep, keep_chain=True)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / nstep
+        _, _, _, nacc, nprop = S.state()
+        rows[f"sampler_{nw}"] = {"value": nw / (ms / 1e3), "ms_per_step": ms,
+                                 "acceptance": nacc / max(nprop, 1),
+                                 "path": "tll_sampler_run: stretch move, likelihood, accept on "
+                                         f"the GPU; one step = {nw} evaluations"}
+        S.close()
     L.close()
     return rows
 
@@ -1295,7 +1297,8 @@ def main(argv=None):
     ap.add_argument("--skip-rows", action="store_true",
                     help="omit the short measurements of the other workloads")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--conv", choices=["fused", "split-direct", "split-tc"], default="fused")
+    ap.add_argument("--conv", choices=["fused", "split-direct", "split-tc", "split-bf16"],
+                    default="fused")
     ap.add_argument("--split-chunk", type=int, default=1024)
     ap.add_argument("--stream-jobs", type=int, default=32)
     ap.add_argument("--stream-iters", type=int, default=100)

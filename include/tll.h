@@ -364,6 +364,10 @@ int tll_lens_shape(const tll_lens *L, tll_shape_t *out);
  *                         matrix on the tensor cores (tcgen05, TF32 with
  *                         three products per term for FP32-level accuracy);
  *                         PSF side <= 33
+ *   TLL_CONV_SPLIT_TOEPLITZ_BF16  the same GEMM with both operands split
+ *                         into three BF16 parts (hi + mid + lo, every FP32
+ *                         mantissa bit) and the six products down to 2^-24
+ *                         relative (tcgen05 kind::f16); PSF side <= 33
  * The split variants exist to compare the two convolutions on the same
  * inputs.  chunk: vectors per pass of the split pipeline (0: 1024); it holds
  * 16 B per pixel per vector of device memory.  Waits for the device first.
@@ -373,7 +377,8 @@ int tll_lens_shape(const tll_lens *L, tll_shape_t *out);
 enum {
     TLL_CONV_FUSED = 0,
     TLL_CONV_SPLIT_DIRECT = 1,
-    TLL_CONV_SPLIT_TOEPLITZ_TC = 2
+    TLL_CONV_SPLIT_TOEPLITZ_TC = 2,
+    TLL_CONV_SPLIT_TOEPLITZ_BF16 = 3
 };
 int tll_set_conv(tll_lens *L, int variant, int chunk);
 

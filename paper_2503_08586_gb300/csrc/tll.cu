@@ -194,6 +194,10 @@ struct tll_lens {
     float *d_unbl = nullptr, *d_sblur = nullptr, *d_tiles = nullptr;
     float *d_thi = nullptr, *d_tlo = nullptr;   // TF32 parts, chunk-major (Toeplitz)
     CUtensorMap tm_hi, tm_lo;                   // their tensor maps
+    void *d_bpart[3] = {nullptr, nullptr, nullptr};   // BF16 parts (split-BF16 Toeplitz)
+    CUtensorMap tm_b[3];                        // their tensor maps
+    uint16_t *d_btiles = nullptr;               // BF16 Toeplitz tiles
+    size_t bf_part_bytes_each = 0;
     int *d_tc_status = nullptr;
     int split_cap = 0;
     size_t tc_part_bytes = 0;
@@ -374,6 +378,9 @@ int run_split(tll_lens *L, const float *kc, int B, double *out, cudaStream_t st)
         if (L->conv_variant == TLL_CONV_SPLIT_TOEPLITZ_TC)
             CUDA_TRY(launch_conv_tc(d, L->d_unbl, nb, L->d_thi, L->d_tlo, L->tm_hi, L->tm_lo,
                                     L->d_sblur, L->d_tiles, L->d_tc_status, nsm, st));
+        else if (L->conv_variant == TLL_CONV_SPLIT_TOEPLITZ_BF16)
+            CUDA_TRY(launch_conv_bf(d, L->d_unbl, nb, L->d_bpart, L->tm_b, L->d_sblur,
+                                    L->d_btiles, L->d_tc_status, nsm, st));
         else
             CUDA_TRY(launch_conv_direct_split(d, L->d_unbl, nb, L->d_sblur,
                                               std::min(2 * nb, nsm), st));
@@ -615,7 +622,7 @@ void free_lens(tll_lens *L)
                     L->d_stage_p, L->d_stage_o, L->d_p1, L->d_kc1, L->d_unb,
                     L->d_blur, L->d_img, L->d_res, L->d_out1, L->d_unbl, L->d_sblur,
                     L->d_tiles, L->d_tc_status, L->d_thi, L->d_tlo, L->d_nscr, L->d_nres,
-                    L->d_tlist};
+                    L->d_tlist, L->d_bpart[0], L->d_bpart[1], L->d_bpart[2], L->d_btiles};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : L->prof_ev)
@@ -1260,7 +1267,7 @@ extern "C" int tll_set_conv(tll_lens *L, int variant, int chunk)
 {
     if (!L) return fail(TLL_EINVAL, "lens is NULL");
     if (variant != TLL_CONV_FUSED && variant != TLL_CONV_SPLIT_DIRECT &&
-        variant != TLL_CONV_SPLIT_TOEPLITZ_TC)
+        variant != TLL_CONV_SPLIT_TOEPLITZ_TC && variant != TLL_CONV_SPLIT_TOEPLITZ_BF16)
         return fail(TLL_EINVAL, "unknown convolution variant %d", variant);
     if (chunk < 0 || chunk > (1 << 20)) return fail(TLL_EINVAL, "chunk %d out of range", chunk);
     if (int rc = reject_nc(L, "tll_set_conv")) return rc;
@@ -1276,7 +1283,9 @@ extern "C" int tll_set_conv(tll_lens *L, int variant, int chunk)
     const LensDev d = lens_dev(L);
     if (variant == TLL_CONV_SPLIT_DIRECT && conv_direct_split_smem(d) > (size_t)D.optin)
         return fail(TLL_EINVAL, "padded %d x %d image does not fit shared memory", L->ny, L->nx);
-    if (variant == TLL_CONV_SPLIT_TOEPLITZ_TC && L->K > kTcMaxK)
+    const bool toeplitz = variant == TLL_CONV_SPLIT_TOEPLITZ_TC ||
+                          variant == TLL_CONV_SPLIT_TOEPLITZ_BF16;
+    if (toeplitz && L->K > kTcMaxK)
         return fail(TLL_EINVAL, "Toeplitz tiles hold PSF sides up to %d", kTcMaxK);
     const int cap = chunk > 0 ? chunk : 1024;
     const bool regrow = cap != L->split_cap || !L->d_unbl;
@@ -1323,6 +1332,33 @@ extern "C" int tll_set_conv(tll_lens *L, int variant, int chunk)
         L->dev_bytes += t.size() * sizeof(float);
         CUDA_TRY(cudaMemcpy(L->d_tiles, t.data(), t.size() * sizeof(float),
                             cudaMemcpyHostToDevice));
+    }
+    if (variant == TLL_CONV_SPLIT_TOEPLITZ_BF16 && (regrow || !L->d_bpart[0])) {
+        const size_t pb = bf_part_bytes(2 * cap, L->ny, L->nx);
+        for (int q = 0; q < 3; ++q)
+            if (L->d_bpart[q]) {
+                cudaFree(L->d_bpart[q]);
+                L->d_bpart[q] = nullptr;
+                L->dev_bytes -= L->bf_part_bytes_each;
+            }
+        L->bf_part_bytes_each = 0;
+        for (int q = 0; q < 3; ++q) {
+            CUDA_TRY(cudaMalloc(&L->d_bpart[q], pb));
+            L->dev_bytes += pb;
+        }
+        L->bf_part_bytes_each = pb;
+        if (make_bf_maps(L->d_bpart, 2 * cap, L->ny, L->nx, L->K, L->tm_b))
+            return fail(TLL_ECUDA, "cuTensorMapEncodeTiled failed for the BF16 Toeplitz operands");
+    }
+    if (variant == TLL_CONV_SPLIT_TOEPLITZ_BF16 && !L->d_btiles) {
+        std::vector<uint16_t> t(bf_tile_elems(L->K));
+        build_bf_tiles(L->psf_norm.data(), L->K, t.data());
+        CUDA_TRY(cudaMalloc(&L->d_btiles, t.size() * sizeof(uint16_t)));
+        L->dev_bytes += t.size() * sizeof(uint16_t);
+        CUDA_TRY(cudaMemcpy(L->d_btiles, t.data(), t.size() * sizeof(uint16_t),
+                            cudaMemcpyHostToDevice));
+    }
+    if (toeplitz && !L->d_tc_status) {
         CUDA_TRY(cudaMalloc(&L->d_tc_status, sizeof(int)));
         L->dev_bytes += sizeof(int);
         CUDA_TRY(cudaMemset(L->d_tc_status, 0, sizeof(int)));

@@ -190,15 +190,44 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
            ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor: D F32, A and B TF32, both K-major, N and M.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                              ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+// The two operand kinds of the Toeplitz GEMM.
+//  TF32: x = hi + lo, hi the TF32 rounding of x (lo exact in FP32); the
+//   products hi*hi + hi*lo + lo*hi; tcgen05.mma kind::tf32, K = 8 per step.
+//  BF16: x = hi + mid + lo, each the BF16 rounding of what the earlier parts
+//   leave (24 mantissa bits in all, so x exactly for FP32 x); the products
+//   hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi -- every term down to
+//   2^-24 relative, the dropped ones (mid*lo, lo*mid, lo*lo) below 2^-32;
+//   tcgen05.mma kind::f16 with both operands BF16, K = 16 per step.
+// Either way a 16-byte chunk holds kChunk consecutive columns of a row and
+// an MMA step spans two chunks, so the shared-memory layouts and matrix
+// descriptors are the same.  Instruction descriptor: D F32 (bit 4), A and B
+// formats (bits 7, 10: TF32 2 under kind::tf32, BF16 1 under kind::f16),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <bool BF>
+struct TcKind {
+    static constexpr int kParts = BF ? 3 : 2, kElem = BF ? 2 : 4, kChunk = 16 / kElem;
+    static constexpr int kProducts = BF ? 6 : 3;
+    static constexpr int kChunks = kTcKd / kChunk;       // chunks of the window
+    static constexpr int kSteps = kTcKd / (2 * kChunk);  // MMA steps per PSF row
+    static constexpr int kPartTileBytes = kTcKd * kTcN * kElem;
+    static constexpr int kTileBytes = kParts * kPartTileBytes;   // one PSF row
+    static constexpr int kABytes = kChunks * kTcRows * 16;       // one part of one A buffer
+    static constexpr uint32_t kIdesc = (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+                                       ((uint32_t)(kTcN >> 3) << 17) |
+                                       ((uint32_t)(kTcM >> 4) << 24);
+    // parts of A and B in product p
+    __host__ __device__ static constexpr int apart(int p)
+    {
+        return BF ? (p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0) : (p == 2 ? 1 : 0);
+    }
+    __host__ __device__ static constexpr int bpart(int p)
+    {
+        return BF ? (p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0) : (p == 1 ? 1 : 0);
+    }
+};
 
-constexpr int kTcTileFloats = 2 * kTcKd * kTcN;   // one PSF row, both parts
-constexpr int kTcTileBytes = kTcTileFloats * 4;
 constexpr int kTcStages = 3;                      // Toeplitz ring
 constexpr int kTcNCol = 2 * kTcN;                 // TMEM columns: two accumulators
-constexpr int kTcABytes = kTcKd / 4 * kTcRows * 16;   // one part of one A buffer (max)
 constexpr uint32_t kTcSpin = 1u << 22;            // wait limit (iterations)
 
 // Wait for phase `parity` of an mbarrier; false (and the abort flag set)
@@ -287,26 +316,88 @@ __global__ void k_tf32_split(const float *__restrict__ unbl, int nimg, int ny, i
     }
 }
 
-__global__ void __launch_bounds__(192, 1)
-k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap tm_hi,
-          const __grid_constant__ CUtensorMap tm_lo, int nimg, float *__restrict__ blur,
-          const float *__restrict__ tiles, int *status)
+// BF16 bits of x rounded to nearest, ties to even (finite x).
+__host__ __device__ __forceinline__ uint32_t bf16_bits(float x)
 {
+#ifdef __CUDA_ARCH__
+    const uint32_t u = __float_as_uint(x);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+#endif
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__host__ __device__ __forceinline__ float bf16_value(uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b << 16);
+#else
+    const uint32_t u = b << 16;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+#endif
+}
+// x as hi + mid + lo BF16 parts (bits).
+__host__ __device__ __forceinline__ void bf16_split3(float x, uint32_t *p)
+{
+    p[0] = bf16_bits(x);
+    const float r1 = x - bf16_value(p[0]);
+    p[1] = bf16_bits(r1);
+    p[2] = bf16_bits(r1 - bf16_value(p[1]));
+}
+
+// Images (row-major, nimg of ny x nx) -> BF16 hi, mid and lo parts,
+// chunk-major [image][chunk of 8 columns][row][8], columns past nx as zeros.
+__global__ void k_bf16_split(const float *__restrict__ unbl, int nimg, int ny, int nx, int nch,
+                             uint4 *__restrict__ p0, uint4 *__restrict__ p1,
+                             uint4 *__restrict__ p2)
+{
+    const long long n = (long long)nimg * nch * ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(t % ny);
+        const long long q = t / ny;
+        const int ch = (int)(q % nch);
+        const long long img = q / nch;
+        const float *src = unbl + (img * ny + row) * nx + 8 * ch;
+        uint32_t w[3][4] = {};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t b[3];
+            bf16_split3((8 * ch + k < nx) ? src[k] : 0.0f, b);
+#pragma unroll
+            for (int part = 0; part < 3; ++part) w[part][k >> 1] |= b[part] << (16 * (k & 1));
+        }
+        p0[t] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+        p1[t] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+        p2[t] = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+    }
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(192, 1)
+k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap tm0,
+          const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
+          int nimg, float *__restrict__ blur, const unsigned char *__restrict__ tiles,
+          int *status)
+{
+    using KD = TcKind<BF>;
     extern __shared__ __align__(1024) unsigned char dsm[];
-    // A: [2 buffers][2 parts][kTcABytes], B: [kTcStages][kTcTileBytes]
+    // A: [2 buffers][kParts][kABytes], B: [kTcStages][kTileBytes]
     unsigned char *sA = dsm;
-    unsigned char *sB = dsm + 4 * kTcABytes;
+    unsigned char *sB = dsm + 2 * KD::kParts * KD::kABytes;
     __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[kTcStages],
         b_empty[kTcStages], acc_full[2], acc_empty[2], drained;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int K = L.K, h = (K - 1) / 2, o = (h + 3) & ~3;
+    const int K = L.K, h = (K - 1) / 2, o = (h + KD::kChunk - 1) & ~(KD::kChunk - 1);
     const int nx = L.nx, ny = L.ny, npix = L.npix;
     const int nrb = (ny + kTcM - 1) / kTcM, ncb = (nx + kTcN - 1) / kTcN;
     const long long items = (long long)nimg * nrb * ncb;
     const int arows = kTcM + K - 1;                       // rows of the TMA box
-    const uint32_t abox = (uint32_t)(kTcKd / 4 * arows * 16);
+    const uint32_t abox = (uint32_t)(KD::kChunks * arows * 16);
     if (tid == 0) {
         abort_flag = 0;
         for (int q = 0; q < 2; ++q) {
@@ -341,11 +432,13 @@ k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap
                 const int img = (int)(rest / nrb);
                 if (!(ok = tc_wait(smem_u32(&a_empty[ab]), ae_par[ab], &abort_flag))) break;
                 ae_par[ab] ^= 1u;
-                mbar_expect_tx(&a_full[ab], 2 * abox);
-                const int c0 = 0, c1 = rb * kTcM - h, c2 = (cb * kTcN - o) / 4, c3 = img;
-                for (int part = 0; part < 2; ++part) {
-                    const uint32_t dst = smem_u32(sA + (2 * ab + part) * kTcABytes);
-                    const CUtensorMap *tm = part ? &tm_lo : &tm_hi;
+                mbar_expect_tx(&a_full[ab], KD::kParts * abox);
+                // innermost coordinate 0 (16-byte aligned); the chunk and row
+                // coordinates may leave the image (zero fill)
+                const int c0 = 0, c1 = rb * kTcM - h, c2 = (cb * kTcN - o) / KD::kChunk, c3 = img;
+                for (int part = 0; part < KD::kParts; ++part) {
+                    const uint32_t dst = smem_u32(sA + (KD::kParts * ab + part) * KD::kABytes);
+                    const CUtensorMap *tm = part == 0 ? &tm0 : part == 1 ? &tm1 : &tm2;
                     asm volatile(
                         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                         " [%0], [%1, {%2, %3, %4, %5}], [%6];"
@@ -357,12 +450,12 @@ k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap
                 for (int r = 0; r < K; ++r) {
                     if (!(ok = tc_wait(smem_u32(&b_empty[st]), be_par[st], &abort_flag))) break;
                     be_par[st] ^= 1u;
-                    mbar_expect_tx(&b_full[st], kTcTileBytes);
+                    mbar_expect_tx(&b_full[st], KD::kTileBytes);
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
                         " [%0], [%1], %2, [%3];"
-                        :: "r"(smem_u32(sB + st * kTcTileBytes)),
-                           "l"(tiles + (size_t)r * kTcTileFloats), "r"(kTcTileBytes),
+                        :: "r"(smem_u32(sB + st * KD::kTileBytes)),
+                           "l"(tiles + (size_t)r * KD::kTileBytes), "r"(KD::kTileBytes),
                            "r"(smem_u32(&b_full[st])) : "memory");
                     ++b_iss[st];
                     st = (st + 1) % kTcStages;
@@ -387,8 +480,10 @@ k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap
             for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
                 if (!(ok = tc_wait(smem_u32(&a_full[ab]), af_par[ab], &abort_flag))) break;
                 af_par[ab] ^= 1u;
-                const uint32_t a_hi = smem_u32(sA + (2 * ab) * kTcABytes);
-                const uint32_t a_lo = smem_u32(sA + (2 * ab + 1) * kTcABytes);
+                uint32_t a_part[KD::kParts];
+#pragma unroll
+                for (int part = 0; part < KD::kParts; ++part)
+                    a_part[part] = smem_u32(sA + (KD::kParts * ab + part) * KD::kABytes);
                 for (int r = 0; r < K; ++r) {
                     const int acc = r & 1;
                     if (!(ok = tc_wait(smem_u32(&b_full[st]), bf_par[st], &abort_flag))) break;
@@ -397,22 +492,29 @@ k_conv_tc(const __grid_constant__ LensDev L, const __grid_constant__ CUtensorMap
                     ce_par[acc] ^= 1u;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t rowoff = 16u * (uint32_t)(2 * h - r);
-                    const uint32_t b_hi = smem_u32(sB + st * kTcTileBytes);
-                    const uint32_t b_lo = b_hi + (uint32_t)(kTcKd * kTcN * 4);
+                    const uint32_t b_base = smem_u32(sB + st * KD::kTileBytes);
                     const uint32_t d = tmem + (uint32_t)(acc * kTcN);
 #pragma unroll 1
-                    for (int ks = 0; ks < kTcKd / 8; ++ks) {
+                    for (int ks = 0; ks < KD::kSteps; ++ks) {
                         const uint32_t ao = (uint32_t)(2 * ks) * lbo_a + rowoff;
                         const uint32_t bo = (uint32_t)(2 * ks * kTcN * 16);
 #pragma unroll
-                        for (int term = 0; term < 3; ++term) {
-                            const uint64_t ad = tc_desc((term == 2 ? a_lo : a_hi) + ao, lbo_a, 128);
-                            const uint64_t bd = tc_desc((term == 1 ? b_lo : b_hi) + bo, kTcN * 16, 128);
+                        for (int term = 0; term < KD::kProducts; ++term) {
+                            const uint64_t ad = tc_desc(a_part[KD::apart(term)] + ao, lbo_a, 128);
+                            const uint64_t bd =
+                                tc_desc(b_base + (uint32_t)(KD::bpart(term) * KD::kPartTileBytes) + bo,
+                                        kTcN * 16, 128);
                             const uint32_t accum = (ks > 0 || term > 0) ? 1u : 0u;
-                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                         :: "r"(d), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(accum)
-                                         : "memory");
+                            if constexpr (BF)
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                             :: "r"(d), "l"(ad), "l"(bd), "r"(KD::kIdesc), "r"(accum)
+                                             : "memory");
+                            else
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                             :: "r"(d), "l"(ad), "l"(bd), "r"(KD::kIdesc), "r"(accum)
+                                             : "memory");
                         }
                     }
                     tc_commit(&b_empty[st]);
@@ -504,20 +606,50 @@ size_t conv_direct_split_smem(const LensDev &L)
     return (size_t)(L.ny + 2 * L.h) * L.W * sizeof(float);
 }
 
-size_t conv_tc_smem() { return (size_t)4 * kTcABytes + (size_t)kTcStages * kTcTileBytes; }
+void build_bf_tiles(const float *psf, int K, uint16_t *out)
+{
+    using KD = TcKind<true>;
+    const int h = (K - 1) / 2, o = (h + KD::kChunk - 1) & ~(KD::kChunk - 1);
+    for (int r = 0; r < K; ++r)
+        for (int kc = 0; kc < KD::kChunks; ++kc)
+            for (int n = 0; n < kTcN; ++n)
+                for (int kk = 0; kk < KD::kChunk; ++kk) {
+                    const int k = KD::kChunk * kc + kk, c = n + h + o - k;
+                    uint32_t b[3];
+                    bf16_split3((c >= 0 && c < K) ? psf[r * K + c] : 0.0f, b);
+                    for (int part = 0; part < 3; ++part)
+                        out[(((((size_t)r * 3 + part) * KD::kChunks + kc) * kTcN + n) *
+                              KD::kChunk) + kk] = (uint16_t)b[part];
+                }
+}
+
+size_t bf_tile_elems(int K) { return (size_t)K * TcKind<true>::kTileBytes / 2; }
+
+size_t conv_tc_smem(bool bf)
+{
+    return bf ? (size_t)2 * TcKind<true>::kParts * TcKind<true>::kABytes +
+                    (size_t)kTcStages * TcKind<true>::kTileBytes
+              : (size_t)2 * TcKind<false>::kParts * TcKind<false>::kABytes +
+                    (size_t)kTcStages * TcKind<false>::kTileBytes;
+}
+
+size_t bf_part_bytes(int nimg, int ny, int nx)
+{
+    return (size_t)nimg * ((nx + 7) / 8) * ny * 16;
+}
 
 size_t tc_part_floats(int nimg, int ny, int nx)
 {
     return (size_t)nimg * ((nx + 3) / 4) * ny * 4;
 }
 
-int make_tc_maps(const float *hi, const float *lo, int nimg, int ny, int nx, int K,
-                 CUtensorMap *mhi, CUtensorMap *mlo)
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn tensor_map_encoder()
 {
-    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     static EncodeFn encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -525,9 +657,38 @@ int make_tc_maps(const float *hi, const float *lo, int nimg, int ny, int nx, int
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                              cudaEnableDefault, &q) != cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !fn)
-            return 1;
+            return nullptr;
         encode = reinterpret_cast<EncodeFn>(fn);
     }
+    return encode;
+}
+}  // namespace
+
+int make_bf_maps(void *const *parts, int nimg, int ny, int nx, int K, CUtensorMap *maps)
+{
+    const EncodeFn encode = tensor_map_encoder();
+    if (!encode) return 1;
+    using KD = TcKind<true>;
+    const int nch = (nx + 7) / 8;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)ny, (cuuint64_t)nch, (cuuint64_t)nimg};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)ny * 16, (cuuint64_t)nch * ny * 16};
+    const cuuint32_t box[4] = {8, (cuuint32_t)(kTcM + K - 1), KD::kChunks, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int part = 0; part < 3; ++part) {
+        const CUresult r = encode(&maps[part], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, parts[part],
+                                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return 2;
+    }
+    return 0;
+}
+
+int make_tc_maps(const float *hi, const float *lo, int nimg, int ny, int nx, int K,
+                 CUtensorMap *mhi, CUtensorMap *mlo)
+{
+    const EncodeFn encode = tensor_map_encoder();
+    if (!encode) return 1;
     const int nch = (nx + 3) / 4;
     const cuuint64_t dims[4] = {4, (cuuint64_t)ny, (cuuint64_t)nch, (cuuint64_t)nimg};
     const cuuint64_t strides[3] = {16, (cuuint64_t)ny * 16, (cuuint64_t)nch * ny * 16};
@@ -585,10 +746,36 @@ cudaError_t launch_conv_tc(const LensDev &L, const float *unbl, int nvec, float 
                                      reinterpret_cast<float4 *>(hi), reinterpret_cast<float4 *>(lo));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = conv_tc_smem();
-    e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = conv_tc_smem(false);
+    e = cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_tc<<<grid, 192, smem, st>>>(L, mhi, mlo, nimg, blur, tiles, status);
+    k_conv_tc<false><<<grid, 192, smem, st>>>(L, mhi, mlo, mlo, nimg, blur,
+                                              reinterpret_cast<const unsigned char *>(tiles),
+                                              status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_bf(const LensDev &L, const float *unbl, int nvec, void *const *parts,
+                           const CUtensorMap *maps, float *blur, const uint16_t *tiles,
+                           int *status, int grid, cudaStream_t st)
+{
+    const int nimg = 2 * nvec, nch = (L.nx + 7) / 8;
+    const long long n = (long long)nimg * nch * L.ny;
+    const int sg = (int)std::min<long long>((n + 255) / 256, 65535);
+    k_bf16_split<<<sg, 256, 0, st>>>(unbl, nimg, L.ny, L.nx, nch,
+                                     reinterpret_cast<uint4 *>(parts[0]),
+                                     reinterpret_cast<uint4 *>(parts[1]),
+                                     reinterpret_cast<uint4 *>(parts[2]));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = conv_tc_smem(true);
+    e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_conv_tc<true><<<grid, 192, smem, st>>>(L, maps[0], maps[1], maps[2], nimg, blur,
+                                             reinterpret_cast<const unsigned char *>(tiles),
+                                             status);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "tll_core.cuh"
 
@@ -54,9 +55,21 @@ int make_tc_maps(const float *hi, const float *lo, int nimg, int ny, int nx, int
 cudaError_t launch_sums_split(const LensDev &L, const float *kc, const float *blur,
                               int nvec, double *out, int grid, cudaStream_t st);
 
+// The split-BF16 variant: the images as BF16 hi, mid and lo parts (three
+// buffers of bf_part_bytes, chunk-major [image][8 columns][row][8]) under
+// the tensor maps maps[0..2] (make_bf_maps); Toeplitz tiles of three BF16
+// parts per PSF row (build_bf_tiles, bf_tile_elems 16-bit values).
+void build_bf_tiles(const float *psf, int K, uint16_t *out);
+size_t bf_tile_elems(int K);
+size_t bf_part_bytes(int nimg, int ny, int nx);
+int make_bf_maps(void *const *parts, int nimg, int ny, int nx, int K, CUtensorMap *maps);
+cudaError_t launch_conv_bf(const LensDev &L, const float *unbl, int nvec, void *const *parts,
+                           const CUtensorMap *maps, float *blur, const uint16_t *tiles,
+                           int *status, int grid, cudaStream_t st);
+
 // Shared memory the direct split kernel needs for one padded image (bytes),
-// and the Toeplitz kernel's (constant).
+// and the Toeplitz kernel's (constant per operand kind).
 size_t conv_direct_split_smem(const LensDev &L);
-size_t conv_tc_smem();
+size_t conv_tc_smem(bool bf);
 
 }  // namespace tll

@@ -80,7 +80,7 @@ def comp(type: str, plane: str, free_scale: bool = True, free_index: bool = Fals
 
 
 PLACEMENTS = {0: "global", 1: "smem", 2: "padded", 3: "banded"}
-CONV_FUSED, CONV_SPLIT_DIRECT, CONV_SPLIT_TOEPLITZ_TC = 0, 1, 2
+CONV_FUSED, CONV_SPLIT_DIRECT, CONV_SPLIT_TOEPLITZ_TC, CONV_SPLIT_TOEPLITZ_BF16 = 0, 1, 2, 3
 
 
 class Shape(ctypes.Structure):
@@ -416,8 +416,9 @@ class Lens:
 
     def set_conv(self, variant: int, chunk: int = 0):
         """Convolution variant of the one-lens batched path: CONV_FUSED
-        (default), CONV_SPLIT_DIRECT or CONV_SPLIT_TOEPLITZ_TC (split
-        pipeline, chunk vectors per pass, 0: 1024)."""
+        (default), CONV_SPLIT_DIRECT, CONV_SPLIT_TOEPLITZ_TC (3xTF32) or
+        CONV_SPLIT_TOEPLITZ_BF16 (split-BF16) (split pipeline, chunk vectors
+        per pass, 0: 1024)."""
         _check(load().tll_set_conv(self._h, int(variant), int(chunk)))
 
     def conv_check(self):

@@ -248,7 +248,8 @@ def main():
     print(report_served(), flush=True)
     # the hst200 convolution (Eq. 3) run three ways
     for conv in (("split, direct FP32", tll.CONV_SPLIT_DIRECT),
-                 ("split, Toeplitz 3xTF32 tensor cores", tll.CONV_SPLIT_TOEPLITZ_TC)):
+                 ("split, Toeplitz 3xTF32 tensor cores", tll.CONV_SPLIT_TOEPLITZ_TC),
+                 ("split, Toeplitz split-BF16 tensor cores", tll.CONV_SPLIT_TOEPLITZ_BF16)):
         print(report("hst200", conv=conv), flush=True)
 
 

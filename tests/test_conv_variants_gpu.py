@@ -1,8 +1,9 @@
-"""The PSF convolution (Eq. 3) three ways on the same lens and vectors: the
+"""The PSF convolution (Eq. 3) four ways on the same lens and vectors: the
 fused kernel (default), the split pipeline with a direct FP32 convolution, and
-the split pipeline with the banded-Toeplitz GEMM on the tensor cores (TF32,
-three products per term).  Each against the FP64 oracle: blurred model columns
-within the pixel gate, log L within the parity gates."""
+the split pipeline with the banded-Toeplitz GEMM on the tensor cores, in TF32
+(three products per term) and in split BF16 (three parts per operand, six
+products).  Each against the FP64 oracle: blurred model columns within the
+pixel gate, log L within the parity gates."""
 import numpy as np
 import pytest
 
@@ -16,7 +17,8 @@ from test_parity_gpu import _ll_ok, _pix_allowance, _pix_ok
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [tll.CONV_FUSED, tll.CONV_SPLIT_DIRECT, tll.CONV_SPLIT_TOEPLITZ_TC]
+VARIANTS = [tll.CONV_FUSED, tll.CONV_SPLIT_DIRECT, tll.CONV_SPLIT_TOEPLITZ_TC,
+            tll.CONV_SPLIT_TOEPLITZ_BF16]
 # (ny, nx, pixel scale, s, PSF side, kind): the hst200 geometry at a smaller
 # batch; ragged sizes with a small PSF; a PSF side the compiled split kernel
 # does not cover; the largest side the Toeplitz tiles hold
@@ -46,7 +48,8 @@ def cases():
     return out
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=["fused", "split_direct", "split_tc"])
+@pytest.mark.parametrize("variant", VARIANTS,
+                         ids=["fused", "split_direct", "split_tc", "split_bf16"])
 @pytest.mark.parametrize("idx", range(len(LENSES)))
 def test_variant_against_oracle(cases, idx, variant):
     sl, P, ref, cols, allows = cases[idx]
