@@ -289,7 +289,8 @@ LensDev lens_dev(const tll_lens *L)
     d.tlist = L->d_tlist;
     d.ntrace = L->d_tlist ? L->ntrace : L->npix;
     d.nx_mul = (unsigned)(((1ULL << 32) + (unsigned long long)L->nx - 1) / L->nx);
-    d.nx_fast = (unsigned long long)L->nx * L->nx * (L->ny + 8) < (1ULL << 32) ? 1 : 0;
+    // (nx = 1: ceil(2^32 / nx) does not fit 32 bits; the division is used)
+    d.nx_fast = L->nx > 1 && (unsigned long long)L->nx * L->nx * (L->ny + 8) < (1ULL << 32) ? 1 : 0;
     for (int k = 0; k < kMaxK * (kMaxK + 1); ++k) d.tk[k] = 0.0f;
     if (L->K <= kMaxK) {
         const int ts = tap_stride(L->K);

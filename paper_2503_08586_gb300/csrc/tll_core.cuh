@@ -44,13 +44,41 @@ struct LensDev {
     int nc_smem;      // multi-column kernel: dynamic shared memory of the launch
     // n / nx as __umulhi(n, nx_mul), nx_mul = ceil(2^32 / nx): exact for
     // n < 2^32 / nx, which nx_fast records for every index a kernel divides
-    // (pixel indices and column-pass units, n < nx (ny + 8))
+    // (pixel indices and column-pass units, n < nx (ny + 8)); 0 for nx = 1
     unsigned nx_mul;
     int nx_fast;
     float tu[kMaxTaps], tv[kMaxTaps];   // the separable factors again, by value
     // the full PSF (direct convolution), row r at tk[r * tap_stride(K)]
     alignas(8) float tk[kMaxK * (kMaxK + 1)];
 };
+
+// Asynchronous global -> shared copies (cp.async): the copies of a thread
+// complete at its cp_async_wait_all (or the group's wait), visible to the
+// other threads after a barrier.  cp_async4_zfill with valid = false reads
+// nothing from src and writes 0.
+__device__ __forceinline__ void cp_async4_zfill(float *dst, const float *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float4 *dst, const float4 *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Barrier over the threads taking part in a phase: BAR 0 is the whole CTA
 // (__syncthreads); BAR > 0 is named barrier BAR over the first nthr threads

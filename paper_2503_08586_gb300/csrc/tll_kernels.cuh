@@ -326,6 +326,33 @@ __device__ __forceinline__ void conv_sep_cols(const LensDev &L, const float *Pl,
     }
 }
 
+// Band staging: buffer rows [0, nbr) of both channels (Ps = Pl + off_s)
+// <- image rows [b0 - h, b0 - h + nbr) of Il / Is, rows outside the image
+// as zero.  The images sit in global memory (L2, or DRAM once evicted):
+// every element is an asynchronous copy, so a band costs about one memory
+// round trip.  Entry t = (channel, buffer row, column) flattened; its row is
+// t / nx by a multiply-high where nx > 1 and t nx < 2^32 (exact there:
+// nx_mul = ceil(2^32 / nx)), else by a division.  Ends with the thread's own
+// copies complete; no barrier.
+__device__ __forceinline__ void stage_band(const LensDev &L, const float *Il, const float *Is,
+                                           float *Pl, int off_s, int b0, int nbr, int tid,
+                                           int nthr)
+{
+    const int nx = L.nx, ny = L.ny, W = L.W, HL = L.HL, r0 = b0 - L.h;
+    const int tot = 2 * nbr * nx;
+    const bool fast = nx > 1 && (unsigned long long)tot * (unsigned)nx < (1ULL << 32);
+    for (int t = tid; t < tot; t += nthr) {
+        const int row = fast ? (int)__umulhi((unsigned)t, L.nx_mul) : t / nx;
+        const int j = t - row * nx;
+        const int ch = row >= nbr ? 1 : 0;
+        const int br = row - ch * nbr, ir = r0 + br;
+        const bool in = ir >= 0 && ir < ny;
+        cp_async4_zfill(Pl + ch * off_s + br * W + HL + j, (ch ? Is : Il) + (in ? ir * nx + j : 0),
+                        in);
+    }
+    cp_async_wait_all();
+}
+
 template <int K, class Sink, int BAR = 0>
 __device__ __forceinline__ void conv_sep_band(const LensDev &L, float *Pl, float *Ps,
                                               int b0, int nrows, int rlo, int rhi, int tid,
@@ -603,13 +630,7 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
             if (banded) {
                 // buffer rows [0, nrows + 2h) <- image rows [b0 - h, b0 + nrows + h)
                 const int nbr = nrows + 2 * h;
-                for (int t = tid; t < 2 * nbr * nx; t += nthr) {
-                    const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
-                    const int br = rem / nx, j = rem - br * nx;
-                    const int ir = b0 - h + br;
-                    const float v = (ir >= 0 && ir < ny) ? (ch ? P.Is : P.Il)[ir * nx + j] : 0.0f;
-                    (ch ? Ps : Pl)[br * W + HL + j] = v;
-                }
+                stage_band(L, P.Il, P.Is, Pl, (int)(Ps - Pl), b0, nbr, tid, nthr);
                 __syncthreads();
                 rlo = max(0, h - b0);
                 rhi = min(nbr, ny - b0 + h);

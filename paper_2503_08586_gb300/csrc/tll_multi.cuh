@@ -216,20 +216,36 @@ __device__ __forceinline__ void trace_pass(const LensDev &L, const VecConst &v,
 }
 
 // ----------------------------------------------------- normal equations
-// Shared-memory tile of the sums, for pixels [p0, p0 + T): every blurred
-// column M_c (row stride T + 1, odd, so the lanes of a warp -- consecutive
-// columns at one pixel -- hit distinct banks), then every weighted column
-// w M_c as an exact float pair (same stride), then the pixels' w d pairs.
+// Shared-memory tiles of the sums, T pixels each, in float offsets from the
+// base: two buffers of the blurred columns M_c (R0 at 0, R1 at nc TS; row
+// stride TS = T + 1, odd, so the lanes of a warp -- different columns at
+// one pixel -- hit distinct banks), the pair operands at WM (every weighted
+// column w M_c as an exact float pair, then the pixels' w d pairs as row nc;
+// same stride) and two buffers of the pixels' weight records at WW (float4,
+// 16-byte aligned).  The next tile's columns and records are copied
+// asynchronously into the other buffers while the current tile is summed.
+struct NcTileLayout {
+    int TS;
+    long long r1, wm, ww, floats;
+    __host__ __device__ NcTileLayout(int nc, int T)
+    {
+        TS = T + 1;
+        r1 = (long long)nc * TS;
+        wm = (2 * r1 + 3) & ~3LL;
+        ww = (wm + 2LL * (nc + 1) * TS + 3) & ~3LL;
+        floats = ww + 8LL * T;
+    }
+};
+
 __host__ __device__ inline long long nc_tile_bytes(int nc, int T)
 {
-    const long long ts = (long long)nc * (T + 1);
-    return 4 * ((ts + 1) & ~1LL) + 8 * ts + 8LL * T;
+    return 4 * NcTileLayout(nc, T).floats;
 }
 
 // The largest tile (pixels, a multiple of 32 in [32, 4096]) that fits.
 __host__ __device__ inline int nc_tile_pixels(int nc, long long smem_bytes)
 {
-    long long t = (smem_bytes - 12LL * nc - 4) / (12LL * nc + 8);
+    long long t = smem_bytes / (16LL * nc + 40);
     t = t < 32 ? 32 : (t & ~31LL) > 4096 ? 4096 : (t & ~31LL);
     while (t > 32 && nc_tile_bytes(nc, (int)t) > smem_bytes) t -= 32;
     return (int)t;
@@ -306,55 +322,80 @@ __device__ __forceinline__ void nc_unit(int nc, int u, int *r, int *c, int *sx)
 // r, r + R, ... of every tile in double-float; FP64 partials to part[0..3].
 // Every term is a float pair times a float, the product kept exact as a
 // pair: A[a][e] takes (w M_a) M_e, b_e takes (w d) M_e, where the pairs
-// w M_a are formed once per tile pixel at staging.  Each pixel reads two
-// pairs and two floats for four terms through running pointers.  Every
-// thread of the CTA takes part in the tile loads (unit < 0: no sums).
+// w M_a are formed once per tile pixel from the staged columns.  Each pixel
+// reads two pairs and two floats for four terms through running pointers.
+// Every thread of the CTA takes part in the copies (unit < 0: no sums).
+// Per tile: wait for its copies, barrier, start the next tile's copies, form
+// the pairs, barrier, sum; a final barrier frees the shared memory.
 __device__ __forceinline__ void nc_tile_sums22(const LensDev &L, const float *M, int nc, int unit,
                                                int r, int R, float *tile, int T, int tid,
                                                int nthr, double *part)
 {
-    const int npix = L.npix, TS = T + 1;
-    float2 *wm = reinterpret_cast<float2 *>(tile + ((nc * TS + 1) & ~1));
-    float2 *wd = wm + nc * TS;          // = row nc of the pair operands
+    const int npix = L.npix;
+    const NcTileLayout lay(nc, T);
+    const int TS = lay.TS;
+    float2 *wm = reinterpret_cast<float2 *>(tile + lay.wm);
+    float4 *ww = reinterpret_cast<float4 *>(tile + lay.ww);
     int rr[2], cc[2], sx[4];
     nc_unit(nc, max(unit, 0), rr, cc, sx);
     float hi[4], lo[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) hi[g] = lo[g] = 0.0f;
-    for (int p0 = 0; p0 < npix; p0 += T) {
+    // copies of tile [p0, p0 + n) into buffer b: entry k = c n + i of the
+    // columns, c = k / n by a multiply-high (exact as k n < 2^32: nc <= 32
+    // columns of n <= 4096 pixels; nmul = ceil(2^32 / n) for n > 1, and
+    // n = 1 takes c = k), then the n weight records
+    auto issue = [&](int p0, int b) {
         const int n = min(T, npix - p0);
-        for (int i = tid; i < n; i += nthr) {
-            const float4 w = L.wpack[p0 + i];
-            wd[i] = make_float2(w.z, w.w);
-        }
-        // every thread stages (column, pixel) entries k = c n + i
+        const unsigned nmul = 0xffffffffu / (unsigned)n + 1u;
+        float *Rb = tile + b * lay.r1;
         for (int k = tid; k < nc * n; k += nthr) {
-            const int c = k / n, i = k - c * n;
-            const float2 w = *reinterpret_cast<const float2 *>(&L.wpack[p0 + i]);
-            const float m = M[(size_t)c * npix + p0 + i];
+            const int c = n > 1 ? (int)__umulhi((unsigned)k, nmul) : k, i = k - c * n;
+            cp_async4(Rb + c * TS + i, M + (size_t)c * npix + p0 + i);
+        }
+        for (int i = tid; i < n; i += nthr) cp_async16(ww + b * T + i, L.wpack + p0 + i);
+        cp_async_commit();
+    };
+    if (npix > 0) issue(0, 0);
+    int b = 0;
+    for (int p0 = 0; p0 < npix; p0 += T, b ^= 1) {
+        const int n = min(T, npix - p0);
+        cp_async_wait_all();
+        __syncthreads();
+        if (p0 + T < npix) issue(p0 + T, b ^ 1);
+        const float *Rc = tile + b * lay.r1;
+        const float4 *wc = ww + b * T;
+        const unsigned nmul = 0xffffffffu / (unsigned)n + 1u;
+        for (int k = tid; k < nc * n; k += nthr) {
+            const int c = n > 1 ? (int)__umulhi((unsigned)k, nmul) : k, i = k - c * n;
+            const float m = Rc[c * TS + i];
+            const float4 w = wc[i];
             const float p1 = w.x * m;
             float e1 = fmaf(w.x, m, -p1);
             e1 = fmaf(w.y, m, e1);
-            tile[c * TS + i] = m;
             wm[c * TS + i] = make_float2(p1, e1);
+        }
+        for (int i = tid; i < n; i += nthr) {
+            const float4 w = wc[i];
+            wm[nc * TS + i] = make_float2(w.z, w.w);
         }
         __syncthreads();
         if (unit >= 0) {
             const float2 *q0 = wm + rr[0] * TS + r, *q1 = wm + rr[1] * TS + r;
-            const float *f0 = tile + cc[0] * TS + r, *f1 = tile + cc[1] * TS + r;
+            const float *f0 = Rc + cc[0] * TS + r, *f1 = Rc + cc[1] * TS + r;
 #pragma unroll 2
             for (int i = r; i < n; i += R, q0 += R, q1 += R, f0 += R, f1 += R) {
-                const float2 a = *q0, b = *q1;
+                const float2 a = *q0, bq = *q1;
                 const float x = *f0, y = *f1;
                 float p, er;
                 p = a.x * x; er = fmaf(a.x, x, -p); er = fmaf(a.y, x, er); df_acc(hi[0], lo[0], p, er);
                 p = a.x * y; er = fmaf(a.x, y, -p); er = fmaf(a.y, y, er); df_acc(hi[1], lo[1], p, er);
-                p = b.x * x; er = fmaf(b.x, x, -p); er = fmaf(b.y, x, er); df_acc(hi[2], lo[2], p, er);
-                p = b.x * y; er = fmaf(b.x, y, -p); er = fmaf(b.y, y, er); df_acc(hi[3], lo[3], p, er);
+                p = bq.x * x; er = fmaf(bq.x, x, -p); er = fmaf(bq.y, x, er); df_acc(hi[2], lo[2], p, er);
+                p = bq.x * y; er = fmaf(bq.x, y, -p); er = fmaf(bq.y, y, er); df_acc(hi[3], lo[3], p, er);
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
 #pragma unroll
     for (int g = 0; g < 4; ++g) part[g] = (double)hi[g] + (double)lo[g];
 }
@@ -655,13 +696,7 @@ __device__ __forceinline__ void nc_vector(const LensDev &L, const MultiDev &M, c
                     for (int b0 = 0; b0 < ny; b0 += step) {
                         const int nrows = min(step, ny - b0);
                         const int nbr = nrows + 2 * h;
-                        for (int t = tid; t < 2 * nbr * nx; t += nwk) {
-                            const int ch = t / (nbr * nx), rem = t - ch * nbr * nx;
-                            const int br = rem / nx, j = rem - br * nx;
-                            const int ir = b0 - h + br;
-                            const float val = (ir >= 0 && ir < ny) ? (ch ? Is : Il)[ir * nx + j] : 0.0f;
-                            (ch ? Ps : Pl)[br * W + HL + j] = val;
-                        }
+                        stage_band(L, Il, Is, Pl, (int)(Ps - Pl), b0, nbr, tid, nwk);
                         phase_sync<1>(nwk);
                         if (L.sep)
                             conv_sep_band<K, PairStore<ROWS>, 1>(L, Pl, Ps, b0, nrows,

@@ -48,6 +48,7 @@ CASES = [
     ("many20_generic", 34, 30, 0.08, 2, 33, "moffat", MANY, "sie"),
     ("tiny_1x1", 1, 1, 0.1, 1, 1, "gaussian", W.SLACS_COMPS, "sie"),
     ("tiny_3x2", 3, 2, 0.2, 4, 5, "moffat", MIXED, "sie"),
+    ("column_7x1", 7, 1, 0.1, 3, 5, "gaussian", MIXED, "sie"),
 ]
 
 

@@ -287,6 +287,7 @@ SHAPES = [
     (37, 53, 0.06, 3, ("gauss", 7), 0, True),
     (29, 41, 0.07, 2, ("moffat", 9), 1, False),
     (1, 1, 0.1, 1, ("gauss", 1), 0, False),
+    (7, 1, 0.1, 3, ("gauss", 5), 0, False),          # one column: row = pixel index
     (3, 2, 0.2, 4, ("gauss", 5), 0, False),
     (6, 300, 0.03, 1, ("gauss", 5), 0, False),       # nx > 256: global path
     (180, 170, 0.05, 1, ("moffat", 11), 0, False),   # > shared memory
