@@ -442,9 +442,9 @@ int ensure_kc(tll_lens *L, int B)
 }
 
 // Shared memory kept free for the kernels' static part (the multi-lens
-// kernel's copy of a lens descriptor, the EPL series), so every lens also
-// fits that kernel.
-constexpr int kSmemReserve = 8192;
+// kernel's copy of a lens descriptor, the EPL series' table), so every lens
+// also fits that kernel.
+constexpr int kSmemReserve = 12288;
 
 // Let kernel k use all the dynamic shared memory the opt-in limit leaves
 // beside its static part.

@@ -16,6 +16,17 @@ namespace tll {
 constexpr int NPAR = 21;
 constexpr int NPAR_EPL = 22;     // elliptical power-law mass: slope gamma at [21]
 constexpr int kEplMaxN = 63;     // highest power of the EPL deflection series
+// The EPL series as a per-vector table over cos(2 vphi) in [-1, 1]:
+// kEplTab cubic Hermite intervals of width 2 / kEplTab, one more at each
+// end (kEplTab + 2 in all), two float4 per interval; used where the
+// series' ratio (1 - q)/(1 + q) is at most kEplTabR (q >= 0.48), where the
+// interpolation is below 2e-8 of the sum for slopes 1.2 .. 2.8.
+constexpr int kEplTab = 128;
+constexpr float kEplTabR = 0.35f;
+// shared memory of the EPL staging per vector: the table, or the series'
+// coefficients c_0 .. c_63 where the table is not used
+constexpr int kEplSmemFloats = 8 * (kEplTab + 2);
+static_assert(kEplSmemFloats >= kEplMaxN + 1, "EPL staging");
 
 // Per-vector constants written by the prologue, NCONST floats per vector.
 // Every coordinate a subpixel needs is an affine function of its integer
@@ -42,8 +53,8 @@ enum : int {
     K_IEL, K_IES,
     // elliptical power law (Eq. 12 at any slope): flag, highest power N of
     // the deflection series, the magnitude's exponent e0 + e1 log2(psi^2)
-    // (hi, lo each)
-    K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L,
+    // (hi, lo each), and whether the kernels take the series from a table
+    K_EPL, K_EN, K_E0H, K_E0L, K_E1H, K_E1L, K_ETAB,
     // the lo parts (float4-aligned), then the EPL series coefficients c_0 .. c_N
     K_LO = (K_E1L + 4) & ~3,
     K_EC0 = K_LO + 28,
@@ -60,6 +71,7 @@ enum : int {
 };
 constexpr int NCONST = 336;
 static_assert(NCONST_USED <= NCONST, "constant block too small");
+static_assert(K_ETAB < K_LO, "constant slots");
 static_assert(K_LO % 4 == 0 && LO_N % 4 == 0 && NCONST % 4 == 0 && K_EC0 == K_LO + LO_N,
               "float4 reads of the lo block");
 
@@ -348,6 +360,7 @@ __device__ inline void decode_vector(const float *__restrict__ p, float *__restr
                     if (fabs(cn) < 1e-9) break;   // the rest of the series is below float rounding
                 }
                 o[K_EN] = (float)N;
+                o[K_ETAB] = -fr <= (double)kEplTabR ? 1.0f : 0.0f;
                 c1 = c2 = 1.0;
                 Am = 2.0 * A / (1.0 + qm);
             }
@@ -371,6 +384,7 @@ struct VecConst {
     float khl, bhl, khs, bhs;
     float q11h, q12h, q21h, q22h;
     bool epl;                       // elliptical power-law mass
+    bool etab;                      // its series from the table
     int en;                         // highest power of its series
     float e0h, e0l, e1h, e1l;       // its magnitude's exponent
 };
@@ -392,6 +406,7 @@ __device__ __forceinline__ VecConst load_consts(const float *kc)
     v.khl = kc[K_KHL]; v.bhl = kc[K_BHL]; v.khs = kc[K_KHS]; v.bhs = kc[K_BHS];
     v.q11h = kc[K_Q11H]; v.q12h = kc[K_Q12H]; v.q21h = kc[K_Q21H]; v.q22h = kc[K_Q22H];
     v.epl = kc[K_EPL] != 0.0f;
+    v.etab = kc[K_ETAB] != 0.0f;
     v.en = (int)kc[K_EN];
     v.e0h = kc[K_E0H]; v.e0l = kc[K_E0L]; v.e1h = kc[K_E1H]; v.e1l = kc[K_E1L];
     return v;
@@ -605,7 +620,13 @@ __device__ __forceinline__ void sie_unit(const VecConst &v, float ql, float fl, 
 // ec: the coefficients c_0 .. c_63 staged in shared memory per vector,
 // 16-byte aligned and zero beyond N, read four at a time.  ql: the lo part
 // of q (read when FIRST).
-template <bool FIRST>
+// TAB: the two sums F1 = b_0 - b_1 and F2 = b_0 + b_1, functions of
+// x = cos th alone, from the vector's table at ec (epl_table): interval k
+// covers x in [-1 + (k - 1) h, -1 + k h], h = 2 / kEplTab; its position
+// U = (x + 1)/h + 1 is split as k = floor(U) by rounding U - 1/2 against
+// 1.5 * 2^23 (the integer in the sum's low mantissa bits) and t = U - k,
+// then one cubic per sum, ((a3 t + a2) t + a1) t + a0.
+template <bool FIRST, bool TAB = false>
 __device__ __forceinline__ void epl_unit(const VecConst &v, float ql, float xp, float yp,
                                          const float *ec, PixelLo &P, float &ux, float &uy)
 {
@@ -616,21 +637,85 @@ __device__ __forceinline__ void epl_unit(const VecConst &v, float ql, float xp, 
     const float c = qx * rpsi, s = yp * rpsi;            // e^{i vphi}
     const float al = 2.0f * fmaf(c, c, -s * s);          // 2 cos th
     const float4 *ec4 = reinterpret_cast<const float4 *>(ec);
-    float b1 = 0.0f, b2 = 0.0f;
+    float F1, F2;
+    if constexpr (TAB) {
+        constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23
+        const float um = fmaf(al, 0.25f * kEplTab, 0.5f * kEplTab + 0.5f);   // U - 1/2
+        const float sm = __fadd_rn(um, kMagic);
+        const float fk = __fsub_rn(sm, kMagic);
+        const float t = __fadd_rn(__fsub_rn(um, fk), 0.5f);
+        const int k = min(max(__float_as_int(sm) - 0x4B400000, 0), kEplTab + 1);
+        const float4 A = ec4[2 * k], B = ec4[2 * k + 1];
+        F1 = fmaf(fmaf(fmaf(A.w, t, A.z), t, A.y), t, A.x);
+        F2 = fmaf(fmaf(fmaf(B.w, t, B.z), t, B.y), t, B.x);
+    } else {
+        float b1 = 0.0f, b2 = 0.0f;
 #pragma unroll 1
-    for (int g = v.en >> 2; g >= 0; --g) {
-        const float4 cc = ec4[g];
-        float b0;
-        b0 = fmaf(al, b1, cc.w - b2); b2 = b1; b1 = b0;
-        b0 = fmaf(al, b1, cc.z - b2); b2 = b1; b1 = b0;
-        b0 = fmaf(al, b1, cc.y - b2); b2 = b1; b1 = b0;
-        b0 = fmaf(al, b1, cc.x - b2); b2 = b1; b1 = b0;
+        for (int g = v.en >> 2; g >= 0; --g) {
+            const float4 cc = ec4[g];
+            float b0;
+            b0 = fmaf(al, b1, cc.w - b2); b2 = b1; b1 = b0;
+            b0 = fmaf(al, b1, cc.z - b2); b2 = b1; b1 = b0;
+            b0 = fmaf(al, b1, cc.y - b2); b2 = b1; b1 = b0;
+            b0 = fmaf(al, b1, cc.x - b2); b2 = b1; b1 = b0;
+        }
+        F1 = b1 - b2;
+        F2 = b1 + b2;
     }
     const float L = sfu_lg2(a);
     if (FIRST) P.dfx = fmaf(v.e1l, L, v.e0l);   // de
     const float m = exp2_rr<false>(fmaf(v.e1h, L, P.dfx) + v.e0h);
-    ux = (m * c) * (b1 - b2);
-    uy = (m * s) * (b1 + b2);
+    ux = (m * c) * F1;
+    uy = (m * s) * F2;
+}
+
+// One vector's EPL staging in shared memory (buf, kEplSmemFloats floats,
+// 16-byte aligned), before its trace: the table when v.etab, else the
+// series' coefficients.  Table interval k (threads take one each): the
+// sums F1, F2 and their x-derivatives at both ends by the Clenshaw
+// recurrence in alpha = 2x with its derivative
+//   b_k' = b_{k+1} + alpha b_{k+1}' - b_{k+2}',
+// then the cubic Hermite coefficients on t in [0, 1]:
+//   a0 = F(x0), a1 = h F'(x0), a2 = 3 (F(x1) - F(x0)) - h (2 F'(x0) + F'(x1)),
+//   a3 = 2 (F(x0) - F(x1)) + h (F'(x0) + F'(x1)).
+// No barrier.
+__device__ __forceinline__ void epl_sums_d(const float *c, int en, float x, float &F1, float &F2,
+                                           float &D1, float &D2)
+{
+    const float al = 2.0f * x;
+    float b1 = 0.0f, b2 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+    for (int n = en; n >= 0; --n) {
+        const float b0 = fmaf(al, b1, c[n] - b2);
+        const float d0 = fmaf(al, d1, b1 - d2);
+        b2 = b1; b1 = b0;
+        d2 = d1; d1 = d0;
+    }
+    F1 = b1 - b2;
+    F2 = b1 + b2;
+    D1 = 2.0f * (d1 - d2);       // d/dx = 2 d/dalpha
+    D2 = 2.0f * (d1 + d2);
+}
+
+__device__ __forceinline__ void epl_stage(const float *kc, const VecConst &v, float *buf, int tid,
+                                          int nthr)
+{
+    if (!v.etab) {
+        for (int t = tid; t <= kEplMaxN; t += nthr) buf[t] = kc[K_EC0 + t];
+        return;
+    }
+    const float *c = kc + K_EC0;
+    const float h = 2.0f / kEplTab;
+    float4 *tab = reinterpret_cast<float4 *>(buf);
+    for (int k = tid; k < kEplTab + 2; k += nthr) {
+        const float x0 = fmaf((float)(k - 1), h, -1.0f), x1 = x0 + h;
+        float F1a, F2a, D1a, D2a, F1b, F2b, D1b, D2b;
+        epl_sums_d(c, v.en, x0, F1a, F2a, D1a, D2a);
+        epl_sums_d(c, v.en, x1, F1b, F2b, D1b, D2b);
+        tab[2 * k] = make_float4(F1a, h * D1a, 3.0f * (F1b - F1a) - h * (2.0f * D1a + D1b),
+                                 2.0f * (F1a - F1b) + h * (D1a + D1b));
+        tab[2 * k + 1] = make_float4(F2a, h * D2a, 3.0f * (F2b - F2a) - h * (2.0f * D2a + D2b),
+                                     2.0f * (F2a - F2b) + h * (D2a + D2b));
+    }
 }
 
 // The two unit columns at one subpixel (fj, fi), given the row terms
@@ -683,14 +768,16 @@ __device__ __forceinline__ RowTerms row_terms(const VecConst &v, const PixOrigin
 
 // The mass deflection (the lens equation's alpha, Eq. 1) in its frame at
 // subpixel column fj of row r.  MODE: 0 SIE fast form, 1 SIE general form,
-// 2 EPL (series ec), 4 SIE mid form.  ql, fl: lo parts of q and f (FIRST).
+// 2 EPL (series ec), 4 SIE mid form, 5 EPL from the table at ec.  ql, fl:
+// lo parts of q and f (FIRST).
 template <int MODE, bool FIRST>
 __device__ __forceinline__ void deflect(const VecConst &v, float ql, float fl, const RowTerms &r,
                                         float fj, const float *ec, PixelLo &P, float &ux,
                                         float &uy)
 {
-    if constexpr (MODE == 2)
-        epl_unit<FIRST>(v, ql, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec, P, ux, uy);
+    if constexpr (MODE == 2 || MODE == 5)
+        epl_unit<FIRST, MODE == 5>(v, ql, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), ec,
+                                   P, ux, uy);
     else
         sie_unit<MODE == 0 ? 0 : MODE == 4 ? 2 : 1, FIRST>(
             v, ql, fl, fmaf(v.px.cj, fj, r.px), fmaf(v.py.cj, fj, r.py), P, ux, uy);

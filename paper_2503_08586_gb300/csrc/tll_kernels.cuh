@@ -115,7 +115,7 @@ __device__ __forceinline__ void finish_pending(PendingFinish &pf, const double *
 // offsets (fj, fi) = (J - JCX, I - JCY) from the grid centre; every
 // coordinate is an affine function of them (see decode_vector).
 // MODE: 0 SIE fast form, 1 SIE general form, 2 EPL (series coefficients ec),
-// 4 SIE mid form.
+// 4 SIE mid form, 5 EPL (the series' table at ec).
 // skip: trace only the lens's listed pixels (L.tlist), those within the PSF's
 // reach of an unmasked pixel; the others keep whatever finite value they
 // hold, which only ever meets a zero weight.
@@ -657,8 +657,9 @@ __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, con
 // with the fused sums, reduce, finish; log L goes to *outp.  Ends with a
 // block barrier.
 // Trace one vector with the deflection form it needs (the branch is uniform
-// over the CTA); an EPL vector's series coefficients are first staged in
-// sepl (kEplMaxN + 1 floats of shared memory).  Ends with a block barrier.
+// over the CTA); an EPL vector's series table (or its coefficients) is
+// first staged in sepl (kEplSmemFloats floats of shared memory,
+// epl_stage).  Ends with a block barrier.
 template <int SUB>
 __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, float *Il,
                                              float *Is, int stride, int off, float *sepl,
@@ -668,9 +669,12 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
 {
     const VecConst v = load_consts(kc);
     if (v.epl) {
-        for (int t = tid; t <= kEplMaxN; t += nthr) sepl[t] = kc[K_EC0 + t];
+        epl_stage(kc, v, sepl, tid, nthr);
         __syncthreads();
-        trace_image<SUB, 2>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
+        if (v.etab)
+            trace_image<SUB, 5>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
+        else
+            trace_image<SUB, 2>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.fast) {
         trace_image<SUB, 0>(L, v, kc, Il, Is, stride, off, tid, nthr, sepl, skip);
     } else if (v.mid) {
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(kThreads)
 k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(16) float sepl[kEplMaxN + 1];
+    __shared__ __align__(16) float sepl[kEplSmemFloats];
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *sred = reinterpret_cast<double *>(smem);
@@ -803,7 +807,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LensDev sL;
     __shared__ int s_t, s_seg;
-    __shared__ __align__(16) float sepl[kEplMaxN + 1];
+    __shared__ __align__(16) float sepl[kEplSmemFloats];
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) spf.valid = 0;

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kThreads)
 k_trace_split(const __grid_constant__ LensDev L, const float *__restrict__ kc, int nvec,
               float *__restrict__ unbl)
 {
-    __shared__ __align__(16) float sepl[kEplMaxN + 1];
+    __shared__ __align__(16) float sepl[kEplSmemFloats];
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int b = blockIdx.x; b < nvec; b += gridDim.x) {
         const float *k = kc + (size_t)b * NCONST;
