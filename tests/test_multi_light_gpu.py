@@ -144,6 +144,35 @@ def test_multi_model_image_and_amplitudes(cases):
         g.close()
 
 
+def test_multi_sie_form_boundaries(cases):
+    """The multi-column kernel's SIE closed forms (fast for q >= sqrt(3)/2,
+    mid for 1/sqrt(2) <= q < sqrt(3)/2, general below) on both sides of each
+    switch, at two position angles: blurred columns within the pixel gate
+    and log L within the gates."""
+    sl, P, o, ref = cases[1]
+    comps = CASES[1][7]
+    g = _gpu(sl, comps)
+    vecs = []
+    for q in (0.99, 0.8662, 0.8659, 0.7072, 0.7070, 0.55):
+        for phi in (0.3, 1.9):
+            p = np.array(P[0], np.float64)
+            e = (1.0 - q) / (1.0 + q)
+            p[1], p[2] = e * np.cos(2 * phi), e * np.sin(2 * phi)
+            vecs.append(p.astype(np.float32))
+    Q = np.stack(vecs)
+    for p in Q:
+        gc = g.model_columns_n(p, blurred=True)
+        oc = o.model(p.astype(np.float64))[1]
+        al = _allowance(o, p, True)
+        for c in range(len(comps)):
+            ok, worst = _pix_ok(gc[c], oc[c], al[c])
+            assert ok, f"column {c}: worst/tol {worst:.3f}"
+    got = g.loglike_batch(torch.from_numpy(Q).cuda())
+    torch.cuda.synchronize()
+    _ll_ok(got.cpu().numpy(), o.loglike_batch(Q.astype(np.float64)), sl)
+    g.close()
+
+
 def test_multi_invalid_vectors(cases):
     sl, P, o, ref = cases[2]      # MIXED: slots 15 r_e, 16 n, 17 sigma, 18 r_e, 19 r_e, 20 n, 21 sigma
     Q = np.repeat(P[:1], 9, axis=0)

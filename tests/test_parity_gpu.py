@@ -217,13 +217,13 @@ def test_columns_parity_plain64():
 
 def test_sie_form_boundaries():
     """The SIE's three forms (fast for q >= sqrt(3)/2, mid for 1/sqrt(2) <= q
-    < sqrt(3)/2, general below) on both sides of each switch and at two
-    position angles: unblurred columns within the pixel gate and log L
-    within the gates."""
+    < sqrt(3)/2, general below, down to q = 0.3) on both sides of each
+    switch and at two position angles: unblurred columns within the pixel
+    gate and log L within the gates."""
     lens, _ = _workload("plain64", batch=8)
     g, o = _pair(lens)
     vecs = []
-    for q in (0.99, 0.8662, 0.8659, 0.7072, 0.7070, 0.55):
+    for q in (0.99, 0.8662, 0.8659, 0.7072, 0.7070, 0.55, 0.3):
         for phi in (0.3, 1.9):
             p = np.array(lens.truth, np.float64)
             e = (1.0 - q) / (1.0 + q)
