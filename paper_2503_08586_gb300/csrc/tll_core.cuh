@@ -12,7 +12,7 @@ namespace tll {
 
 constexpr int kThreads = 1024;     // CTA size of k_loglike (64 registers, 32 warps per SM)
 constexpr int kHMax = 8;           // in-place row pass holds nx <= 32*kHMax
-constexpr int kRedBytes = 32 * 5 * 8;
+constexpr int kRedBytes = 32 * 5 * 8;   // the warps' five partial sums, a float pair each
 
 constexpr int kMaxTaps = 32;   // separable PSF factors carried in the parameter block
 constexpr int kMaxK = 31;      // largest PSF side of the compiled convolutions

@@ -840,6 +840,20 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, float p, float e)
     lo += err + e;
 }
 
+// a += b in double-float with the result symmetric in a and b bit for bit
+// (TwoSum's error term is exact either way and the lo parts are added first),
+// so both lanes of a butterfly step end with the same pair.
+__device__ __forceinline__ void df_add_sym(float &ahi, float &alo, float bhi, float blo)
+{
+    const float s = ahi + bhi;
+    const float bp = s - ahi;
+    const float err = (ahi - (s - bp)) + (bhi - bp);
+    const float lo = err + (alo + blo);
+    const float hi = s + lo;
+    alo = lo - (hi - s);
+    ahi = hi;
+}
+
 __device__ __forceinline__ void df_add(float &ahi, float &alo, float bhi, float blo)
 {
     const float s = ahi + bhi;

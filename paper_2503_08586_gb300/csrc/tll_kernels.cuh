@@ -65,18 +65,32 @@ __device__ __forceinline__ void finish_vector(const LensDev &L, const double *S,
     finish_core(L.mode, L.dWd, L.lognorm, S, IeL, IeS, sl_o, ss_o, ll_o);
 }
 
-// The five sums of a vector from the warps' FP64 partials sred[w*5 + k]
-// (w < nwarp): one warp adds them as a butterfly over its lanes (every lane
-// ends with the same bits); called by all 32 lanes of that warp.
-__device__ __forceinline__ void block_sums(const double *sred, int nwarp, int lane, double *S)
+// The five sums of a vector from the warps' double-float partials
+// sred[w*5 + k] (w < nwarp): one warp adds them as a double-float butterfly
+// over its lanes (every lane ends with the same bits) and converts each sum
+// to FP64 once; called by all 32 lanes of that warp.  (FP64 runs at a small
+// fraction of the FP32 rate here, so the partials stay float pairs until
+// the end.)
+__device__ __forceinline__ void block_sums(const float2 *sred, int nwarp, int lane, double *S)
 {
+    float a[10];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) S[k] = lane < nwarp ? sred[lane * 5 + k] : 0.0;
+    for (int k = 0; k < 5; ++k) {
+        const float2 v = lane < nwarp ? sred[lane * 5 + k] : make_float2(0.0f, 0.0f);
+        a[2 * k] = v.x;
+        a[2 * k + 1] = v.y;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o);
+        for (int k = 0; k < 5; ++k) {
+            const float oh = __shfl_xor_sync(0xffffffffu, a[2 * k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, a[2 * k + 1], o);
+            df_add_sym(a[2 * k], a[2 * k + 1], oh, ol);
+        }
     }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) S[k] = (double)a[2 * k] + (double)a[2 * k + 1];
 }
 
 // The amplitude solve and log L of a vector whose five sums wait in sred
@@ -93,7 +107,7 @@ struct PendingFinish {
     int mode, valid;
 };
 
-__device__ __forceinline__ void finish_pending(PendingFinish &pf, const double *sred,
+__device__ __forceinline__ void finish_pending(PendingFinish &pf, const float2 *sred,
                                                int lane, int nwarp)
 {
     if (!pf.valid) return;
@@ -583,8 +597,9 @@ __device__ __forceinline__ void setup_lens(const LensDev &L, float *spsf, int ti
 }
 
 // Warp reduction of a thread's five double-float sums; lane 0 stores the
-// warp's sums in FP64 to sred[warp*5 + k] (add: adds to what is there).
-__device__ __forceinline__ void warp_sums(float *acc, double *sred, int lane, int warp, bool add)
+// warp's sums as float pairs to sred[warp*5 + k] (add: adds to what is
+// there, in double-float).
+__device__ __forceinline__ void warp_sums(float *acc, float2 *sred, int lane, int warp, bool add)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -598,21 +613,25 @@ __device__ __forceinline__ void warp_sums(float *acc, double *sred, int lane, in
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const double v = (double)acc[2 * k] + (double)acc[2 * k + 1];
-            sred[warp * 5 + k] = add ? sred[warp * 5 + k] + v : v;
+            float h = acc[2 * k], l = acc[2 * k + 1];
+            if (add) {
+                const float2 o = sred[warp * 5 + k];
+                df_add(h, l, o.x, o.y);
+            }
+            sred[warp * 5 + k] = make_float2(h, l);
         }
     }
 }
 
 // Convolve the two images with the fused sums; each warp's sums end in
-// sred[warp*5 + k] (FP64).  K > 0: the compiled convolution of side K on
+// sred[warp*5 + k] (float pairs).  K > 0: the compiled convolution of side K on
 // zero-padded bands (IMG_PADDED: the whole image is one band already in
 // place; IMG_BANDED: bands filled from the global slot), each band's sums
 // reduced over the warp as it ends, so that no accumulator stays live
 // across bands; K == 0: the generic convolution (IMG_SMEM, IMG_GLOBAL).
 template <int K, bool WRITE>
 __device__ __forceinline__ void convolve(const LensDev &L, const RunArgs &R, const ImgPtrs &P,
-                                         float *spsf, double *sred, int tid, int nthr)
+                                         float *spsf, float2 *sred, int tid, int nthr)
 {
     const int lane = tid & 31, warp = tid >> 5;
     if constexpr (K > 0) {
@@ -665,7 +684,7 @@ __device__ __forceinline__ void trace_vector(const LensDev &L, const float *kc, 
                                              float *Is, int stride, int off, float *sepl,
                                              int tid, int nthr, bool skip,
                                              PendingFinish *pf = nullptr,
-                                             const double *sred = nullptr)
+                                             const float2 *sred = nullptr)
 {
     const VecConst v = load_consts(kc);
     if (v.epl) {
@@ -704,7 +723,7 @@ __device__ __forceinline__ void zero_untraced(const LensDev &L, const ImgPtrs &P
 template <int SUB, int K, bool WRITE>
 __device__ __forceinline__ void vector_body(const LensDev &L, const RunArgs &R,
                                             const float *kc, double *outp, const ImgPtrs &P,
-                                            float *spsf, double *sred, float *sepl,
+                                            float *spsf, float2 *sred, float *sepl,
                                             PendingFinish &pf, int tid, int nthr)
 {
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -764,7 +783,7 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
     __shared__ __align__(16) float sepl[kEplSmemFloats];
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    double *sred = reinterpret_cast<double *>(smem);
+    float2 *sred = reinterpret_cast<float2 *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
     if (tid == 0) spf.valid = 0;
     const bool gslot = L.img == IMG_GLOBAL || L.img == IMG_BANDED;
@@ -811,7 +830,7 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     __shared__ PendingFinish spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) spf.valid = 0;
-    double *sred = reinterpret_cast<double *>(smem);
+    float2 *sred = reinterpret_cast<float2 *>(smem);
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
     float *gslot = A.gscr ? A.gscr + (size_t)blockIdx.x * A.gslot_floats : nullptr;
     const MultiHdr hd = A.groups[group];

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads)
 k_sums_split(const __grid_constant__ LensDev L, const float *__restrict__ kc,
              const float *__restrict__ blur, int nvec, double *__restrict__ out)
 {
-    __shared__ double sred[32 * 5];
+    __shared__ float2 sred[32 * 5];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     for (int b = blockIdx.x; b < nvec; b += gridDim.x) {
@@ -134,12 +134,8 @@ k_sums_split(const __grid_constant__ LensDev L, const float *__restrict__ kc,
         warp_sums(acc, sred, lane, warp, false);
         __syncthreads();
         if (warp == 0) {
-            double sacc = 0.0;
-            if (lane < 5)
-                for (int w = 0; w < nwarp; ++w) sacc += sred[w * 5 + lane];
             double S[5];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) S[q] = __shfl_sync(0xffffffffu, sacc, q);
+            block_sums(sred, nwarp, lane, S);
             if (lane == 0) {
                 double sl, ss, ll;
                 finish_vector(L, S, k[K_IEL], k[K_IES], &sl, &ss, &ll);
