@@ -418,7 +418,8 @@ def stream_lenses(n_jobs: int, workload: str, seed_offset: int = 20):
 
 
 def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload: str,
-               seed_offset: int = 20, lenses=None):
+               seed_offset: int = 20, lenses=None, max_vectors: int = 16384,
+               inflight: int = 2):
     """A Poisson stream of lens-modelling jobs through the server, each a
     closed-loop synthetic sampler: `iters` batches of U{500..5000} vectors
     drawn from a Gaussian shrinking around its lens's truth, each submitted
@@ -426,7 +427,9 @@ def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload
     the served path (requests of all jobs merged per launch, 2 launches in
     flight, graph replay); False is the plain path (one request per launch,
     one at a time).  lenses: the jobs' lenses (stream_lenses), made here
-    when not given.  Returns throughput and request latencies."""
+    when not given; max_vectors, inflight: the served path's cap on vectors
+    per launch and launches in flight.  Returns throughput and request
+    latencies."""
     import threading
     from paper_2503_08586_gb300 import tll
     from paper_2503_08586_gb300 import workloads as W
@@ -438,8 +441,8 @@ def run_stream(coalesce: bool, n_jobs: int, iters: int, rate_hz: float, workload
     n_jobs = len(lenses)
     arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
     seeds = rng.integers(0, 2 ** 31, n_jobs)
-    S = tll.Server(max_jobs=max(64, n_jobs), max_vectors_per_launch=16384,
-                   max_inflight=2 if coalesce else 1, coalesce=coalesce,
+    S = tll.Server(max_jobs=max(64, n_jobs), max_vectors_per_launch=max_vectors,
+                   max_inflight=inflight if coalesce else 1, coalesce=coalesce,
                    use_graph=coalesce)
     lat, vecs, errors, admit = [], [0], [], []
     lock = threading.Lock()
