@@ -391,7 +391,7 @@ int run_split(tll_lens *L, const float *kc, int B, double *out, cudaStream_t st)
 }
 
 int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t st,
-              bool write, float *kc)
+              bool write, float *kc, const StretchStep *ss = nullptr)
 {
     const bool prof = L->prof_on && !write;
     if (prof) CUDA_TRY(cudaEventRecord(L->prof_ev[0], st));
@@ -402,6 +402,7 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     // likelihood kernel itself: one launch instead of two, which is most of
     // the gain for small batches (a sampler's few hundred walkers)
     const bool fused = !write && B <= L->shape.grid_cap && L->conv_variant == TLL_CONV_FUSED;
+    if (ss && !fused) return fail(TLL_EINVAL, "a fused sampler step needs a batch within the grid");
     if (!fused) {
         k_prologue<<<(B + kPrologueVectors - 1) / kPrologueVectors, dim3(kPrologueVectors, 4),
                      0, st>>>(params, B, kc, xc, yc, d, L->bn_tab, L->epl);
@@ -417,6 +418,10 @@ int run_batch(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     R.params = params;
     R.XC = xc; R.YC = yc; R.d = d;
     R.bn_tab = L->bn_tab;
+    if (ss) {
+        R.smp = *ss;
+        R.smp_on = 1;
+    }
     const int grid = std::min(B, L->shape.grid_cap);
     if (write) return launch_main(L, R, 1, true, st);
     const int rc = L->conv_variant == TLL_CONV_FUSED ? launch_main(L, R, grid, false, st)
@@ -803,6 +808,18 @@ int lens_eval(tll_lens *L, const float *params, int B, double *out, cudaStream_t
     if (B <= 0) return TLL_OK;
     return L->nc ? run_batch_nc(L, params, B, out, st, kc, nullptr)
                  : run_batch(L, params, B, out, st, false, kc);
+}
+
+bool lens_eval_fuses(const tll_lens *L, int B)
+{
+    return !L->nc && B > 0 && B <= L->shape.grid_cap && L->conv_variant == TLL_CONV_FUSED;
+}
+
+int lens_eval_stretch(tll_lens *L, float *params, int B, double *out, cudaStream_t st,
+                      float *kc, const StretchStep &ss)
+{
+    if (!lens_eval_fuses(L, B)) return fail(TLL_EINVAL, "no fused sampler step for this batch");
+    return run_batch(L, params, B, out, st, false, kc, &ss);
 }
 
 int lens_nparam(const tll_lens *L) { return L->nparam; }

@@ -7,6 +7,7 @@
 
 #include "tll.h"
 #include "tll_device.cuh"
+#include "tll_stretch.cuh"
 
 namespace tll {
 
@@ -124,6 +125,11 @@ struct RunArgs {
     float *wr_blurred;   // WRITE: [2][npix]
     float *wr_blurred_s; // WRITE: the second column there instead, when not null
     double *wr_res;      // WRITE: [8] All Als Ass bl bs sl ss logL
+    // fused (only): a stretch-move half step around the likelihood -- each
+    // vector's walker proposed into its params row before the decode,
+    // accepted or rejected after its log L (smp_on)
+    StretchStep smp;
+    int smp_on;
 };
 
 // One term of the five weighted sums (Sec. 2.3: A = M^T W M, b = M^T W d)

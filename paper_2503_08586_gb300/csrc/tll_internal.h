@@ -16,6 +16,17 @@ namespace tll {
 int lens_eval(tll_lens *L, const float *params, int B, double *out, cudaStream_t st, float *kc);
 // Allocate what lens_eval needs besides kc (the one-lens image slots).
 int lens_prepare(tll_lens *L);
+struct StretchStep;   // tll_stretch.cuh
+// Whether lens_eval_stretch applies to B vectors: a two-column lens on the
+// fused convolution path whose batch fits the likelihood kernel's grid
+// (each CTA one vector, decoded by the kernel itself).
+bool lens_eval_fuses(const tll_lens *L, int B);
+// lens_eval with a stretch-move half step fused into the likelihood launch:
+// CTA b writes walker b's proposal into params row b (device [B][nparam]),
+// its log L into out[b], then takes its accept / reject (ss).  TLL_EINVAL
+// where lens_eval_fuses does not hold.
+int lens_eval_stretch(tll_lens *L, float *params, int B, double *out, cudaStream_t st,
+                      float *kc, const StretchStep &ss);
 int lens_nparam(const tll_lens *L);
 int lens_device(const tll_lens *L);
 // Set the calling thread's tll_last_error message; returns code.

@@ -795,6 +795,16 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
     for (int b = blockIdx.x; b < R.B; b += gridDim.x) {
         const float *kc = R.kc + (size_t)b * NCONST;
         if (!WRITE && R.fused) {
+            if (R.smp_on) {
+                // the walker's proposal into the vector's parameter row (warp
+                // 0, entries over the lanes), visible to the decode after
+                // the barrier
+                if (tid < 32)
+                    stretch_propose_entries(R.smp, b, tid, 32,
+                                            const_cast<float *>(R.params) + (size_t)b * R.np,
+                                            nullptr);
+                __syncthreads();
+            }
             // the vector's four decode parts on lane 0 of warps 0-3 (four
             // sub-partitions), visible to the CTA after the barrier
             if ((tid & 31) == 0 && tid < 128)
@@ -812,6 +822,14 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
         vector_body<SUB, K, WRITE>(L, R, kc, R.out + b, P, spsf, sred, sepl, spf, tid, nthr);
     }
     if (!WRITE && (tid >> 5) == (nthr >> 5) - 1) finish_pending(spf, sred, tid & 31, nthr >> 5);
+    if (!WRITE && R.smp_on) {
+        // the accept / reject of the vector's walker once its log L is in
+        // out (written by the last warp, or by thread 0 for an invalid one)
+        __syncthreads();
+        if (tid == 0)
+            for (int b = blockIdx.x; b < R.B; b += gridDim.x)
+                stretch_accept_one(R.smp, b, R.params + (size_t)b * R.np, R.out[b]);
+    }
 }
 
 // ----------------------------------------------------- multi-lens kernel

@@ -21,8 +21,12 @@
 //   accept   when log((r2 + 1/2) 2^-32) < (ndim - 1) log z + lp(Y) - lp(x_k),
 //            lp(Y) = log L(Y) inside the box prior [lo, hi] (coordinates with
 //            lo == hi are fixed), -inf outside.
-// Launches per half step: proposals, the likelihood's two, accept; plus two
-// copies per step into the caller's chain buffers.
+// (The per-walker steps are in tll_stretch.cuh.)  Launches per half step:
+// when the half fits the likelihood kernel's grid (each CTA one vector,
+// the kernel decoding its own vector), ONE -- the likelihood kernel makes
+// its walker's proposal before the decode and takes the accept / reject
+// after its log L; otherwise proposals, the likelihood's two, accept.  Plus
+// two copies per step into the caller's chain buffers.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -34,106 +38,26 @@
 
 #include "tll.h"
 #include "tll_internal.h"
+#include "tll_stretch.cuh"
 
 using namespace tll;
 
 namespace {
 
-// Philox4x32-10: ten rounds; in each, the 32 x 32 -> 64-bit products of
-// counter words 0 and 2 with the round multipliers are split into high and
-// low halves and mixed with words 1, 3 and the key; the key advances by the
-// Weyl constants between rounds.
-__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1)
+// Proposals of half s.h: one thread per walker of the half.
+__global__ void k_stretch_propose(const StretchStep s, float *__restrict__ Y)
 {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-    }
-}
-
-__device__ __forceinline__ void walker_draws(unsigned long long seed, long long step, int h,
-                                             int k, uint32_t r[4])
-{
-    r[0] = (uint32_t)k;
-    r[1] = (uint32_t)h;
-    r[2] = (uint32_t)((unsigned long long)step & 0xffffffffull);
-    r[3] = (uint32_t)((unsigned long long)step >> 32);
-    philox10(r, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
-}
-
-__device__ __forceinline__ double unit_open(uint32_t v)
-{
-    return __dmul_rn(__dadd_rn((double)v, 0.5), 2.3283064365386963e-10);
-}
-
-// Proposals of half h: one thread per walker of the half.
-__global__ void k_stretch_propose(const float *__restrict__ x, int W, int P, int h,
-                                  long long step, unsigned long long seed, double a,
-                                  float *__restrict__ Y, double *__restrict__ zo)
-{
-    const int half = W / 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= half) return;
-    const int k = h * half + t;
-    uint32_t r[4];
-    walker_draws(seed, step, h, k, r);
-    const int j = (1 - h) * half + (int)(((unsigned long long)r[0] * (unsigned long long)half) >> 32);
-    const double w = __dadd_rn(__dmul_rn(__dsub_rn(a, 1.0), unit_open(r[1])), 1.0);
-    const double z = __ddiv_rn(__dmul_rn(w, w), a);
-    const float *xk = x + (size_t)k * P, *xj = x + (size_t)j * P;
-    float *y = Y + (size_t)t * P;
-    for (int i = 0; i < P; ++i) {
-        const double dj = (double)xj[i];
-        y[i] = __double2float_rn(__dadd_rn(dj, __dmul_rn(z, __dsub_rn((double)xk[i], dj))));
-    }
-    zo[t] = z;
+    if (t < s.W / 2) stretch_propose_entries(s, t, 0, 1, Y + (size_t)t * s.P, nullptr);
 }
 
-// Box prior: -inf outside [lo, hi] on a free coordinate (lo < hi).
-__device__ __forceinline__ bool in_box(const float *v, const float *lo, const float *hi, int P)
+// Accept / reject half s.h: one thread per walker of the half.  lpY holds
+// the proposals' log L.
+__global__ void k_stretch_accept(const StretchStep s, const float *__restrict__ Y,
+                                 const double *__restrict__ lpY)
 {
-    bool ok = true;
-    for (int i = 0; i < P; ++i)
-        if (lo[i] < hi[i] && !(v[i] >= lo[i] && v[i] <= hi[i])) ok = false;
-    return ok;
-}
-
-// Accept / reject half h: one thread per walker of the half.  lpY holds the
-// proposals' log L; lp_prop (optional, [W]) receives each walker's
-// proposal's log posterior.
-__global__ void k_stretch_accept(float *__restrict__ x, double *__restrict__ lp, int W, int P,
-                                 int h, long long step, unsigned long long seed, int ndim,
-                                 const float *__restrict__ Y, const double *__restrict__ z,
-                                 const double *__restrict__ lpY, const float *__restrict__ lo,
-                                 const float *__restrict__ hi, double *__restrict__ lp_prop,
-                                 unsigned long long *__restrict__ nacc)
-{
-    const int half = W / 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= half) return;
-    const int k = h * half + t;
-    uint32_t r[4];
-    walker_draws(seed, step, h, k, r);
-    const float *y = Y + (size_t)t * P;
-    const double lpy = in_box(y, lo, hi, P) ? lpY[t] : -INFINITY;
-    const double lu = log(unit_open(r[2]));
-    const double rhs = __dsub_rn(__dadd_rn(__dmul_rn((double)(ndim - 1), log(z[t])), lpy), lp[k]);
-    if (lp_prop) lp_prop[k] = lpy;
-    if (lu < rhs) {
-        for (int i = 0; i < P; ++i) x[(size_t)k * P + i] = y[i];
-        lp[k] = lpy;
-        atomicAdd(nacc, 1ull);
-    }
+    if (t < s.W / 2) stretch_accept_one(s, t, Y + (size_t)t * s.P, lpY[t]);
 }
 
 // Initial walkers: log posterior = log L inside the box, -inf outside.
@@ -175,7 +99,7 @@ struct tll_sampler {
     long long step = 0, proposed = 0;
     bool ready = false;
     float *d_x = nullptr, *d_Y = nullptr, *d_lo = nullptr, *d_hi = nullptr, *d_kc = nullptr;
-    double *d_lp = nullptr, *d_lpY = nullptr, *d_z = nullptr;
+    double *d_lp = nullptr, *d_lpY = nullptr;
     unsigned long long *d_nacc = nullptr;
 };
 
@@ -183,8 +107,7 @@ namespace {
 void sampler_free(tll_sampler *S)
 {
     if (!S) return;
-    void *ptrs[] = {S->d_x, S->d_Y, S->d_lo, S->d_hi, S->d_kc, S->d_lp, S->d_lpY, S->d_z,
-                    S->d_nacc};
+    void *ptrs[] = {S->d_x, S->d_Y, S->d_lo, S->d_hi, S->d_kc, S->d_lp, S->d_lpY, S->d_nacc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete S;
@@ -233,7 +156,6 @@ int tll_sampler_create(tll_lens *L, int nwalkers, const float *lo, const float *
     alloc((void **)&S->d_kc, W * (size_t)const_block_floats() * sizeof(float));
     alloc((void **)&S->d_lp, W * sizeof(double));
     alloc((void **)&S->d_lpY, half * sizeof(double));
-    alloc((void **)&S->d_z, half * sizeof(double));
     alloc((void **)&S->d_nacc, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(S->d_lo, lo, P * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(S->d_hi, hi, P * sizeof(float), cudaMemcpyHostToDevice);
@@ -275,16 +197,32 @@ int tll_sampler_run(tll_sampler *S, int nsteps, float *chain, double *lp_chain,
     DevGuard g(S->dev);
     cudaStream_t st = (cudaStream_t)stream;
     const int half = S->W / 2, blocks = (half + 127) / 128;
+    const bool fused = lens_eval_fuses(S->L, half);
     for (int s = 0; s < nsteps; ++s) {
         for (int h = 0; h < 2; ++h) {
-            k_stretch_propose<<<blocks, 128, 0, st>>>(S->d_x, S->W, S->P, h, S->step, S->seed,
-                                                      S->a, S->d_Y, S->d_z);
+            StretchStep ss;
+            ss.x = S->d_x;
+            ss.lp = S->d_lp;
+            ss.lp_prop = lp_prop_chain ? lp_prop_chain + (size_t)s * S->W : nullptr;
+            ss.nacc = S->d_nacc;
+            ss.lo = S->d_lo;
+            ss.hi = S->d_hi;
+            ss.step = S->step;
+            ss.seed = S->seed;
+            ss.a = S->a;
+            ss.W = S->W;
+            ss.P = S->P;
+            ss.h = h;
+            ss.ndim = S->ndim;
+            if (fused) {
+                if (int rc = lens_eval_stretch(S->L, S->d_Y, half, S->d_lpY, st, S->d_kc, ss))
+                    return rc;
+                continue;
+            }
+            k_stretch_propose<<<blocks, 128, 0, st>>>(ss, S->d_Y);
             S_TRY(cudaGetLastError());
             if (int rc = lens_eval(S->L, S->d_Y, half, S->d_lpY, st, S->d_kc)) return rc;
-            k_stretch_accept<<<blocks, 128, 0, st>>>(
-                S->d_x, S->d_lp, S->W, S->P, h, S->step, S->seed, S->ndim, S->d_Y, S->d_z,
-                S->d_lpY, S->d_lo, S->d_hi,
-                lp_prop_chain ? lp_prop_chain + (size_t)s * S->W : nullptr, S->d_nacc);
+            k_stretch_accept<<<blocks, 128, 0, st>>>(ss, S->d_Y, S->d_lpY);
             S_TRY(cudaGetLastError());
         }
         if (chain)
