@@ -839,9 +839,12 @@ int set_error(int code, const char *fmt, ...)
 
 // ------------------------------------------------------- batch context
 // Reusable buffers for multi-lens launches (and their CUDA graph).  The
-// entries of a run are grouped by (supersampling class, convolution class);
-// each group is one launch of its k_loglike_multi<SUB, K>.
-constexpr int kMaxGroups = 64;
+// entries of a run are grouped by (supersampling class, convolution class,
+// launch shape); each group is one launch of its k_loglike_multi<SUB, K>
+// (two-column lenses: at most kMultiSlots lenses per group, their
+// descriptors in the launch's parameters) or k_loglike_nc_multi<SUB, K>.
+constexpr int kMaxGroups = kMultiCounters;
+constexpr int kCounterInts = kMultiCounters * (1 + kMultiSlots);
 
 namespace {
 // One group's launch: kernel, CTA size, grid and dynamic shared memory.
@@ -866,11 +869,12 @@ struct tll_batcher {
     Segment *d_segs = nullptr, *h_segs = nullptr;
     MultiHdr *d_groups = nullptr, *h_groups = nullptr; // [kMaxGroups] + the whole list
     float *d_kc = nullptr, *d_gscr = nullptr;
-    int *d_counter = nullptr;                          // [kMaxGroups]
+    int *d_counter = nullptr;   // [kMaxGroups] group counters, then kMultiSlots per group
     const double *bn_tab = nullptr;
     cudaEvent_t staged = nullptr;      // staging may be refilled after this
     bool staged_pending = false;
     std::vector<GroupLaunch> glaunch;  // this run's group launches
+    std::vector<LensSlots> gslots;     // ... and their lens slots (n = 0: multi-column)
     std::vector<MultiKernel> kern_ready;  // kernels whose shared-memory limit is set
     int dyn_smem_nc = 0;              // dynamic shared memory of the multi-column kernels
     cudaGraphExec_t gexec = nullptr;
@@ -924,7 +928,7 @@ int batcher_reserve(tll_batcher *b, int lenses, int segs, int items, long long g
     CUDA_TRY(cudaMalloc(&b->d_segs, cs * sizeof(Segment)));
     CUDA_TRY(cudaMalloc(&b->d_groups, (kMaxGroups + 1) * sizeof(MultiHdr)));
     CUDA_TRY(cudaMalloc(&b->d_kc, (size_t)ci * NCONST * sizeof(float)));
-    CUDA_TRY(cudaMalloc(&b->d_counter, kMaxGroups * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&b->d_counter, kCounterInts * sizeof(int)));
     if (cg > 0) CUDA_TRY(cudaMalloc(&b->d_gscr, (size_t)cc * cg * sizeof(float)));
     CUDA_TRY(cudaMallocHost(&b->h_lenses, cl * sizeof(LensDev)));
     CUDA_TRY(cudaMallocHost(&b->h_segs, cs * sizeof(Segment)));
@@ -968,14 +972,14 @@ int batcher_enqueue(tll_batcher *b, int nl, int ns, int total, bool full, cudaSt
                              cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(b->d_groups, b->h_groups, (kMaxGroups + 1) * sizeof(MultiHdr),
                              cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, kMaxGroups * sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, kCounterInts * sizeof(int), st));
     const MultiArgs A = batcher_args(b);
     k_prologue_multi<<<(items + kPrologueVectors - 1) / kPrologueVectors,
                        dim3(kPrologueVectors, 4), 0, st>>>(A);
     CUDA_TRY(cudaGetLastError());
     for (int g = 0; g < (int)b->glaunch.size(); ++g) {
         const GroupLaunch &gl = b->glaunch[g];
-        gl.kern<<<gl.grid, gl.threads, gl.smem, st>>>(A, g);
+        gl.kern<<<gl.grid, gl.threads, gl.smem, st>>>(A, g, b->gslots[g]);
         CUDA_TRY(cudaGetLastError());
     }
     return TLL_OK;
@@ -1112,11 +1116,16 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
     }
     if (total == 0) return TLL_OK;
     if (total > (1LL << 30)) return fail(TLL_EINVAL, "batch too large");
+    // per-vector cost estimate (subpixels) orders a group's lenses (largest
+    // first) and splits its CTAs among lens slots; ties by lens, so that a
+    // lens's segments are adjacent
+    auto cost = [&](int k) {
+        return (long long)lenses[k]->npix * lenses[k]->sub * lenses[k]->sub;
+    };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         if (key[a] != key[c]) return key[a] < key[c];
-        const long long wa = (long long)lenses[a]->npix * lenses[a]->sub * lenses[a]->sub;
-        const long long wc = (long long)lenses[c]->npix * lenses[c]->sub * lenses[c]->sub;
-        return wa > wc;
+        if (cost(a) != cost(c)) return cost(a) > cost(c);
+        return lid[a] < lid[c];
     });
     int rc = batcher_reserve(b, (int)uniq.size(), n, (int)total, gslot, ctas);
     if (rc) return rc;
@@ -1127,12 +1136,20 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         if (!uniq[u]->nc) b->h_mdevs[u].nc = 0;
     }
     b->glaunch.clear();
+    b->gslots.clear();
     int first = 0, ns = 0, ng = 0;
     for (size_t q = 0; q < order.size(); ++q) {
         const int k = order[q];
         const bool ncl = lenses[k]->nc > 0;
         const Shape &S = ncl ? lenses[k]->nc_shape : lenses[k]->shape;
-        if (q == 0 || key[k] != key[order[q - 1]]) {
+        // a new group at a new key, or at a (kMultiSlots + 1)-th lens of a
+        // two-column group
+        bool fresh = q == 0 || key[k] != key[order[q - 1]];
+        if (!fresh && !ncl) {
+            const LensSlots &ls = b->gslots.back();
+            fresh = lid[k] != lid[order[q - 1]] && ls.n == kMultiSlots;
+        }
+        if (fresh) {
             if (ng == kMaxGroups) return fail(TLL_EINVAL, "more than %d kernel groups", kMaxGroups);
             const int Kc = conv_class(S.img, lenses[k]->K);
             const MultiKernel mk = ncl ? find_nc_multi(lenses[k]->sub, Kc)
@@ -1149,10 +1166,25 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
             gl.threads = S.threads;
             gl.grid = b->nsm * S.per_sm;
             b->glaunch.push_back(gl);
+            b->gslots.emplace_back();
+            b->gslots.back().n = 0;
             b->h_groups[ng] = MultiHdr{first, 0, ns, 0};
             ++ng;
         }
         b->glaunch.back().smem = std::max(b->glaunch.back().smem, S.smem);
+        if (!ncl) {
+            // the lens's slot in the group: a new one, or the previous
+            // segment's (a lens's segments are adjacent)
+            LensSlots &ls = b->gslots.back();
+            if (ls.n == 0 || lid[k] != lid[order[q - 1]]) {
+                ls.lens[ls.n] = b->h_lenses[lid[k]];
+                ls.first[ls.n] = first;
+                ls.count[ls.n] = 0;
+                ls.cta_end[ls.n] = 0;
+                ++ls.n;
+            }
+            ls.count[ls.n - 1] += counts[k];
+        }
         Segment &sg = b->h_segs[ns++];
         sg.lens = lid[k];
         sg.first = first;
@@ -1165,29 +1197,61 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         b->h_groups[ng - 1].nseg += 1;
     }
     b->h_groups[kMaxGroups] = MultiHdr{0, (int)total, 0, ns};
+    // each two-column group's CTAs split among its lens slots in proportion
+    // to their cost (vectors x subpixels), at least one each
+    for (int g = 0; g < ng; ++g) {
+        LensSlots &ls = b->gslots[g];
+        if (ls.n == 0) continue;
+        const int grid = b->glaunch[g].grid;
+        double w[kMultiSlots], wsum = 0.0;
+        for (int s2 = 0; s2 < ls.n; ++s2) {
+            w[s2] = (double)ls.count[s2] * (double)ls.lens[s2].npix * ls.lens[s2].sub *
+                    ls.lens[s2].sub;
+            wsum += w[s2];
+        }
+        int end = 0;
+        for (int s2 = 0; s2 < ls.n; ++s2) {
+            const int left = ls.n - 1 - s2;   // slots after this one keep >= 1 CTA each
+            int c = (int)((double)grid * w[s2] / std::max(wsum, 1.0));
+            c = std::max(1, std::min(c, grid - end - left));
+            end = s2 + 1 == ls.n ? grid : end + c;
+            ls.cta_end[s2] = end;
+        }
+    }
     const bool graph = b->use_graph && st != nullptr;
     if (graph) {
-        if (!b->gexec || b->gstream != st || !(b->gcaptured == b->glaunch)) {
+        // the lens slots are launch parameters: captured anew every run and
+        // the instantiated graph updated in place (same topology while the
+        // group launches are the same), instantiated again otherwise
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        rc = batcher_enqueue(b, 0, 0, 0, true, st);
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(TLL_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+        bool updated = false;
+        if (b->gexec && b->gstream == st && b->gcaptured == b->glaunch) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(b->gexec, g, &info) == cudaSuccess;
+            if (!updated) cudaGetLastError();
+        }
+        if (!updated) {
             if (b->gexec) {
                 cudaGraphExecDestroy(b->gexec);
                 b->gexec = nullptr;
             }
-            cudaGraph_t g = nullptr;
-            CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            rc = batcher_enqueue(b, 0, 0, 0, true, st);
-            const cudaError_t ce = cudaStreamEndCapture(st, &g);
-            if (rc) {
-                if (g) cudaGraphDestroy(g);
-                return rc;
-            }
-            if (ce != cudaSuccess) return fail(TLL_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
             const cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
-            cudaGraphDestroy(g);
-            if (ie != cudaSuccess)
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(g);
                 return fail(TLL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
-            b->gstream = st;
-            b->gcaptured = b->glaunch;
+            }
         }
+        cudaGraphDestroy(g);
+        b->gstream = st;
+        b->gcaptured = b->glaunch;
         CUDA_TRY(cudaGraphLaunch(b->gexec, st));
     } else {
         rc = batcher_enqueue(b, (int)uniq.size(), ns, (int)total, false, st);

@@ -194,6 +194,25 @@ struct Segment {
 struct MultiHdr {        // one group: items [first, first + total), segments [seg0, seg0 + nseg)
     int first, total, seg0, nseg;
 };
+// The lenses of one two-column multi-lens launch, by value in the kernel's
+// parameters (constant bank) rather than copied to shared memory: read
+// through a block-uniform slot index, the lens constants (the PSF taps of
+// the convolutions' inner loops above all) stay operands of the arithmetic
+// instead of shared-memory loads.  Slot s: lens[s], its vectors are items
+// [first[s], first[s] + count[s]) of the work list, handed out by counter
+// A.counter[kMultiCounters + g kMultiSlots + s]; CTAs [cta_end[s-1],
+// cta_end[s]) start on slot s (in proportion to its work) and move on to
+// the following slots when it runs dry.  n = 0: not used (multi-column
+// groups).
+constexpr int kMultiSlots = 6;
+constexpr int kMultiCounters = 1024;   // groups per run; slot counters follow
+struct LensSlots {
+    int n;
+    int cta_end[kMultiSlots];
+    int first[kMultiSlots], count[kMultiSlots];
+    LensDev lens[kMultiSlots];
+};
+
 struct MultiDev;   // the component list of a multi-column lens (tll_multi.cuh)
 struct MultiArgs {
     const LensDev *lenses;

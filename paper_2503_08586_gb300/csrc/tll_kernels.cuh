@@ -833,16 +833,21 @@ k_loglike(const __grid_constant__ LensDev L, const __grid_constant__ RunArgs R)
 }
 
 // ----------------------------------------------------- multi-lens kernel
-// One launch over the vectors of one group of segments (lenses sharing the
-// supersampling class SUB and the convolution class K): CTAs take items from
-// the group's atomic counter and copy a lens's descriptor into shared memory
-// when they switch lens.
+// One launch over the vectors of one group of segments: at most kMultiSlots
+// two-column lenses sharing the supersampling class SUB and the convolution
+// class K, their items contiguous per lens (LensSlots).  Each CTA starts on
+// its home slot and then takes the following ones in turn, every slot's
+// vectors handed out by its counter; the lens descriptor is read from the
+// kernel's parameters through the slot index, which depends on blockIdx
+// and the loop count only (block-uniform), so its constants stay operands
+// of the arithmetic (a copy in shared memory made every tap a load: 10 %
+// slower).
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constant__ MultiArgs A,
-                                                            int group)
+                                                            int group,
+                                                            const __grid_constant__ LensSlots S)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LensDev sL;
     __shared__ int s_t, s_seg;
     __shared__ __align__(16) float sepl[kEplSmemFloats];
     __shared__ PendingFinish spf;
@@ -852,45 +857,51 @@ __global__ void __launch_bounds__(kThreads) k_loglike_multi(const __grid_constan
     float *spsf = reinterpret_cast<float *>(smem + kRedBytes);
     float *gslot = A.gscr ? A.gscr + (size_t)blockIdx.x * A.gslot_floats : nullptr;
     const MultiHdr hd = A.groups[group];
-    int *counter = A.counter + group;
-    int cur = -1;
-    for (;;) {
-        if (tid == 0) {
-            const int t = hd.first + atomicAdd(counter, 1);
-            s_t = t;
-            s_seg = t < hd.first + hd.total ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+    int home = 0;
+    while (home < S.n - 1 && (int)blockIdx.x >= S.cta_end[home]) ++home;
+    for (int k = 0; k < S.n; ++k) {
+        int s = home + k;
+        if (s >= S.n) s -= S.n;
+        const LensDev &L = S.lens[s];
+        int *ctr = A.counter + kMultiCounters + group * kMultiSlots + s;
+        bool ready = false;
+        for (;;) {
+            if (tid == 0) {
+                const int i = atomicAdd(ctr, 1);
+                const int t = i < S.count[s] ? S.first[s] + i : -1;
+                s_t = t;
+                s_seg = t >= 0 ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+            }
+            __syncthreads();
+            const int t = s_t;
+            if (t < 0) break;
+            if (!ready) {
+                // the slot's lens in the CTA's shared memory (halos, taps)
+                setup_lens(L, spsf, tid, nthr);
+                zero_untraced(L, img_ptrs(L, spsf, gslot), tid, nthr);
+                __syncthreads();
+                ready = true;
+            }
+            const Segment sg = A.segs[s_seg];
+            const float *kc = A.kc + (size_t)t * NCONST;
+            double *outp = sg.out + (t - sg.first);
+            if (kc[K_VALID] == 0.0f) {
+                if (tid == 0) *outp = -INFINITY;
+                __syncthreads();
+                continue;
+            }
+            RunArgs R = {};
+            const ImgPtrs P = img_ptrs(L, spsf, gslot);
+            vector_body<SUB, K, false>(L, R, kc, outp, P, spsf, sred, sepl, spf, tid, nthr);
         }
         __syncthreads();
-        const int t = s_t;
-        if (t >= hd.first + hd.total) break;
-        const Segment sg = A.segs[s_seg];
-        if (sg.lens != cur) {
-            const unsigned *src = reinterpret_cast<const unsigned *>(A.lenses + sg.lens);
-            unsigned *dst = reinterpret_cast<unsigned *>(&sL);
-            for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
-            __syncthreads();
-            setup_lens(sL, spsf, tid, nthr);
-            zero_untraced(sL, img_ptrs(sL, spsf, gslot), tid, nthr);
-            __syncthreads();
-            cur = sg.lens;
-        }
-        const float *kc = A.kc + (size_t)t * NCONST;
-        double *outp = sg.out + (t - sg.first);
-        if (kc[K_VALID] == 0.0f) {
-            if (tid == 0) *outp = -INFINITY;
-            __syncthreads();
-            continue;
-        }
-        RunArgs R = {};
-        const ImgPtrs P = img_ptrs(sL, spsf, gslot);
-        vector_body<SUB, K, false>(sL, R, kc, outp, P, spsf, sred, sepl, spf, tid, nthr);
     }
     if ((tid >> 5) == (nthr >> 5) - 1) finish_pending(spf, sred, tid & 31, nthr >> 5);
 }
 
 // --------------------------------------------------------------- registry
 using SingleKernel = void (*)(const LensDev, const RunArgs);
-using MultiKernel = void (*)(const MultiArgs, int);
+using MultiKernel = void (*)(const MultiArgs, int, const LensSlots);
 
 // Supersampling classes with an unrolled subpixel loop.
 __host__ __device__ inline int sub_class(int sub) { return (sub == 4 || sub == 5) ? sub : 0; }

@@ -820,7 +820,8 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
 // into shared memory when they switch lens (as k_loglike_multi).
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_constant__ MultiArgs A,
-                                                               int group)
+                                                               int group,
+                                                               const __grid_constant__ LensSlots)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ NcShared sh;
