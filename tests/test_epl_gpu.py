@@ -70,6 +70,29 @@ def test_epl_columns_and_loglike(cases, idx):
     g.close()
 
 
+def test_epl_table_switch(cases):
+    """Either side of the switch between the per-vector table of the
+    deflection's series and the per-subpixel recurrence ((1-q)/(1+q) = |eps|
+    = 0.35), at two position angles: columns within the pixel gate and log L
+    within the gates."""
+    sl, P, o, ref = cases[1]
+    g = _gpu(sl)
+    Q = np.repeat(P[:1], 4, axis=0)
+    for i, (e, phi) in enumerate(((0.3499, 0.4), (0.3501, 0.4), (0.3499, 2.0), (0.3501, 2.0))):
+        Q[i, 1], Q[i, 2] = e * np.cos(2 * phi), e * np.sin(2 * phi)
+    for p in Q:
+        il, is_ = o.unblurred(p.astype(np.float64))
+        gl, gs = g.model_columns(p, blurred=False)
+        au = _pix_allowance(o, p, blurred=False)
+        for gg, oo, aa, nm in ((gl, il, au[0], "lens"), (gs, is_, au[1], "source")):
+            ok, worst = _pix_ok(np.asarray(gg).reshape(oo.shape), oo, aa)
+            assert ok, f"|eps| {np.hypot(p[1], p[2]):.4f} {nm}: worst error / tol {worst:.3f}"
+    out = g.loglike_batch(torch.from_numpy(Q).cuda())
+    torch.cuda.synchronize()
+    _ll_ok(out.cpu().numpy(), o.loglike_batch(Q.astype(np.float64)), sl)
+    g.close()
+
+
 def test_epl_slope_validity(cases):
     sl, P, o, ref = cases[1]
     Q = P[:8].copy()
