@@ -101,3 +101,50 @@ def test_multi_repeated_lens_and_empty_entries(setup):
     fin = np.isfinite(ref)
     assert np.allclose(got[fin], ref[fin], rtol=1e-12, atol=1e-9)
     b.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_multi_lens_slots_split_and_update(use_graph):
+    """Nine two-column lenses of one shape class: a launch group holds at
+    most six (their descriptors in the launch parameters), so the seventh
+    starts a second group; one lens appears in two non-adjacent entries.
+    Runs with other lens sets (in graph form: the captured graph updated in
+    place, or instantiated again when the groups change) must again equal
+    the one-lens launches."""
+    build.build()
+    tll.load()
+    psf = W.gaussian_psf(11, 1.8)
+    render = oracle.columns_renderer(0.05, 4, psf, 40, 44)
+    items = []
+    for k in range(9):
+        rng = np.random.Generator(np.random.PCG64(900 + k))
+        sl = W.synth_lens(rng, 40, 44, 0.05, 4, psf, render, "sky")
+        P = np.concatenate([sl.truth[None], W.shrinking_draws(rng, sl.truth, 11 + 7 * k)])
+        g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0)
+        items.append((g, P.astype(np.float32)))
+    b = tll.Batcher(use_graph=use_graph)
+    stream = torch.cuda.Stream()
+    # the second run keeps the group launches (graph updated in place), the
+    # third has one group fewer (graph instantiated again)
+    runs = [list(range(9)) + [2], [8, 7, 6, 5, 4, 3, 1, 0, 2, 6], [8, 5, 1, 7, 3]]
+    for sel in runs:
+        lenses = [items[k][0] for k in sel]
+        parts = []
+        for j, k in enumerate(sel):
+            P = items[k][1]
+            parts.append(P[: len(P) // 2] if sel.count(k) > 1 and j == sel.index(k) else
+                         P[len(P) // 2:] if sel.count(k) > 1 else P)
+        params = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in parts]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            outs = b.run(lenses, params, stream=stream)
+        stream.synchronize()
+        for k, p, o in zip(sel, parts, outs):
+            ref = _single(items[k][0], p)
+            got = o.cpu().numpy()
+            assert np.array_equal(np.isneginf(got), np.isneginf(ref))
+            fin = np.isfinite(ref)
+            assert np.allclose(got[fin], ref[fin], rtol=1e-12, atol=1e-9), k
+    b.close()
+    for g, _ in items:
+        g.close()
