@@ -674,7 +674,7 @@ int nc_configure(tll_lens *L)
         const MultiKernel km = find_nc_multi(L->sub, L->K);
         if (!k || !km) return fail(TLL_ECUDA, "no multi-column kernel for s=%d K=%d", L->sub, L->K);
         // the band must fit both the one-lens kernel and the batcher's
-        // multi-lens one (which also holds a lens descriptor)
+        // multi-lens one (their static shared memory differs)
         cudaFuncAttributes fa, fm;
         CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k));
         CUDA_TRY(cudaFuncGetAttributes(&fm, (const void *)km));
@@ -840,9 +840,9 @@ int set_error(int code, const char *fmt, ...)
 // ------------------------------------------------------- batch context
 // Reusable buffers for multi-lens launches (and their CUDA graph).  The
 // entries of a run are grouped by (supersampling class, convolution class,
-// launch shape); each group is one launch of its k_loglike_multi<SUB, K>
-// (two-column lenses: at most kMultiSlots lenses per group, their
-// descriptors in the launch's parameters) or k_loglike_nc_multi<SUB, K>.
+// launch shape) and at most kMultiSlots lenses; each group is one launch of
+// its k_loglike_multi<SUB, K> (two-column lenses) or k_loglike_nc_multi<SUB,
+// K>, the lenses' descriptors in the launch's parameters (LensSlots).
 constexpr int kMaxGroups = kMultiCounters;
 constexpr int kCounterInts = kMultiCounters * (1 + kMultiSlots);
 
@@ -874,7 +874,7 @@ struct tll_batcher {
     cudaEvent_t staged = nullptr;      // staging may be refilled after this
     bool staged_pending = false;
     std::vector<GroupLaunch> glaunch;  // this run's group launches
-    std::vector<LensSlots> gslots;     // ... and their lens slots (n = 0: multi-column)
+    std::vector<LensSlots> gslots;     // ... and their lens slots
     std::vector<MultiKernel> kern_ready;  // kernels whose shared-memory limit is set
     int dyn_smem_nc = 0;              // dynamic shared memory of the multi-column kernels
     cudaGraphExec_t gexec = nullptr;
@@ -1142,10 +1142,9 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         const int k = order[q];
         const bool ncl = lenses[k]->nc > 0;
         const Shape &S = ncl ? lenses[k]->nc_shape : lenses[k]->shape;
-        // a new group at a new key, or at a (kMultiSlots + 1)-th lens of a
-        // two-column group
+        // a new group at a new key, or at a (kMultiSlots + 1)-th lens
         bool fresh = q == 0 || key[k] != key[order[q - 1]];
-        if (!fresh && !ncl) {
+        if (!fresh) {
             const LensSlots &ls = b->gslots.back();
             fresh = lid[k] != lid[order[q - 1]] && ls.n == kMultiSlots;
         }
@@ -1172,12 +1171,13 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
             ++ng;
         }
         b->glaunch.back().smem = std::max(b->glaunch.back().smem, S.smem);
-        if (!ncl) {
+        {
             // the lens's slot in the group: a new one, or the previous
             // segment's (a lens's segments are adjacent)
             LensSlots &ls = b->gslots.back();
             if (ls.n == 0 || lid[k] != lid[order[q - 1]]) {
                 ls.lens[ls.n] = b->h_lenses[lid[k]];
+                ls.md[ls.n] = b->h_mdevs[lid[k]];
                 ls.first[ls.n] = first;
                 ls.count[ls.n] = 0;
                 ls.cta_end[ls.n] = 0;
@@ -1197,8 +1197,8 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         b->h_groups[ng - 1].nseg += 1;
     }
     b->h_groups[kMaxGroups] = MultiHdr{0, (int)total, 0, ns};
-    // each two-column group's CTAs split among its lens slots in proportion
-    // to their cost (vectors x subpixels), at least one each
+    // each group's CTAs split among its lens slots in proportion to their
+    // cost (vectors x subpixels x columns), at least one each
     for (int g = 0; g < ng; ++g) {
         LensSlots &ls = b->gslots[g];
         if (ls.n == 0) continue;
@@ -1206,7 +1206,7 @@ int tll_batcher_run(tll_batcher *b, tll_lens *const *lenses, const float *const 
         double w[kMultiSlots], wsum = 0.0;
         for (int s2 = 0; s2 < ls.n; ++s2) {
             w[s2] = (double)ls.count[s2] * (double)ls.lens[s2].npix * ls.lens[s2].sub *
-                    ls.lens[s2].sub;
+                    ls.lens[s2].sub * (ls.md[s2].nc > 0 ? ls.md[s2].nc : 2);
             wsum += w[s2];
         }
         int end = 0;

@@ -194,7 +194,23 @@ struct Segment {
 struct MultiHdr {        // one group: items [first, first + total), segments [seg0, seg0 + nseg)
     int first, total, seg0, nseg;
 };
-// The lenses of one two-column multi-lens launch, by value in the kernel's
+constexpr int kMaxComps = 32;       // components (columns) per lens
+constexpr int kPassMax = 8;         // components of one trace pass (lens-plane Gaussians)
+constexpr int kMaxPasses = 16;      // trace passes per vector
+
+// A multi-column lens's component list and its trace schedule (kernel
+// parameter; tll_multi.cuh).
+struct MultiDev {
+    int nc, npar, npass;
+    int type[kMaxComps], plane[kMaxComps], flags[kMaxComps];
+    float scale[kMaxComps], index[kMaxComps];
+    // pass p: plane, component count, Gaussian-only (up to kPassMax
+    // components) or mixed (up to kPassMix), component indices
+    int pass_plane[kMaxPasses], pass_n[kMaxPasses], pass_gauss[kMaxPasses];
+    int pass_comp[kMaxPasses][kPassMax];
+};
+
+// The lenses of one multi-lens launch, by value in the kernel's
 // parameters (constant bank) rather than copied to shared memory: read
 // through a block-uniform slot index, the lens constants (the PSF taps of
 // the convolutions' inner loops above all) stay operands of the arithmetic
@@ -202,18 +218,18 @@ struct MultiHdr {        // one group: items [first, first + total), segments [s
 // [first[s], first[s] + count[s]) of the work list, handed out by counter
 // A.counter[kMultiCounters + g kMultiSlots + s]; CTAs [cta_end[s-1],
 // cta_end[s]) start on slot s (in proportion to its work) and move on to
-// the following slots when it runs dry.  n = 0: not used (multi-column
-// groups).
-constexpr int kMultiSlots = 6;
+// the following slots when it runs dry.  Multi-column lenses also carry
+// their component lists (md[s]; 28.8 KB in all of the 32 KB the parameters
+// may take).
+constexpr int kMultiSlots = 5;
 constexpr int kMultiCounters = 1024;   // groups per run; slot counters follow
 struct LensSlots {
     int n;
     int cta_end[kMultiSlots];
     int first[kMultiSlots], count[kMultiSlots];
     LensDev lens[kMultiSlots];
+    MultiDev md[kMultiSlots];
 };
-
-struct MultiDev;   // the component list of a multi-column lens (tll_multi.cuh)
 struct MultiArgs {
     const LensDev *lenses;
     const MultiDev *mdevs;     // per lens: its component list (nc = 0: two columns)

@@ -32,11 +32,8 @@
 
 namespace tll {
 
-constexpr int kMaxComps = 32;       // components (columns) per lens
-constexpr int kPassMax = 8;         // components of one trace pass (lens-plane Gaussians)
 constexpr int kPassSrcG = 6;        // ... source-plane Gaussians (the deflection's registers)
 constexpr int kPassMix = 4;         // ... a pass with Sersic components
-constexpr int kMaxPasses = 16;      // trace passes per vector
 constexpr int K_C0 = NCONST_USED;   // per-component constants, 6 floats each
 static_assert(K_C0 + 6 * kMaxComps <= NCONST, "constant block too small");
 
@@ -44,17 +41,6 @@ enum : int { COMP_SERSIC = 0, COMP_GAUSS = 1 };
 enum : int { PLANE_LENS = 0, PLANE_SOURCE = 1 };
 enum : int { FREE_SCALE = 1, FREE_INDEX = 2 };
 constexpr int kMultiHead = 15;      // mass (7), lens geometry (4), source geometry (4)
-
-// A lens's component list and its trace schedule (kernel parameter).
-struct MultiDev {
-    int nc, npar, npass;
-    int type[kMaxComps], plane[kMaxComps], flags[kMaxComps];
-    float scale[kMaxComps], index[kMaxComps];
-    // pass p: plane, component count, Gaussian-only (up to kPassMax
-    // components) or mixed (up to kPassMix), component indices
-    int pass_plane[kMaxPasses], pass_n[kMaxPasses], pass_gauss[kMaxPasses];
-    int pass_comp[kMaxPasses][kPassMax];
-};
 
 // Arguments of one multi-column launch.
 struct NcArgs {
@@ -815,18 +801,18 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
     if (tid >= nthr - 32) nc_solve_pending(sh, spf, tid & 31);
 }
 
-// Many lenses (the batcher's multi-column groups): CTAs take items from the
-// group's atomic counter and copy a lens's descriptor and component list
-// into shared memory when they switch lens (as k_loglike_multi).
+// Many lenses (the batcher's multi-column groups): at most kMultiSlots
+// lenses per launch, their descriptors and component lists in the launch's
+// parameters (LensSlots) read through a block-uniform slot index; each CTA
+// starts on its home slot and then takes the following ones in turn, every
+// slot's vectors handed out by its counter (as k_loglike_multi).
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_constant__ MultiArgs A,
                                                                int group,
-                                                               const __grid_constant__ LensSlots)
+                                                               const __grid_constant__ LensSlots S)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ NcShared sh;
-    __shared__ LensDev sL;
-    __shared__ MultiDev sM;
     __shared__ int s_t, s_seg;
     __shared__ NcPending spf;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -834,41 +820,46 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
     float *spsf = reinterpret_cast<float *>(smem);
     float *U = A.gscr + (size_t)blockIdx.x * A.gslot_floats;
     const MultiHdr hd = A.groups[group];
-    int *counter = A.counter + group;
-    int cur = -1;
-    for (;;) {
-        if (tid == 0) {
-            const int t = hd.first + atomicAdd(counter, 1);
-            s_t = t;
-            s_seg = t < hd.first + hd.total ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+    int home = 0;
+    while (home < S.n - 1 && (int)blockIdx.x >= S.cta_end[home]) ++home;
+    for (int k = 0; k < S.n; ++k) {
+        int s = home + k;
+        if (s >= S.n) s -= S.n;
+        const LensDev &L = S.lens[s];
+        const MultiDev &M = S.md[s];
+        int *ctr = A.counter + kMultiCounters + group * kMultiSlots + s;
+        bool ready = false;
+        for (;;) {
+            if (tid == 0) {
+                const int i = atomicAdd(ctr, 1);
+                const int t = i < S.count[s] ? S.first[s] + i : -1;
+                s_t = t;
+                s_seg = t >= 0 ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+            }
+            __syncthreads();
+            const int t = s_t;
+            if (t < 0) break;
+            if (!ready) {
+                // the slot's lens in the CTA's shared memory; pixels never
+                // traced (masked lenses) start finite
+                setup_lens(L, spsf, tid, nthr);
+                if (L.tlist)
+                    for (int q = tid; q < M.nc * L.npix; q += nthr) U[q] = 0.0f;
+                __syncthreads();
+                ready = true;
+            }
+            const Segment sg = A.segs[s_seg];
+            const float *kc = A.kc + (size_t)t * NCONST;
+            double *outp = sg.out + (t - sg.first);
+            if (kc[K_VALID] == 0.0f) {
+                if (tid == 0) *outp = -INFINITY;
+                __syncthreads();
+                continue;
+            }
+            nc_vector<SUB, K, 1>(L, M, kc, outp, nullptr, U, spsf, sh, spf, true,
+                                 nc_tile_pixels(M.nc, (long long)L.nc_smem), tid, nthr);
         }
         __syncthreads();
-        const int t = s_t;
-        if (t >= hd.first + hd.total) break;
-        const Segment sg = A.segs[s_seg];
-        if (sg.lens != cur) {
-            const unsigned *src = reinterpret_cast<const unsigned *>(A.lenses + sg.lens);
-            unsigned *dst = reinterpret_cast<unsigned *>(&sL);
-            for (int k = tid; k < (int)(sizeof(LensDev) / 4); k += nthr) dst[k] = src[k];
-            const unsigned *msrc = reinterpret_cast<const unsigned *>(A.mdevs + sg.lens);
-            unsigned *mdst = reinterpret_cast<unsigned *>(&sM);
-            for (int k = tid; k < (int)(sizeof(MultiDev) / 4); k += nthr) mdst[k] = msrc[k];
-            __syncthreads();
-            setup_lens(sL, spsf, tid, nthr);
-            if (sL.tlist)
-                for (int k = tid; k < sM.nc * sL.npix; k += nthr) U[k] = 0.0f;
-            __syncthreads();
-            cur = sg.lens;
-        }
-        const float *kc = A.kc + (size_t)t * NCONST;
-        double *outp = sg.out + (t - sg.first);
-        if (kc[K_VALID] == 0.0f) {
-            if (tid == 0) *outp = -INFINITY;
-            __syncthreads();
-            continue;
-        }
-        nc_vector<SUB, K, 1>(sL, sM, kc, outp, nullptr, U, spsf, sh, spf, true,
-                          nc_tile_pixels(sM.nc, (long long)sL.nc_smem), tid, nthr);
     }
     if (tid >= nthr - 32) nc_solve_pending(sh, spf, tid & 31);
 }

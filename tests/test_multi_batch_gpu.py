@@ -124,3 +124,57 @@ def test_batch_only_multi_lens_defers_its_slots(setups):
     torch.cuda.synchronize()
     assert torch.equal(a, out)
     g.close()
+
+
+def test_multi_column_lens_slots_split_and_update():
+    """Seven multi-component lenses of one shape class (the SLACS direct
+    case's geometry, each with its own data): a launch group holds at most
+    five lens slots (their descriptors and component lists in the launch
+    parameters), so the sixth starts a second group; one lens appears in two
+    non-adjacent entries.  Later runs keep the group launches (graph updated
+    in place) or drop one (graph instantiated again); every result must equal
+    the lens's own one-lens evaluation bit for bit."""
+    build.build()
+    tll.load()
+    name, ny, nx, dpix, sub, ks, kind, comps, mass = CASES[0]
+    psf = W.moffat_psf(ks, 2.2, 3.0)
+    render = oracle.multi_columns_renderer(W.f32(dpix), sub, psf, ny, nx, comps, mass=mass)
+    items = []
+    for k in range(7):
+        rng = np.random.Generator(np.random.PCG64(9100 + k))
+        sl = W.synth_multi_lens(rng, ny, nx, dpix, sub, psf, render, comps, mass=mass)
+        P = np.concatenate([sl.truth[None],
+                            W.shrinking_draws_multi(rng, sl.truth, 9 + 6 * k, comps,
+                                                    lo_frac=1e-6)]).astype(np.float32)
+        g = tll.Lens(sl.data, sl.noise, sl.psf, sl.pixel_scale, sl.sub, sl.x0, sl.y0,
+                     mass=mass)
+        g.set_light(_to_tll(comps))
+        items.append((g, P))
+    alone = {}
+    b = tll.Batcher(use_graph=True)
+    st = torch.cuda.Stream()
+    runs = [list(range(7)) + [3], [6, 5, 4, 3, 1, 0, 2, 5], [6, 2, 4]]
+    for sel in runs:
+        parts = []
+        for j, k in enumerate(sel):
+            P = items[k][1]
+            h = len(P) // 2
+            parts.append((k, P[:h] if sel.count(k) > 1 and j == sel.index(k) else
+                          P[h:] if sel.count(k) > 1 else P))
+        params = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for _, p in parts]
+        for (k, p), t in zip(parts, params):
+            key = (k, p.shape[0], float(p[0, 0]))
+            if key not in alone:
+                out = items[k][0].loglike_batch(t)
+                torch.cuda.synchronize()
+                alone[key] = out.cpu().numpy()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            outs = b.run([items[k][0] for k, _ in parts], params, stream=st)
+        st.synchronize()
+        for (k, p), o in zip(parts, outs):
+            got = o.cpu().numpy()
+            assert np.array_equal(got, alone[(k, p.shape[0], float(p[0, 0]))]), (sel, k)
+    b.close()
+    for g, _ in items:
+        g.close()

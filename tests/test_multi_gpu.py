@@ -106,7 +106,7 @@ def test_multi_repeated_lens_and_empty_entries(setup):
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_multi_lens_slots_split_and_update(use_graph):
     """Nine two-column lenses of one shape class: a launch group holds at
-    most six (their descriptors in the launch parameters), so the seventh
+    most five (their descriptors in the launch parameters), so the sixth
     starts a second group; one lens appears in two non-adjacent entries.
     Runs with other lens sets (in graph form: the captured graph updated in
     place, or instantiated again when the groups change) must again equal
