@@ -813,32 +813,42 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ NcShared sh;
-    __shared__ int s_t, s_seg;
     __shared__ NcPending spf;
+    // the vector in hand and its output, in shared memory (tid 0 writes
+    // them between barriers) so that they take no registers across a vector
+    __shared__ int s_t;
+    __shared__ double *s_out;
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) spf.valid = 0;
     float *spsf = reinterpret_cast<float *>(smem);
-    float *U = A.gscr + (size_t)blockIdx.x * A.gslot_floats;
-    const MultiHdr hd = A.groups[group];
     int home = 0;
     while (home < S.n - 1 && (int)blockIdx.x >= S.cta_end[home]) ++home;
     for (int k = 0; k < S.n; ++k) {
-        int s = home + k;
-        if (s >= S.n) s -= S.n;
-        const LensDev &L = S.lens[s];
-        const MultiDev &M = S.md[s];
-        int *ctr = A.counter + kMultiCounters + group * kMultiSlots + s;
-        bool ready = false;
-        for (;;) {
+        int s0 = home + k;
+        if (s0 >= S.n) s0 -= S.n;
+        for (bool ready = false;; ready = true) {
+            // the slot index made opaque for each vector: with it fixed for
+            // the whole slot the compiler keeps lens fields in registers
+            // across nc_vector and spills (736 B of spill stores, 1344 B of
+            // loads per thread, against 60 and 100 this way)
+            int s = s0;
+            asm volatile("" : "+r"(s));
+            const LensDev &L = S.lens[s];
+            const MultiDev &M = S.md[s];
             if (tid == 0) {
-                const int i = atomicAdd(ctr, 1);
+                const int i = atomicAdd(A.counter + kMultiCounters + group * kMultiSlots + s, 1);
                 const int t = i < S.count[s] ? S.first[s] + i : -1;
                 s_t = t;
-                s_seg = t >= 0 ? find_segment(A.segs, hd.seg0, hd.nseg, t) : 0;
+                if (t >= 0) {
+                    const MultiHdr hd = A.groups[group];
+                    const Segment &sg = A.segs[find_segment(A.segs, hd.seg0, hd.nseg, t)];
+                    s_out = sg.out + (t - sg.first);
+                }
             }
             __syncthreads();
             const int t = s_t;
             if (t < 0) break;
+            float *U = A.gscr + (size_t)blockIdx.x * A.gslot_floats;
             if (!ready) {
                 // the slot's lens in the CTA's shared memory; pixels never
                 // traced (masked lenses) start finite
@@ -846,20 +856,17 @@ __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_cons
                 if (L.tlist)
                     for (int q = tid; q < M.nc * L.npix; q += nthr) U[q] = 0.0f;
                 __syncthreads();
-                ready = true;
             }
-            const Segment sg = A.segs[s_seg];
             const float *kc = A.kc + (size_t)t * NCONST;
-            double *outp = sg.out + (t - sg.first);
             if (kc[K_VALID] == 0.0f) {
-                if (tid == 0) *outp = -INFINITY;
-                __syncthreads();
-                continue;
+                if (tid == 0) *s_out = -INFINITY;
+            } else {
+                nc_vector<SUB, K, 1>(L, M, kc, s_out, nullptr, U, spsf, sh, spf, true,
+                                     nc_tile_pixels(M.nc, (long long)L.nc_smem), tid, nthr);
             }
-            nc_vector<SUB, K, 1>(L, M, kc, outp, nullptr, U, spsf, sh, spf, true,
-                                 nc_tile_pixels(M.nc, (long long)L.nc_smem), tid, nthr);
+            // every thread has read s_t and s_out before tid 0 rewrites them
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (tid >= nthr - 32) nc_solve_pending(sh, spf, tid & 31);
 }
