@@ -803,9 +803,10 @@ k_loglike_nc(const __grid_constant__ LensDev L, const __grid_constant__ MultiDev
 
 // Many lenses (the batcher's multi-column groups): at most kMultiSlots
 // lenses per launch, their descriptors and component lists in the launch's
-// parameters (LensSlots) read through a block-uniform slot index; each CTA
-// starts on its home slot and then takes the following ones in turn, every
-// slot's vectors handed out by its counter (as k_loglike_multi).
+// parameters (LensSlots) read through the slot index where they are used;
+// each CTA starts on its home slot and then takes the following ones in
+// turn, every slot's vectors handed out by its counter (as
+// k_loglike_multi).
 template <int SUB, int K>
 __global__ void __launch_bounds__(kThreads) k_loglike_nc_multi(const __grid_constant__ MultiArgs A,
                                                                int group,
