@@ -765,7 +765,10 @@ double ora_loglike_multi(const ora_lens *L, const ora_comp_spec *c, int nc,
     double A[ORA_MAXC * ORA_MAXC] = {0}, b[ORA_MAXC] = {0}, x[ORA_MAXC];
     for (int a = 0; a < nc; ++a) {
         const double *ma = mc + (size_t)a * npix;
-        for (int t = 0; t < npix; ++t) b[a] += w[t] * ma[t] * L->data[t];
+        /* masked pixels (R8) carry no term: skipped, not weighted by 0, since
+         * their datum may be non-finite and 0 * NaN is NaN */
+        for (int t = 0; t < npix; ++t)
+            if (w[t] != 0.0) b[a] += w[t] * ma[t] * L->data[t];
         for (int e = 0; e < nc; ++e) {
             const double *me = mc + (size_t)e * npix;
             double v = 0.0;

@@ -252,6 +252,34 @@ def test_exact_multi_model_recovers_amplitudes():
     assert abs(ll - C) < 1e-9 * abs(C)
 
 
+
+def test_multi_masked_pixels_leave_the_fit():
+    """Masked pixels (sigma <= 0, non-finite sigma or data) drop out of Eq. 5
+    and of the N-column FNNLS: with noisy data, the oracle equals a library
+    NNLS fit (scipy) of its blurred columns to the unmasked pixels alone.
+    The masked pixels hold +-1e6 or NaN, so a leak would show at once."""
+    r = np.random.default_rng(32)
+    comps = _comps_slacs()
+    ny, nx = 26, 24
+    psf = np.exp(-0.5 * ((np.arange(7) - 3.0)[:, None] ** 2 + (np.arange(7) - 3.0)[None, :] ** 2) / 1.8)
+    p = _mvec([0.5, 0.9, 0.12, 0.3])
+    cols = oracle.multi_columns_renderer(0.06, 3, psf, ny, nx, comps)(p)
+    sig = r.uniform(0.4, 1.6, (ny, nx))
+    d = np.tensordot(np.array([3.0, 1.0, 7.0, 2.0]), cols, axes=1) + r.normal(0.0, 1.0, (ny, nx)) * sig
+    for (i, j), (sv, dv) in zip([(0, 0), (3, 7), (ny // 2, nx // 2), (ny - 1, nx - 1), (5, 5)],
+                                [(0.0, 1e6), (-2.0, -1e6), (np.inf, 5e5), (np.nan, 1e6),
+                                 (1.0, np.nan)]):
+        sig[i, j], d[i, j] = sv, dv
+    ok = np.isfinite(sig) & (sig > 0) & np.isfinite(d)
+    assert ok.sum() == ny * nx - 5
+    w = 1.0 / sig[ok]
+    A = np.stack([c[ok] * w for c in cols], axis=1)
+    x_ref, rnorm = optimize.nnls(A, d[ok] * w)
+    ll_ref = -0.5 * rnorm ** 2 - 0.5 * np.sum(np.log(2 * math.pi * sig[ok] ** 2))
+    ll, _, _, amps = oracle.MultiLens(d, sig, psf, 0.06, 3, comps).model(p)
+    assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
+    assert np.allclose(amps, x_ref, rtol=1e-7, atol=1e-9 * x_ref.max())
+
 def test_multi_invalid_vectors():
     comps = _comps_slacs() + [dict(type="sersic", plane="lens", free_index=True)]
     lens = oracle.MultiLens(np.zeros((8, 8)), np.ones((8, 8)), np.ones((1, 1)), 0.1, 1, comps)

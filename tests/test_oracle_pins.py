@@ -561,6 +561,50 @@ def test_exact_model_recovers_amplitudes():
     assert abs(ll - norm) < 1e-9
 
 
+
+def _masked_noisy(r, ml_cols, amps, ny, nx):
+    """Noisy data from the columns, then five masked pixels whose values
+    would dominate any fit that used them: sigma 0, negative, infinite or
+    NaN, and a NaN datum under a valid sigma."""
+    sig = r.uniform(0.4, 1.6, (ny, nx))
+    d = np.tensordot(amps, ml_cols, axes=1) + r.normal(0.0, 1.0, (ny, nx)) * sig
+    spots = [(0, 0), (3, 7), (ny // 2, nx // 2), (ny - 1, nx - 1), (5, 5)]
+    vals = [(0.0, 1e6), (-2.0, -1e6), (np.inf, 5e5), (np.nan, 1e6), (1.0, np.nan)]
+    for (i, j), (sv, dv) in zip(spots, vals):
+        sig[i, j], d[i, j] = sv, dv
+    ok = np.isfinite(sig) & (sig > 0) & np.isfinite(d)
+    assert ok.sum() == ny * nx - 5
+    return d, sig, ok
+
+
+def _library_fit(cols, d, sig, ok):
+    """Eq. 5 over the unmasked pixels at the NNLS amplitudes, with the NNLS
+    taken from scipy on the sigma-weighted columns."""
+    w = 1.0 / sig[ok]
+    A = np.stack([c[ok] * w for c in cols], axis=1)
+    x, rnorm = optimize.nnls(A, d[ok] * w)
+    return -0.5 * rnorm ** 2 - 0.5 * np.sum(np.log(2 * math.pi * sig[ok] ** 2)), x
+
+
+def test_masked_pixels_leave_the_fit():
+    """Masked pixels drop out of Eq. 5 and of the amplitudes' NNLS: with
+    noisy data, the oracle's log L and amplitudes equal a library NNLS fit of
+    its blurred unit columns to the unmasked pixels alone.  A masked pixel
+    that reached the normal equations or either term of Eq. 5 would move the
+    result by orders of magnitude (their data are +-1e6 or NaN)."""
+    r = np.random.default_rng(31)
+    ny, nx = 22, 26
+    psf = np.exp(-0.5 * ((np.arange(7) - 3.0)[:, None] ** 2 + (np.arange(7) - 3.0)[None, :] ** 2) / 1.4)
+    p = _vec(theta_E=0.7, eps1_m=0.1, eps2_m=-0.05, x_S=0.04, y_S=-0.03, re_S=0.2,
+             re_L=0.4, n_L=3.0, eps1_L=0.1)
+    lens0 = oracle.Lens(np.zeros((ny, nx)), np.ones((ny, nx)), psf, 0.06, 3)
+    _, ml, ms, _, _ = lens0.model(p, mode=1)
+    d, sig, ok = _masked_noisy(r, np.stack([ml, ms]), np.array([2.5, 6.0]), ny, nx)
+    ll_ref, x_ref = _library_fit([ml, ms], d, sig, ok)
+    ll, _, _, _, amps = oracle.Lens(d, sig, psf, 0.06, 3).model(p, mode=0)
+    assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
+    assert np.allclose(amps, x_ref, rtol=1e-8, atol=1e-10)
+
 def test_invalid_vectors():
     lens = oracle.Lens(np.zeros((4, 4)), np.ones((4, 4)), np.ones((1, 1)), 0.1, 1)
     bad = [dict(eps1_m=0.8, eps2_m=0.7), dict(eps1_L=1.0), dict(eps2_S=-1.2),
