@@ -280,6 +280,39 @@ def test_multi_masked_pixels_leave_the_fit():
     assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
     assert np.allclose(amps, x_ref, rtol=1e-7, atol=1e-9 * x_ref.max())
 
+
+def test_zero_column_and_component_order():
+    """Structure of the amplitude fit (Eq. 7 with the non-negative
+    penalty): a component whose column is identically zero (a fixed
+    Gaussian of width 1e-6 arcsec off every subpixel centre) gets amplitude
+    0 and leaves log L and the other amplitudes exactly as without it,
+    wherever it sits in the list; reordering the components permutes the
+    amplitudes and leaves log L unchanged up to rounding."""
+    r = np.random.default_rng(33)
+    ny, nx = 24, 22
+    psf = np.exp(-0.5 * ((np.arange(5) - 2.0)[:, None] ** 2 + (np.arange(5) - 2.0)[None, :] ** 2) / 1.2)
+    base = _comps_slacs()
+    p = _mvec([0.5, 0.9, 0.12, 0.3], x_L=0.0123, y_L=-0.0171)
+    cols = oracle.multi_columns_renderer(0.06, 3, psf, ny, nx, base)(p)
+    sig = r.uniform(0.5, 1.5, (ny, nx))
+    d = np.tensordot(np.array([3.0, 1.0, 7.0, 2.0]), cols, axes=1) + r.normal(0, 1, (ny, nx)) * sig
+    ll0, _, _, a0 = oracle.MultiLens(d, sig, psf, 0.06, 3, base).model(p)
+    assert np.all(a0 > 0)
+    tiny = dict(type="gauss", plane="lens", free_scale=False, scale=1e-6)
+    for pos in (0, 2, 4):
+        comps = base[:pos] + [tiny] + base[pos:]
+        ll1, c1, _, a1 = oracle.MultiLens(d, sig, psf, 0.06, 3, comps).model(p)
+        assert not np.any(c1[pos])
+        assert ll1 == ll0
+        assert a1[pos] == 0.0 and np.array_equal(np.delete(a1, pos), a0)
+    # the free radii follow their components: slots 15..18 are the four
+    # components' r_e in list order
+    perm = [2, 0, 3, 1]
+    q = np.concatenate([p[:15], p[15:][perm]])
+    llp, _, _, ap = oracle.MultiLens(d, sig, psf, 0.06, 3, [base[k] for k in perm]).model(q)
+    assert abs(llp - ll0) <= 1e-10 * abs(ll0)
+    assert np.allclose(ap, a0[perm], rtol=1e-9)
+
 def test_multi_invalid_vectors():
     comps = _comps_slacs() + [dict(type="sersic", plane="lens", free_index=True)]
     lens = oracle.MultiLens(np.zeros((8, 8)), np.ones((8, 8)), np.ones((1, 1)), 0.1, 1, comps)
