@@ -605,6 +605,23 @@ def test_masked_pixels_leave_the_fit():
     assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
     assert np.allclose(amps, x_ref, rtol=1e-8, atol=1e-10)
 
+
+def test_fully_masked_lens():
+    """No unmasked pixel: both sums of Eq. 5 are empty, so log L = 0 and the
+    amplitudes are 0, for either kind of mask and for the multi-component
+    model too."""
+    ny, nx = 10, 12
+    psf = np.ones((3, 3))
+    comps = [dict(type="sersic", plane="lens", index=1.0),
+             dict(type="gauss", plane="source")]
+    mp = np.concatenate([_vec()[:7], [0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 0.0, 0.0], [0.5, 0.2]])
+    for d, sig in ((np.full((ny, nx), np.nan), np.ones((ny, nx))),
+                   (np.ones((ny, nx)), np.full((ny, nx), np.inf))):
+        ll, _, _, _, amps = oracle.Lens(d, sig, psf, 0.1, 2).model(_vec(), mode=0)
+        assert ll == 0.0 and not np.any(amps)
+        llm, _, _, ampm = oracle.MultiLens(d, sig, psf, 0.1, 2, comps).model(mp)
+        assert llm == 0.0 and not np.any(ampm)
+
 def test_invalid_vectors():
     lens = oracle.Lens(np.zeros((4, 4)), np.ones((4, 4)), np.ones((1, 1)), 0.1, 1)
     bad = [dict(eps1_m=0.8, eps2_m=0.7), dict(eps1_L=1.0), dict(eps2_S=-1.2),
