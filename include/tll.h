@@ -39,7 +39,9 @@
  *     theta_E < 0, an EPL slope outside (1, 3), a non-finite entry) give
  *     log L = -INFINITY; the rest of the batch is unaffected.
  *   Masking: a pixel whose noise sigma is not finite and > 0, or whose datum
- *     is not finite, has weight 0 and no normalisation term.  (The paper fits
+ *     is not finite, has weight 0 and no normalisation term.  Unmasked
+ *     pixels need 1/sigma^2 and d/sigma^2 within the FP32 range (sigma above
+ *     about 1e-19 for data of order 1): the weights are stored as FP32 pairs.  (The paper fits
  *     only a region of the image, Appendix A; give the other pixels an
  *     infinite sigma.)  The batched kernels trace only the pixels within the
  *     PSF's reach of an unmasked pixel (the unmasked set dilated by the
